@@ -1,0 +1,62 @@
+"""Pins of the oracle's plain (dense) time march (CPU only)."""
+import numpy as np
+
+from oracle import dense
+from oracle import kernel as kn
+from paper_1903_02118_gb300 import inputs
+
+
+def test_march_equals_quadruple_loop():
+    N, M = 5, 7
+    el = kn.element_table(inputs.kinked_fault(N))
+    K = kn.discrete_kernel(el, 0.5, M, 1.0, 1.0)
+    D = np.random.default_rng(1).standard_normal((M, N))
+    T = dense.march(K, D)
+    for n in range(M):
+        for i in range(N):
+            s = 0.0
+            for m in range(n + 1):
+                for j in range(N):
+                    s += K[m, i, j] * D[n - m, j]
+            assert abs(T[n, i] - s) < 1e-14 * (1 + abs(s))
+
+
+def test_uniform_slip_rate_gives_radiation_damping_until_edge_waves():
+    # Sec. 6: -mu/(2 cs) is the radiation damping; on an (effectively) infinite planar fault
+    # under uniform slip rate V the stress stays exactly -mu V /(2 cs) (1-D plane wave) until
+    # the waves from the fault ends reach the receiver.
+    N, M, mu, cs, dt = 200, 120, 1.0, 1.0, 0.5
+    el = kn.element_table(inputs.straight_fault(N))
+    K = kn.discrete_kernel(el, dt, M, mu, cs)
+    D = np.full((M, N), 0.7)
+    T = dense.march(K, D)
+    i = 100
+    edge = el["mx"][i] - 0.0       # distance to the nearer fault end
+    for n in range(M):
+        if cs * (n + 1) * dt < edge - 1e-9:
+            assert abs(T[n, i] - (-mu * 0.7 / (2 * cs))) < 1e-13
+    assert abs(T[M - 1, 199] - (-mu * 0.7 / (2 * cs))) > 1e-3   # the end element feels its edge
+
+
+def test_causality_of_march():
+    N, M = 60, 80
+    el = kn.element_table(inputs.curved_fault(N, 9))
+    K = kn.discrete_kernel(el, 0.5, M, 1.0, 1.0)
+    D = np.zeros((M, N))
+    D[10:, 0] = 1.0
+    T = dense.march(K, D)
+    d = np.hypot(el["mx"] - el["bx"][0], el["my"] - el["by"][0])   # distance to nearest end of element 0
+    for i in range(1, N):
+        first = int(np.ceil(d[i] / 0.5)) - 1 + 10   # first step whose window reaches the front
+        assert np.all(T[:max(first - 1, 0), i] == 0.0)
+
+
+def test_fft_rows_equal_march():
+    N, M = 40, 90
+    el = kn.element_table(inputs.curved_fault(N, 3))
+    K = kn.discrete_kernel(el, 0.5, M, 1.0, 1.0)
+    D = inputs.gaussian_filtered_history(N, M, 4)
+    T = dense.march(K, D)
+    rows = [0, 7, 39]
+    Tr = dense.march_rows_fft(K[:, rows, :], D)
+    assert np.abs(Tr - T[:, rows]).max() < 1e-12 * np.abs(T).max()

@@ -1,0 +1,304 @@
+"""Benchmark of the FDP=H time step on one GB300 (element-steps/s).
+
+Workload (default): 2-D antiplane curved fault, N = 4096 elements of length dx = 1,
+M = 4096 steps at CFL cs dt / dx = 1/2, eps = 1e-4, eta = 1/2, leaf 32, eps_st = 1e-6,
+Gaussian slip-rate pulse.  A "step" is one time step of the whole hot path (push, Eq. 32 FIR,
+Eq. 42 scatter, transient convolution, near field, Eq. 39 gather) over the N elements.  The
+march is first rolled forward past the longest near-field window so that every timed step does
+the steady-state work.  The operator (several GB) is larger than L2, so no flush is needed.
+
+--impl reference times the CPU oracle (plain FP64 ST-BIEM step on sampled receivers).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    "fdph": dict(name="FDP=H single scenario, 2-D antiplane curved fault", N=4096, M=4096, eps=1e-4, eta=0.5,
+                 leaf=32, eps_st=1e-6, geometry="curved"),
+    "plain": dict(name="Plain dense ST-BIEM, 2-D antiplane straight fault", N=256, M=256, eps=0.0, eta=0.0,
+                  leaf=32, eps_st=0.0, geometry="straight"),
+}
+DT = 0.5
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(cfg, rank):
+    from paper_1903_02118_gb300 import inputs
+    k = 1 if cfg["geometry"] == "curved" else 0
+    N, M = cfg["N"], cfg["M"]
+    if cfg["geometry"] == "curved":
+        xy = inputs.curved_fault(N, inputs.seed_for(k, inputs.GEOMETRY))
+        D = inputs.gaussian_pulse(N, M, DT, inputs.seed_for(k + 10 * rank, inputs.SLIP))
+    else:
+        xy = inputs.straight_fault(N)
+        D = inputs.gaussian_filtered_history(N, M, inputs.seed_for(k + 10 * rank, inputs.SLIP))
+    return xy, D
+
+
+def oracle_rows(xy, D, rows):
+    """Plain FP64 ST-BIEM (Eq. 4) kernel rows and march for the sampled receivers."""
+    from oracle import dense
+    from oracle import kernel as kn
+    el = kn.element_table(xy)
+    M = D.shape[0]
+    K = kn.discrete_kernel(el, DT, M, 1.0, 1.0, receivers=rows)
+    return K, dense.march_rows_fft(K, D)
+
+
+def oracle_step_rate(K, D, steps, n_hi):
+    """Time the oracle's plain step T_n = sum_m K_m D_{n-m} for the sampled receivers."""
+    t0 = time.perf_counter()
+    acc = 0.0
+    for n in range(n_hi - steps, n_hi):
+        acc += float(np.einsum("mrj,mj->r", K[:n + 1], D[n::-1][:n + 1]).sum())
+    dt = time.perf_counter() - t0
+    return K.shape[1] * steps / dt, dt
+
+
+def run_reference(args, cfg):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    xy, D = make_workload(cfg, 0)
+    rows = np.array([7, cfg["N"] // 2 + 1])
+    from oracle import kernel as kn
+    el = kn.element_table(xy)
+    M = cfg["M"]
+    K = kn.discrete_kernel(el, DT, M, 1.0, 1.0, receivers=rows)
+    per = 8
+    for _ in range(args.warmup):
+        oracle_step_rate(K, D, 1, M)
+    rate, secs = oracle_step_rate(K, D, per * args.steps, M)
+    line = {"impl": "reference", "metric": "element-steps/s", "value": rate, "unit": "element-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": cfg["N"], "M": M, "receivers_sampled": int(rows.size)},
+            "cpu_baseline": {"value": rate, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": "plain FP64 ST-BIEM step (Eq. 4, stored kernel rows) for %d receivers x "
+                                       "%d steps at n ~ M" % (rows.size, per * args.steps)},
+            "e2e": {"value": rate, "unit": "element-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fdph", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1903_02118_gb300 import build, fdph
+    build.build()
+    N, M = cfg["N"], cfg["M"]
+    xy, D = make_workload(cfg, rank)
+    stream = torch.cuda.current_stream()
+    prec = fdph.FP32 if args.precision == "fp32" else fdph.FP64
+    t0 = time.perf_counter()
+    plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
+                     precision=prec, device=local, stream=stream.cuda_stream)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    # full march once (accuracy check and warm-up of everything)
+    plan.run(M, Dd, Td)
+    plan.synchronize()
+    T_full = Td.cpu().numpy()
+
+    K, W = args.steps, args.warmup
+    n0 = max(0, min(st["max_window"], M - W - K))
+    if n0 + W + K > M:
+        raise SystemExit("steps + warmup exceed the planned M = %d" % M)
+
+    def roll_to(n):
+        plan.reset()
+        if n:
+            plan.run(n, Dd, Td)
+
+    roll_to(n0)
+    plan.run(W, Dd[n0:], Td[n0:])
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        s0.record(stream)
+        plan.run(K, Dd[n0 + W:], Td[n0 + W:])
+        s1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(s0.elapsed_time(s1), world)
+    value = world * N * K / (ms * 1e-3)
+
+    # per-kernel times (CUDA events inside the library, same stream) for the roofline
+    roll_to(n0 + W)
+    plan.set_profiling(True)
+    plan.run(K, Dd[n0 + W:], Td[n0 + W:])
+    kt = plan.kernel_times()
+    plan.set_profiling(False)
+    near_ms = kt["near"][0] / max(kt["near"][1], 1)
+    near_bytes = st["near_bytes_per_step"]
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = near_bytes / (near_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "near_kernel",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)" if peaks else "fallback 6.8 TB/s",
+                "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in kt.items()}}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    roll_to(n0 + W)
+    hD = torch.from_numpy(D).pin_memory()
+    hT = torch.empty((N,), dtype=torch.float64).pin_memory()
+    import ctypes
+    L = fdph.lib()
+    barrier(world)
+    te0 = time.perf_counter()
+    for s in range(K):
+        rc = L.fdph_step_host(plan.handle, ctypes.c_void_p(hD[n0 + W + s].data_ptr()), ctypes.c_void_p(hT.data_ptr()))
+        if rc:
+            raise SystemExit("fdph_step_host failed: %d" % rc)
+    te = max_over_ranks(time.perf_counter() - te0, world)
+    e2e = {"value": world * N * K / te, "unit": "element-steps/s", "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
+
+    line = {"metric": "element-steps/s", "value": value, "unit": "element-steps/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == fdph.FP64 else "f32-storage/f64-accumulate",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
+                       "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "cfl": 0.5, "first_timed_step": n0 + W,
+                       "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in kt.values()) // 1),
+            "gpu_launches_note": "library kernels per timed run of %d steps" % K,
+            "roofline": roofline, "clocks": clk.summary(),
+            "plan": {"seconds": plan_s, "bytes_per_step": st["bytes_per_step"],
+                     "near_bytes_per_step": near_bytes, "flops_per_step": st["flops_per_step"],
+                     "n_admissible": st["n_admissible"], "n_near": st["n_near"], "mean_rank": st["mean_rank"],
+                     "max_window": st["max_window"], "arena_bytes": st["arena_bytes"]}}
+    if rank == 0 and not args.no_cpu:
+        rows = np.array([7, N // 2 + 1])
+        Kr, T_or = oracle_rows(xy, D, rows)
+        line["rel_err_vs_plain_fp64"] = float(np.linalg.norm(T_full[:, rows] - T_or) / np.linalg.norm(T_or))
+        line["rel_err_note"] = "relative L2 over all %d steps at %d sampled receivers vs the CPU FP64 plain march" % (
+            M, rows.size)
+        rate, secs = oracle_step_rate(Kr, D, 64, M)
+        line["cpu_baseline"] = {"value": rate, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": "plain FP64 ST-BIEM step (Eq. 4, stored kernel rows) for %d receivers "
+                                          "x 64 steps at n ~ M; %.1f s" % (rows.size, secs)}
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()

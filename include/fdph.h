@@ -1,0 +1,190 @@
+/*
+ * fdph.h -- C ABI of the FDP=H space-time BIEM hot path (2-D antiplane, GB300 / sm_103a).
+ *
+ * The library evaluates, one time step at a time, the discretised space-time
+ * boundary integral equation of Sato & Ando (arXiv 1903.02118), Sec. 2.1.2, Eq. 4:
+ *
+ *     T_n = sum_{m >= 0} K_m D_{n-m}
+ *
+ * for N piecewise-constant fault elements, where D_n is the slip rate of step n
+ * and T_n the traction at the element midpoints at time (n + 1) dt.  The kernel
+ * tensor is never stored densely: the plan splits it into
+ *   - admissible leaves of the H-matrix block tree (Sec. 2.3, Eq. 8), whose
+ *     wavefront part (Domain F, Sec. 2.2) is a low-rank amplitude (Eqs. 12-13)
+ *     times a per-source normalised waveform placed by the ART integers
+ *     (Eqs. 29-31, App. C.3), followed by the static part (Domain S, App. B.1)
+ *     and the 2-D transient of Domain S (App. B.3, App. H);
+ *   - inadmissible leaves (Eq. 9, App. E): the exact kernel up to the start of
+ *     Domain S, then the static kernel.
+ * eta = 0 and eps_st = 0 give back the plain (dense) ST-BIEM of Eq. 4.
+ *
+ * Conventions common to every call:
+ *   - Status: 0 = FDPH_OK, negative = error (see fdph_status); no exception
+ *     crosses the ABI.  fdph_strerror gives a message; fdph_last_error gives the
+ *     detail of the last failure in this thread.
+ *   - Ownership: the caller owns every buffer it passes; the library owns the
+ *     plan, its device arena and its time-stepping state.
+ *   - Threads / streams: a plan is bound to one CUDA device and one stream and is
+ *     not thread safe.  Distinct plans are independent.
+ *   - Element order: D and T are indexed in the order of the geometry given to
+ *     fdph_plan (the library's internal cluster order is hidden).
+ */
+#ifndef FDPH_H
+#define FDPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fdph_status {
+    FDPH_OK = 0,
+    FDPH_E_ARG = -1,       /* invalid argument (null pointer, n <= 0, dt <= 0, ...) */
+    FDPH_E_OOM = -2,       /* host or device allocation failed */
+    FDPH_E_CAUSALITY = -3, /* discretised causality min(dm_i + mbar_j) >= 1 fails (Sec. 5.2, App. D) */
+    FDPH_E_CUDA = -4,      /* a CUDA runtime call failed */
+    FDPH_E_TIMEOUT = -5,   /* a bounded device wait gave up */
+    FDPH_E_NAN = -6,       /* non-finite value found where the call checks for one */
+    FDPH_E_STATE = -7      /* call not valid in the plan's current state (e.g. past M steps) */
+} fdph_status;
+
+typedef enum fdph_precision {
+    FDPH_FP64 = 0,         /* factors, waveforms and near-field tensor stored and multiplied in FP64 */
+    FDPH_FP32 = 1          /* stored in FP32; near-field products summed in FP32 within one work
+                              item (<= 64 steps x 32 sources) and in FP64 across items; far-field
+                              sums, rings and accumulators stay FP64 */
+} fdph_precision;
+
+typedef struct fdph_plan_s* fdph_plan_t;
+
+/* Fault geometry: n straight elements, host memory, xy[4*e + (0,1,2,3)] = (x0, y0, x1, y1)
+ * of element e.  Collocation point = midpoint; normal = tangent rotated by +90 degrees
+ * (Sec. 2.1.2).  Read during fdph_plan only. */
+typedef struct fdph_geometry {
+    int32_t n;
+    const double* xy;
+} fdph_geometry;
+
+/* Homogeneous full space: shear modulus mu and S-wave speed cs (Sec. 2.1.1). */
+typedef struct fdph_material {
+    double mu;
+    double cs;
+} fdph_material;
+
+/* Plan parameters (Sec. 6 / Sec. 7.1 names).  Fill with fdph_default_params first. */
+typedef struct fdph_params {
+    double eta;           /* admissibility diam < eta * dist (Eq. 8); 0 => no admissible leaf */
+    double lmin;          /* inadmissibility diam < l_min (Eq. 9); default 0 */
+    double eps_st;        /* Domain-S start: absolute kernel error bound, in units of mu/(2 cs)
+                             (App. H); 0 => the exact kernel is kept for all M steps */
+    int32_t leaf_size;    /* a block whose two clusters have at most leaf_size elements is an
+                             inadmissible leaf (default 32) */
+    int32_t extra_steps;  /* additional Domain-F width n_c in steps (App. H); < 0 => default
+                             ceil(10 * max element length / (cs dt)) */
+    int32_t precision;    /* fdph_precision, default FDPH_FP64 */
+    int32_t device;       /* CUDA device ordinal, default 0 */
+    void* cuda_stream;    /* cudaStream_t the plan runs on; NULL => a stream the plan creates */
+} fdph_params;
+
+/* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */
+typedef struct fdph_stats {
+    int32_t n;                 /* elements */
+    int32_t M;                 /* planned steps */
+    int32_t n_admissible;      /* admissible leaves */
+    int32_t n_near;            /* inadmissible leaves */
+    int32_t n_subblocks;       /* low-rank operators (leaf x domain x stress component) */
+    int32_t max_rank;
+    int32_t extra_steps;       /* n_c used */
+    int32_t max_window;        /* largest inadmissible-leaf window (steps of exact kernel) */
+    double mean_rank;
+    int64_t near_entries;      /* stored kernel coefficients of the inadmissible leaves */
+    int64_t far_entries;       /* stored factor / waveform coefficients */
+    int64_t arena_bytes;       /* device bytes of the plan (operator data) */
+    int64_t state_bytes;       /* device bytes of the time-stepping state (rings, accumulators) */
+    double bytes_per_step;     /* algorithmic HBM bytes of one full step at steady state */
+    double near_bytes_per_step;/* of which the near-field kernel tensor */
+    double flops_per_step;     /* multiply-adds x 2 of one full step */
+    double plan_seconds;       /* wall time of fdph_plan */
+} fdph_stats;
+
+/* Fill *p with the defaults above. Never fails. */
+void fdph_default_params(fdph_params* p);
+
+/* Build the plan of the FDP=H operator for `geometry` (Secs. 2.3, 4, App. C.3, App. E, App. H)
+ * and upload it to the device.  dt: time step; M: number of steps the plan will be run
+ * for (kernel windows and Domain-S cuts are evaluated up to M); eps: low-rank tolerance
+ * eps_H of the Frobenius criterion |K_a - K_a,LRA| < eps |K_a| (Sec. 2.3), eps <= 0 keeps
+ * every admissible block exact.  params may be NULL (defaults).  On success *out is a new
+ * plan positioned at step 0.  Errors: FDPH_E_ARG, FDPH_E_OOM, FDPH_E_CAUSALITY, FDPH_E_CUDA. */
+int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, double dt, int32_t M,
+              double eps, const fdph_params* params, fdph_plan_t* out);
+
+/* One time step of Eq. 4: consumes D_n (device, n doubles) and writes T_n (device, n doubles),
+ * n being the plan's current step, then advances to n + 1.  Asynchronous on the plan's stream;
+ * D_n may be reused once the stream has passed this call.  Errors: FDPH_E_ARG (null plan or
+ * pointer), FDPH_E_STATE (n == M), FDPH_E_CUDA (launch failure). */
+int fdph_step(fdph_plan_t plan, const double* D_n, double* T_n);
+
+/* `steps` consecutive steps: D (device, steps * n doubles, step-major) -> T (device, same shape).
+ * Equivalent to `steps` calls of fdph_step.
+ * Errors as fdph_step; FDPH_E_STATE if the plan would pass step M. */
+int fdph_run(fdph_plan_t plan, int32_t steps, const double* D, double* T);
+
+/* Like fdph_step but D_n and T_n are HOST buffers; the call copies D_n in, steps, copies T_n
+ * out and returns when T_n is ready (synchronous). */
+int fdph_step_host(fdph_plan_t plan, const double* D_n_host, double* T_n_host);
+
+/* Return the plan to step 0 with zero history (rings, accumulators). */
+int fdph_reset(fdph_plan_t plan);
+
+/* Current step index (number of steps taken since plan or reset). */
+int fdph_current_step(fdph_plan_t plan, int32_t* n);
+
+/* Wait for all work queued on the plan's stream. */
+int fdph_synchronize(fdph_plan_t plan);
+
+/* Copy the plan's statistics. */
+int fdph_get_stats(fdph_plan_t plan, fdph_stats* stats);
+
+/* Save / restore the time-stepping state (rings, accumulators, step index) to / from a host
+ * buffer.  fdph_save_state with buf == NULL sets *len to the size needed.  Restoring into a
+ * plan built from the same inputs reproduces the continuation bit for bit. */
+int fdph_save_state(fdph_plan_t plan, void* buf, size_t* len);
+int fdph_load_state(fdph_plan_t plan, const void* buf, size_t len);
+
+/* Release the plan and its device memory.  NULL is ignored. */
+void fdph_destroy(fdph_plan_t plan);
+
+/* Per-kernel timing with CUDA events on the plan's stream (off by default).  Kernel ids:
+ * 0 push, 1 fir (Eq. 32), 2 scatter (Eq. 42), 3 transient convolution (App. B.3),
+ * 4 near field (App. E), 5 gather (Eq. 39).  fdph_kernel_times synchronises the stream and
+ * returns, per id, the summed milliseconds and the launch count since profiling was enabled
+ * (arrays of length FDPH_NUM_KERNELS).  Enabling resets the counters. */
+#define FDPH_NUM_KERNELS 6
+int fdph_set_profiling(fdph_plan_t plan, int enable);
+int fdph_kernel_times(fdph_plan_t plan, double* ms, int64_t* launches);
+
+/* Host-only inspection of the block-cluster tree and ART integers (Secs. 2.3, 4.2.2, 4.3,
+ * App. C.3), no device needed.  Writes an int32 stream to buf (capacity cap entries; *len
+ * receives the length needed, call with buf == NULL to size it):
+ *   N, perm[N]                      (perm[p] = geometry index of internal position p)
+ *   n_leaves, then per leaf:
+ *     kind (1 admissible, 0 inadmissible), r0, nr, s0, ns   (internal positions)
+ *     if admissible: dm[nr], mbar[ns], Dm[ns]
+ * Errors: FDPH_E_ARG; FDPH_E_CAUSALITY if an admissible leaf violates causality. */
+int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* material, double dt,
+                     const fdph_params* params, int32_t* buf, int64_t cap, int64_t* len);
+
+/* Message for a status code (static string). */
+const char* fdph_strerror(int status);
+
+/* Detail of the last error raised in the calling thread (static thread-local string). */
+const char* fdph_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDPH_H */

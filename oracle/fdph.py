@@ -164,6 +164,8 @@ def lra(A, eps):
     normA = np.linalg.norm(A)
     if normA == 0.0:
         return np.zeros_like(A), 0, False
+    if eps <= 0.0:
+        return A.copy(), min(nr, ns), True
     U, s, Vt = np.linalg.svd(A, full_matrices=False)
     tail = np.sqrt(np.cumsum((s * s)[::-1])[::-1])   # tail[r] = sqrt(sum_{l >= r} s_l^2)
     tail = np.append(tail, 0.0)

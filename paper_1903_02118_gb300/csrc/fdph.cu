@@ -1,0 +1,993 @@
+// fdph.cu -- device side of the FDP=H time step and the C ABI (include/fdph.h).
+//
+// One time step n (Eq. 4 evaluated through the plan's operator) runs these kernels in order
+// on the plan's stream:
+//   push     D_n -> slip-rate ring (internal order); cumulative slip C_j(n) = sum_{s<=n} D_j,s
+//            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring
+//   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}
+//   scatter  formula 2 (Eq. 42): Tbar'_l[n + delay_j] += g_{l,j} u_j for every run of sources
+//            with equal delay (no atomics: one writer per ring slot); u = Dhat (Domain F),
+//            dt * C (Domain S, App. B.1 written on the cumulative slip), D (transient);
+//            the ring is the shift operator M of Eq. 40 as a base-pointer increment
+//   trconv   transient (App. B.3): Z_l(n - min dm) = sum_{m < Dm_tr} h^tr_m Y_l(n - min dm - m)
+//   near     inadmissible leaves (App. E): sum_{k < W} K_{ij,k} D_{j,n-k} + Kstat_ij dt C_j(n-W),
+//            per (leaf, chunk of k) work item into a partial-sum slot
+//   gather   formula 3 (Eq. 39): T_i = sum_{blocks} sum_l f_{l,i} Tbar'_l[n - dm_i] + near
+//            partials, written in the caller's element order
+// Causality (min(dm + delay) >= 1, checked at plan time) guarantees that the ring slots read
+// at step n were completed by steps < n and that the slots written at step n are not read.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/fdph.h"
+#include "internal.h"
+#include "kernel2d.cuh"
+#include "plan.h"
+
+namespace fdph {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace fdph
+
+using namespace fdph;
+
+#define FDPH_CUDA(call)                                                                      \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+            return FDPH_E_CUDA;                                                              \
+        }                                                                                    \
+    } while (0)
+
+static const int kChunk = 64;      // steps of exact kernel per near-field work item
+static const int kNearThreads = 128;
+
+// ------------------------------------------------------------------------------------------
+// device-side views
+
+struct SbDev {
+    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0;
+    long long f, g, h, ring, zring, dhat, delay, dm;
+};
+
+struct NearDev {
+    int r0, nr, s0, ns, W, pad;
+    long long tensor, stat;
+};
+
+template <class T>
+struct StepArgs {
+    int n, N, WD, WC;
+    double dt;
+    const double* D_in;       // caller's D_n (geometry order)
+    double* T_out;            // caller's T_n (geometry order)
+    const int* perm;          // internal -> geometry
+    double* Dring;            // [WD][N]
+    double* Cring;            // [WC][N]
+    double* C;                // [N] cumulative slip (rounded sum)
+    double* Ccomp;            // [N] Kahan compensation
+    // far field
+    const SbDev* sbs;
+    const T* fac;
+    const int* ints;
+    const int* run_delay;
+    const int* run_start;
+    const int* run_len;
+    const int* src_order;
+    const int* scat_sb;
+    const int* scat_run;
+    int n_scat;
+    const int* fir_sb;
+    const int* fir_j;
+    int n_fir;
+    const int* tr_sb;
+    const int* tr_l;
+    int n_tr;
+    const int* g_ptr;
+    const int* g_sb;
+    const int* g_il;
+    double* ring;
+    double* zring;
+    double* dhat;
+    // near field
+    const NearDev* near;
+    const int4* items;
+    int n_items;
+    const T* tensor;
+    const double* stat;
+    double* partial;          // [n_items][32]
+    const int* np_ptr;
+    const int* np_idx;
+};
+
+__device__ __forceinline__ int pmod(long long a, int L) {
+    long long r = a % L;
+    return (int)(r < 0 ? r + L : r);
+}
+
+template <class T>
+__global__ void push_kernel(StepArgs<T> a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    const double d = a.D_in[a.perm[p]];
+    a.Dring[(size_t)pmod(a.n, a.WD) * a.N + p] = d;
+    // compensated running sum of the slip (units of dt)
+    const double y = d - a.Ccomp[p];
+    const double c0 = a.C[p];
+    const double t = c0 + y;
+    a.Ccomp[p] = (t - c0) - y;
+    a.C[p] = t;
+    a.Cring[(size_t)pmod(a.n, a.WC) * a.N + p] = t;
+}
+
+template <class T>
+__global__ void fir_kernel(StepArgs<T> a) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n_fir) return;
+    const SbDev sb = a.sbs[a.fir_sb[q]];
+    const int jl = a.fir_j[q];
+    const int col = sb.s0 + jl;
+    double s = 0.0;
+    const int taps = min(sb.taps, a.n + 1);
+    for (int m = 0; m < taps; ++m)
+        s += (double)a.fac[sb.h + (long long)m * sb.ns + jl] * a.Dring[(size_t)pmod(a.n - m, a.WD) * a.N + col];
+    a.dhat[sb.dhat + jl] = s;
+}
+
+template <class T>
+__global__ void scatter_kernel(StepArgs<T> a) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n_scat) return;
+    const SbDev sb = a.sbs[a.scat_sb[q]];
+    const int run = a.scat_run[q];
+    const int delay = a.run_delay[run];
+    const int st = a.run_start[run];
+    const int len = a.run_len[run];
+    const int slot = pmod((long long)a.n + delay, sb.L);
+    const bool first = delay == sb.maxdelay;   // the newest slot starts fresh
+    for (int l = 0; l < sb.rank; ++l) {
+        double s = 0.0;
+        for (int u = 0; u < len; ++u) {
+            const int jl = a.src_order[st + u];
+            double v;
+            if (sb.kind == SB_F) v = a.dhat[sb.dhat + jl];
+            else if (sb.kind == SB_S) v = a.dt * a.C[sb.s0 + jl];
+            else v = a.Dring[(size_t)pmod(a.n, a.WD) * a.N + sb.s0 + jl];
+            s += (double)a.fac[sb.g + (long long)jl * sb.rank + l] * v;
+        }
+        double* r = a.ring + sb.ring + (long long)l * sb.L + slot;
+        *r = first ? s : *r + s;
+    }
+}
+
+template <class T>
+__global__ void trconv_kernel(StepArgs<T> a) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n_tr) return;
+    const SbDev sb = a.sbs[a.tr_sb[q]];
+    const int l = a.tr_l[q];
+    const long long t0 = (long long)a.n - sb.mindm;
+    const double* Y = a.ring + sb.ring + (long long)l * sb.L;
+    double z = 0.0;
+    for (int m = 0; m < sb.taps; ++m) z += (double)a.fac[sb.h + m] * Y[pmod(t0 - m, sb.L)];
+    a.zring[sb.zring + (long long)l * sb.LZ + pmod(t0, sb.LZ)] = z;
+}
+
+// Near field: one CTA per work item (leaf, k in [k0, k1)); each warp takes every
+// (blockDim/32)-th step, lane i owns receiver i, sources are broadcast by shuffle.  Products
+// and the sum over one item are formed in the storage type T (FP64 or FP32); items are
+// combined in FP64 by the gather.
+template <class T>
+__global__ void __launch_bounds__(kNearThreads) near_kernel(StepArgs<T> a) {
+    __shared__ double red[kNearThreads / 32][32];
+    const int item = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 it = a.items[item];
+    const NearDev L = a.near[it.x];
+    const int kend = min(it.z, a.n + 1);
+    T acc = (T)0;
+    for (int k = it.y + warp; k < kend; k += kNearThreads / 32) {
+        const T dv = lane < L.ns ? (T)a.Dring[(size_t)pmod(a.n - k, a.WD) * a.N + L.s0 + lane] : (T)0;
+        const T* tile = a.tensor + L.tensor + (long long)k * L.ns * L.nr;
+        for (int j = 0; j < L.ns; ++j) {
+            const T dj = __shfl_sync(0xffffffffu, dv, j);
+            if (lane < L.nr) acc += tile[j * L.nr + lane] * dj;
+        }
+    }
+    double accd = (double)acc;
+    if (it.y == 0 && warp == 0 && a.n - L.W >= 0) {
+        const long long t = (long long)a.n - L.W;
+        const double cv = lane < L.ns ? a.Cring[(size_t)pmod(t, a.WC) * a.N + L.s0 + lane] : 0.0;
+        for (int j = 0; j < L.ns; ++j) {
+            const double cj = __shfl_sync(0xffffffffu, cv, j);
+            if (lane < L.nr) accd += a.stat[L.stat + j * L.nr + lane] * cj;
+        }
+    }
+    red[warp][lane] = accd;
+    __syncthreads();
+    if (warp == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kNearThreads / 32; ++w) s += red[w][lane];
+        a.partial[(size_t)item * 32 + lane] = s;
+    }
+}
+
+template <class T>
+__global__ void gather_kernel(StepArgs<T> a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    double s = 0.0;
+    for (int e = a.g_ptr[p]; e < a.g_ptr[p + 1]; ++e) {
+        const SbDev sb = a.sbs[a.g_sb[e]];
+        const int il = a.g_il[e];
+        const long long t = (long long)a.n - a.ints[sb.dm + il];
+        const T* f = a.fac + sb.f + (long long)il * sb.rank;
+        if (sb.kind == SB_TR) {
+            const double* z = a.zring + sb.zring + pmod(t, sb.LZ);
+            for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * z[(long long)l * sb.LZ];
+        } else {
+            const double* r = a.ring + sb.ring + pmod(t, sb.L);
+            for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[(long long)l * sb.L];
+        }
+    }
+    for (int e = a.np_ptr[p]; e < a.np_ptr[p + 1]; ++e) s += a.partial[a.np_idx[e]];
+    a.T_out[a.perm[p]] = s;
+}
+
+// ------------------------------------------------------------------------------------------
+// plan-time device kernels: near-field windows and exact-kernel tensors
+
+struct GeoDev {
+    const double *px, *py, *nx, *ny, *ax, *ay, *tx, *ty, *len;
+};
+
+__device__ __forceinline__ Seg dev_seg(const GeoDev& g, int p) {
+    Seg s;
+    s.ax = g.ax[p];
+    s.ay = g.ay[p];
+    s.tx = g.tx[p];
+    s.ty = g.ty[p];
+    s.len = g.len[p];
+    return s;
+}
+
+// m_S(i, j) = 1 + last k < M with |K_ijk - Kstat_ij dt| >= thr (App. H), 0 if none; M if thr == 0
+__global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const int* ps, const int* pns,
+                               const long long* pair0, long long npairs, int nleaf, int M, double dt,
+                               double mu, double c, double thr, int* ms) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pair0[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const long long loc = q - pair0[lo];
+    const int il = (int)(loc / pns[lo]), jl = (int)(loc % pns[lo]);
+    const int pi = pr[lo] + il, pj = ps[lo] + jl;
+    if (thr <= 0.0) {
+        ms[q] = M;
+        return;
+    }
+    const Seg s = dev_seg(g, pj);
+    int res = 0;
+    for (int k = M - 1; k >= 0; --k) {
+        const Stress2 v = stress_tail(g.px[pi], g.py[pi], s, (double)k * dt, (double)(k + 1) * dt, mu, c);
+        const double tval = g.nx[pi] * v.x + g.ny[pi] * v.y;
+        if (fabs(tval) >= thr) {
+            res = k + 1;
+            break;
+        }
+    }
+    ms[q] = res;
+}
+
+// coefficients [k][j][i] for k < W: exact kernel below m_S(i, j), static * dt above
+template <class T>
+__global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double dt, double mu, double c,
+                                 T* tensor, double* stat) {
+    const long long total = (long long)L.W * L.ns * L.nr;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int il = (int)(q % L.nr);
+        const long long r = q / L.nr;
+        const int jl = (int)(r % L.ns);
+        const int k = (int)(r / L.ns);
+        const int pi = L.r0 + il, pj = L.s0 + jl;
+        const Seg s = dev_seg(g, pj);
+        double v;
+        const int mS = ms_leaf[il * L.ns + jl];
+        if (k < mS) {
+            const Stress2 w = stress_jump(g.px[pi], g.py[pi], s, (double)k * dt, (double)(k + 1) * dt, mu, c);
+            v = g.nx[pi] * w.x + g.ny[pi] * w.y;
+        } else {
+            const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
+            v = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
+        }
+        tensor[L.tensor + q] = (T)v;
+        if (k == 0) {
+            const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
+            stat[L.stat + (long long)jl * L.nr + il] = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// the plan object
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct fdph_plan_s {
+    int device = 0;
+    int precision = FDPH_FP64;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int N = 0, M = 0, n = 0, WD = 1, WC = 1;
+    double dt = 0;
+    HostPlan hp;
+    fdph_stats st;
+    // device memory
+    std::vector<void*> allocs;
+    int* perm = nullptr;
+    SbDev* sbs = nullptr;
+    void* fac = nullptr;
+    int *ints = nullptr, *run_delay = nullptr, *run_start = nullptr, *run_len = nullptr, *src_order = nullptr;
+    int *scat_sb = nullptr, *scat_run = nullptr, *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
+        *tr_l = nullptr, *g_ptr = nullptr, *g_sb = nullptr, *g_il = nullptr;
+    NearDev* near = nullptr;
+    int4* items = nullptr;
+    void* tensor = nullptr;
+    double* stat = nullptr;
+    int *np_ptr = nullptr, *np_idx = nullptr;
+    // state
+    double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
+    double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
+    size_t state_bytes = 0;
+    // host staging for fdph_step_host
+    double *hD = nullptr, *hT = nullptr, *dD = nullptr, *dT = nullptr;
+    // per-kernel event timing
+    bool prof = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+    double prof_ms[FDPH_NUM_KERNELS] = {0};
+    int64_t prof_n[FDPH_NUM_KERNELS] = {0};
+    // graph of one step for fdph_run
+    cudaGraphExec_t graph = nullptr;
+    const double* graph_D = nullptr;
+    double* graph_T = nullptr;
+};
+
+template <class T>
+static int dalloc(fdph_plan_t P, T** out, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return FDPH_E_OOM;
+    }
+    P->allocs.push_back(p);
+    *out = (T*)p;
+    return FDPH_OK;
+}
+
+template <class T>
+static int upload(fdph_plan_t P, T** out, const std::vector<T>& v) {
+    int rc = dalloc(P, out, v.size());
+    if (rc) return rc;
+    if (!v.empty()) FDPH_CUDA(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FDPH_OK;
+}
+
+template <class T>
+static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
+    StepArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.n = P->n;
+    a.N = P->N;
+    a.WD = P->WD;
+    a.WC = P->WC;
+    a.dt = P->dt;
+    a.D_in = D;
+    a.T_out = T_;
+    a.perm = P->perm;
+    a.Dring = P->Dring;
+    a.Cring = P->Cring;
+    a.C = P->C;
+    a.Ccomp = P->Ccomp;
+    a.sbs = P->sbs;
+    a.fac = (const T*)P->fac;
+    a.ints = P->ints;
+    a.run_delay = P->run_delay;
+    a.run_start = P->run_start;
+    a.run_len = P->run_len;
+    a.src_order = P->src_order;
+    a.scat_sb = P->scat_sb;
+    a.scat_run = P->scat_run;
+    a.n_scat = (int)P->hp.scat_sb.size();
+    a.fir_sb = P->fir_sb;
+    a.fir_j = P->fir_j;
+    a.n_fir = (int)P->hp.fir_sb.size();
+    a.tr_sb = P->tr_sb;
+    a.tr_l = P->tr_l;
+    a.n_tr = (int)P->hp.tr_sb.size();
+    a.g_ptr = P->g_ptr;
+    a.g_sb = P->g_sb;
+    a.g_il = P->g_il;
+    a.ring = P->ring;
+    a.zring = P->zring;
+    a.dhat = P->dhat;
+    a.near = P->near;
+    a.items = P->items;
+    a.n_items = (int)P->hp.items.size();
+    a.tensor = (const T*)P->tensor;
+    a.stat = P->stat;
+    a.partial = P->partial;
+    a.np_ptr = P->np_ptr;
+    a.np_idx = P->np_idx;
+    return a;
+}
+
+static inline int blocks(long long n, int t) { return (int)std::max<long long>(1, (n + t - 1) / t); }
+
+struct ProfScope {
+    fdph_plan_t P;
+    int id;
+    cudaEvent_t b = nullptr, e = nullptr;
+    ProfScope(fdph_plan_t P_, int id_);
+    ~ProfScope();
+};
+
+template <class T>
+static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
+    StepArgs<T> a = make_args<T>(P, D, Tout);
+    cudaStream_t s = P->stream;
+    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
+    if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
+    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks(a.n_tr, 128), 128, 0, s>>>(a); }
+    if (a.n_items) { ProfScope ps(P, 4); near_kernel<T><<<a.n_items, kNearThreads, 0, s>>>(a); }
+    { ProfScope ps(P, 5); gather_kernel<T><<<blocks(a.N, 128), 128, 0, s>>>(a); }
+    FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
+}
+
+ProfScope::ProfScope(fdph_plan_t P_, int id_) : P(P_), id(id_) {
+    if (!P->prof) return;
+    cudaEventCreate(&b);
+    cudaEventCreate(&e);
+    cudaEventRecord(b, P->stream);
+}
+
+ProfScope::~ProfScope() {
+    if (!P->prof || !b) return;
+    cudaEventRecord(e, P->stream);
+    P->prof_ev.push_back({id, {b, e}});
+}
+
+static void prof_drain(fdph_plan_t P) {
+    for (auto& q : P->prof_ev) {
+        float ms = 0.f;
+        cudaEventSynchronize(q.second.second);
+        cudaEventElapsedTime(&ms, q.second.first, q.second.second);
+        P->prof_ms[q.first] += ms;
+        P->prof_n[q.first] += 1;
+        cudaEventDestroy(q.second.first);
+        cudaEventDestroy(q.second.second);
+    }
+    P->prof_ev.clear();
+}
+
+static int step_impl(fdph_plan_t P, const double* D, double* T_) {
+    int rc = P->precision == FDPH_FP32 ? launch_step<float>(P, D, T_) : launch_step<double>(P, D, T_);
+    if (rc == FDPH_OK) P->n += 1;
+    return rc;
+}
+
+template <class T>
+static int build_near(fdph_plan_t P, const PlanInputs& in) {
+    HostPlan& hp = P->hp;
+    const int nl = (int)hp.near_r0.size();
+    GeoDev g;
+    double *px, *py, *nx, *ny, *ax, *ay, *tx, *ty, *ln;
+    int rc;
+    if ((rc = upload(P, &px, hp.px)) || (rc = upload(P, &py, hp.py)) || (rc = upload(P, &nx, hp.pnx)) ||
+        (rc = upload(P, &ny, hp.pny)) || (rc = upload(P, &ax, hp.sax)) || (rc = upload(P, &ay, hp.say)) ||
+        (rc = upload(P, &tx, hp.stx)) || (rc = upload(P, &ty, hp.sty)) || (rc = upload(P, &ln, hp.slen)))
+        return rc;
+    g.px = px; g.py = py; g.nx = nx; g.ny = ny; g.ax = ax; g.ay = ay; g.tx = tx; g.ty = ty; g.len = ln;
+    std::vector<long long> pair0(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) pair0[l + 1] = pair0[l] + (long long)hp.near_nr[l] * hp.near_ns[l];
+    const long long npairs = pair0[nl];
+    std::vector<int32_t> W(nl, 0);
+    std::vector<int> ms;
+    int *d_ms = nullptr, *d_r = nullptr, *d_nr = nullptr, *d_s = nullptr, *d_ns = nullptr;
+    long long* d_p0 = nullptr;
+    if (nl > 0) {
+        if ((rc = dalloc(P, &d_ms, npairs)) || (rc = upload(P, &d_r, hp.near_r0)) ||
+            (rc = upload(P, &d_nr, hp.near_nr)) || (rc = upload(P, &d_s, hp.near_s0)) ||
+            (rc = upload(P, &d_ns, hp.near_ns)))
+            return rc;
+        std::vector<long long> p0(pair0.begin(), pair0.end() - 1);
+        if ((rc = upload(P, &d_p0, p0))) return rc;
+        const double thr = in.eps_st * in.mu / (2.0 * in.cs);
+        near_ms_kernel<<<blocks(npairs, 128), 128>>>(g, d_r, d_nr, d_s, d_ns, d_p0, npairs, nl, in.M, in.dt,
+                                                      in.mu, in.cs, thr, d_ms);
+        FDPH_CUDA(cudaGetLastError());
+        ms.resize(npairs);
+        FDPH_CUDA(cudaMemcpy(ms.data(), d_ms, npairs * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int l = 0; l < nl; ++l)
+            for (long long q = pair0[l]; q < pair0[l + 1]; ++q) W[l] = std::max(W[l], ms[q]);
+    }
+    finish_near_layout(hp, W, kChunk);
+    std::vector<NearDev> nd(nl);
+    for (int l = 0; l < nl; ++l) {
+        const NearLeaf& L = hp.near[l];
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, 0, (long long)L.tensor, (long long)L.stat};
+    }
+    if ((rc = upload(P, &P->near, nd))) return rc;
+    T* tens = nullptr;
+    if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &P->stat, hp.near_stat_len))) return rc;
+    P->tensor = tens;
+    for (int l = 0; l < nl; ++l) {
+        const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
+        if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
+        // static tile is written by k == 0 entries; a leaf with W == 0 still needs it
+        NearDev L = nd[l];
+        if (L.W == 0) {
+            // temporarily fill one k-slice into a scratch to get the static tile
+            T* tmp = nullptr;
+            if ((rc = dalloc(P, &tmp, (size_t)L.ns * L.nr))) return rc;
+            NearDev L1 = L;
+            L1.W = 1;
+            L1.tensor = 0;
+            near_fill_kernel<T><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
+                                                                            in.mu, in.cs, tmp, P->stat);
+        } else {
+            near_fill_kernel<T><<<std::min<long long>(blocks(tot, 256), 4096), 256>>>(
+                g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, P->stat);
+        }
+        FDPH_CUDA(cudaGetLastError());
+    }
+    std::vector<int4> it(hp.items.size());
+    for (size_t q = 0; q < it.size(); ++q) it[q] = make_int4(hp.items[q].leaf, hp.items[q].k0, hp.items[q].k1, 0);
+    if ((rc = upload(P, &P->items, it)) || (rc = upload(P, &P->np_ptr, hp.np_ptr)) ||
+        (rc = upload(P, &P->np_idx, hp.np_idx)))
+        return rc;
+    FDPH_CUDA(cudaDeviceSynchronize());
+    return FDPH_OK;
+}
+
+static void fill_stats(fdph_plan_t P) {
+    HostPlan& hp = P->hp;
+    fdph_stats& s = P->st;
+    const double ps = P->precision == FDPH_FP32 ? 4.0 : 8.0;
+    s.n = hp.n;
+    s.M = hp.M;
+    s.n_admissible = hp.n_adm;
+    s.n_near = hp.n_near;
+    s.n_subblocks = (int)hp.sbs.size();
+    s.max_rank = hp.max_rank;
+    s.mean_rank = hp.mean_rank;
+    s.extra_steps = hp.tree.nc;
+    s.max_window = hp.max_W;
+    s.near_entries = hp.near_tensor_len;
+    s.far_entries = hp.far_entries;
+    // algorithmic bytes of one steady-state step
+    double near_b = 0, far_b = 0, flops = 0;
+    for (const NearLeaf& L : hp.near) {
+        near_b += (double)L.W * L.ns * L.nr * ps + (double)L.ns * L.nr * 8.0;  // tensor + static tile
+        near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
+        flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
+    }
+    for (const SubBlock& sb : hp.sbs) {
+        const double r = sb.rank;
+        far_b += (sb.nr + sb.ns) * r * ps + (sb.nr + sb.ns) * 4.0;          // f, g, delays
+        far_b += sb.nr * r * 8.0 + sb.nruns * r * 16.0;                     // ring reads / RMW
+        flops += 2.0 * (sb.nr + sb.ns) * r;
+        if (sb.kind == SB_F) {
+            far_b += (double)sb.taps * sb.ns * (ps + 8.0) + sb.ns * 16.0;   // h, D history, Dhat
+            flops += 2.0 * sb.taps * sb.ns;
+        }
+        if (sb.kind == SB_TR) {
+            far_b += r * (sb.taps * 8.0 + sb.taps * ps + 8.0);
+            flops += 2.0 * r * sb.taps;
+        }
+    }
+    const double push_b = hp.n * (8.0 + 8.0 + 32.0 + 8.0 + 4.0);           // D in, ring, C/comp, Cring, perm
+    const double out_b = hp.n * (8.0 + 4.0) + (double)hp.np_idx.size() * 12.0;
+    s.bytes_per_step = near_b + far_b + push_b + out_b;
+    s.near_bytes_per_step = near_b;
+    s.flops_per_step = flops;
+    s.state_bytes = (long long)P->state_bytes;
+    long long arena = 0;
+    arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
+    arena += (long long)(hp.near_tensor_len * ps) + hp.near_stat_len * 8;
+    s.arena_bytes = arena;
+}
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+void fdph_default_params(fdph_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->eta = 0.5;
+    p->lmin = 0.0;
+    p->eps_st = 1e-6;
+    p->leaf_size = 32;
+    p->extra_steps = -1;
+    p->precision = FDPH_FP64;
+    p->device = 0;
+    p->cuda_stream = nullptr;
+}
+
+const char* fdph_strerror(int s) {
+    switch (s) {
+        case FDPH_OK: return "ok";
+        case FDPH_E_ARG: return "invalid argument";
+        case FDPH_E_OOM: return "out of memory";
+        case FDPH_E_CAUSALITY: return "discretised causality violated (increase l_min/eta or reduce dt)";
+        case FDPH_E_CUDA: return "CUDA error";
+        case FDPH_E_TIMEOUT: return "device wait timed out";
+        case FDPH_E_NAN: return "non-finite value";
+        case FDPH_E_STATE: return "invalid plan state";
+        default: return "unknown status";
+    }
+}
+
+const char* fdph_last_error(void) { return g_last_error.c_str(); }
+
+static int check_inputs(const fdph_geometry* g, const fdph_material* m, double dt, const fdph_params* p) {
+    if (!g || !m || !g->xy || g->n <= 0 || !(dt > 0.0) || !(m->mu > 0.0) || !(m->cs > 0.0)) {
+        set_error("geometry, material and dt must be given, n > 0, dt, mu, cs > 0");
+        return FDPH_E_ARG;
+    }
+    if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 ||
+              (p->precision != FDPH_FP64 && p->precision != FDPH_FP32))) {
+        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64 or FP32");
+        return FDPH_E_ARG;
+    }
+    for (int k = 0; k < 4 * g->n; ++k)
+        if (!std::isfinite(g->xy[k])) {
+            set_error("geometry holds a non-finite coordinate");
+            return FDPH_E_NAN;
+        }
+    for (int e = 0; e < g->n; ++e) {
+        const double dx = g->xy[4 * e + 2] - g->xy[4 * e], dy = g->xy[4 * e + 3] - g->xy[4 * e + 1];
+        if (dx * dx + dy * dy == 0.0) {
+            set_error("element " + std::to_string(e) + " has zero length");
+            return FDPH_E_ARG;
+        }
+    }
+    return FDPH_OK;
+}
+
+static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double eps, const fdph_params& p) {
+    PlanInputs in;
+    in.mu = m->mu;
+    in.cs = m->cs;
+    in.dt = dt;
+    in.M = M;
+    in.eps = eps;
+    in.eta = p.eta;
+    in.lmin = p.lmin;
+    in.eps_st = p.eps_st;
+    in.leaf = p.leaf_size;
+    in.extra_steps = p.extra_steps;
+    return in;
+}
+
+int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* material, double dt,
+                     const fdph_params* params, int32_t* buf, int64_t cap, int64_t* len) {
+    int rc = check_inputs(geometry, material, dt, params);
+    if (rc) return rc;
+    if (!len) return FDPH_E_ARG;
+    fdph_params p;
+    fdph_default_params(&p);
+    if (params) p = *params;
+    PlanInputs in = make_inputs(material, dt, 1, 0.0, p);
+    Elements el = make_elements(geometry->n, geometry->xy);
+    Tree tr;
+    build_tree(el, in, tr);
+    std::vector<int32_t> out;
+    out.push_back(el.n);
+    out.insert(out.end(), tr.perm.begin(), tr.perm.end());
+    out.push_back((int32_t)tr.leaves.size());
+    for (const Leaf& lf : tr.leaves) {
+        const ClusterNode& tn = tr.nodes[lf.tau];
+        const ClusterNode& sn = tr.nodes[lf.sig];
+        out.push_back(lf.kind);
+        out.push_back(tn.lo);
+        out.push_back(tn.hi - tn.lo);
+        out.push_back(sn.lo);
+        out.push_back(sn.hi - sn.lo);
+        if (lf.kind == 1) {
+            ArtInts a = art_integers(el, tr, lf, in);
+            if (a.causal < 1) {
+                set_error("discretised causality violated");
+                return FDPH_E_CAUSALITY;
+            }
+            out.insert(out.end(), a.dm.begin(), a.dm.end());
+            out.insert(out.end(), a.mbar.begin(), a.mbar.end());
+            out.insert(out.end(), a.Dm.begin(), a.Dm.end());
+        }
+    }
+    *len = (int64_t)out.size();
+    if (buf) {
+        if (cap < (int64_t)out.size()) {
+            set_error("buffer too small");
+            return FDPH_E_ARG;
+        }
+        memcpy(buf, out.data(), out.size() * sizeof(int32_t));
+    }
+    return FDPH_OK;
+}
+
+int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, double dt, int32_t M, double eps,
+              const fdph_params* params, fdph_plan_t* out) {
+    if (!out) return FDPH_E_ARG;
+    *out = nullptr;
+    int rc = check_inputs(geometry, material, dt, params);
+    if (rc) return rc;
+    if (M <= 0) {
+        set_error("M must be positive");
+        return FDPH_E_ARG;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    fdph_params p;
+    fdph_default_params(&p);
+    if (params) p = *params;
+    fdph_plan_s* P = new (std::nothrow) fdph_plan_s();
+    if (!P) return FDPH_E_OOM;
+    P->device = p.device;
+    P->precision = p.precision;
+    P->N = geometry->n;
+    P->M = M;
+    P->dt = dt;
+    auto fail = [&](int code) {
+        fdph_destroy(P);
+        return code;
+    };
+    if (cudaSetDevice(p.device) != cudaSuccess) {
+        set_error("cudaSetDevice failed");
+        return fail(FDPH_E_CUDA);
+    }
+    if (p.cuda_stream) {
+        P->stream = (cudaStream_t)p.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("cudaStreamCreate failed");
+            return fail(FDPH_E_CUDA);
+        }
+        P->own_stream = true;
+    }
+    PlanInputs in = make_inputs(material, dt, M, eps, p);
+    Elements el = make_elements(geometry->n, geometry->xy);
+    HostPlan& hp = P->hp;
+    rc = build_host_plan(el, in, hp);
+    if (rc == -3) return fail(FDPH_E_CAUSALITY);
+    if (rc) return fail(FDPH_E_ARG);
+    // ---- upload the far-field operator
+    std::vector<SbDev> sd(hp.sbs.size());
+    for (size_t q = 0; q < sd.size(); ++q) {
+        const SubBlock& b = hp.sbs[q];
+        sd[q] = {b.kind, b.rank, b.r0, b.nr, b.s0, b.ns, b.L, b.LZ, b.taps, b.maxdelay, b.mindm, b.run0,
+                 (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
+                 (long long)b.dhat, (long long)b.delay, (long long)b.dm};
+    }
+    if ((rc = upload(P, &P->perm, hp.perm)) || (rc = upload(P, &P->sbs, sd)) || (rc = upload(P, &P->ints, hp.ints)) ||
+        (rc = upload(P, &P->run_delay, hp.run_delay)) || (rc = upload(P, &P->run_start, hp.run_start)) ||
+        (rc = upload(P, &P->run_len, hp.run_len)) || (rc = upload(P, &P->src_order, hp.src_order)) ||
+        (rc = upload(P, &P->scat_sb, hp.scat_sb)) || (rc = upload(P, &P->scat_run, hp.scat_run)) ||
+        (rc = upload(P, &P->fir_sb, hp.fir_sb)) || (rc = upload(P, &P->fir_j, hp.fir_j)) ||
+        (rc = upload(P, &P->tr_sb, hp.tr_sb)) || (rc = upload(P, &P->tr_l, hp.tr_l)) ||
+        (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
+        (rc = upload(P, &P->g_il, hp.g_il)))
+        return fail(rc);
+    if (P->precision == FDPH_FP32) {
+        std::vector<float> f(hp.fac.begin(), hp.fac.end());
+        float* d = nullptr;
+        if ((rc = upload(P, &d, f))) return fail(rc);
+        P->fac = d;
+    } else {
+        double* d = nullptr;
+        if ((rc = upload(P, &d, hp.fac))) return fail(rc);
+        P->fac = d;
+    }
+    // ---- near field (device-evaluated kernel windows)
+    rc = P->precision == FDPH_FP32 ? build_near<float>(P, in) : build_near<double>(P, in);
+    if (rc) return fail(rc);
+    // ---- state
+    P->WD = std::max(std::max(hp.max_W, hp.max_taps), 1);
+    P->WC = hp.max_W + 1;
+    size_t sb = 0;
+    auto st = [&](double** p, size_t cnt) {
+        sb += std::max<size_t>(cnt, 1) * 8;
+        return dalloc(P, p, cnt);
+    };
+    if ((rc = st(&P->Dring, (size_t)P->WD * P->N)) || (rc = st(&P->Cring, (size_t)P->WC * P->N)) ||
+        (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
+        (rc = st(&P->zring, hp.zring_len)) || (rc = st(&P->dhat, hp.dhat_len)) ||
+        (rc = st(&P->partial, hp.items.size() * 32)))
+        return fail(rc);
+    P->state_bytes = sb;
+    if ((rc = fdph_reset(P))) return fail(rc);
+    fill_stats(P);
+    P->st.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return FDPH_OK;
+}
+
+int fdph_reset(fdph_plan_t P) {
+    if (!P) return FDPH_E_ARG;
+    cudaSetDevice(P->device);
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->dhat, P->partial};
+    size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
+                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.dhat_len,
+                    P->hp.items.size() * 32};
+    for (int q = 0; q < 8; ++q)
+        if (bufs[q] && cnt[q]) FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, cnt[q] * sizeof(double), P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    P->n = 0;
+    return FDPH_OK;
+}
+
+int fdph_step(fdph_plan_t P, const double* D_n, double* T_n) {
+    if (!P || !D_n || !T_n) return FDPH_E_ARG;
+    if (P->n >= P->M) {
+        set_error("the plan has already taken M steps");
+        return FDPH_E_STATE;
+    }
+    return step_impl(P, D_n, T_n);
+}
+
+int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
+    if (!P || !D || !T || steps < 0) return FDPH_E_ARG;
+    if (P->n + steps > P->M) {
+        set_error("run would pass step M");
+        return FDPH_E_STATE;
+    }
+    for (int s = 0; s < steps; ++s) {
+        int rc = step_impl(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
+        if (rc) return rc;
+    }
+    return FDPH_OK;
+}
+
+int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
+    if (!P || !D_n_host || !T_n_host) return FDPH_E_ARG;
+    if (!P->dD) {
+        int rc;
+        if ((rc = dalloc(P, &P->dD, P->N)) || (rc = dalloc(P, &P->dT, P->N))) return rc;
+    }
+    FDPH_CUDA(cudaMemcpyAsync(P->dD, D_n_host, P->N * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    int rc = fdph_step(P, P->dD, P->dT);
+    if (rc) return rc;
+    FDPH_CUDA(cudaMemcpyAsync(T_n_host, P->dT, P->N * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    return FDPH_OK;
+}
+
+int fdph_current_step(fdph_plan_t P, int32_t* n) {
+    if (!P || !n) return FDPH_E_ARG;
+    *n = P->n;
+    return FDPH_OK;
+}
+
+int fdph_synchronize(fdph_plan_t P) {
+    if (!P) return FDPH_E_ARG;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    return FDPH_OK;
+}
+
+int fdph_get_stats(fdph_plan_t P, fdph_stats* s) {
+    if (!P || !s) return FDPH_E_ARG;
+    *s = P->st;
+    return FDPH_OK;
+}
+
+int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
+    if (!P || !len) return FDPH_E_ARG;
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring};
+    size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
+                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len};
+    size_t need = sizeof(int32_t) * 2;
+    for (int q = 0; q < 6; ++q) need += cnt[q] * sizeof(double);
+    if (!buf) {
+        *len = need;
+        return FDPH_OK;
+    }
+    if (*len < need) return FDPH_E_ARG;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    char* o = (char*)buf;
+    int32_t hdr[2] = {P->n, P->N};
+    memcpy(o, hdr, sizeof(hdr));
+    o += sizeof(hdr);
+    for (int q = 0; q < 6; ++q) {
+        if (cnt[q]) FDPH_CUDA(cudaMemcpy(o, bufs[q], cnt[q] * sizeof(double), cudaMemcpyDeviceToHost));
+        o += cnt[q] * sizeof(double);
+    }
+    *len = need;
+    return FDPH_OK;
+}
+
+int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
+    if (!P || !buf) return FDPH_E_ARG;
+    size_t need = 0;
+    int rc = fdph_save_state(P, nullptr, &need);
+    if (rc) return rc;
+    if (len != need) {
+        set_error("state buffer size does not match this plan");
+        return FDPH_E_ARG;
+    }
+    const char* o = (const char*)buf;
+    int32_t hdr[2];
+    memcpy(hdr, o, sizeof(hdr));
+    if (hdr[1] != P->N || hdr[0] < 0 || hdr[0] > P->M) {
+        set_error("state buffer belongs to another plan");
+        return FDPH_E_ARG;
+    }
+    o += sizeof(hdr);
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring};
+    size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
+                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len};
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    for (int q = 0; q < 6; ++q) {
+        if (cnt[q]) FDPH_CUDA(cudaMemcpy(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice));
+        o += cnt[q] * sizeof(double);
+    }
+    P->n = hdr[0];
+    return FDPH_OK;
+}
+
+int fdph_set_profiling(fdph_plan_t P, int enable) {
+    if (!P) return FDPH_E_ARG;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    prof_drain(P);
+    for (int k = 0; k < FDPH_NUM_KERNELS; ++k) {
+        P->prof_ms[k] = 0.0;
+        P->prof_n[k] = 0;
+    }
+    P->prof = enable != 0;
+    return FDPH_OK;
+}
+
+int fdph_kernel_times(fdph_plan_t P, double* ms, int64_t* launches) {
+    if (!P || !ms || !launches) return FDPH_E_ARG;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    prof_drain(P);
+    for (int k = 0; k < FDPH_NUM_KERNELS; ++k) {
+        ms[k] = P->prof_ms[k];
+        launches[k] = P->prof_n[k];
+    }
+    return FDPH_OK;
+}
+
+void fdph_destroy(fdph_plan_t P) {
+    if (!P) return;
+    cudaSetDevice(P->device);
+    if (P->stream) cudaStreamSynchronize(P->stream);
+    prof_drain(P);
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    for (void* p : P->allocs) cudaFree(p);
+    if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
+    delete P;
+}
+
+}  // extern "C"

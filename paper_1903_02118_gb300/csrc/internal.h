@@ -1,0 +1,67 @@
+// internal.h -- host-side plan structures shared by the plan builder and the CUDA code.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace fdph {
+
+struct Elements {
+    int n = 0;
+    std::vector<double> ax, ay, bx, by, mx, my, len, tx, ty, nx, ny;
+};
+
+struct Box {
+    double lo[2], hi[2];
+};
+
+struct ClusterNode {
+    Box box;
+    int lo, hi;        // range of internal positions
+    int level;
+    int kid[2];        // child nodes (-1 = none)
+    bool split_done;
+};
+
+struct Leaf {
+    int kind;          // 1 admissible, 0 inadmissible
+    int tau, sig;      // cluster nodes
+    double diam, dist, rbar;
+};
+
+// Tree, permutation and ART integers (everything decided bit-exactly on the host).
+struct Tree {
+    std::vector<int> perm;            // perm[p] = geometry index of internal position p
+    std::vector<ClusterNode> nodes;
+    std::vector<Leaf> leaves;
+    int nc = 0;                        // extra Domain-F steps
+};
+
+struct ArtInts {                      // per admissible leaf
+    std::vector<int> dm, mbar, Dm;    // dm[nr], mbar[ns], Dm[ns]
+    int causal = 0;                   // min(dm + mbar)
+};
+
+struct PlanInputs {
+    double mu, cs, dt, eps, eta, lmin, eps_st;
+    int M, leaf, extra_steps;
+};
+
+Elements make_elements(int n, const double* xy);
+void build_tree(const Elements& el, const PlanInputs& in, Tree& tr);
+ArtInts art_integers(const Elements& el, const Tree& tr, const Leaf& lf, const PlanInputs& in);
+
+// Truncated SVD low-rank approximation with the Frobenius criterion.
+// A is m x n row-major.  On return: rank r, F (m x r, row-major), G (n x r, row-major) with
+// A_r = F G^T; exact = true when the block is kept exact (rank * (m + n) >= m * n).
+struct LowRank {
+    int m = 0, n = 0, rank = 0;
+    bool exact = false;
+    std::vector<double> F, G;
+};
+void low_rank(const double* A, int m, int n, double eps, LowRank& out);
+
+void set_error(const std::string& msg);
+
+}  // namespace fdph

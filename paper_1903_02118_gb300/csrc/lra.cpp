@@ -1,0 +1,208 @@
+// lra.cpp -- low-rank approximation of one H-matrix block (Sec. 2.3, Eq. 13).
+//
+// The criterion of the paper is |K_a - K_a,LRA|_F < eps |K_a|_F.  The best approximation of a
+// given rank is the truncated SVD, so the rank chosen here is the smallest r whose discarded
+// singular values satisfy the criterion.  The SVD is computed in two exact stages:
+//   1. Householder QR with column pivoting, stopped once the trailing block is below
+//      1e-15 |A|_F (A P = Q R + E, |E| tiny): the numerical rank k is small for admissible
+//      blocks, so this costs O(m n k);
+//   2. one-sided (Hestenes) Jacobi SVD of the k x n row space R P^T.
+// Factors are balanced: F = U_r sqrt(S_r), G = V_r sqrt(S_r).  When the chosen rank would
+// store at least as many numbers as the block (rank (m + n) >= m n) the block is kept exact
+// (the fallback of Sec. 6.2): F = I, G = A^T (or F = A, G = I).
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace fdph {
+
+namespace {
+
+// One-sided Jacobi on the columns of X (rows x cols, column-major), accumulating V.
+// On return columns of X are mutually orthogonal: X_in = X_out V^T.
+void hestenes(std::vector<double>& X, int rows, int cols, std::vector<double>& V) {
+    V.assign((size_t)cols * cols, 0.0);
+    for (int i = 0; i < cols; ++i) V[(size_t)i * cols + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < cols - 1; ++p) {
+            for (int q = p + 1; q < cols; ++q) {
+                double* xp = &X[(size_t)p * rows];
+                double* xq = &X[(size_t)q * rows];
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int i = 0; i < rows; ++i) {
+                    a += xp[i] * xp[i];
+                    b += xq[i] * xq[i];
+                    g += xp[i] * xq[i];
+                }
+                if (g == 0.0 || fabs(g) <= 1e-15 * sqrt(a * b)) continue;
+                off = std::max(off, fabs(g) / sqrt(a * b));
+                const double zeta = (b - a) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t);
+                const double s = c * t;
+                for (int i = 0; i < rows; ++i) {
+                    const double u = xp[i], v = xq[i];
+                    xp[i] = c * u - s * v;
+                    xq[i] = s * u + c * v;
+                }
+                double* vp = &V[(size_t)p * cols];
+                double* vq = &V[(size_t)q * cols];
+                for (int i = 0; i < cols; ++i) {
+                    const double u = vp[i], v = vq[i];
+                    vp[i] = c * u - s * v;
+                    vq[i] = s * u + c * v;
+                }
+            }
+        }
+        if (off <= 1e-15) break;
+    }
+}
+
+}  // namespace
+
+void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
+    out.m = m;
+    out.n = n;
+    out.rank = 0;
+    out.exact = false;
+    out.F.clear();
+    out.G.clear();
+    double norm2 = 0.0;
+    for (long i = 0; i < (long)m * n; ++i) norm2 += A[i] * A[i];
+    if (norm2 == 0.0) return;
+    auto keep_exact = [&]() {
+        out.exact = true;
+        if (m <= n) {
+            out.rank = m;
+            out.F.assign((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i) out.F[(size_t)i * m + i] = 1.0;
+            out.G.resize((size_t)n * m);
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < m; ++i) out.G[(size_t)j * m + i] = A[(size_t)i * n + j];
+        } else {
+            out.rank = n;
+            out.F.assign(A, A + (size_t)m * n);
+            out.G.assign((size_t)n * n, 0.0);
+            for (int j = 0; j < n; ++j) out.G[(size_t)j * n + j] = 1.0;
+        }
+    };
+    if (eps <= 0.0) {
+        keep_exact();
+        return;
+    }
+    // ---- stage 1: QR with column pivoting on a column-major copy
+    std::vector<double> W((size_t)m * n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) W[(size_t)j * m + i] = A[(size_t)i * n + j];
+    std::vector<int> piv(n);
+    std::iota(piv.begin(), piv.end(), 0);
+    std::vector<double> cn(n), tau;
+    std::vector<std::vector<double>> hv;  // Householder vectors (length m - k)
+    const int kmax = std::min(m, n);
+    int k = 0;
+    const double stop2 = 1e-30 * norm2;
+    for (; k < kmax; ++k) {
+        double trail = 0.0;
+        int best = k;
+        for (int j = k; j < n; ++j) {
+            const double* col = &W[(size_t)j * m];
+            double s = 0.0;
+            for (int i = k; i < m; ++i) s += col[i] * col[i];
+            cn[j] = s;
+            trail += s;
+            if (s > cn[best]) best = j;
+        }
+        if (trail <= stop2) break;
+        if (best != k) {
+            std::swap_ranges(&W[(size_t)k * m], &W[(size_t)k * m] + m, &W[(size_t)best * m]);
+            std::swap(piv[k], piv[best]);
+            std::swap(cn[k], cn[best]);
+        }
+        double* col = &W[(size_t)k * m];
+        const double alpha = sqrt(cn[k]);
+        const double beta = col[k] >= 0 ? -alpha : alpha;
+        std::vector<double> v(col + k, col + m);
+        v[0] -= beta;
+        double vn2 = 0.0;
+        for (double x : v) vn2 += x * x;
+        if (vn2 > 0.0) {
+            for (int j = k + 1; j < n; ++j) {
+                double* cj = &W[(size_t)j * m];
+                double d = 0.0;
+                for (int i = 0; i < m - k; ++i) d += v[i] * cj[k + i];
+                const double f = 2.0 * d / vn2;
+                for (int i = 0; i < m - k; ++i) cj[k + i] -= f * v[i];
+            }
+        }
+        col[k] = beta;
+        for (int i = k + 1; i < m; ++i) col[i] = 0.0;
+        hv.push_back(v);
+        tau.push_back(vn2);
+    }
+    const int kr = k;  // numerical rank of the QR stage
+    double resid2 = 0.0;
+    for (int j = kr; j < n; ++j) {
+        const double* col = &W[(size_t)j * m];
+        for (int i = kr; i < m; ++i) resid2 += col[i] * col[i];
+    }
+    if (kr == 0) return;
+    // ---- stage 2: SVD of B = R P^T (kr x n) via Jacobi on B^T (n x kr, column-major)
+    std::vector<double> BT((size_t)n * kr, 0.0);
+    for (int j = 0; j < n; ++j) {
+        const double* col = &W[(size_t)j * m];
+        for (int i = 0; i < std::min(kr, j + 1); ++i) BT[(size_t)i * n + piv[j]] = col[i];
+    }
+    std::vector<double> V;
+    hestenes(BT, n, kr, V);
+    std::vector<double> sv(kr);
+    for (int c = 0; c < kr; ++c) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += BT[(size_t)c * n + i] * BT[(size_t)c * n + i];
+        sv[c] = sqrt(s);
+    }
+    std::vector<int> ord(kr);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return sv[a] > sv[b]; });
+    // rank: smallest r with sqrt(sum_{l >= r} s_l^2 + resid) < eps |A|
+    std::vector<double> tail(kr + 1, 0.0);
+    tail[kr] = resid2;
+    for (int l = kr - 1; l >= 0; --l) tail[l] = tail[l + 1] + sv[ord[l]] * sv[ord[l]];
+    const double lim = eps * sqrt(norm2);
+    int r = kr;
+    for (int l = 0; l <= kr; ++l)
+        if (sqrt(tail[l]) < lim) { r = l; break; }
+    if ((long)r * (m + n) >= (long)m * n) {
+        keep_exact();
+        return;
+    }
+    out.rank = r;
+    if (r == 0) return;
+    // left vectors: Q * V[:, c]  (Q from the Householder reflectors, kr columns)
+    // B = V S U^T with U columns = BT columns / s; A ~ Q B = (Q V) S U^T
+    out.F.assign((size_t)m * r, 0.0);
+    out.G.assign((size_t)n * r, 0.0);
+    for (int l = 0; l < r; ++l) {
+        const int c = ord[l];
+        const double s = sv[c];
+        const double rs = sqrt(s);
+        // y = Q * e where e = V column c padded to length m
+        std::vector<double> y(m, 0.0);
+        for (int i = 0; i < kr; ++i) y[i] = V[(size_t)c * kr + i];
+        for (int h = kr - 1; h >= 0; --h) {
+            const std::vector<double>& v = hv[h];
+            double d = 0.0;
+            for (int i = 0; i < m - h; ++i) d += v[i] * y[h + i];
+            const double f = 2.0 * d / tau[h];
+            for (int i = 0; i < m - h; ++i) y[h + i] -= f * v[i];
+        }
+        for (int i = 0; i < m; ++i) out.F[(size_t)i * r + l] = y[i] * rs;
+        for (int j = 0; j < n; ++j) out.G[(size_t)j * r + l] = BT[(size_t)c * n + j] / s * rs;
+    }
+}
+
+}  // namespace fdph

@@ -1,0 +1,353 @@
+// plan.cpp -- host construction of the FDP=H operator (Secs. 2.3, 4, App. B.1, B.3, C.3, E, H).
+//
+// For every admissible leaf (receivers i, sources j, representative points i*, j* = box centres):
+//   a_ij = dm_i + mbar_j          start of the pair's discrete Domain F (Eq. 31)
+//   kS_ij = a_ij + Dm_j           start of Domain S
+//   Domain F, per global stress component c (App. C.2, stress first, traction afterwards):
+//     amplitude  Khat^c_ij = R^c_ij(kS dt) - R^c_ij(a dt)       (Eq. 28), low-rank after the
+//                projection n^c_i                                (Eq. 13)
+//     waveform   h^c_{j,m} = K^c_{i* j, mbar_j + m} / Khat^c_{i* j}  (Eq. 29), or, when
+//                component c is nearly nodal at i*, the waveform of the stress vector
+//                projected on its impulse direction
+//   Domain S: static traction kernel per unit slip, low-rank, applied as dt * slip from kS on
+//             (App. B.1; the App. C.3 integers make its second term vanish)
+//   transient (App. B.3, App. H): K - Khat^S dt ~ Khat^tr h^tr with the temporal pivot at kS
+//             and the spatial pivot at the largest |entry| of the leaf; Dm_tr from eps_st
+// Inadmissible leaves only get their geometry here; their exact-kernel windows are computed on
+// the device (fdph.cu) because they need O(pairs * M) kernel evaluations.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+
+#include "kernel2d.cuh"
+#include "plan.h"
+
+namespace fdph {
+
+namespace {
+
+const double kNodalTau = 0.2;
+
+struct LeafOut {
+    ArtInts art;
+    int r0, nr, s0, ns;
+    int HM = 0;
+    LowRank F[2], S, TR[2];
+    std::vector<double> h[2];      // [HM][ns]
+    std::vector<double> htr[2];
+    int Dtr[2] = {0, 0};
+    bool ok = true;
+};
+
+Seg seg_of(const Elements& el, int e) {
+    Seg s;
+    s.ax = el.ax[e];
+    s.ay = el.ay[e];
+    s.tx = el.tx[e];
+    s.ty = el.ty[e];
+    s.len = el.len[e];
+    return s;
+}
+
+void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanInputs& in, LeafOut& o) {
+    const ClusterNode& tn = tr.nodes[lf.tau];
+    const ClusterNode& sn = tr.nodes[lf.sig];
+    o.r0 = tn.lo;
+    o.nr = tn.hi - tn.lo;
+    o.s0 = sn.lo;
+    o.ns = sn.hi - sn.lo;
+    o.art = art_integers(el, tr, lf, in);
+    if (o.art.causal < 1) {
+        o.ok = false;
+        return;
+    }
+    const int nr = o.nr, ns = o.ns;
+    const double dt = in.dt, mu = in.mu, c = in.cs;
+    const double ist[2] = {0.5 * (tn.box.lo[0] + tn.box.hi[0]), 0.5 * (tn.box.lo[1] + tn.box.hi[1])};
+    std::vector<double> Ax((size_t)nr * ns), Ay((size_t)nr * ns), Ks((size_t)nr * ns);
+    std::vector<double> tx((size_t)nr * ns), ty((size_t)nr * ns);
+    for (int il = 0; il < nr; ++il) {
+        const int ei = tr.perm[o.r0 + il];
+        const double px = el.mx[ei], py = el.my[ei], nx = el.nx[ei], ny = el.ny[ei];
+        for (int jl = 0; jl < ns; ++jl) {
+            const int ej = tr.perm[o.s0 + jl];
+            const Seg s = seg_of(el, ej);
+            const long a = (long)o.art.dm[il] + o.art.mbar[jl];
+            const long kS = a + o.art.Dm[jl];
+            const Stress2 amp = stress_jump(px, py, s, (double)a * dt, (double)kS * dt, mu, c);
+            const Stress2 st = stress_static(px, py, s, mu);
+            const Stress2 tl = stress_tail(px, py, s, (double)kS * dt, (double)(kS + 1) * dt, mu, c);
+            const size_t q = (size_t)il * ns + jl;
+            Ax[q] = nx * amp.x;
+            Ay[q] = ny * amp.y;
+            Ks[q] = nx * st.x + ny * st.y;
+            tx[q] = tl.x;
+            ty[q] = tl.y;
+        }
+    }
+    // waveforms at i*
+    int HM = 0;
+    for (int jl = 0; jl < ns; ++jl) HM = std::max(HM, o.art.Dm[jl]);
+    o.HM = HM;
+    o.h[0].assign((size_t)HM * ns, 0.0);
+    o.h[1].assign((size_t)HM * ns, 0.0);
+    std::vector<double> wx(HM), wy(HM);
+    for (int jl = 0; jl < ns; ++jl) {
+        const int ej = tr.perm[o.s0 + jl];
+        const Seg s = seg_of(el, ej);
+        const int mb = o.art.mbar[jl], D = o.art.Dm[jl];
+        const Stress2 amp = stress_jump(ist[0], ist[1], s, (double)mb * dt, (double)(mb + D) * dt, mu, c);
+        for (int m = 0; m < D; ++m) {
+            const double t1 = (double)(mb + m) * dt;
+            const Stress2 w = stress_jump(ist[0], ist[1], s, t1, t1 + dt, mu, c);
+            wx[m] = w.x;
+            wy[m] = w.y;
+        }
+        const double nrm2 = amp.x * amp.x + amp.y * amp.y;
+        const double nrm = sqrt(nrm2);
+        const double den = nrm2 > 0.0 ? nrm2 : 1.0;
+        for (int cc = 0; cc < 2; ++cc) {
+            const double ac = cc == 0 ? amp.x : amp.y;
+            const bool own = fabs(ac) >= kNodalTau * nrm && ac != 0.0;
+            for (int m = 0; m < D; ++m) {
+                const double v = own ? (cc == 0 ? wx[m] : wy[m]) / ac : (amp.x * wx[m] + amp.y * wy[m]) / den;
+                o.h[cc][(size_t)m * ns + jl] = v;
+            }
+        }
+    }
+    low_rank(Ax.data(), nr, ns, in.eps, o.F[0]);
+    low_rank(Ay.data(), nr, ns, in.eps, o.F[1]);
+    low_rank(Ks.data(), nr, ns, in.eps, o.S);
+    // transient, per component
+    const double thr = in.eps_st * mu / (2.0 * c);
+    for (int cc = 0; cc < 2; ++cc) {
+        const std::vector<double>& t = cc == 0 ? tx : ty;
+        size_t best = 0;
+        for (size_t q = 1; q < t.size(); ++q)
+            if (fabs(t[q]) > fabs(t[best])) best = q;
+        if (t[best] == 0.0) continue;
+        const int pi = (int)(best / ns), pj = (int)(best % ns);
+        const int ei = tr.perm[o.r0 + pi], ej = tr.perm[o.s0 + pj];
+        const Seg s = seg_of(el, ej);
+        const long k0 = (long)o.art.dm[pi] + o.art.mbar[pj] + o.art.Dm[pj];
+        std::vector<double> fib(in.M);
+        int last = -1;
+        for (int m = 0; m < in.M; ++m) {
+            const Stress2 v = stress_tail(el.mx[ei], el.my[ei], s, (double)(k0 + m) * dt,
+                                          (double)(k0 + m + 1) * dt, mu, c);
+            fib[m] = cc == 0 ? v.x : v.y;
+            if (fabs(fib[m]) >= thr) last = m;
+        }
+        const int Dtr = last + 1;
+        if (Dtr == 0) continue;
+        std::vector<double> B((size_t)nr * ns);
+        for (int il = 0; il < nr; ++il) {
+            const int e = tr.perm[o.r0 + il];
+            const double nc = cc == 0 ? el.nx[e] : el.ny[e];
+            for (int jl = 0; jl < ns; ++jl) B[(size_t)il * ns + jl] = nc * t[(size_t)il * ns + jl];
+        }
+        low_rank(B.data(), nr, ns, in.eps, o.TR[cc]);
+        o.Dtr[cc] = Dtr;
+        o.htr[cc].resize(Dtr);
+        for (int m = 0; m < Dtr; ++m) o.htr[cc][m] = fib[m] / fib[0];
+    }
+}
+
+template <class T>
+int64_t append(std::vector<T>& dst, const T* src, size_t n) {
+    const int64_t off = (int64_t)dst.size();
+    dst.insert(dst.end(), src, src + n);
+    return off;
+}
+
+}  // namespace
+
+int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
+    hp.n = el.n;
+    hp.M = in.M;
+    hp.dt = in.dt;
+    hp.mu = in.mu;
+    hp.cs = in.cs;
+    build_tree(el, in, hp.tree);
+    const Tree& tr = hp.tree;
+    const int n = el.n;
+    hp.perm.assign(tr.perm.begin(), tr.perm.end());
+    auto fill = [&](std::vector<double>& v, const std::vector<double>& src) {
+        v.resize(n);
+        for (int p = 0; p < n; ++p) v[p] = src[tr.perm[p]];
+    };
+    fill(hp.px, el.mx); fill(hp.py, el.my); fill(hp.pnx, el.nx); fill(hp.pny, el.ny);
+    fill(hp.sax, el.ax); fill(hp.say, el.ay); fill(hp.stx, el.tx); fill(hp.sty, el.ty);
+    fill(hp.slen, el.len);
+
+    std::vector<const Leaf*> adm;
+    for (const Leaf& lf : tr.leaves) {
+        if (lf.kind == 1) adm.push_back(&lf);
+        else {
+            const ClusterNode& tn = tr.nodes[lf.tau];
+            const ClusterNode& sn = tr.nodes[lf.sig];
+            hp.near_r0.push_back(tn.lo);
+            hp.near_nr.push_back(tn.hi - tn.lo);
+            hp.near_s0.push_back(sn.lo);
+            hp.near_ns.push_back(sn.hi - sn.lo);
+        }
+    }
+    hp.n_adm = (int)adm.size();
+    hp.n_near = (int)hp.near_r0.size();
+    std::vector<LeafOut> outs(adm.size());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long a = 0; a < (long)adm.size(); ++a) admissible(el, tr, *adm[a], in, outs[a]);
+    for (const LeafOut& o : outs)
+        if (!o.ok) {
+            set_error("discretised causality min(dm_i + mbar_j) >= 1 violated by an admissible leaf");
+            return -3;
+        }
+
+    // ---- assemble sub-blocks
+    std::vector<std::vector<std::pair<int, int>>> recv(n);   // receiver -> (sb, il)
+    double rank_sum = 0;
+    int rank_cnt = 0;
+    for (const LeafOut& o : outs) {
+        const int64_t dm_off = append(hp.ints, o.art.dm.data(), o.art.dm.size());
+        std::vector<int32_t> dF(o.ns), dS(o.ns);
+        for (int j = 0; j < o.ns; ++j) {
+            dF[j] = o.art.mbar[j];
+            dS[j] = o.art.mbar[j] + o.art.Dm[j];
+        }
+        const int64_t dF_off = append(hp.ints, dF.data(), dF.size());
+        const int64_t dS_off = append(hp.ints, dS.data(), dS.size());
+        const int mindm = *std::min_element(o.art.dm.begin(), o.art.dm.end());
+        const int maxdm = *std::max_element(o.art.dm.begin(), o.art.dm.end());
+        auto add = [&](int kind, const LowRank& lr, const std::vector<int32_t>& dl, int64_t dl_off,
+                       const std::vector<double>* h, int taps) {
+            if (lr.rank <= 0) return;
+            SubBlock sb;
+            memset(&sb, 0, sizeof(sb));
+            sb.kind = kind;
+            sb.rank = lr.rank;
+            sb.r0 = o.r0; sb.nr = o.nr; sb.s0 = o.s0; sb.ns = o.ns;
+            sb.maxdelay = *std::max_element(dl.begin(), dl.end());
+            sb.mindelay = *std::min_element(dl.begin(), dl.end());
+            sb.mindm = mindm;
+            sb.maxdm = maxdm;
+            sb.taps = taps;
+            sb.f = append(hp.fac, lr.F.data(), lr.F.size());
+            sb.g = append(hp.fac, lr.G.data(), lr.G.size());
+            sb.h = h ? append(hp.fac, h->data(), h->size()) : 0;
+            sb.delay = dl_off;
+            sb.dm = dm_off;
+            if (kind == SB_TR) {
+                sb.L = sb.maxdelay + mindm + taps;
+                sb.LZ = maxdm - mindm + 1;
+            } else {
+                sb.L = sb.maxdelay + maxdm + 1;
+                sb.LZ = 0;
+            }
+            sb.ring = hp.ring_len;
+            hp.ring_len += (int64_t)sb.rank * sb.L;
+            sb.zring = hp.zring_len;
+            hp.zring_len += (int64_t)sb.rank * sb.LZ;
+            sb.dhat = hp.dhat_len;
+            if (kind == SB_F) hp.dhat_len += o.ns;
+            // scatter runs: sources sorted by delay
+            std::vector<int> ord(o.ns);
+            for (int j = 0; j < o.ns; ++j) ord[j] = j;
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return dl[a] < dl[b]; });
+            const int32_t src0 = (int32_t)hp.src_order.size();
+            for (int j : ord) hp.src_order.push_back(j);
+            sb.run0 = (int32_t)hp.run_delay.size();
+            int q = 0;
+            while (q < o.ns) {
+                int e = q;
+                while (e < o.ns && dl[ord[e]] == dl[ord[q]]) ++e;
+                hp.run_delay.push_back(dl[ord[q]]);
+                hp.run_start.push_back(src0 + q);
+                hp.run_len.push_back(e - q);
+                q = e;
+            }
+            sb.nruns = (int32_t)hp.run_delay.size() - sb.run0;
+            const int id = (int)hp.sbs.size();
+            hp.sbs.push_back(sb);
+            for (int r = 0; r < sb.nruns; ++r) {
+                hp.scat_sb.push_back(id);
+                hp.scat_run.push_back(sb.run0 + r);
+            }
+            if (kind == SB_F)
+                for (int j = 0; j < o.ns; ++j) {
+                    hp.fir_sb.push_back(id);
+                    hp.fir_j.push_back(j);
+                }
+            if (kind == SB_TR)
+                for (int l = 0; l < sb.rank; ++l) {
+                    hp.tr_sb.push_back(id);
+                    hp.tr_l.push_back(l);
+                }
+            for (int il = 0; il < o.nr; ++il) recv[o.r0 + il].push_back({id, il});
+            hp.max_rank = std::max(hp.max_rank, sb.rank);
+            hp.max_taps = std::max(hp.max_taps, kind == SB_F ? taps : 0);
+            rank_sum += sb.rank;
+            rank_cnt += 1;
+            hp.far_entries += (int64_t)lr.F.size() + lr.G.size() + (h ? h->size() : 0);
+        };
+        add(SB_F, o.F[0], dF, dF_off, &o.h[0], o.HM);
+        add(SB_F, o.F[1], dF, dF_off, &o.h[1], o.HM);
+        add(SB_S, o.S, dS, dS_off, nullptr, 0);
+        for (int cc = 0; cc < 2; ++cc)
+            if (o.Dtr[cc] > 0) add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc]);
+    }
+    hp.mean_rank = rank_cnt ? rank_sum / rank_cnt : 0.0;
+    hp.g_ptr.assign(n + 1, 0);
+    for (int p = 0; p < n; ++p) {
+        hp.g_ptr[p + 1] = hp.g_ptr[p] + (int32_t)recv[p].size();
+        for (auto& e : recv[p]) {
+            hp.g_sb.push_back(e.first);
+            hp.g_il.push_back(e.second);
+        }
+    }
+    return 0;
+}
+
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk) {
+    const int nl = (int)hp.near_r0.size();
+    hp.near.resize(nl);
+    hp.items.clear();
+    hp.near_tensor_len = 0;
+    hp.near_stat_len = 0;
+    hp.max_W = 0;
+    std::vector<std::vector<int32_t>> slots(hp.n);
+    for (int l = 0; l < nl; ++l) {
+        NearLeaf& L = hp.near[l];
+        L.r0 = hp.near_r0[l];
+        L.nr = hp.near_nr[l];
+        L.s0 = hp.near_s0[l];
+        L.ns = hp.near_ns[l];
+        L.W = W[l];
+        L.tensor = hp.near_tensor_len;
+        hp.near_tensor_len += (int64_t)L.W * L.ns * L.nr;
+        L.stat = hp.near_stat_len;
+        hp.near_stat_len += (int64_t)L.ns * L.nr;
+        hp.max_W = std::max(hp.max_W, L.W);
+        // one work item per chunk of steps; the first item also carries the static tail
+        const int nchunk = std::max(1, (L.W + chunk - 1) / chunk);
+        for (int c = 0; c < nchunk; ++c) {
+            NearItem it;
+            it.leaf = l;
+            it.k0 = c * chunk;
+            it.k1 = std::min(L.W, (c + 1) * chunk);
+            it.pad = 0;
+            const int id = (int)hp.items.size();
+            hp.items.push_back(it);
+            for (int il = 0; il < L.nr; ++il) slots[L.r0 + il].push_back(id * 32 + il);
+        }
+    }
+    hp.np_ptr.assign(hp.n + 1, 0);
+    hp.np_idx.clear();
+    for (int p = 0; p < hp.n; ++p) {
+        hp.np_ptr[p + 1] = hp.np_ptr[p] + (int32_t)slots[p].size();
+        hp.np_idx.insert(hp.np_idx.end(), slots[p].begin(), slots[p].end());
+    }
+}
+
+}  // namespace fdph

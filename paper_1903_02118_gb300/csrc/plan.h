@@ -1,0 +1,73 @@
+// plan.h -- flat, device-ready description of an FDP=H operator (built on the host).
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace fdph {
+
+enum SubKind { SB_F = 0, SB_S = 1, SB_TR = 2 };
+
+// One low-rank operator: admissible leaf x domain (F / S / transient) x stress component.
+// Receivers [r0, r0 + nr), sources [s0, s0 + ns) in internal order.
+struct SubBlock {
+    int32_t kind, rank, r0, nr, s0, ns;
+    int32_t L;         // ring length (F, S: representative-stress ring; TR: source-sum ring Y)
+    int32_t LZ;        // TR: length of the convolved ring Z
+    int32_t taps;      // F: waveform taps (max Dm of the leaf); TR: Dm_tr
+    int32_t maxdelay, mindelay, mindm, maxdm;
+    int64_t f, g, h;   // offsets into the factor array (f: nr x rank, g: ns x rank, h: taps x ns or taps)
+    int64_t ring, zring, dhat;   // offsets into state arrays
+    int64_t delay, dm; // offsets into the int array (delay[ns], dm[nr])
+    int32_t run0, nruns;
+};
+
+struct NearLeaf {
+    int32_t r0, nr, s0, ns, W;   // W = window of exact kernel steps stored
+    int64_t tensor;              // offset of [W][ns][nr] coefficients
+    int64_t stat;                // offset of the [ns][nr] static tile (x dt), FP64
+};
+
+struct NearItem {
+    int32_t leaf, k0, k1, pad;
+};
+
+struct HostPlan {
+    int n = 0, M = 0;
+    double dt = 0, mu = 0, cs = 0;
+    Tree tree;
+    std::vector<int32_t> perm;                       // internal -> geometry index
+    // internal-order geometry for the device near-field builder
+    std::vector<double> px, py, pnx, pny, sax, say, stx, sty, slen;
+    // far field
+    std::vector<SubBlock> sbs;
+    std::vector<double> fac;                         // f, g, h, htr (FP64 master copy)
+    std::vector<int32_t> ints;                       // delays, dm
+    std::vector<int32_t> run_delay, run_start, run_len, src_order;
+    std::vector<int32_t> scat_sb, scat_run;          // scatter tasks
+    std::vector<int32_t> fir_sb, fir_j;              // FIR tasks
+    std::vector<int32_t> tr_sb, tr_l;                // transient convolution tasks
+    std::vector<int32_t> g_ptr, g_sb, g_il;          // gather CSR (receiver-major)
+    int64_t ring_len = 0, zring_len = 0, dhat_len = 0;
+    int32_t max_taps = 0;
+    // near field
+    std::vector<NearLeaf> near;
+    std::vector<int32_t> near_r0, near_nr, near_s0, near_ns;   // for the m_S kernel
+    std::vector<NearItem> items;
+    std::vector<int32_t> np_ptr, np_idx;             // receiver -> partial slots
+    int64_t near_tensor_len = 0, near_stat_len = 0;
+    int32_t max_W = 0;
+    // stats
+    int n_adm = 0, n_near = 0, max_rank = 0;
+    double mean_rank = 0;
+    int64_t far_entries = 0;
+};
+
+// Everything except the near-field windows (which need the device). Returns status.
+int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
+// Second stage once the near-field windows W are known (fills offsets, items, CSR).
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk);
+
+}  // namespace fdph

@@ -1,0 +1,247 @@
+"""ctypes binding of the C ABI in include/fdph.h (argument marshalling only).
+
+Every step of the method runs inside libfdph.so; this module only converts
+Python / numpy / torch arguments to the plain pointers and sizes of the ABI.
+Loading fails loudly if the library has not been built: there is no fallback.
+Device buffers are anything with ``data_ptr()`` (a torch CUDA tensor) or a raw
+integer address; they must hold float64 values, contiguous.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdph.so")
+
+OK, E_ARG, E_OOM, E_CAUSALITY, E_CUDA, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, FP32 = 0, 1
+
+
+class FdphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("fdph status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("xy", ctypes.POINTER(ctypes.c_double))]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("cs", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("lmin", ctypes.c_double), ("eps_st", ctypes.c_double),
+                ("leaf_size", ctypes.c_int32), ("extra_steps", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("M", ctypes.c_int32), ("n_admissible", ctypes.c_int32),
+                ("n_near", ctypes.c_int32), ("n_subblocks", ctypes.c_int32), ("max_rank", ctypes.c_int32),
+                ("extra_steps", ctypes.c_int32), ("max_window", ctypes.c_int32),
+                ("mean_rank", ctypes.c_double), ("near_entries", ctypes.c_int64),
+                ("far_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("state_bytes", ctypes.c_int64), ("bytes_per_step", ctypes.c_double),
+                ("near_bytes_per_step", ctypes.c_double), ("flops_per_step", ctypes.c_double),
+                ("plan_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset",
+           "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
+           "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
+           "fdph_kernel_times"]
+KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
+
+
+def lib():
+    """The loaded libfdph.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfdph.so is not built (run __graft_entry__.build() or "
+                              "python paper_1903_02118_gb300/build.py); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        c_p = ctypes.c_void_p
+        L.fdph_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.fdph_default_params.restype = None
+        L.fdph_plan.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Material), ctypes.c_double, ctypes.c_int32,
+                                ctypes.c_double, ctypes.POINTER(Params), ctypes.POINTER(c_p)]
+        L.fdph_step.argtypes = [c_p, c_p, c_p]
+        L.fdph_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
+        L.fdph_step_host.argtypes = [c_p, c_p, c_p]
+        L.fdph_reset.argtypes = [c_p]
+        L.fdph_current_step.argtypes = [c_p, ctypes.POINTER(ctypes.c_int32)]
+        L.fdph_synchronize.argtypes = [c_p]
+        L.fdph_get_stats.argtypes = [c_p, ctypes.POINTER(Stats)]
+        L.fdph_save_state.argtypes = [c_p, c_p, ctypes.POINTER(ctypes.c_size_t)]
+        L.fdph_load_state.argtypes = [c_p, c_p, ctypes.c_size_t]
+        L.fdph_destroy.argtypes = [c_p]
+        L.fdph_destroy.restype = None
+        L.fdph_tree_export.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Material), ctypes.c_double,
+                                       ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        L.fdph_set_profiling.argtypes = [c_p, ctypes.c_int]
+        L.fdph_kernel_times.argtypes = [c_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.fdph_strerror.argtypes = [ctypes.c_int]
+        L.fdph_strerror.restype = ctypes.c_char_p
+        L.fdph_last_error.argtypes = []
+        L.fdph_last_error.restype = ctypes.c_char_p
+        for name in ("fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset", "fdph_current_step",
+                     "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
+                     "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        L = lib()
+        raise FdphError(rc, "%s (%s)" % (L.fdph_strerror(rc).decode(), L.fdph_last_error().decode()))
+
+
+def _ptr(x):
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def default_params():
+    p = Params()
+    lib().fdph_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
+                device=None, stream=None):
+    p = default_params()
+    for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
+                 ("extra_steps", extra_steps), ("precision", precision), ("device", device)):
+        if v is not None:
+            setattr(p, k, v)
+    if stream is not None:
+        p.cuda_stream = ctypes.c_void_p(stream)
+    return p
+
+
+def _geometry(xy):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    g = Geometry(xy.shape[0], xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return g, xy
+
+
+class Plan:
+    """Owner of an fdph_plan_t (see fdph_plan in include/fdph.h)."""
+
+    def __init__(self, xy, dt, M, eps, mu=1.0, cs=1.0, **params):
+        L = lib()
+        g, self._xy = _geometry(xy)
+        mat = Material(mu, cs)
+        p = make_params(**params)
+        h = ctypes.c_void_p()
+        _check(L.fdph_plan(ctypes.byref(g), ctypes.byref(mat), dt, M, eps, ctypes.byref(p), ctypes.byref(h)))
+        self.handle = h
+        self.n = int(xy.shape[0])
+        self.M = int(M)
+
+    def step(self, D_n, T_n):
+        _check(lib().fdph_step(self.handle, _ptr(D_n), _ptr(T_n)))
+
+    def run(self, steps, D, T):
+        _check(lib().fdph_run(self.handle, int(steps), _ptr(D), _ptr(T)))
+
+    def step_host(self, D_n, T_n=None):
+        D_n = np.ascontiguousarray(D_n, dtype=np.float64)
+        if T_n is None:
+            T_n = np.empty(self.n)
+        _check(lib().fdph_step_host(self.handle, ctypes.c_void_p(D_n.ctypes.data), ctypes.c_void_p(T_n.ctypes.data)))
+        return T_n
+
+    def reset(self):
+        _check(lib().fdph_reset(self.handle))
+
+    def current_step(self):
+        n = ctypes.c_int32()
+        _check(lib().fdph_current_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def synchronize(self):
+        _check(lib().fdph_synchronize(self.handle))
+
+    def stats(self):
+        s = Stats()
+        _check(lib().fdph_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def set_profiling(self, on=True):
+        _check(lib().fdph_set_profiling(self.handle, 1 if on else 0))
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        ms = (ctypes.c_double * len(KERNEL_NAMES))()
+        cnt = (ctypes.c_int64 * len(KERNEL_NAMES))()
+        _check(lib().fdph_kernel_times(self.handle, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_NAMES)}
+
+    def save_state(self):
+        n = ctypes.c_size_t()
+        _check(lib().fdph_save_state(self.handle, None, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().fdph_save_state(self.handle, ctypes.c_void_p(buf.ctypes.data), ctypes.byref(n)))
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().fdph_load_state(self.handle, ctypes.c_void_p(buf.ctypes.data), buf.size))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fdph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tree_export(xy, dt, mu=1.0, cs=1.0, **params):
+    """Host-only block tree + ART integers (fdph_tree_export), parsed."""
+    L = lib()
+    g, keep = _geometry(xy)
+    mat = Material(mu, cs)
+    p = make_params(**params)
+    n = ctypes.c_int64()
+    _check(L.fdph_tree_export(ctypes.byref(g), ctypes.byref(mat), dt, ctypes.byref(p), None, 0, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.int32)
+    _check(L.fdph_tree_export(ctypes.byref(g), ctypes.byref(mat), dt, ctypes.byref(p),
+                              buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value, ctypes.byref(n)))
+    N = int(buf[0])
+    perm = buf[1:1 + N].copy()
+    q = 1 + N
+    nl = int(buf[q])
+    q += 1
+    leaves = []
+    for _ in range(nl):
+        kind, r0, nr, s0, ns = (int(v) for v in buf[q:q + 5])
+        q += 5
+        lf = dict(kind=kind, r0=r0, nr=nr, s0=s0, ns=ns)
+        if kind == 1:
+            lf["dm"] = buf[q:q + nr].copy()
+            q += nr
+            lf["mbar"] = buf[q:q + ns].copy()
+            q += ns
+            lf["Dm"] = buf[q:q + ns].copy()
+            q += ns
+        leaves.append(lf)
+    return dict(perm=perm, leaves=leaves)

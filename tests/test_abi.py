@@ -1,0 +1,94 @@
+"""CPU tests of the C-ABI library: exports, argument checks, bit-exact tree and integers."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fdph as ofd
+from oracle import kernel as kn
+from paper_1903_02118_gb300 import build, fdph, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return fdph.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "fdph.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(fdph_[a-z_]+)\s*\(", hdr))
+    assert len(declared) >= 17
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared <= set(fdph.EXPORTS)
+
+
+def test_invalid_arguments_are_rejected_without_a_device(L):
+    g = fdph.Geometry(0, None)
+    m = fdph.Material(1.0, 1.0)
+    h = ctypes.c_void_p()
+    assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_ARG
+    xy = np.ascontiguousarray(inputs.straight_fault(8))
+    g = fdph.Geometry(8, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), -1.0, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_ARG
+    p = fdph.make_params(leaf_size=64)
+    assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
+    bad = xy.copy()
+    bad[3, 2] = np.nan
+    gb = fdph.Geometry(8, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert L.fdph_plan(ctypes.byref(gb), ctypes.byref(m), 0.5, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_NAN
+    assert not h.value
+    assert L.fdph_step(None, None, None) == fdph.E_ARG
+    assert L.fdph_strerror(fdph.E_CAUSALITY)
+
+
+def _compare_tree(xy, eta, leaf):
+    tr = fdph.tree_export(xy, 0.5, eta=eta, leaf_size=leaf)
+    perm = tr["perm"]
+    el = kn.element_table(xy)
+    p = ofd.Params(eta=eta, leaf=leaf)
+    leaves = ofd.block_tree(el, p)
+    key = lambda a, b: (tuple(sorted(a)), tuple(sorted(b)))
+    mine = {}
+    for lf in tr["leaves"]:
+        R = perm[lf["r0"]:lf["r0"] + lf["nr"]].tolist()
+        S = perm[lf["s0"]:lf["s0"] + lf["ns"]].tolist()
+        mine[key(R, S)] = (lf, R, S)
+    assert len(mine) == len(leaves)
+    nc = ofd.default_extra_steps(el, p)
+    for ol in leaves:
+        k = key(ol["tau"].idx.tolist(), ol["sig"].idx.tolist())
+        assert k in mine
+        lf, R, S = mine[k]
+        assert lf["kind"] == (1 if ol["kind"] == "adm" else 0)
+        if lf["kind"] == 1:
+            d = ofd.admissible_leaf(el, ol, p, nc, need_operator=False)
+            dm = dict(zip(ol["tau"].idx.tolist(), d["dm"].tolist()))
+            mb = dict(zip(ol["sig"].idx.tolist(), d["mbar"].tolist()))
+            Dm = dict(zip(ol["sig"].idx.tolist(), d["Dm"].tolist()))
+            assert [dm[e] for e in R] == lf["dm"].tolist()
+            assert [mb[e] for e in S] == lf["mbar"].tolist()
+            assert [Dm[e] for e in S] == lf["Dm"].tolist()
+    # every cluster is a contiguous range of the permutation
+    assert sorted(perm.tolist()) == list(range(xy.shape[0]))
+
+
+@pytest.mark.parametrize("geom,N,eta,leaf", [("straight", 300, 0.5, 16), ("curved", 700, 0.5, 32),
+                                             ("kinked", 400, 1.0, 8), ("curved", 4096, 0.5, 32),
+                                             ("scatter", 500, 0.25, 8)])
+def test_tree_and_art_integers_bit_exact(L, geom, N, eta, leaf):
+    if geom == "scatter":
+        rng = np.random.default_rng(2)
+        c = rng.uniform(0, 120, (N, 2))
+        a = rng.uniform(0, 2 * np.pi, N)
+        xy = np.stack([c[:, 0], c[:, 1], c[:, 0] + np.cos(a), c[:, 1] + np.sin(a)], 1)
+    else:
+        xy = {"straight": inputs.straight_fault(N), "curved": inputs.curved_fault(N, inputs.seed_for(1, 0)),
+              "kinked": inputs.kinked_fault(N)}[geom]
+    _compare_tree(xy, eta, leaf)

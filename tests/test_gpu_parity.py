@@ -1,0 +1,139 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Tolerances (relative L2 over all receivers and steps):
+* FP64 path: 1e-10 against the oracle (plain march and compressed operator alike).  The two
+  sides differ only by rounding order of O(1e5) products per output and by the two
+  independent SVDs of each block (agreeing to ~1e-14 of the block norm).
+* FP32 storage: 5e-6 (FP32 rounding 6e-8 per coefficient, summed over <= 2048 products in
+  FP32 per near-field work item, then FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import dense
+from oracle import fdph as ofd
+from oracle import kernel as kn
+from paper_1903_02118_gb300 import fdph, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-10
+TOL32 = 5e-6
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02118_gb300 import build
+    build.build()
+
+
+def _run(plan, D):
+    Dd = torch.from_numpy(np.ascontiguousarray(D)).cuda()
+    Td = torch.empty_like(Dd)
+    plan.run(D.shape[0], Dd, Td)
+    plan.synchronize()
+    return Td.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _geom(name, N):
+    return {"straight": inputs.straight_fault(N), "curved": inputs.curved_fault(N, inputs.seed_for(1, 0)),
+            "kinked": inputs.kinked_fault(N)}[name]
+
+
+@pytest.mark.parametrize("geom,N,M", [("straight", 256, 256), ("kinked", 203, 150)])
+def test_plain_st_biem_fp64(geom, N, M):
+    """Config 1 (N = 256, M = 256, CFL 1/2, Gaussian-filtered slip rate) and a ragged kinked case."""
+    _need_gpu()
+    xy = _geom(geom, N)
+    D = inputs.gaussian_filtered_history(N, M, inputs.seed_for(0, inputs.SLIP))
+    plan = fdph.Plan(xy, 0.5, M, 0.0, eta=0.0, eps_st=0.0, leaf_size=32)
+    T = _run(plan, D)
+    el = kn.element_table(xy)
+    K = kn.discrete_kernel(el, 0.5, M, 1.0, 1.0)
+    T0 = dense.march(K, D)
+    assert _rel(T, T0) < TOL64
+    st = plan.stats()
+    assert st["n_admissible"] == 0 and st["max_window"] == M
+
+
+def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6):
+    el = kn.element_table(xy)
+    p = ofd.Params(eta=0.5, leaf=leaf, eps=eps, eps_st=eps_st, M=M)
+    plan = ofd.build_plan(el, p)
+    Kc = ofd.operator_rows(el, plan, np.arange(xy.shape[0]))
+    return dense.march(Kc, D), plan
+
+
+@pytest.mark.parametrize("geom,N,leaf", [("straight", 256, 16), ("curved", 256, 16), ("kinked", 233, 13)])
+def test_fdph_fp64_equals_compressed_operator(geom, N, leaf):
+    _need_gpu()
+    M, eps = 320, 1e-5
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-6, leaf_size=leaf)
+    T = _run(plan, D)
+    st = plan.stats()
+    assert st["n_admissible"] == len(oplan["adm"]) and st["n_near"] == len(oplan["near"])
+    assert _rel(T, T0) < TOL64
+
+
+def test_fdph_fp32_storage():
+    _need_gpu()
+    N, M, eps, leaf = 256, 320, 1e-5, 16
+    xy = _geom("curved", N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, _ = _oracle_fdph(xy, M, eps, leaf, D)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-6, leaf_size=leaf, precision=fdph.FP32)
+    T = _run(plan, D)
+    assert _rel(T, T0) < TOL32
+
+
+def test_step_run_host_reset_and_state_are_consistent():
+    _need_gpu()
+    N, M = 150, 120
+    xy = _geom("curved", N)
+    D = inputs.gaussian_filtered_history(N, M, 3)
+    plan = fdph.Plan(xy, 0.5, M, 1e-4, eta=0.5, eps_st=1e-6, leaf_size=8)
+    T_run = _run(plan, D)
+    plan.reset()
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    for n in range(60):
+        plan.step(Dd[n], Td[n])
+    saved = plan.save_state()
+    for n in range(60, M):
+        plan.step(Dd[n], Td[n])
+    plan.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), T_run)            # bit for bit
+    plan.load_state(saved)
+    assert plan.current_step() == 60
+    T_host = np.stack([plan.step_host(D[n]) for n in range(60, M)])
+    assert np.array_equal(T_host, T_run[60:])
+    with pytest.raises(fdph.FdphError):
+        plan.step(Dd[0], Td[0])                                 # past M
+
+
+def test_config2_full_size_sampled_receivers():
+    """Config 2 at full size (curved N = 4096, M = 4096, eps = 1e-4, leaf 32, eta = 1/2), in the
+    launch configuration the benchmark times, against the oracle's compressed operator on sampled
+    receivers (all steps)."""
+    _need_gpu()
+    N, M, eps = 4096, 4096, 1e-4
+    xy = _geom("curved", N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-6, leaf_size=32)
+    T = _run(plan, D)
+    rows = np.array([7, 2049])
+    el = kn.element_table(xy)
+    p = ofd.Params(eta=0.5, leaf=32, eps=eps, eps_st=1e-6, M=M)
+    oplan = ofd.build_plan(el, p, receivers=rows)
+    Kc = ofd.operator_rows(el, oplan, rows)
+    T0 = dense.march_rows_fft(Kc, D)
+    assert _rel(T[:, rows], T0) < 1e-9

@@ -187,8 +187,16 @@ def main():
     ap.add_argument("--workload", default="fdph", choices=sorted(CONFIGS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--quick", action="store_true",
+                    help="plan + roll forward + warm-up + timed steps only (for profiler launch lists)")
+    ap.add_argument("--n", type=int, default=None, help="override N (profiling of smaller cases)")
+    ap.add_argument("--m", type=int, default=None, help="override M")
     args = ap.parse_args()
-    cfg = CONFIGS[args.workload]
+    cfg = dict(CONFIGS[args.workload])
+    if args.n:
+        cfg["N"] = args.n
+    if args.m:
+        cfg["M"] = args.m
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -199,7 +207,10 @@ def main():
     build.build()
     N, M = cfg["N"], cfg["M"]
     xy, D = make_workload(cfg, rank)
-    stream = torch.cuda.current_stream()
+    # the plan runs on this (non-default) torch stream so that events recorded on it bracket
+    # the library's kernels
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     prec = fdph.FP32 if args.precision == "fp32" else fdph.FP64
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
@@ -208,12 +219,26 @@ def main():
     st = plan.stats()
     Dd = torch.from_numpy(D).cuda()
     Td = torch.empty_like(Dd)
+    K, W = args.steps, args.warmup
+    if args.quick:
+        n0 = max(0, min(st["max_window"], M - W - K))
+        plan.run(n0 + W, Dd, Td)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        plan.run(K, Dd[n0 + W:], Td[n0 + W:])
+        s1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"quick": True, "ms_per_step": s0.elapsed_time(s1) / K, "steps_before_timed": n0 + W,
+                          "timed_steps": K, "n_near": st["n_near"], "N": N, "M": M}))
+        plan.close()
+        return
     # full march once (accuracy check and warm-up of everything)
     plan.run(M, Dd, Td)
     plan.synchronize()
     T_full = Td.cpu().numpy()
 
-    K, W = args.steps, args.warmup
     n0 = max(0, min(st["max_window"], M - W - K))
     if n0 + W + K > M:
         raise SystemExit("steps + warmup exceed the planned M = %d" % M)

@@ -51,7 +51,10 @@ using namespace fdph;
     } while (0)
 
 static const int kChunk = 64;      // steps of exact kernel per near-field work item
-static const int kNearThreads = 128;
+static const int kNearThreads = 256;
+static const int kStages = 4;      // shared-memory pipeline depth of the near-field kernel
+static const int kStageBytes = 12288;
+static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls before giving up
 
 // ------------------------------------------------------------------------------------------
 // device-side views
@@ -62,7 +65,7 @@ struct SbDev {
 };
 
 struct NearDev {
-    int r0, nr, s0, ns, W, pad;
+    int r0, nr, s0, ns, W, sl;
     long long tensor, stat;
 };
 
@@ -87,7 +90,13 @@ struct StepArgs {
     const int* src_order;
     const int* scat_sb;
     const int* scat_run;
+    const int* scat_l;
     int n_scat;
+    const int* e_sb;
+    const int* e_il;
+    const int* e_pos;
+    int n_ent;
+    double* fval;             // [n_ent] far-field value of each (block, receiver) entry, CSR order
     const int* fir_sb;
     const int* fir_j;
     int n_fir;
@@ -109,6 +118,7 @@ struct StepArgs {
     double* partial;          // [n_items][32]
     const int* np_ptr;
     const int* np_idx;
+    int* err;                 // device error word (1 = a bounded wait gave up)
 };
 
 __device__ __forceinline__ int pmod(long long a, int L) {
@@ -151,62 +161,161 @@ __global__ void scatter_kernel(StepArgs<T> a) {
     if (q >= a.n_scat) return;
     const SbDev sb = a.sbs[a.scat_sb[q]];
     const int run = a.scat_run[q];
+    const int l = a.scat_l[q];
     const int delay = a.run_delay[run];
     const int st = a.run_start[run];
     const int len = a.run_len[run];
     const int slot = pmod((long long)a.n + delay, sb.L);
-    const bool first = delay == sb.maxdelay;   // the newest slot starts fresh
-    for (int l = 0; l < sb.rank; ++l) {
-        double s = 0.0;
-        for (int u = 0; u < len; ++u) {
-            const int jl = a.src_order[st + u];
-            double v;
-            if (sb.kind == SB_F) v = a.dhat[sb.dhat + jl];
-            else if (sb.kind == SB_S) v = a.dt * a.C[sb.s0 + jl];
-            else v = a.Dring[(size_t)pmod(a.n, a.WD) * a.N + sb.s0 + jl];
-            s += (double)a.fac[sb.g + (long long)jl * sb.rank + l] * v;
-        }
-        double* r = a.ring + sb.ring + (long long)l * sb.L + slot;
-        *r = first ? s : *r + s;
+    const size_t dslot = (size_t)pmod(a.n, a.WD) * a.N;
+    double s = 0.0;
+    for (int u = 0; u < len; ++u) {
+        const int jl = a.src_order[st + u];
+        double v;
+        if (sb.kind == SB_F) v = a.dhat[sb.dhat + jl];
+        else if (sb.kind == SB_S) v = a.dt * a.C[sb.s0 + jl];
+        else v = a.Dring[dslot + sb.s0 + jl];
+        s += (double)a.fac[sb.g + (long long)jl * sb.rank + l] * v;
     }
+    double* r = a.ring + sb.ring + (long long)l * sb.L + slot;
+    *r = delay == sb.maxdelay ? s : *r + s;   // the newest slot starts fresh
 }
 
+// one warp per (transient block, rank index)
 template <class T>
 __global__ void trconv_kernel(StepArgs<T> a) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (q >= a.n_tr) return;
     const SbDev sb = a.sbs[a.tr_sb[q]];
     const int l = a.tr_l[q];
     const long long t0 = (long long)a.n - sb.mindm;
     const double* Y = a.ring + sb.ring + (long long)l * sb.L;
     double z = 0.0;
-    for (int m = 0; m < sb.taps; ++m) z += (double)a.fac[sb.h + m] * Y[pmod(t0 - m, sb.L)];
-    a.zring[sb.zring + (long long)l * sb.LZ + pmod(t0, sb.LZ)] = z;
+    for (int m = lane; m < sb.taps; m += 32) z += (double)a.fac[sb.h + m] * Y[pmod(t0 - m, sb.L)];
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    if (lane == 0) a.zring[sb.zring + (long long)l * sb.LZ + pmod(t0, sb.LZ)] = z;
 }
 
-// Near field: one CTA per work item (leaf, k in [k0, k1)); each warp takes every
-// (blockDim/32)-th step, lane i owns receiver i, sources are broadcast by shuffle.  Products
-// and the sum over one item are formed in the storage type T (FP64 or FP32); items are
-// combined in FP64 by the gather.
+// ---- bulk-async copy + mbarrier helpers (PTX)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
+    const unsigned a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Near field: one CTA per work item (leaf, k in [k0, k1)).  The item's coefficients are one
+// contiguous block [k][sl]; thread 0 streams it into a kStages-deep ring of shared-memory stages
+// with cp.async.bulk + mbarrier, all four warps consume: warp w takes every 4th slice of a
+// stage, lane i owns receiver i, the slip rates D_{n-k, j} are broadcast by shuffle.  Products
+// and the sum over one item are formed in the storage type T; items are combined in FP64.
 template <class T>
-__global__ void __launch_bounds__(kNearThreads) near_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
+    extern __shared__ __align__(128) unsigned char stage_mem[];
+    __shared__ __align__(8) unsigned long long bar[kStages];
     __shared__ double red[kNearThreads / 32][32];
     const int item = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 it = a.items[item];
     const NearDev L = a.near[it.x];
-    const int kend = min(it.z, a.n + 1);
+    const int k0 = it.y;
+    const int nsl = min(it.z, a.n + 1) - k0;              // slices needed at this step
+    const int per = max(1, kStageBytes / (L.sl * (int)sizeof(T)));
+    const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;  // stage loads
+    T* sd = (T*)(stage_mem + kStages * kStageBytes);      // [kChunk][32] slip rates D_{n-k, j}
     T acc = (T)0;
-    for (int k = it.y + warp; k < kend; k += kNearThreads / 32) {
-        const T dv = lane < L.ns ? (T)a.Dring[(size_t)pmod(a.n - k, a.WD) * a.N + L.s0 + lane] : (T)0;
-        const T* tile = a.tensor + L.tensor + (long long)k * L.ns * L.nr;
-        for (int j = 0; j < L.ns; ++j) {
-            const T dj = __shfl_sync(0xffffffffu, dv, j);
-            if (lane < L.nr) acc += tile[j * L.nr + lane] * dj;
+    bool failed = false;
+    if (nst > 0) {
+        const T* src = a.tensor + L.tensor + (long long)k0 * L.sl;
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+            mbar_fence_init();
+            for (int q = 0; q < min(kStages, nst); ++q) {
+                const int cnt = min(per, nsl - q * per);
+                const unsigned bytes = (unsigned)(cnt * L.sl * sizeof(T));
+                mbar_expect_tx(&bar[q], bytes);
+                bulk_g2s(stage_mem + q * kStageBytes, src + (long long)q * per * L.sl, bytes, &bar[q]);
+            }
+        }
+        // slip-rate history of the item's sources, while the first stages are in flight
+        for (int e = threadIdx.x; e < nsl * 32; e += kNearThreads) {
+            const int kk = e >> 5, j = e & 31;
+            sd[e] = j < L.ns ? (T)a.Dring[(size_t)pmod(a.n - (k0 + kk), a.WD) * a.N + L.s0 + j] : (T)0;
+        }
+        __syncthreads();
+        for (int q = 0; q < nst; ++q) {
+            const int s = q % kStages;
+            const bool ok = mbar_wait_bounded(&bar[s], (unsigned)((q / kStages) & 1));
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const T* buf = (const T*)(stage_mem + s * kStageBytes);
+            const int cnt = min(per, nsl - q * per);
+            if (lane < L.nr) {
+                for (int kk = warp; kk < cnt; kk += kNearThreads / 32) {
+                    const T* tile = buf + kk * L.sl + lane;
+                    const T* d = sd + (q * per + kk) * 32;
+                    T s0 = (T)0, s1 = (T)0;
+                    int j = 0;
+                    for (; j + 1 < L.ns; j += 2) {
+                        s0 += tile[j * L.nr] * d[j];
+                        s1 += tile[(j + 1) * L.nr] * d[j + 1];
+                    }
+                    if (j < L.ns) s0 += tile[j * L.nr] * d[j];
+                    acc += s0 + s1;
+                }
+            }
+            __syncthreads();
+            const int nq = q + kStages;
+            if (threadIdx.x == 0 && nq < nst) {
+                fence_proxy_async();
+                const int c2 = min(per, nsl - nq * per);
+                const unsigned bytes = (unsigned)(c2 * L.sl * sizeof(T));
+                mbar_expect_tx(&bar[s], bytes);
+                bulk_g2s(stage_mem + s * kStageBytes, src + (long long)nq * per * L.sl, bytes, &bar[s]);
+            }
         }
     }
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(a.err, 1);
+        // give the copies still in flight a bounded chance to land before the CTA exits
+        for (int s = 0; s < kStages; ++s) (void)mbar_wait_bounded(&bar[s], 0u);
+        return;
+    }
     double accd = (double)acc;
-    if (it.y == 0 && warp == 0 && a.n - L.W >= 0) {
+    if (k0 == 0 && warp == 0 && a.n - L.W >= 0) {
         const long long t = (long long)a.n - L.W;
         const double cv = lane < L.ns ? a.Cring[(size_t)pmod(t, a.WC) * a.N + L.s0 + lane] : 0.0;
         for (int j = 0; j < L.ns; ++j) {
@@ -223,26 +332,37 @@ __global__ void __launch_bounds__(kNearThreads) near_kernel(StepArgs<T> a) {
     }
 }
 
+// Eq. 39, one thread per (block, receiver) entry, blocks in order: f_{l,i} Tbar'_l[n - dm_i]
+template <class T>
+__global__ void far_eval_kernel(StepArgs<T> a) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.n_ent) return;
+    const SbDev sb = a.sbs[a.e_sb[e]];
+    const int il = a.e_il[e];
+    const long long t = (long long)a.n - a.ints[sb.dm + il];
+    const T* f = a.fac + sb.f + (long long)il * sb.rank;
+    double s = 0.0;
+    if (sb.kind == SB_TR) {
+        const double* z = a.zring + sb.zring + pmod(t, sb.LZ);
+        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * z[(long long)l * sb.LZ];
+    } else {
+        const double* r = a.ring + sb.ring + pmod(t, sb.L);
+        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[(long long)l * sb.L];
+    }
+    a.fval[a.e_pos[e]] = s;
+}
+
+// one warp per receiver: sum of its far entries and near-field partials, fixed order
 template <class T>
 __global__ void gather_kernel(StepArgs<T> a) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= a.N) return;
     double s = 0.0;
-    for (int e = a.g_ptr[p]; e < a.g_ptr[p + 1]; ++e) {
-        const SbDev sb = a.sbs[a.g_sb[e]];
-        const int il = a.g_il[e];
-        const long long t = (long long)a.n - a.ints[sb.dm + il];
-        const T* f = a.fac + sb.f + (long long)il * sb.rank;
-        if (sb.kind == SB_TR) {
-            const double* z = a.zring + sb.zring + pmod(t, sb.LZ);
-            for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * z[(long long)l * sb.LZ];
-        } else {
-            const double* r = a.ring + sb.ring + pmod(t, sb.L);
-            for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[(long long)l * sb.L];
-        }
-    }
-    for (int e = a.np_ptr[p]; e < a.np_ptr[p + 1]; ++e) s += a.partial[a.np_idx[e]];
-    a.T_out[a.perm[p]] = s;
+    for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
+    for (int e = a.np_ptr[p] + lane; e < a.np_ptr[p + 1]; e += 32) s += a.partial[a.np_idx[e]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) a.T_out[a.perm[p]] = s;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -315,7 +435,7 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
             v = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
         }
-        tensor[L.tensor + q] = (T)v;
+        tensor[L.tensor + (long long)k * L.sl + (q % ((long long)L.ns * L.nr))] = (T)v;
         if (k == 0) {
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
             stat[L.stat + (long long)jl * L.nr + il] = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
@@ -346,6 +466,8 @@ struct fdph_plan_s {
     SbDev* sbs = nullptr;
     void* fac = nullptr;
     int *ints = nullptr, *run_delay = nullptr, *run_start = nullptr, *run_len = nullptr, *src_order = nullptr;
+    int *scat_l = nullptr, *e_sb = nullptr, *e_il = nullptr, *e_pos = nullptr;
+    double* fval = nullptr;
     int *scat_sb = nullptr, *scat_run = nullptr, *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
         *tr_l = nullptr, *g_ptr = nullptr, *g_sb = nullptr, *g_il = nullptr;
     NearDev* near = nullptr;
@@ -353,6 +475,7 @@ struct fdph_plan_s {
     void* tensor = nullptr;
     double* stat = nullptr;
     int *np_ptr = nullptr, *np_idx = nullptr;
+    int* err = nullptr;
     // state
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
@@ -417,6 +540,12 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.src_order = P->src_order;
     a.scat_sb = P->scat_sb;
     a.scat_run = P->scat_run;
+    a.scat_l = P->scat_l;
+    a.e_sb = P->e_sb;
+    a.e_il = P->e_il;
+    a.e_pos = P->e_pos;
+    a.n_ent = (int)P->hp.e_sb.size();
+    a.fval = P->fval;
     a.n_scat = (int)P->hp.scat_sb.size();
     a.fir_sb = P->fir_sb;
     a.fir_j = P->fir_j;
@@ -438,6 +567,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.partial = P->partial;
     a.np_ptr = P->np_ptr;
     a.np_idx = P->np_idx;
+    a.err = P->err;
     return a;
 }
 
@@ -458,9 +588,16 @@ static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
     if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
-    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks(a.n_tr, 128), 128, 0, s>>>(a); }
-    if (a.n_items) { ProfScope ps(P, 4); near_kernel<T><<<a.n_items, kNearThreads, 0, s>>>(a); }
-    { ProfScope ps(P, 5); gather_kernel<T><<<blocks(a.N, 128), 128, 0, s>>>(a); }
+    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
+    if (a.n_items) {
+        ProfScope ps(P, 4);
+        near_kernel<T><<<a.n_items, kNearThreads, kStages * kStageBytes + kChunk * 32 * sizeof(T), s>>>(a);
+    }
+    {
+        ProfScope ps(P, 5);
+        if (a.n_ent) far_eval_kernel<T><<<blocks(a.n_ent, 128), 128, 0, s>>>(a);
+        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+    }
     FDPH_CUDA(cudaGetLastError());
     return FDPH_OK;
 }
@@ -489,6 +626,19 @@ static void prof_drain(fdph_plan_t P) {
         cudaEventDestroy(q.second.second);
     }
     P->prof_ev.clear();
+}
+
+// after a stream synchronisation: report a bounded device wait that gave up
+static int check_device_error(fdph_plan_t P) {
+    int e = 0;
+    if (!P->err) return FDPH_OK;
+    FDPH_CUDA(cudaMemcpy(&e, P->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        set_error("a bounded mbarrier wait in the near-field kernel gave up; results of the step are invalid");
+        cudaMemset(P->err, 0, sizeof(int));
+        return FDPH_E_TIMEOUT;
+    }
+    return FDPH_OK;
 }
 
 static int step_impl(fdph_plan_t P, const double* D, double* T_) {
@@ -536,12 +686,13 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
-        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, 0, (long long)L.tensor, (long long)L.stat};
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
     T* tens = nullptr;
     if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &P->stat, hp.near_stat_len))) return rc;
     P->tensor = tens;
+    if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(T)));  // slice padding
     for (int l = 0; l < nl; ++l) {
         const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
         if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
@@ -554,6 +705,7 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             NearDev L1 = L;
             L1.W = 1;
             L1.tensor = 0;
+            L1.sl = L.ns * L.nr;
             near_fill_kernel<T><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
                                                                             in.mu, in.cs, tmp, P->stat);
         } else {
@@ -795,6 +947,8 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = upload(P, &P->run_delay, hp.run_delay)) || (rc = upload(P, &P->run_start, hp.run_start)) ||
         (rc = upload(P, &P->run_len, hp.run_len)) || (rc = upload(P, &P->src_order, hp.src_order)) ||
         (rc = upload(P, &P->scat_sb, hp.scat_sb)) || (rc = upload(P, &P->scat_run, hp.scat_run)) ||
+        (rc = upload(P, &P->scat_l, hp.scat_l)) || (rc = upload(P, &P->e_sb, hp.e_sb)) ||
+        (rc = upload(P, &P->e_il, hp.e_il)) || (rc = upload(P, &P->e_pos, hp.e_pos)) ||
         (rc = upload(P, &P->fir_sb, hp.fir_sb)) || (rc = upload(P, &P->fir_j, hp.fir_j)) ||
         (rc = upload(P, &P->tr_sb, hp.tr_sb)) || (rc = upload(P, &P->tr_l, hp.tr_l)) ||
         (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
@@ -813,6 +967,12 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     // ---- near field (device-evaluated kernel windows)
     rc = P->precision == FDPH_FP32 ? build_near<float>(P, in) : build_near<double>(P, in);
     if (rc) return fail(rc);
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kStages * kStageBytes + kChunk * 32 * (int)sizeof(double)));
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kStages * kStageBytes + kChunk * 32 * (int)sizeof(float)));
+    if ((rc = dalloc(P, &P->err, 1))) return fail(rc);
+    FDPH_CUDA(cudaMemset(P->err, 0, sizeof(int)));
     // ---- state
     P->WD = std::max(std::max(hp.max_W, hp.max_taps), 1);
     P->WC = hp.max_W + 1;
@@ -824,7 +984,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if ((rc = st(&P->Dring, (size_t)P->WD * P->N)) || (rc = st(&P->Cring, (size_t)P->WC * P->N)) ||
         (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
         (rc = st(&P->zring, hp.zring_len)) || (rc = st(&P->dhat, hp.dhat_len)) ||
-        (rc = st(&P->partial, hp.items.size() * 32)))
+        (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_sb.size())))
         return fail(rc);
     P->state_bytes = sb;
     if ((rc = fdph_reset(P))) return fail(rc);
@@ -881,7 +1041,7 @@ int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
     if (rc) return rc;
     FDPH_CUDA(cudaMemcpyAsync(T_n_host, P->dT, P->N * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
-    return FDPH_OK;
+    return check_device_error(P);
 }
 
 int fdph_current_step(fdph_plan_t P, int32_t* n) {
@@ -893,7 +1053,7 @@ int fdph_current_step(fdph_plan_t P, int32_t* n) {
 int fdph_synchronize(fdph_plan_t P) {
     if (!P) return FDPH_E_ARG;
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
-    return FDPH_OK;
+    return check_device_error(P);
 }
 
 int fdph_get_stats(fdph_plan_t P, fdph_stats* s) {

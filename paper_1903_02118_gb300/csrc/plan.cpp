@@ -270,10 +270,12 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.nruns = (int32_t)hp.run_delay.size() - sb.run0;
             const int id = (int)hp.sbs.size();
             hp.sbs.push_back(sb);
-            for (int r = 0; r < sb.nruns; ++r) {
-                hp.scat_sb.push_back(id);
-                hp.scat_run.push_back(sb.run0 + r);
-            }
+            for (int r = 0; r < sb.nruns; ++r)
+                for (int l = 0; l < sb.rank; ++l) {
+                    hp.scat_sb.push_back(id);
+                    hp.scat_run.push_back(sb.run0 + r);
+                    hp.scat_l.push_back(l);
+                }
             if (kind == SB_F)
                 for (int j = 0; j < o.ns; ++j) {
                     hp.fir_sb.push_back(id);
@@ -306,6 +308,18 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             hp.g_il.push_back(e.second);
         }
     }
+    // block-major list of the same entries; recv[p] was filled in increasing block order, so the
+    // k-th visit of receiver p is its k-th CSR slot
+    std::vector<int32_t> cnt(n, 0);
+    for (int id = 0; id < (int)hp.sbs.size(); ++id) {
+        const SubBlock& sb = hp.sbs[id];
+        for (int il = 0; il < sb.nr; ++il) {
+            const int p = sb.r0 + il;
+            hp.e_sb.push_back(id);
+            hp.e_il.push_back(il);
+            hp.e_pos.push_back(hp.g_ptr[p] + cnt[p]++);
+        }
+    }
     return 0;
 }
 
@@ -324,8 +338,9 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk) 
         L.s0 = hp.near_s0[l];
         L.ns = hp.near_ns[l];
         L.W = W[l];
-        L.tensor = hp.near_tensor_len;
-        hp.near_tensor_len += (int64_t)L.W * L.ns * L.nr;
+        L.sl = (L.ns * L.nr + 3) / 4 * 4;
+        L.tensor = hp.near_tensor_len;                     // stays a multiple of 4 elements
+        hp.near_tensor_len += (int64_t)L.W * L.sl;
         L.stat = hp.near_stat_len;
         hp.near_stat_len += (int64_t)L.ns * L.nr;
         hp.max_W = std::max(hp.max_W, L.W);

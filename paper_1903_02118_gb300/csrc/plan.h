@@ -26,7 +26,8 @@ struct SubBlock {
 
 struct NearLeaf {
     int32_t r0, nr, s0, ns, W;   // W = window of exact kernel steps stored
-    int64_t tensor;              // offset of [W][ns][nr] coefficients
+    int32_t sl;                  // slice stride: ns * nr rounded up to a multiple of 4 (16-byte rows)
+    int64_t tensor;              // offset of [W][sl] coefficients (slice k: [ns][nr]), 4-aligned
     int64_t stat;                // offset of the [ns][nr] static tile (x dt), FP64
 };
 
@@ -46,10 +47,11 @@ struct HostPlan {
     std::vector<double> fac;                         // f, g, h, htr (FP64 master copy)
     std::vector<int32_t> ints;                       // delays, dm
     std::vector<int32_t> run_delay, run_start, run_len, src_order;
-    std::vector<int32_t> scat_sb, scat_run;          // scatter tasks
+    std::vector<int32_t> scat_sb, scat_run, scat_l;  // scatter tasks (block, run, rank index)
     std::vector<int32_t> fir_sb, fir_j;              // FIR tasks
     std::vector<int32_t> tr_sb, tr_l;                // transient convolution tasks
     std::vector<int32_t> g_ptr, g_sb, g_il;          // gather CSR (receiver-major)
+    std::vector<int32_t> e_sb, e_il, e_pos;          // the same entries block-major, with their CSR slot
     int64_t ring_len = 0, zring_len = 0, dhat_len = 0;
     int32_t max_taps = 0;
     // near field

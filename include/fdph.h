@@ -177,6 +177,29 @@ int fdph_kernel_times(fdph_plan_t plan, double* ms, int64_t* launches);
 int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* material, double dt,
                      const fdph_params* params, int32_t* buf, int64_t cap, int64_t* len);
 
+/* Allocation-free plain step.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (code running inside another runtime's memory pool or
+ * allocator budget, or where a cudaMalloc would synchronise the device at a bad moment).
+ *
+ * Computes one step of Eq. 4 from buffers the caller owns:
+ *     T[i] = sum_{k=0}^{min(step, W-1)} sum_j K[(k * n + j) * n + i] * D_hist[((step - k) mod hist_len) * n + j]
+ * K: device, W * n * n doubles (kernel step k, source j, receiver i); D_hist: device ring of
+ * hist_len >= min(step + 1, W) slip-rate rows of n doubles, row s mod hist_len holding step s;
+ * T: device, n doubles (written); stream: cudaStream_t or NULL.  Asynchronous on the stream.
+ *
+ * Its split-k partial sums live in one file-scope device array of FDPH_NOALLOC_MAX_PARTIALS
+ * doubles (512 KiB), held by every GPU that loads the library until the process exits; the
+ * call allocates nothing.  Sizes with ceil(n / 32) * ceil(min(step + 1, W) / 64) * 32 above
+ * that maximum are rejected with FDPH_E_ARG (message in fdph_last_error).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the array, which
+ * keeps the last call's contents (each call overwrites every slot it reads): calls that overlap
+ * on the GPU race and must be ordered by the caller (one stream, or events).
+ * Errors: FDPH_E_ARG, FDPH_E_CUDA. */
+#define FDPH_NOALLOC_MAX_PARTIALS 65536
+int fdph_plain_step_noalloc(const double* K, int32_t n, int32_t W, const double* D_hist, int32_t hist_len,
+                            int32_t step, double* T, void* stream);
+
 /* Message for a status code (static string). */
 const char* fdph_strerror(int status);
 

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdph.so")
-SOURCES = ["fdph.cu", "tree.cpp", "lra.cpp", "plan.cpp"]
+SOURCES = ["fdph.cu", "noalloc.cu", "tree.cpp", "lra.cpp", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

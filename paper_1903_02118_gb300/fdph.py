@@ -58,7 +58,7 @@ _lib = None
 EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset",
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
-           "fdph_kernel_times"]
+           "fdph_kernel_times", "fdph_plain_step_noalloc"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -91,13 +91,15 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int64)]
         L.fdph_set_profiling.argtypes = [c_p, ctypes.c_int]
         L.fdph_kernel_times.argtypes = [c_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.fdph_plain_step_noalloc.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, c_p, ctypes.c_int32,
+                                              ctypes.c_int32, c_p, c_p]
         L.fdph_strerror.argtypes = [ctypes.c_int]
         L.fdph_strerror.restype = ctypes.c_char_p
         L.fdph_last_error.argtypes = []
         L.fdph_last_error.restype = ctypes.c_char_p
         for name in ("fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset", "fdph_current_step",
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
-                     "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times"):
+                     "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -213,6 +215,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def plain_step_noalloc(K, n, W, D_hist, hist_len, step, T, stream=None):
+    """fdph_plain_step_noalloc: one plain step from caller-held device buffers, no allocation."""
+    s = ctypes.c_void_p(stream) if stream else None
+    _check(lib().fdph_plain_step_noalloc(_ptr(K), int(n), int(W), _ptr(D_hist), int(hist_len), int(step), _ptr(T), s))
 
 
 def tree_export(xy, dt, mu=1.0, cs=1.0, **params):

@@ -85,6 +85,17 @@ typedef struct fdph_params {
                              ceil(10 * max element length / (cs dt)) */
     int32_t precision;    /* fdph_precision, default FDPH_FP64 */
     int32_t device;       /* CUDA device ordinal, default 0 */
+    int32_t soe_terms;    /* 0 (default): the paper's Domain-S cut -- beyond eps_st the kernel is
+                             the static kernel alone.  Q in [4, 16]: extension of this library --
+                             beyond the exact window, the remainder K - Kstat dt of each
+                             inadmissible pair and of each transient fibre is kept as its
+                             least-squares fit on Q decaying exponentials, evaluated by Q
+                             recursive filter states per source; inadmissible windows then also
+                             cover each pair's wave passage (+ extra_steps) */
+    int32_t art_interp;   /* 0 (default): receiver delays rounded down to whole steps (Eq. 30).
+                             1: extension -- the representative stress is read at the exact
+                             delay dm_i + phi_i by linear interpolation between steps n - dm_i and
+                             n - dm_i - 1 (the higher-order interpolation Sec. 4.3.1 mentions) */
     void* cuda_stream;    /* cudaStream_t the plan runs on; NULL => a stream the plan creates */
 } fdph_params;
 
@@ -128,9 +139,40 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
 int fdph_step(fdph_plan_t plan, const double* D_n, double* T_n);
 
 /* `steps` consecutive steps: D (device, steps * n doubles, step-major) -> T (device, same shape).
- * Equivalent to `steps` calls of fdph_step.
+ * Equivalent to `steps` calls of fdph_step; from 8 steps on (and with profiling off) the call
+ * captures one step as a CUDA graph and replays it, which removes the per-kernel launch cost.
  * Errors as fdph_step; FDPH_E_STATE if the plan would pass step M. */
 int fdph_run(fdph_plan_t plan, int32_t steps, const double* D, double* T);
+
+/* Dynamic rupture (Sec. 6.2): the slip rate is not prescribed but follows from a friction law
+ * at every element.  The unruptured element keeps zero slip rate; it ruptures when the shear
+ * traction reaches its strength, then the traction equals the strength, with linear slip
+ * weakening (the paper uses exponential weakening; linear is the reading of the configs):
+ *     strength(u) = sigma_n * (mu_s - (mu_s - mu_d) * min(u / Dc, 1)),  u = accumulated slip.
+ * The instantaneous term of Eq. 4 is local (K_{ij,0} = 0 for j != i when cs dt <= dx/2,
+ * K_{ii,0} = -mu/(2 cs) the radiation damping), so each step is: predict the traction with
+ * D_n = 0, solve D_n >= 0 element by element (explicit strength at the slip of the previous
+ * step), then commit D_n to the history. */
+typedef struct fdph_friction {
+    const double* tau0;   /* device, n doubles (geometry order): background shear traction */
+    double sigma_n;       /* normal stress (compression positive) */
+    double mu_s, mu_d;    /* static and dynamic friction coefficients */
+    double Dc;            /* slip-weakening distance */
+} fdph_friction;
+
+/* Attach a friction law to a plan (copies tau0; zero slip).  Errors: FDPH_E_ARG, FDPH_E_OOM,
+ * FDPH_E_CUDA, FDPH_E_STATE (instantaneous term not local: cs dt > min element length / 2). */
+int fdph_rupture_init(fdph_plan_t plan, const fdph_friction* friction);
+
+/* One rupture step: writes the solved slip rate D_n and the total shear traction
+ * tau0 + T_n (both device, n doubles, geometry order) and advances to n + 1. */
+int fdph_rupture_step(fdph_plan_t plan, double* D_n, double* T_n);
+
+/* `steps` rupture steps into D, T (device, steps * n doubles). */
+int fdph_rupture_run(fdph_plan_t plan, int32_t steps, double* D, double* T);
+
+/* Copy the accumulated slip (device, n doubles, geometry order). */
+int fdph_rupture_slip(fdph_plan_t plan, double* slip);
 
 /* Like fdph_step but D_n and T_n are HOST buffers; the call copies D_n in, steps, copies T_n
  * out and returns when T_n is ready (synchronous). */

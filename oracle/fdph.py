@@ -73,9 +73,23 @@ NODAL_TAU = 0.2   # nodal-direction threshold of the waveform choice (reading, s
 
 class Params:
     def __init__(self, eta=0.5, leaf=32, eps=1e-4, eps_st=1e-6, extra_steps=-1, lmin=0.0,
-                 mu=1.0, cs=1.0, dt=0.5, M=256):
+                 mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False):
         self.eta, self.leaf, self.eps, self.eps_st = eta, leaf, eps, eps_st
         self.extra_steps, self.lmin, self.mu, self.cs, self.dt, self.M = extra_steps, lmin, mu, cs, dt, M
+        self.soe_terms = soe_terms
+        self.eps_tr = eps_st if eps_tr is None else eps_tr
+        self.art_interp = art_interp
+
+
+def soe_min_len(W):
+    """The exponential tail is fitted only over at least max(512, 2 W) steps: shorter ranges
+    make the basis nearly singular, and there the exact kernel is cheap to keep anyway."""
+    return max(512, 2 * W)
+
+
+def soe_rates(M, Q):
+    """Decay rates of the exponential tail basis: Q rates spaced geometrically in [0.5/M, 1]."""
+    return np.exp(np.log(0.5 / M) + np.arange(Q) / (Q - 1.0) * (np.log(1.0) - np.log(0.5 / M)))
 
 
 def default_extra_steps(el, p):
@@ -192,9 +206,10 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
     r_isj = _dist(istar[0], istar[1], el["mx"][J], el["my"][J])
     half = 0.5 * el["len"][J]
     dm = np.floor((r_ijs - rbar) / cdt).astype(np.int64)
+    phi = (r_ijs - rbar) / cdt - dm          # sub-step part of the receiver delay, in [0, 1)
     mbar = np.floor((r_isj - half) / cdt).astype(np.int64)
     Dm = (np.ceil((r_isj + half) / cdt).astype(np.int64) - mbar + nc)
-    out = dict(I=I, J=J, dm=dm, mbar=mbar, Dm=Dm, causal=int((dm[:, None] + mbar[None, :]).min()))
+    out = dict(I=I, J=J, dm=dm, mbar=mbar, Dm=Dm, phi=phi, causal=int((dm[:, None] + mbar[None, :]).min()))
     if not need_operator:
         return out
     mu, cs, dt = p.mu, p.cs, p.dt
@@ -234,7 +249,7 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
     Ks = kn.static_kernel(el, mu, I, J)
     Sr, rS, exS = lra(Ks, p.eps)
     # --- Domain S transient (per stress component)
-    thr = p.eps_st * mu / (2.0 * cs)
+    thr = p.eps_tr * mu / (2.0 * cs)
     txz, tyz = kn.stress_tail(PX, PY, srcJ, kS * dt, (kS + 1) * dt, mu, cs)
     TR = {}
     for c, tc, Nc in (("x", txz, NX), ("y", tyz, NY)):
@@ -251,16 +266,35 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
         big = np.nonzero(np.abs(fib) >= thr)[0]
         Dtr = 0 if big.size == 0 else int(big.max()) + 1
         Br, rT, exT = lra(Nc * tc, p.eps)
-        TR[c] = dict(op=Br, rank=rT, exact=exT, h=fib[:Dtr] / fib[0], Dm=Dtr, pivot=(pi, pj))
+        h = fib[:Dtr] / fib[0]
+        tail_fit = np.zeros(0)
+        if p.soe_terms > 0:
+            # extension (not the paper's): beyond the Dm_tr exact taps the normalised fibre is
+            # carried by its least-squares fit on the exponential basis instead of being dropped
+            Dtr = max(Dtr, 1)
+            h = fib[:Dtr] / fib[0]
+            if p.M - Dtr >= soe_min_len(Dtr):
+                lam = soe_rates(p.M, p.soe_terms)
+                B = np.exp(-lam[None, :] * np.arange(p.M - Dtr, dtype=np.float64)[:, None])
+                coef, *_ = np.linalg.lstsq(B, fib[Dtr:] / fib[0], rcond=None)
+                tail_fit = B @ coef
+        TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit)
     out.update(a=a, kS=kS, F=F, S=dict(op=Sr, rank=rS, exact=exS), TR=TR)
     return out
 
 
 def near_leaf(el, lf, p):
-    """Exact kernel up to m_S(i, j), then the static kernel (App. E, App. H)."""
+    """Exact kernel up to m_S(i, j), then the static kernel (App. E, App. H).
+
+    With p.soe_terms = Q > 0 (an extension of this implementation, not the paper's): the exact
+    kernel is kept for every pair of the leaf up to W = max m_S, and beyond W the difference
+    K - K_stat dt is represented by its least-squares fit on the exponentials
+    exp(-lambda_q (k - W)), q < Q (soe_rates), instead of being dropped.
+    """
     I, J = lf["tau"].idx, lf["sig"].idx
     K = kn.discrete_kernel(el, p.dt, p.M, p.mu, p.cs, I, J)          # [M, nr, ns]
     Ks = kn.static_kernel(el, p.mu, I, J)
+    tail = None
     if p.eps_st > 0.0:
         thr = p.eps_st * p.mu / (2.0 * p.cs)
         tail = kn.tail_kernel(el, p.dt, p.M, p.mu, p.cs, I, J)
@@ -270,7 +304,28 @@ def near_leaf(el, lf, p):
         mS = np.where(any_big, last + 1, 0)
     else:
         mS = np.full((I.size, J.size), p.M, dtype=np.int64)
-    return dict(I=I, J=J, K=K, Ks=Ks, mS=mS)
+    out = dict(I=I, J=J, K=K, Ks=Ks, mS=mS)
+    if p.soe_terms > 0:
+        Q = p.soe_terms
+        # the window must also outlast the wave passage of every pair (both end points' fronts
+        # plus the n_c extra steps of Domain F), since a fit on smooth exponentials cannot
+        # represent a wavefront
+        nc = default_extra_steps(el, p) if p.extra_steps < 0 else p.extra_steps
+        far_end = np.maximum(_dist(el["mx"][I][:, None], el["my"][I][:, None], el["ax"][J][None, :], el["ay"][J][None, :]),
+                             _dist(el["mx"][I][:, None], el["my"][I][:, None], el["bx"][J][None, :], el["by"][J][None, :]))
+        passage = np.ceil(far_end / (p.cs * p.dt)).astype(np.int64) + nc
+        W = int(max(mS.max(), passage.max()))
+        if p.M - W < soe_min_len(W):     # too short a tail to fit well: keep the kernel exact
+            W = p.M
+        fit = np.zeros((p.M - W, I.size, J.size))
+        if W < p.M:
+            lam = soe_rates(p.M, Q)
+            B = np.exp(-lam[None, :] * np.arange(p.M - W, dtype=np.float64)[:, None])   # [M-W, Q]
+            Y = tail[W:].reshape(p.M - W, -1)
+            coef, *_ = np.linalg.lstsq(B, Y, rcond=None)
+            fit = (B @ coef).reshape(p.M - W, I.size, J.size)
+        out.update(W=W, fit=fit)
+    return out
 
 
 def build_plan(el, p, receivers=None):
@@ -321,6 +376,17 @@ def operator_rows(el, plan, receivers):
                     if T["rank"] > 0 and T["Dm"] > 0:
                         L = min(T["Dm"], max(M - kS, 0))
                         col[kS:kS + L] += T["op"][il, jl] * T["h"][:L]
+                        nt = T["tail"].size
+                        if nt:
+                            k1 = kS + T["Dm"]
+                            L2 = min(nt, max(M - k1, 0))
+                            col[k1:k1 + L2] += T["op"][il, jl] * T["tail"][:L2]
+                if p.art_interp:
+                    # extension (Sec. 4.3.1 suggests higher-order interpolation of the receiver
+                    # delay): read the representative stress at the exact delay dm_i + phi_i by
+                    # linear interpolation between the two neighbouring steps
+                    ph = d["phi"][il]
+                    col = (1.0 - ph) * col + ph * np.concatenate([[0.0], col[:-1]])
                 Kc[:, r, j] += col
     for d in plan["near"]:
         for il, i in enumerate(d["I"]):
@@ -328,6 +394,11 @@ def operator_rows(el, plan, receivers):
                 continue
             r = pos[int(i)]
             for jl, j in enumerate(d["J"]):
+                if "W" in d:     # exact window, then static + fitted exponential tail
+                    W = d["W"]
+                    Kc[:W, r, j] += d["K"][:W, il, jl]
+                    Kc[W:, r, j] += d["Ks"][il, jl] * dt + d["fit"][:, il, jl]
+                    continue
                 mS = int(d["mS"][il, jl])
                 Kc[:mS, r, j] += d["K"][:mS, il, jl]
                 Kc[mS:, r, j] += d["Ks"][il, jl] * dt

@@ -6,6 +6,7 @@
 //            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring
 //   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}
 //   scatter  formula 2 (Eq. 42): Tbar'_l[n + delay_j] += g_{l,j} u_j for every run of sources
+//            (rings are stored [slot][rank] so that one receiver's ranks share a sector)
 //            with equal delay (no atomics: one writer per ring slot); u = Dhat (Domain F),
 //            dt * C (Domain S, App. B.1 written on the cumulative slip), D (transient);
 //            the ring is the shift operator M of Eq. 40 as a base-pointer increment
@@ -20,6 +21,8 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <stdlib.h>
 
 #include <algorithm>
 #include <chrono>
@@ -60,18 +63,25 @@ static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls befor
 // device-side views
 
 struct SbDev {
-    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0;
-    long long f, g, h, ring, zring, dhat, delay, dm;
+    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, pad;
+    long long f, g, h, ring, zring, dhat, delay, dm, ustate, trc, phi;
 };
 
 struct NearDev {
     int r0, nr, s0, ns, W, sl;
-    long long tensor, stat;
+    long long tensor, stat, tail, vstate;
 };
+
+static const int kMaxSoe = 16;
 
 template <class T>
 struct StepArgs {
     int n, N, WD, WC;
+    // graph replay: the step index is read from n_dev, and D_in / T_out advance by io_stride
+    // elements per step past n_base (both unused when n_dev is null)
+    const int* n_dev;
+    int n_base;
+    long long io_stride;
     double dt;
     const double* D_in;       // caller's D_n (geometry order)
     double* T_out;            // caller's T_n (geometry order)
@@ -119,6 +129,15 @@ struct StepArgs {
     const int* np_ptr;
     const int* np_idx;
     int* err;                 // device error word (1 = a bounded wait gave up)
+    // exponential tails (extension; soe == 0: the paper's static cut)
+    int soe;
+    const double* rho;        // [soe] decay factors
+    double* ustate;           // transient blocks: [rank][soe] per block
+    const double* trcoef;     // transient blocks: [soe] tail coefficients per block (FP64)
+    const double* phi;        // sub-step receiver delays (interpolated reading; null: rounded)
+    double* vstate;           // inadmissible leaves: [soe][ns] per leaf
+    const double* tail;       // inadmissible leaves: [soe][ns][nr] coefficients per leaf (FP64: the
+                              // fitted coefficients partly cancel, so they are not rounded to FP32)
 };
 
 __device__ __forceinline__ int pmod(long long a, int L) {
@@ -127,36 +146,52 @@ __device__ __forceinline__ int pmod(long long a, int L) {
 }
 
 template <class T>
+__device__ __forceinline__ int step_index(const StepArgs<T>& a) {
+    return a.n_dev ? *a.n_dev : a.n;
+}
+
+__global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
+
+__global__ void set_step_kernel(int* n_dev, int v) { *n_dev = v; }
+
+template <class T>
 __global__ void push_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.N) return;
-    const double d = a.D_in[a.perm[p]];
-    a.Dring[(size_t)pmod(a.n, a.WD) * a.N + p] = d;
+    if (!a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
+        a.Dring[(size_t)pmod(n, a.WD) * a.N + p] = 0.0;
+        return;
+    }
+    const double d = a.D_in[(a.n_dev ? (long long)(n - a.n_base) * a.io_stride : 0) + a.perm[p]];
+    a.Dring[(size_t)pmod(n, a.WD) * a.N + p] = d;
     // compensated running sum of the slip (units of dt)
     const double y = d - a.Ccomp[p];
     const double c0 = a.C[p];
     const double t = c0 + y;
     a.Ccomp[p] = (t - c0) - y;
     a.C[p] = t;
-    a.Cring[(size_t)pmod(a.n, a.WC) * a.N + p] = t;
+    a.Cring[(size_t)pmod(n, a.WC) * a.N + p] = t;
 }
 
 template <class T>
 __global__ void fir_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.n_fir) return;
     const SbDev sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
     const int col = sb.s0 + jl;
     double s = 0.0;
-    const int taps = min(sb.taps, a.n + 1);
+    const int taps = min(sb.taps, n + 1);
     for (int m = 0; m < taps; ++m)
-        s += (double)a.fac[sb.h + (long long)m * sb.ns + jl] * a.Dring[(size_t)pmod(a.n - m, a.WD) * a.N + col];
+        s += (double)a.fac[sb.h + (long long)m * sb.ns + jl] * a.Dring[(size_t)pmod(n - m, a.WD) * a.N + col];
     a.dhat[sb.dhat + jl] = s;
 }
 
 template <class T>
 __global__ void scatter_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.n_scat) return;
     const SbDev sb = a.sbs[a.scat_sb[q]];
@@ -165,8 +200,8 @@ __global__ void scatter_kernel(StepArgs<T> a) {
     const int delay = a.run_delay[run];
     const int st = a.run_start[run];
     const int len = a.run_len[run];
-    const int slot = pmod((long long)a.n + delay, sb.L);
-    const size_t dslot = (size_t)pmod(a.n, a.WD) * a.N;
+    const int slot = pmod((long long)n + delay, sb.L);
+    const size_t dslot = (size_t)pmod(n, a.WD) * a.N;
     double s = 0.0;
     for (int u = 0; u < len; ++u) {
         const int jl = a.src_order[st + u];
@@ -176,24 +211,33 @@ __global__ void scatter_kernel(StepArgs<T> a) {
         else v = a.Dring[dslot + sb.s0 + jl];
         s += (double)a.fac[sb.g + (long long)jl * sb.rank + l] * v;
     }
-    double* r = a.ring + sb.ring + (long long)l * sb.L + slot;
+    double* r = a.ring + sb.ring + (long long)slot * sb.rank + l;   // ring layout [slot][rank]
     *r = delay == sb.maxdelay ? s : *r + s;   // the newest slot starts fresh
 }
 
 // one warp per (transient block, rank index)
 template <class T>
 __global__ void trconv_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (q >= a.n_tr) return;
     const SbDev sb = a.sbs[a.tr_sb[q]];
     const int l = a.tr_l[q];
-    const long long t0 = (long long)a.n - sb.mindm;
-    const double* Y = a.ring + sb.ring + (long long)l * sb.L;
+    const long long t0 = (long long)n - sb.mindm;
+    const double* Y = a.ring + sb.ring + l;
     double z = 0.0;
-    for (int m = lane; m < sb.taps; m += 32) z += (double)a.fac[sb.h + m] * Y[pmod(t0 - m, sb.L)];
+    for (int m = lane; m < sb.taps; m += 32)
+        z += (double)a.fac[sb.h + m] * Y[(long long)pmod(t0 - m, sb.L) * sb.rank];
+    if (lane < sb.soe) {
+        // tail beyond the exact taps: U_q(t) = rho_q U_q(t - 1) + Y(t - taps), z += c_q U_q(t)
+        double* u = a.ustate + sb.ustate + (long long)l * sb.soe + lane;
+        const double un = a.rho[lane] * *u + Y[(long long)pmod(t0 - sb.taps, sb.L) * sb.rank];
+        *u = un;
+        z += a.trcoef[sb.trc + lane] * un;
+    }
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) a.zring[sb.zring + (long long)l * sb.LZ + pmod(t0, sb.LZ)] = z;
+    if (lane == 0) a.zring[sb.zring + (long long)pmod(t0, sb.LZ) * sb.rank + l] = z;
 }
 
 // ---- bulk-async copy + mbarrier helpers (PTX)
@@ -242,6 +286,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 // and the sum over one item are formed in the storage type T; items are combined in FP64.
 template <class T>
 __global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     extern __shared__ __align__(128) unsigned char stage_mem[];
     __shared__ __align__(8) unsigned long long bar[kStages];
     __shared__ double red[kNearThreads / 32][32];
@@ -250,7 +295,7 @@ __global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
     const int4 it = a.items[item];
     const NearDev L = a.near[it.x];
     const int k0 = it.y;
-    const int nsl = min(it.z, a.n + 1) - k0;              // slices needed at this step
+    const int nsl = min(it.z, n + 1) - k0;              // slices needed at this step
     const int per = max(1, kStageBytes / (L.sl * (int)sizeof(T)));
     const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;  // stage loads
     T* sd = (T*)(stage_mem + kStages * kStageBytes);      // [kChunk][32] slip rates D_{n-k, j}
@@ -271,7 +316,7 @@ __global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
         // slip-rate history of the item's sources, while the first stages are in flight
         for (int e = threadIdx.x; e < nsl * 32; e += kNearThreads) {
             const int kk = e >> 5, j = e & 31;
-            sd[e] = j < L.ns ? (T)a.Dring[(size_t)pmod(a.n - (k0 + kk), a.WD) * a.N + L.s0 + j] : (T)0;
+            sd[e] = j < L.ns ? (T)a.Dring[(size_t)pmod(n - (k0 + kk), a.WD) * a.N + L.s0 + j] : (T)0;
         }
         __syncthreads();
         for (int q = 0; q < nst; ++q) {
@@ -315,13 +360,34 @@ __global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
         return;
     }
     double accd = (double)acc;
-    if (k0 == 0 && warp == 0 && a.n - L.W >= 0) {
-        const long long t = (long long)a.n - L.W;
+    if (k0 == 0 && warp == 0 && n - L.W >= 0) {
+        const long long t = (long long)n - L.W;
         const double cv = lane < L.ns ? a.Cring[(size_t)pmod(t, a.WC) * a.N + L.s0 + lane] : 0.0;
         for (int j = 0; j < L.ns; ++j) {
             const double cj = __shfl_sync(0xffffffffu, cv, j);
             if (lane < L.nr) accd += a.stat[L.stat + j * L.nr + lane] * cj;
         }
+    }
+    if (k0 == 0 && L.tail >= 0) {
+        // exponential tail beyond the window (extension): V_qj(n) = rho_q V_qj(n-1) + D_{j,n-W},
+        // T_i += sum_qj c_qji V_qj(n); the state update is done once per step, by this CTA
+        const long long t = (long long)n - L.W;
+        const size_t slot = (size_t)pmod(t, a.WD) * a.N;
+        for (int e = threadIdx.x; e < a.soe * L.ns; e += kNearThreads) {
+            const int q = e / L.ns, j = e - q * L.ns;
+            double* v = a.vstate + L.vstate + e;
+            const double vn = a.rho[q] * *v + (t >= 0 ? a.Dring[slot + L.s0 + j] : 0.0);
+            *v = vn;
+        }
+        __syncthreads();
+        if (lane < L.nr)
+            for (int q = warp; q < a.soe; q += kNearThreads / 32) {
+                const double* c = a.tail + L.tail + (long long)q * L.ns * L.nr + lane;
+                const double* v = a.vstate + L.vstate + (long long)q * L.ns;
+                double s = 0.0;
+                for (int j = 0; j < L.ns; ++j) s += c[j * L.nr] * v[j];
+                accd += s;
+            }
     }
     red[warp][lane] = accd;
     __syncthreads();
@@ -335,19 +401,24 @@ __global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
 // Eq. 39, one thread per (block, receiver) entry, blocks in order: f_{l,i} Tbar'_l[n - dm_i]
 template <class T>
 __global__ void far_eval_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.n_ent) return;
     const SbDev sb = a.sbs[a.e_sb[e]];
     const int il = a.e_il[e];
-    const long long t = (long long)a.n - a.ints[sb.dm + il];
+    const long long t = (long long)n - a.ints[sb.dm + il];
     const T* f = a.fac + sb.f + (long long)il * sb.rank;
     double s = 0.0;
-    if (sb.kind == SB_TR) {
-        const double* z = a.zring + sb.zring + pmod(t, sb.LZ);
-        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * z[(long long)l * sb.LZ];
+    const bool tr = sb.kind == SB_TR;
+    const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
+    const int len = tr ? sb.LZ : sb.L;
+    const double* r = base + (long long)pmod(t, len) * sb.rank;
+    if (a.phi) {   // exact delay dm_i + phi_i: linear interpolation with the next older step
+        const double ph = a.phi[sb.phi + il];
+        const double* r1 = base + (long long)pmod(t - 1, len) * sb.rank;
+        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * ((1.0 - ph) * r[l] + ph * r1[l]);
     } else {
-        const double* r = a.ring + sb.ring + pmod(t, sb.L);
-        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[(long long)l * sb.L];
+        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[l];
     }
     a.fval[a.e_pos[e]] = s;
 }
@@ -355,6 +426,7 @@ __global__ void far_eval_kernel(StepArgs<T> a) {
 // one warp per receiver: sum of its far entries and near-field partials, fixed order
 template <class T>
 __global__ void gather_kernel(StepArgs<T> a) {
+    const int n = step_index(a);
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= a.N) return;
@@ -362,7 +434,29 @@ __global__ void gather_kernel(StepArgs<T> a) {
     for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
     for (int e = a.np_ptr[p] + lane; e < a.np_ptr[p + 1]; e += 32) s += a.partial[a.np_idx[e]];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.T_out[a.perm[p]] = s;
+    if (lane == 0) a.T_out[(a.n_dev ? (long long)(n - a.n_base) * a.io_stride : 0) + a.perm[p]] = s;
+}
+
+// Local friction solve (geometry order): T_pred holds the traction change with D_n = 0.
+struct FrictionDev {
+    const double* tau0;
+    const double* k0;      // instantaneous self coefficient K_{ii,0} (< 0)
+    double* slip;
+    double sigma_n, mu_s, mu_d, Dc, dt;
+};
+
+__global__ void friction_kernel(FrictionDev f, int N, double* D, double* T) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const double tau = f.tau0[e] + T[e];
+    const double u = f.slip[e];
+    const double w = u < f.Dc ? u / f.Dc : 1.0;
+    const double strength = f.sigma_n * (f.mu_s - (f.mu_s - f.mu_d) * w);
+    const double eta = -f.k0[e];
+    const double v = tau > strength ? (tau - strength) / eta : 0.0;
+    D[e] = v;
+    T[e] = tau + f.k0[e] * v;
+    f.slip[e] = u + v * f.dt;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -443,6 +537,45 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
     }
 }
 
+// projections g_q = sum_{k' < M - W} rho_q^k' (K_ij,W+k' - Kstat_ij dt) of every pair of the
+// inadmissible leaves with a tail, on the exponential basis (least-squares right-hand sides);
+// one thread per pair, pairs of leaf l at [pair0[l], pair0[l + 1])
+__global__ void near_soe_proj_kernel(GeoDev g, const NearDev* leaves, const long long* pair0, int nleaf,
+                                     long long npairs, int M, double dt, double mu, double c, int Q,
+                                     const double* rho, double* out) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pair0[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const NearDev L = leaves[lo];
+    const long long loc = q - pair0[lo];
+    const int il = (int)(loc / L.ns), jl = (int)(loc % L.ns);
+    const int pi = L.r0 + il, pj = L.s0 + jl;
+    const Seg s = dev_seg(g, pj);
+    double acc[kMaxSoe], pw[kMaxSoe];
+#pragma unroll
+    for (int r = 0; r < kMaxSoe; ++r) {
+        acc[r] = 0.0;
+        pw[r] = 1.0;
+    }
+    for (int k = L.W; k < M; ++k) {
+        const Stress2 v = stress_tail(g.px[pi], g.py[pi], s, (double)k * dt, (double)(k + 1) * dt, mu, c);
+        const double y = g.nx[pi] * v.x + g.ny[pi] * v.y;
+#pragma unroll
+        for (int r = 0; r < kMaxSoe; ++r)
+            if (r < Q) {
+                acc[r] += pw[r] * y;
+                pw[r] *= rho[r];
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxSoe; ++r)
+        if (r < Q) out[(size_t)q * Q + r] = acc[r];
+}
+
 // ------------------------------------------------------------------------------------------
 // the plan object
 
@@ -476,6 +609,12 @@ struct fdph_plan_s {
     double* stat = nullptr;
     int *np_ptr = nullptr, *np_idx = nullptr;
     int* err = nullptr;
+    double* rho = nullptr;
+    void* tail = nullptr;
+    // rupture state
+    bool rupture = false;
+    FrictionDev fr;
+    double *ustate = nullptr, *vstate = nullptr, *trcoef = nullptr, *phi = nullptr;
     // state
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
@@ -487,10 +626,9 @@ struct fdph_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
     double prof_ms[FDPH_NUM_KERNELS] = {0};
     int64_t prof_n[FDPH_NUM_KERNELS] = {0};
-    // graph of one step for fdph_run
+    // graph of one step for fdph_run (replayed with the step index in n_dev)
     cudaGraphExec_t graph = nullptr;
-    const double* graph_D = nullptr;
-    double* graph_T = nullptr;
+    int* n_dev = nullptr;
 };
 
 template <class T>
@@ -520,6 +658,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     StepArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.n = P->n;
+    a.n_dev = nullptr;
     a.N = P->N;
     a.WD = P->WD;
     a.WC = P->WC;
@@ -568,6 +707,13 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.np_ptr = P->np_ptr;
     a.np_idx = P->np_idx;
     a.err = P->err;
+    a.soe = P->hp.soe;
+    a.rho = P->rho;
+    a.ustate = P->ustate;
+    a.trcoef = P->trcoef;
+    a.phi = P->hp.interp ? P->phi : nullptr;
+    a.vstate = P->vstate;
+    a.tail = (const double*)P->tail;
     return a;
 }
 
@@ -582,9 +728,7 @@ struct ProfScope {
 };
 
 template <class T>
-static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
-    StepArgs<T> a = make_args<T>(P, D, Tout);
-    cudaStream_t s = P->stream;
+static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
     if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
@@ -598,7 +742,56 @@ static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
         if (a.n_ent) far_eval_kernel<T><<<blocks(a.n_ent, 128), 128, 0, s>>>(a);
         gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
     }
+}
+
+template <class T>
+static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
+    StepArgs<T> a = make_args<T>(P, D, Tout);
+    enqueue_step<T>(P, a, P->stream);
     FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
+}
+
+// `steps` steps as replays of one captured step graph; kernels read the step index from n_dev
+// (advanced by the last node) and offset D / T by one row per step
+template <class T>
+static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
+    if (!P->n_dev) {
+        int rc = dalloc(P, &P->n_dev, 1);
+        if (rc) return rc;
+    }
+    cudaStream_t s = P->stream;
+    StepArgs<T> a = make_args<T>(P, D, Tout);
+    a.n_dev = P->n_dev;
+    a.n_base = P->n;
+    a.io_stride = P->N;
+    set_step_kernel<<<1, 1, 0, s>>>(P->n_dev, P->n);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    FDPH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    enqueue_step<T>(P, a, s);
+    advance_step_kernel<<<1, 1, 0, s>>>(P->n_dev);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    for (int k = 0; k < steps; ++k) {
+        e = cudaGraphLaunch(ex, s);
+        if (e != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess) {
+        set_error(std::string("graph launch: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    P->n += steps;
     return FDPH_OK;
 }
 
@@ -648,6 +841,30 @@ static int step_impl(fdph_plan_t P, const double* D, double* T_) {
 }
 
 template <class T>
+static int launch_rupture_step(fdph_plan_t P, double* D, double* Tout) {
+    StepArgs<T> a = make_args<T>(P, nullptr, Tout);
+    cudaStream_t s = P->stream;
+    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }          // D_n = 0
+    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
+    if (a.n_items) {
+        ProfScope ps(P, 4);
+        near_kernel<T><<<a.n_items, kNearThreads, kStages * kStageBytes + kChunk * 32 * sizeof(T), s>>>(a);
+    }
+    {
+        ProfScope ps(P, 5);
+        if (a.n_ent) far_eval_kernel<T><<<blocks(a.n_ent, 128), 128, 0, s>>>(a);
+        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+    }
+    friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, Tout);
+    a.D_in = D;                                                                                // commit D_n
+    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
+    if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
+    FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
+}
+
+template <class T>
 static int build_near(fdph_plan_t P, const PlanInputs& in) {
     HostPlan& hp = P->hp;
     const int nl = (int)hp.near_r0.size();
@@ -682,11 +899,37 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         for (int l = 0; l < nl; ++l)
             for (long long q = pair0[l]; q < pair0[l + 1]; ++q) W[l] = std::max(W[l], ms[q]);
     }
-    finish_near_layout(hp, W, kChunk);
+    std::vector<char> has_tail(nl, 0);
+    if (in.soe > 0) {
+        // exponential tails: the window also covers every pair's wave passage (both end-point
+        // fronts + n_c steps); the exact kernel is kept for all pairs up to the leaf's window
+        const double cdt = in.cs * in.dt;
+        for (int l = 0; l < nl; ++l) {
+            for (int il = 0; il < hp.near_nr[l]; ++il) {
+                const int pi = hp.near_r0[l] + il;
+                for (int jl = 0; jl < hp.near_ns[l]; ++jl) {
+                    const int pj = hp.near_s0[l] + jl;
+                    double dx = hp.px[pi] - hp.sax[pj], dy = hp.py[pi] - hp.say[pj];
+                    const double da = sqrt(dx * dx + dy * dy);
+                    dx = hp.px[pi] - hp.sbx[pj];
+                    dy = hp.py[pi] - hp.sby[pj];
+                    const double db = sqrt(dx * dx + dy * dy);
+                    const int pass = (int)ceil(std::max(da, db) / cdt) + hp.tree.nc;
+                    W[l] = std::max(W[l], pass);
+                }
+            }
+            if (in.M - W[l] < soe_min_len(W[l])) W[l] = in.M;
+            else has_tail[l] = 1;
+            for (long long q = pair0[l]; q < pair0[l + 1]; ++q) ms[q] = W[l];   // exact over the window
+        }
+        FDPH_CUDA(cudaMemcpy(d_ms, ms.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    finish_near_layout(hp, W, has_tail, kChunk);
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
-        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat};
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
+                 (long long)L.vstate};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
     T* tens = nullptr;
@@ -713,6 +956,45 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
                 g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, P->stat);
         }
         FDPH_CUDA(cudaGetLastError());
+    }
+    if (in.soe > 0 && hp.near_tail_len > 0) {
+        // all tail leaves in one launch, then one Cholesky solve per leaf on the host
+        std::vector<NearDev> tl;
+        std::vector<int> tl_id;
+        std::vector<long long> tp0{0};
+        for (int l = 0; l < nl; ++l)
+            if (has_tail[l]) {
+                tl.push_back(nd[l]);
+                tl_id.push_back(l);
+                tp0.push_back(tp0.back() + (long long)nd[l].nr * nd[l].ns);
+            }
+        const long long ntp = tp0.back();
+        NearDev* d_tl = nullptr;
+        long long* d_tp0 = nullptr;
+        double* d_g = nullptr;
+        std::vector<long long> tp0s(tp0.begin(), tp0.end() - 1);
+        if ((rc = upload(P, &d_tl, tl)) || (rc = upload(P, &d_tp0, tp0s)) || (rc = dalloc(P, &d_g, (size_t)ntp * in.soe)))
+            return rc;
+        near_soe_proj_kernel<<<blocks(ntp, 128), 128>>>(g, d_tl, d_tp0, (int)tl.size(), ntp, in.M, in.dt, in.mu, in.cs,
+                                                        in.soe, P->rho, d_g);
+        FDPH_CUDA(cudaGetLastError());
+        std::vector<double> gh((size_t)ntp * in.soe), ch((size_t)ntp * in.soe);
+        FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<double> tail_h(hp.near_tail_len);
+#pragma omp parallel for schedule(dynamic, 8)
+        for (long t = 0; t < (long)tl.size(); ++t) {
+            const NearDev& L = tl[t];
+            const size_t b = (size_t)tp0[t] * in.soe;
+            soe_solve(hp.rho, in.M - L.W, gh.data() + b, ch.data() + b, L.nr * L.ns);
+            for (int il = 0; il < L.nr; ++il)
+                for (int jl = 0; jl < L.ns; ++jl)
+                    for (int q = 0; q < in.soe; ++q)
+                        tail_h[L.tail + ((size_t)q * L.ns + jl) * L.nr + il] =
+                            ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
+        }
+        double* dt_ = nullptr;
+        if ((rc = upload(P, &dt_, tail_h))) return rc;
+        P->tail = dt_;
     }
     std::vector<int4> it(hp.items.size());
     for (size_t q = 0; q < it.size(); ++q) it[q] = make_int4(hp.items[q].leaf, hp.items[q].k0, hp.items[q].k1, 0);
@@ -744,6 +1026,10 @@ static void fill_stats(fdph_plan_t P) {
         near_b += (double)L.W * L.ns * L.nr * ps + (double)L.ns * L.nr * 8.0;  // tensor + static tile
         near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
         flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
+        if (L.tail >= 0) {                                                     // tail coefficients + states
+            near_b += (double)hp.soe * L.ns * L.nr * ps + (double)hp.soe * L.ns * 16.0;
+            flops += 2.0 * hp.soe * L.ns * (L.nr + 1.0);
+        }
     }
     for (const SubBlock& sb : hp.sbs) {
         const double r = sb.rank;
@@ -755,8 +1041,8 @@ static void fill_stats(fdph_plan_t P) {
             flops += 2.0 * sb.taps * sb.ns;
         }
         if (sb.kind == SB_TR) {
-            far_b += r * (sb.taps * 8.0 + sb.taps * ps + 8.0);
-            flops += 2.0 * r * sb.taps;
+            far_b += r * (sb.taps * 8.0 + sb.taps * ps + 8.0) + r * sb.soe * 24.0;
+            flops += 2.0 * r * (sb.taps + 2.0 * sb.soe);
         }
     }
     const double push_b = hp.n * (8.0 + 8.0 + 32.0 + 8.0 + 4.0);           // D in, ring, C/comp, Cring, perm
@@ -767,7 +1053,7 @@ static void fill_stats(fdph_plan_t P) {
     s.state_bytes = (long long)P->state_bytes;
     long long arena = 0;
     arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
-    arena += (long long)(hp.near_tensor_len * ps) + hp.near_stat_len * 8;
+    arena += (long long)(hp.near_tensor_len * ps) + hp.near_stat_len * 8 + (long long)(hp.near_tail_len * ps);
     s.arena_bytes = arena;
 }
 
@@ -811,8 +1097,10 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
         return FDPH_E_ARG;
     }
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 ||
-              (p->precision != FDPH_FP64 && p->precision != FDPH_FP32))) {
-        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64 or FP32");
+              (p->precision != FDPH_FP64 && p->precision != FDPH_FP32) ||
+              (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
+        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64 or FP32, "
+                  "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
     for (int k = 0; k < 4 * g->n; ++k)
@@ -842,6 +1130,8 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.eps_st = p.eps_st;
     in.leaf = p.leaf_size;
     in.extra_steps = p.extra_steps;
+    in.soe = p.soe_terms;
+    in.interp = p.art_interp ? 1 : 0;
     return in;
 }
 
@@ -932,7 +1222,14 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     PlanInputs in = make_inputs(material, dt, M, eps, p);
     Elements el = make_elements(geometry->n, geometry->xy);
     HostPlan& hp = P->hp;
+    const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
+    auto stamp = [&](const char* what) {
+        if (verbose)
+            fprintf(stderr, "[fdph_plan] %-28s %8.3f s\n", what,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+    };
     rc = build_host_plan(el, in, hp);
+    stamp("host plan (tree, LRA)");
     if (rc == -3) return fail(FDPH_E_CAUSALITY);
     if (rc) return fail(FDPH_E_ARG);
     // ---- upload the far-field operator
@@ -940,8 +1237,9 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     for (size_t q = 0; q < sd.size(); ++q) {
         const SubBlock& b = hp.sbs[q];
         sd[q] = {b.kind, b.rank, b.r0, b.nr, b.s0, b.ns, b.L, b.LZ, b.taps, b.maxdelay, b.mindm, b.run0,
-                 (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
-                 (long long)b.dhat, (long long)b.delay, (long long)b.dm};
+                 b.soe, 0, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
+                 (long long)b.dhat, (long long)b.delay, (long long)b.dm, (long long)b.ustate, (long long)b.trc,
+                 (long long)b.phi};
     }
     if ((rc = upload(P, &P->perm, hp.perm)) || (rc = upload(P, &P->sbs, sd)) || (rc = upload(P, &P->ints, hp.ints)) ||
         (rc = upload(P, &P->run_delay, hp.run_delay)) || (rc = upload(P, &P->run_start, hp.run_start)) ||
@@ -964,9 +1262,13 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         if ((rc = upload(P, &d, hp.fac))) return fail(rc);
         P->fac = d;
     }
+    if (hp.soe > 0 && ((rc = upload(P, &P->rho, hp.rho)) || (rc = upload(P, &P->trcoef, hp.trcoef)))) return fail(rc);
+    if (hp.interp && (rc = upload(P, &P->phi, hp.phis))) return fail(rc);
+    stamp("far-field upload");
     // ---- near field (device-evaluated kernel windows)
     rc = P->precision == FDPH_FP32 ? build_near<float>(P, in) : build_near<double>(P, in);
     if (rc) return fail(rc);
+    stamp("near field (windows, tails)");
     FDPH_CUDA(cudaFuncSetAttribute(near_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    kStages * kStageBytes + kChunk * 32 * (int)sizeof(double)));
     FDPH_CUDA(cudaFuncSetAttribute(near_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -974,7 +1276,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if ((rc = dalloc(P, &P->err, 1))) return fail(rc);
     FDPH_CUDA(cudaMemset(P->err, 0, sizeof(int)));
     // ---- state
-    P->WD = std::max(std::max(hp.max_W, hp.max_taps), 1);
+    P->WD = std::max(std::max(hp.max_W + (hp.soe > 0 ? 1 : 0), hp.max_taps), 1);
     P->WC = hp.max_W + 1;
     size_t sb = 0;
     auto st = [&](double** p, size_t cnt) {
@@ -984,7 +1286,8 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if ((rc = st(&P->Dring, (size_t)P->WD * P->N)) || (rc = st(&P->Cring, (size_t)P->WC * P->N)) ||
         (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
         (rc = st(&P->zring, hp.zring_len)) || (rc = st(&P->dhat, hp.dhat_len)) ||
-        (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_sb.size())))
+        (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_sb.size())) ||
+        (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
         return fail(rc);
     P->state_bytes = sb;
     if ((rc = fdph_reset(P))) return fail(rc);
@@ -997,12 +1300,14 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
 int fdph_reset(fdph_plan_t P) {
     if (!P) return FDPH_E_ARG;
     cudaSetDevice(P->device);
-    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->dhat, P->partial};
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->dhat, P->partial,
+                      P->ustate, P->vstate};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.dhat_len,
-                    P->hp.items.size() * 32};
-    for (int q = 0; q < 8; ++q)
+                    P->hp.items.size() * 32, (size_t)P->hp.ustate_len, (size_t)P->hp.vstate_len};
+    for (int q = 0; q < 10; ++q)
         if (bufs[q] && cnt[q]) FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, cnt[q] * sizeof(double), P->stream));
+    if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->n = 0;
     return FDPH_OK;
@@ -1023,6 +1328,8 @@ int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
         set_error("run would pass step M");
         return FDPH_E_STATE;
     }
+    if (steps >= 8 && !P->prof)   // launch-bound steps: replay a captured graph of one step
+        return P->precision == FDPH_FP32 ? run_graph<float>(P, steps, D, T) : run_graph<double>(P, steps, D, T);
     for (int s = 0; s < steps; ++s) {
         int rc = step_impl(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
         if (rc) return rc;
@@ -1064,11 +1371,12 @@ int fdph_get_stats(fdph_plan_t P, fdph_stats* s) {
 
 int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     if (!P || !len) return FDPH_E_ARG;
-    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring};
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
-                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len};
+                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
+                    (size_t)P->hp.vstate_len};
     size_t need = sizeof(int32_t) * 2;
-    for (int q = 0; q < 6; ++q) need += cnt[q] * sizeof(double);
+    for (int q = 0; q < 8; ++q) need += cnt[q] * sizeof(double);
     if (!buf) {
         *len = need;
         return FDPH_OK;
@@ -1079,7 +1387,7 @@ int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     int32_t hdr[2] = {P->n, P->N};
     memcpy(o, hdr, sizeof(hdr));
     o += sizeof(hdr);
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < 8; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpy(o, bufs[q], cnt[q] * sizeof(double), cudaMemcpyDeviceToHost));
         o += cnt[q] * sizeof(double);
     }
@@ -1104,15 +1412,95 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
         return FDPH_E_ARG;
     }
     o += sizeof(hdr);
-    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring};
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
-                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len};
+                    (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
+                    (size_t)P->hp.vstate_len};
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < 8; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpy(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice));
         o += cnt[q] * sizeof(double);
     }
     P->n = hdr[0];
+    return FDPH_OK;
+}
+
+int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
+    if (!P || !f || !f->tau0 || !(f->sigma_n > 0.0) || !(f->Dc > 0.0) || f->mu_d > f->mu_s) {
+        set_error("fdph_rupture_init: friction with tau0, sigma_n > 0, Dc > 0, mu_d <= mu_s required");
+        return FDPH_E_ARG;
+    }
+    const HostPlan& hp = P->hp;
+    double minlen = 1e300;
+    for (int p = 0; p < P->N; ++p) minlen = std::min(minlen, hp.slen[p]);
+    if (hp.cs * P->dt > 0.5 * minlen * (1.0 + 1e-12)) {
+        set_error("fdph_rupture_init: cs dt exceeds half the shortest element; the instantaneous term is not local");
+        return FDPH_E_STATE;
+    }
+    // K_{ii,0}: jump of the ramp response of each element at its own midpoint over [0, dt]
+    std::vector<double> k0(P->N);
+    for (int p = 0; p < P->N; ++p) {
+        Seg sg;
+        sg.ax = hp.sax[p];
+        sg.ay = hp.say[p];
+        sg.tx = hp.stx[p];
+        sg.ty = hp.sty[p];
+        sg.len = hp.slen[p];
+        const Stress2 w = stress_jump(hp.px[p], hp.py[p], sg, 0.0, P->dt, hp.mu, hp.cs);
+        k0[hp.perm[p]] = hp.pnx[p] * w.x + hp.pny[p] * w.y;
+    }
+    if (!P->rupture) {
+        double *tau0 = nullptr, *kk = nullptr, *slip = nullptr;
+        int rc;
+        if ((rc = dalloc(P, &tau0, P->N)) || (rc = dalloc(P, &kk, P->N)) || (rc = dalloc(P, &slip, P->N))) return rc;
+        P->fr.tau0 = tau0;
+        P->fr.k0 = kk;
+        P->fr.slip = slip;
+    }
+    FDPH_CUDA(cudaMemcpy((void*)P->fr.tau0, f->tau0, P->N * sizeof(double), cudaMemcpyDeviceToDevice));
+    FDPH_CUDA(cudaMemcpy((void*)P->fr.k0, k0.data(), P->N * sizeof(double), cudaMemcpyHostToDevice));
+    FDPH_CUDA(cudaMemset(P->fr.slip, 0, P->N * sizeof(double)));
+    P->fr.sigma_n = f->sigma_n;
+    P->fr.mu_s = f->mu_s;
+    P->fr.mu_d = f->mu_d;
+    P->fr.Dc = f->Dc;
+    P->fr.dt = P->dt;
+    P->rupture = true;
+    return FDPH_OK;
+}
+
+int fdph_rupture_step(fdph_plan_t P, double* D_n, double* T_n) {
+    if (!P || !D_n || !T_n) return FDPH_E_ARG;
+    if (!P->rupture) {
+        set_error("fdph_rupture_init has not been called on this plan");
+        return FDPH_E_STATE;
+    }
+    if (P->n >= P->M) {
+        set_error("the plan has already taken M steps");
+        return FDPH_E_STATE;
+    }
+    int rc = P->precision == FDPH_FP32 ? launch_rupture_step<float>(P, D_n, T_n) : launch_rupture_step<double>(P, D_n, T_n);
+    if (rc == FDPH_OK) P->n += 1;
+    return rc;
+}
+
+int fdph_rupture_run(fdph_plan_t P, int32_t steps, double* D, double* T) {
+    if (!P || !D || !T || steps < 0) return FDPH_E_ARG;
+    if (P->n + steps > P->M) {
+        set_error("run would pass step M");
+        return FDPH_E_STATE;
+    }
+    for (int s = 0; s < steps; ++s) {
+        int rc = fdph_rupture_step(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
+        if (rc) return rc;
+    }
+    return FDPH_OK;
+}
+
+int fdph_rupture_slip(fdph_plan_t P, double* slip) {
+    if (!P || !slip) return FDPH_E_ARG;
+    if (!P->rupture) return FDPH_E_STATE;
+    FDPH_CUDA(cudaMemcpyAsync(slip, P->fr.slip, P->N * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
     return FDPH_OK;
 }
 

@@ -40,13 +40,25 @@ struct Tree {
 
 struct ArtInts {                      // per admissible leaf
     std::vector<int> dm, mbar, Dm;    // dm[nr], mbar[ns], Dm[ns]
+    std::vector<double> phi;          // phi[nr]: sub-step part of the receiver delay, in [0, 1)
     int causal = 0;                   // min(dm + mbar)
 };
 
 struct PlanInputs {
     double mu, cs, dt, eps, eta, lmin, eps_st;
     int M, leaf, extra_steps;
+    int soe;           // exponential-tail terms (0 = the paper's static cut)
+    int interp;        // 1: receiver delays interpolated between steps (extension)
 };
+
+// Decay factors rho_q = exp(-lambda_q) of the exponential tail basis, lambda_q spaced
+// geometrically in [0.5/M, 1] (q < Q).
+std::vector<double> soe_rho(int M, int Q);
+// Minimum fitted range of an exponential tail after an exact window of W steps.
+inline int soe_min_len(int W) { return W * 2 > 512 ? W * 2 : 512; }
+// Least-squares coefficients c (Q) of y(k') ~ sum_q c_q rho_q^k', k' < len, from the projections
+// g_q = sum_k' rho_q^k' y(k') (normal equations, closed-form Gram matrix, Cholesky).
+void soe_solve(const std::vector<double>& rho, int len, const double* g, double* c, int count);
 
 Elements make_elements(int n, const double* xy);
 void build_tree(const Elements& el, const PlanInputs& in, Tree& tr);

@@ -206,3 +206,66 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
 }
 
 }  // namespace fdph
+
+namespace fdph {
+
+std::vector<double> soe_rho(int M, int Q) {
+    std::vector<double> r(Q);
+    const double a = log(0.5 / M), b = log(1.0);
+    for (int q = 0; q < Q; ++q) r[q] = exp(-exp(a + (double)q / (Q - 1.0) * (b - a)));
+    return r;
+}
+
+// Gram matrix G_pq = sum_{k < len} (rho_p rho_q)^k = (1 - (rho_p rho_q)^len) / (1 - rho_p rho_q),
+// Cholesky-factored once, then `count` right-hand sides g (count x Q) are solved in place into c.
+void soe_solve(const std::vector<double>& rho, int len, const double* g, double* c, int count) {
+    const int Q = (int)rho.size();
+    std::vector<double> G((size_t)Q * Q);
+    for (int p = 0; p < Q; ++p)
+        for (int q = 0; q < Q; ++q) {
+            const double x = rho[p] * rho[q];
+            G[(size_t)p * Q + q] = (1.0 - pow(x, (double)len)) / (1.0 - x);
+        }
+    // Cholesky G = L L^T (lower, in place); if a pivot is lost to rounding, retry with a small
+    // ridge (relative 1e-13 of the diagonal), which only touches directions the data cannot fix
+    const std::vector<double> G0 = G;
+    double ridge = 0.0;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        G = G0;
+        for (int j = 0; j < Q; ++j) G[(size_t)j * Q + j] *= 1.0 + ridge;
+        bool ok = true;
+        for (int j = 0; j < Q && ok; ++j) {
+            double d = G[(size_t)j * Q + j];
+            for (int k = 0; k < j; ++k) d -= G[(size_t)j * Q + k] * G[(size_t)j * Q + k];
+            if (!(d > 0.0)) {
+                ok = false;
+                break;
+            }
+            d = sqrt(d);
+            G[(size_t)j * Q + j] = d;
+            for (int i = j + 1; i < Q; ++i) {
+                double s = G[(size_t)i * Q + j];
+                for (int k = 0; k < j; ++k) s -= G[(size_t)i * Q + k] * G[(size_t)j * Q + k];
+                G[(size_t)i * Q + j] = s / d;
+            }
+        }
+        if (ok) break;
+        ridge = ridge == 0.0 ? 1e-13 : ridge * 100.0;
+    }
+    for (int r = 0; r < count; ++r) {
+        const double* gr = g + (size_t)r * Q;
+        double* cr = c + (size_t)r * Q;
+        for (int i = 0; i < Q; ++i) {  // L z = g
+            double s = gr[i];
+            for (int k = 0; k < i; ++k) s -= G[(size_t)i * Q + k] * cr[k];
+            cr[i] = s / G[(size_t)i * Q + i];
+        }
+        for (int i = Q - 1; i >= 0; --i) {  // L^T c = z
+            double s = cr[i];
+            for (int k = i + 1; k < Q; ++k) s -= G[(size_t)k * Q + i] * cr[k];
+            cr[i] = s / G[(size_t)i * Q + i];
+        }
+    }
+}
+
+}  // namespace fdph

@@ -36,8 +36,10 @@ struct LeafOut {
     int HM = 0;
     LowRank F[2], S, TR[2];
     std::vector<double> h[2];      // [HM][ns]
-    std::vector<double> htr[2];
+    std::vector<double> htr[2];    // exact taps
+    std::vector<double> trc[2];    // exponential-tail coefficients of the fibre (if any)
     int Dtr[2] = {0, 0};
+    int trsoe[2] = {0, 0};
     bool ok = true;
 };
 
@@ -140,7 +142,29 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
             fib[m] = cc == 0 ? v.x : v.y;
             if (fabs(fib[m]) >= thr) last = m;
         }
-        const int Dtr = last + 1;
+        int Dtr = last + 1;
+        int nsoe = 0;
+        std::vector<double> coef;
+        if (in.soe > 0) {
+            // extension: beyond the exact taps the normalised fibre is kept as its fit on the
+            // exponential basis rather than dropped
+            Dtr = std::max(Dtr, 1);
+            const int len = in.M - Dtr;
+            if (len >= soe_min_len(Dtr)) {
+                const std::vector<double> rho = soe_rho(in.M, in.soe);
+                std::vector<double> g(in.soe, 0.0), pw(in.soe, 1.0);
+                for (int k = 0; k < len; ++k) {
+                    const double y = fib[Dtr + k] / fib[0];
+                    for (int q = 0; q < in.soe; ++q) {
+                        g[q] += pw[q] * y;
+                        pw[q] *= rho[q];
+                    }
+                }
+                coef.resize(in.soe);
+                soe_solve(rho, len, g.data(), coef.data(), 1);
+                nsoe = in.soe;
+            }
+        }
         if (Dtr == 0) continue;
         std::vector<double> B((size_t)nr * ns);
         for (int il = 0; il < nr; ++il) {
@@ -150,8 +174,10 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
         }
         low_rank(B.data(), nr, ns, in.eps, o.TR[cc]);
         o.Dtr[cc] = Dtr;
+        o.trsoe[cc] = nsoe;
         o.htr[cc].resize(Dtr);
         for (int m = 0; m < Dtr; ++m) o.htr[cc][m] = fib[m] / fib[0];
+        o.trc[cc] = coef;
     }
 }
 
@@ -179,7 +205,8 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         for (int p = 0; p < n; ++p) v[p] = src[tr.perm[p]];
     };
     fill(hp.px, el.mx); fill(hp.py, el.my); fill(hp.pnx, el.nx); fill(hp.pny, el.ny);
-    fill(hp.sax, el.ax); fill(hp.say, el.ay); fill(hp.stx, el.tx); fill(hp.sty, el.ty);
+    fill(hp.sax, el.ax); fill(hp.say, el.ay); fill(hp.sbx, el.bx); fill(hp.sby, el.by);
+    fill(hp.stx, el.tx); fill(hp.sty, el.ty);
     fill(hp.slen, el.len);
 
     std::vector<const Leaf*> adm;
@@ -211,6 +238,8 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     int rank_cnt = 0;
     for (const LeafOut& o : outs) {
         const int64_t dm_off = append(hp.ints, o.art.dm.data(), o.art.dm.size());
+        const int64_t phi_off = in.interp ? append(hp.phis, o.art.phi.data(), o.art.phi.size()) : 0;
+        const int ex = in.interp ? 1 : 0;   // one more (older) slot read per receiver
         std::vector<int32_t> dF(o.ns), dS(o.ns);
         for (int j = 0; j < o.ns; ++j) {
             dF[j] = o.art.mbar[j];
@@ -221,7 +250,7 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         const int mindm = *std::min_element(o.art.dm.begin(), o.art.dm.end());
         const int maxdm = *std::max_element(o.art.dm.begin(), o.art.dm.end());
         auto add = [&](int kind, const LowRank& lr, const std::vector<int32_t>& dl, int64_t dl_off,
-                       const std::vector<double>* h, int taps) {
+                       const std::vector<double>* h, int taps, int soe, const std::vector<double>* trc) {
             if (lr.rank <= 0) return;
             SubBlock sb;
             memset(&sb, 0, sizeof(sb));
@@ -238,11 +267,16 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.h = h ? append(hp.fac, h->data(), h->size()) : 0;
             sb.delay = dl_off;
             sb.dm = dm_off;
+            sb.phi = phi_off;
+            sb.soe = soe;
+            sb.trc = trc ? append(hp.trcoef, trc->data(), trc->size()) : 0;
+            sb.ustate = hp.ustate_len;
+            hp.ustate_len += (int64_t)sb.rank * soe;
             if (kind == SB_TR) {
-                sb.L = sb.maxdelay + mindm + taps;
-                sb.LZ = maxdm - mindm + 1;
+                sb.L = sb.maxdelay + mindm + taps + (soe ? 1 : 0);   // + the tail's input Y(t - taps)
+                sb.LZ = maxdm - mindm + 1 + ex;
             } else {
-                sb.L = sb.maxdelay + maxdm + 1;
+                sb.L = sb.maxdelay + maxdm + 1 + ex;
                 sb.LZ = 0;
             }
             sb.ring = hp.ring_len;
@@ -293,13 +327,16 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             rank_cnt += 1;
             hp.far_entries += (int64_t)lr.F.size() + lr.G.size() + (h ? h->size() : 0);
         };
-        add(SB_F, o.F[0], dF, dF_off, &o.h[0], o.HM);
-        add(SB_F, o.F[1], dF, dF_off, &o.h[1], o.HM);
-        add(SB_S, o.S, dS, dS_off, nullptr, 0);
+        add(SB_F, o.F[0], dF, dF_off, &o.h[0], o.HM, 0, nullptr);
+        add(SB_F, o.F[1], dF, dF_off, &o.h[1], o.HM, 0, nullptr);
+        add(SB_S, o.S, dS, dS_off, nullptr, 0, 0, nullptr);
         for (int cc = 0; cc < 2; ++cc)
-            if (o.Dtr[cc] > 0) add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc]);
+            if (o.Dtr[cc] > 0) add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc], o.trsoe[cc], &o.trc[cc]);
     }
     hp.mean_rank = rank_cnt ? rank_sum / rank_cnt : 0.0;
+    hp.soe = in.soe;
+    hp.interp = in.interp;
+    if (in.soe > 0) hp.rho = soe_rho(in.M, in.soe);
     hp.g_ptr.assign(n + 1, 0);
     for (int p = 0; p < n; ++p) {
         hp.g_ptr[p + 1] = hp.g_ptr[p] + (int32_t)recv[p].size();
@@ -323,7 +360,7 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     return 0;
 }
 
-void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk) {
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk) {
     const int nl = (int)hp.near_r0.size();
     hp.near.resize(nl);
     hp.items.clear();
@@ -343,6 +380,14 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk) 
         hp.near_tensor_len += (int64_t)L.W * L.sl;
         L.stat = hp.near_stat_len;
         hp.near_stat_len += (int64_t)L.ns * L.nr;
+        L.tail = -1;
+        L.vstate = 0;
+        if (hp.soe > 0 && has_tail[l]) {
+            L.tail = hp.near_tail_len;
+            hp.near_tail_len += (int64_t)hp.soe * L.ns * L.nr;
+            L.vstate = hp.vstate_len;
+            hp.vstate_len += (int64_t)hp.soe * L.ns;
+        }
         hp.max_W = std::max(hp.max_W, L.W);
         // one work item per chunk of steps; the first item also carries the static tail
         const int nchunk = std::max(1, (L.W + chunk - 1) / chunk);

@@ -22,6 +22,10 @@ struct SubBlock {
     int64_t ring, zring, dhat;   // offsets into state arrays
     int64_t delay, dm; // offsets into the int array (delay[ns], dm[nr])
     int32_t run0, nruns;
+    int32_t soe;       // TR: exponential-tail terms after the `taps` exact taps (0 = none)
+    int64_t trc;       // TR: offset of their FP64 coefficients in HostPlan::trcoef
+    int64_t ustate;    // TR: offset of the [rank][soe] recursive tail states
+    int64_t phi;       // offset of the receivers' sub-step delays in HostPlan::phis (interp only)
 };
 
 struct NearLeaf {
@@ -29,6 +33,8 @@ struct NearLeaf {
     int32_t sl;                  // slice stride: ns * nr rounded up to a multiple of 4 (16-byte rows)
     int64_t tensor;              // offset of [W][sl] coefficients (slice k: [ns][nr]), 4-aligned
     int64_t stat;                // offset of the [ns][nr] static tile (x dt), FP64
+    int64_t tail;                // offset of the [Q][ns][nr] exponential-tail coefficients (-1: none)
+    int64_t vstate;              // offset of the [Q][ns] recursive tail states
 };
 
 struct NearItem {
@@ -41,10 +47,13 @@ struct HostPlan {
     Tree tree;
     std::vector<int32_t> perm;                       // internal -> geometry index
     // internal-order geometry for the device near-field builder
-    std::vector<double> px, py, pnx, pny, sax, say, stx, sty, slen;
+    std::vector<double> px, py, pnx, pny, sax, say, sbx, sby, stx, sty, slen;
     // far field
     std::vector<SubBlock> sbs;
     std::vector<double> fac;                         // f, g, h, htr (FP64 master copy)
+    std::vector<double> trcoef;                      // transient-fibre tail coefficients (FP64)
+    std::vector<double> phis;                        // sub-step receiver delays per leaf
+    int interp = 0;
     std::vector<int32_t> ints;                       // delays, dm
     std::vector<int32_t> run_delay, run_start, run_len, src_order;
     std::vector<int32_t> scat_sb, scat_run, scat_l;  // scatter tasks (block, run, rank index)
@@ -52,14 +61,16 @@ struct HostPlan {
     std::vector<int32_t> tr_sb, tr_l;                // transient convolution tasks
     std::vector<int32_t> g_ptr, g_sb, g_il;          // gather CSR (receiver-major)
     std::vector<int32_t> e_sb, e_il, e_pos;          // the same entries block-major, with their CSR slot
-    int64_t ring_len = 0, zring_len = 0, dhat_len = 0;
+    int64_t ring_len = 0, zring_len = 0, dhat_len = 0, ustate_len = 0;
+    int soe = 0;                                     // exponential-tail terms (0: paper's cut)
+    std::vector<double> rho;                         // their decay factors
     int32_t max_taps = 0;
     // near field
     std::vector<NearLeaf> near;
     std::vector<int32_t> near_r0, near_nr, near_s0, near_ns;   // for the m_S kernel
     std::vector<NearItem> items;
     std::vector<int32_t> np_ptr, np_idx;             // receiver -> partial slots
-    int64_t near_tensor_len = 0, near_stat_len = 0;
+    int64_t near_tensor_len = 0, near_stat_len = 0, near_tail_len = 0, vstate_len = 0;
     int32_t max_W = 0;
     // stats
     int n_adm = 0, n_near = 0, max_rank = 0;
@@ -70,6 +81,6 @@ struct HostPlan {
 // Everything except the near-field windows (which need the device). Returns status.
 int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
-void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, int chunk);
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk);
 
 }  // namespace fdph

@@ -186,13 +186,16 @@ ArtInts art_integers(const Elements& el, const Tree& tr, const Leaf& lf, const P
     const double cdt = in.cs * in.dt;
     ArtInts a;
     a.dm.resize(tn.hi - tn.lo);
+    a.phi.resize(tn.hi - tn.lo);
     a.mbar.resize(sn.hi - sn.lo);
     a.Dm.resize(sn.hi - sn.lo);
     for (int p = tn.lo; p < tn.hi; ++p) {
         const int e = tr.perm[p];
         const double dx = el.mx[e] - jst[0], dy = el.my[e] - jst[1];
         const double r = sqrt(dx * dx + dy * dy);
-        a.dm[p - tn.lo] = (int)floor((r - lf.rbar) / cdt);
+        const double x = (r - lf.rbar) / cdt;
+        a.dm[p - tn.lo] = (int)floor(x);
+        a.phi[p - tn.lo] = x - floor(x);
     }
     for (int p = sn.lo; p < sn.hi; ++p) {
         const int e = tr.perm[p];

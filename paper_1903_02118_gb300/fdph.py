@@ -36,7 +36,12 @@ class Params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("lmin", ctypes.c_double), ("eps_st", ctypes.c_double),
                 ("leaf_size", ctypes.c_int32), ("extra_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Friction(ctypes.Structure):
+    _fields_ = [("tau0", ctypes.c_void_p), ("sigma_n", ctypes.c_double), ("mu_s", ctypes.c_double),
+                ("mu_d", ctypes.c_double), ("Dc", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +63,8 @@ _lib = None
 EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset",
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
-           "fdph_kernel_times", "fdph_plain_step_noalloc"]
+           "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
+           "fdph_rupture_run", "fdph_rupture_slip"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -93,13 +99,18 @@ def lib():
         L.fdph_kernel_times.argtypes = [c_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         L.fdph_plain_step_noalloc.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, c_p, ctypes.c_int32,
                                               ctypes.c_int32, c_p, c_p]
+        L.fdph_rupture_init.argtypes = [c_p, ctypes.POINTER(Friction)]
+        L.fdph_rupture_step.argtypes = [c_p, c_p, c_p]
+        L.fdph_rupture_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
+        L.fdph_rupture_slip.argtypes = [c_p, c_p]
         L.fdph_strerror.argtypes = [ctypes.c_int]
         L.fdph_strerror.restype = ctypes.c_char_p
         L.fdph_last_error.argtypes = []
         L.fdph_last_error.restype = ctypes.c_char_p
         for name in ("fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset", "fdph_current_step",
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
-                     "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc"):
+                     "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc",
+                     "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -124,10 +135,11 @@ def default_params():
 
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
-                device=None, stream=None):
+                device=None, stream=None, soe_terms=None, art_interp=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
-                 ("extra_steps", extra_steps), ("precision", precision), ("device", device)):
+                 ("extra_steps", extra_steps), ("precision", precision), ("device", device),
+                 ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)
     if stream is not None:
@@ -183,6 +195,21 @@ class Plan:
         s = Stats()
         _check(lib().fdph_get_stats(self.handle, ctypes.byref(s)))
         return s.as_dict()
+
+    def rupture_init(self, tau0, sigma_n, mu_s, mu_d, Dc):
+        """Attach linear slip-weakening friction (fdph_rupture_init); tau0 is a device buffer."""
+        self._tau0 = tau0
+        fr = Friction(_ptr(tau0).value, sigma_n, mu_s, mu_d, Dc)
+        _check(lib().fdph_rupture_init(self.handle, ctypes.byref(fr)))
+
+    def rupture_step(self, D_n, T_n):
+        _check(lib().fdph_rupture_step(self.handle, _ptr(D_n), _ptr(T_n)))
+
+    def rupture_run(self, steps, D, T):
+        _check(lib().fdph_rupture_run(self.handle, int(steps), _ptr(D), _ptr(T)))
+
+    def rupture_slip(self, out):
+        _check(lib().fdph_rupture_slip(self.handle, _ptr(out)))
 
     def set_profiling(self, on=True):
         _check(lib().fdph_set_profiling(self.handle, 1 if on else 0))

@@ -1,0 +1,154 @@
+"""Continuous-batching serving loop for independent rupture scenarios on one GPU.
+
+Requests (fault geometry, size N, CFL, friction heterogeneity) arrive over time.  A request is
+admitted as soon as its device footprint (plan operator + time-stepping state + outputs) fits
+the HBM budget and a slot is free; admitted scenarios stay resident and all of them advance
+together, each iteration moving every live scenario forward by `chunk` time steps on its own
+CUDA stream, so that the kernels of different scenarios overlap on the device.  A finished
+scenario releases its memory at once and the next waiting request takes its place.  Per
+request the loop records queueing, plan and run times and the time to solution (arrival to
+last step on the device).
+
+All arithmetic runs in libfdph (fdph_plan, fdph_rupture_init, fdph_rupture_run); this module
+only schedules.  Plans are independent, so a scenario's result is bit-identical alone and in
+the mix (tests/test_gpu_serving.py).
+"""
+import time
+
+import numpy as np
+
+from . import fdph, inputs
+
+
+class Request:
+    def __init__(self, rid, arrival, N, cfl, seed, M=None, eta=0.5, eps=1e-4, eps_st=1e-4, soe_terms=16,
+                 leaf=32, precision=fdph.FP32, geometry="curved"):
+        self.rid, self.arrival, self.N, self.cfl, self.seed = rid, arrival, N, cfl, seed
+        self.M = M if M is not None else int(round(N / cfl))
+        self.eta, self.eps, self.eps_st, self.soe_terms = eta, eps, eps_st, soe_terms
+        self.leaf, self.precision, self.geometry = leaf, precision, geometry
+        # filled by the server
+        self.t_admit = self.t_planned = self.t_done = None
+        self.plan_stats = None
+        self.slip = None
+        self.last_D = self.last_T = None
+
+    def inputs(self):
+        """Fault trace and prestress (config-3 friction: 0.45 + 5 % Gaussian heterogeneity, an
+        overstressed nucleation patch of 64 elements at 0.61; mu_s 0.6, mu_d 0.3, Dc = 6.4)."""
+        if self.geometry == "curved":
+            xy = inputs.curved_fault(self.N, inputs.seed_for(self.seed, inputs.GEOMETRY))
+        else:
+            xy = inputs.straight_fault(self.N)
+        rng = np.random.default_rng(inputs.seed_for(self.seed, inputs.FRICTION))
+        tau0 = 0.45 * (1.0 + 0.05 * rng.standard_normal(self.N))
+        c = self.N // 2
+        w = min(32, self.N // 8)
+        tau0[c - w:c + w] = 0.61
+        return xy, tau0
+
+
+def poisson_requests(count, rate, seed, n_min=512, n_max=16384, cfls=(0.25, 0.5), m_scale=1.0, **kw):
+    """`count` requests with Poisson arrivals at `rate` per second, N log-uniform in
+    [n_min, n_max], CFL uniform over `cfls`, M = N / CFL scaled by m_scale."""
+    rng = np.random.default_rng(inputs.seed_for(seed, inputs.ARRIVALS))
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    out = []
+    for k in range(count):
+        N = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        cfl = float(rng.choice(cfls))
+        M = max(64, int(round(m_scale * N / cfl)))
+        out.append(Request(k, float(t[k]), N, cfl, seed * 1000 + k, M=M, **kw))
+    return out
+
+
+class Server:
+    def __init__(self, hbm_budget=64 << 30, max_live=16, chunk=64, device=0, time_scale=1.0):
+        import torch
+        self.torch = torch
+        self.budget, self.max_live, self.chunk, self.device = hbm_budget, max_live, chunk, device
+        self.time_scale = time_scale
+        self.used = 0
+
+    def _admit(self, req):
+        torch = self.torch
+        xy, tau0 = req.inputs()
+        stream = torch.cuda.Stream(device=self.device)
+        dt = req.cfl  # dx = cs = 1
+        plan = fdph.Plan(xy, dt, req.M, req.eps, eta=req.eta, eps_st=req.eps_st, leaf_size=req.leaf,
+                         precision=req.precision, soe_terms=req.soe_terms, device=self.device,
+                         stream=stream.cuda_stream)
+        st = plan.stats()
+        foot = st["arena_bytes"] + st["state_bytes"] + 3 * req.N * 8 * (self.chunk + 2)
+        with torch.cuda.stream(stream):
+            t0 = torch.from_numpy(tau0).to(f"cuda:{self.device}")
+            D = torch.zeros((self.chunk, req.N), dtype=torch.float64, device=f"cuda:{self.device}")
+            T = torch.zeros_like(D)
+        plan.rupture_init(t0, 1.0, 0.6, 0.3, 6.4)
+        req.plan_stats = st
+        return dict(req=req, plan=plan, stream=stream, tau0=t0, D=D, T=T, n=0, foot=foot)
+
+    def _finish(self, s):
+        torch = self.torch
+        req = s["req"]
+        with torch.cuda.stream(s["stream"]):
+            slip = torch.empty(req.N, dtype=torch.float64, device=f"cuda:{self.device}")
+            s["plan"].rupture_slip(slip)
+        s["plan"].synchronize()
+        req.slip = slip.cpu().numpy()
+        k = (req.M - 1) % self.chunk
+        req.last_D = s["D"][k].cpu().numpy()
+        req.last_T = s["T"][k].cpu().numpy()
+        s["plan"].close()
+        self.used -= s["foot"]
+
+    def serve(self, requests, realtime=True):
+        """Run all requests; returns summary metrics.  With realtime=False arrivals are ignored
+        (everything waits at t = 0), which gives the closed-batch throughput."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        live = []
+        t0 = time.perf_counter()
+        steps_done = 0
+        while pending or live:
+            now = (time.perf_counter() - t0) * self.time_scale
+            while pending and len(live) < self.max_live and (not realtime or pending[0].arrival <= now):
+                est = pending[0].N * 2_000_000      # generous per-element estimate before the plan exists
+                if live and self.used + est > self.budget:
+                    break
+                req = pending.pop(0)
+                req.t_admit = time.perf_counter() - t0
+                s = self._admit(req)
+                req.t_planned = time.perf_counter() - t0
+                self.used += s["foot"]
+                live.append(s)
+            if not live:
+                time.sleep(0.001)
+                continue
+            for s in live:
+                req = s["req"]
+                k = min(self.chunk, req.M - s["n"])
+                s["plan"].rupture_run(k, s["D"], s["T"])
+                s["n"] += k
+                steps_done += k * req.N
+            still = []
+            for s in live:
+                if s["n"] >= s["req"].M:
+                    s["plan"].synchronize()
+                    s["req"].t_done = time.perf_counter() - t0
+                    self._finish(s)
+                else:
+                    still.append(s)
+            live = still
+        wall = time.perf_counter() - t0
+        lat = np.array([r.t_done - (r.arrival / self.time_scale if realtime else 0.0) for r in requests])
+        return {"element_steps_per_s": steps_done / wall, "wall_s": wall, "requests": len(requests),
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "element_steps": steps_done}
+
+
+def run_alone(req, chunk=64, device=0):
+    """The same request served on its own (reference for the mix)."""
+    srv = Server(max_live=1, chunk=chunk, device=device)
+    srv.serve([req], realtime=False)
+    return req

@@ -62,9 +62,9 @@ def test_plain_st_biem_fp64(geom, N, M):
     assert st["n_admissible"] == 0 and st["max_window"] == M
 
 
-def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6):
+def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6, soe_terms=0, eta=0.5, art_interp=False):
     el = kn.element_table(xy)
-    p = ofd.Params(eta=0.5, leaf=leaf, eps=eps, eps_st=eps_st, M=M)
+    p = ofd.Params(eta=eta, leaf=leaf, eps=eps, eps_st=eps_st, M=M, soe_terms=soe_terms, art_interp=art_interp)
     plan = ofd.build_plan(el, p)
     Kc = ofd.operator_rows(el, plan, np.arange(xy.shape[0]))
     return dense.march(Kc, D), plan
@@ -81,6 +81,20 @@ def test_fdph_fp64_equals_compressed_operator(geom, N, leaf):
     T = _run(plan, D)
     st = plan.stats()
     assert st["n_admissible"] == len(oplan["adm"]) and st["n_near"] == len(oplan["near"])
+    assert _rel(T, T0) < TOL64
+
+
+@pytest.mark.parametrize("geom,N,leaf,eta,interp", [("curved", 160, 16, 0.5, False), ("straight", 150, 12, 0.25, False),
+                                                    ("curved", 170, 16, 0.5, True)])
+def test_fdph_exponential_tails_fp64_equals_compressed_operator(geom, N, leaf, eta, interp):
+    _need_gpu()
+    M, eps = 900, 1e-5      # long enough that the exponential tails are used (fit range >= 512)
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-4, soe_terms=16, eta=eta, art_interp=interp)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=eta, eps_st=1e-4, leaf_size=leaf, soe_terms=16, art_interp=interp)
+    T = _run(plan, D)
+    assert plan.stats()["max_window"] == max(d["W"] for d in oplan["near"]) < M
     assert _rel(T, T0) < TOL64
 
 
@@ -137,3 +151,34 @@ def test_config2_full_size_sampled_receivers():
     Kc = ofd.operator_rows(el, oplan, rows)
     T0 = dense.march_rows_fft(Kc, D)
     assert _rel(T[:, rows], T0) < 1e-9
+
+
+@pytest.mark.parametrize("mode", ["plain", "fdph"])
+def test_rupture_matches_oracle(mode):
+    """Dynamic rupture (Sec. 6.2, linear slip weakening): slip rate and traction of every element
+    and step against the oracle's rupture march on the same operator."""
+    _need_gpu()
+    N, M, dt = 200, 240, 0.5
+    xy = _geom("straight", N)
+    rng = np.random.default_rng(inputs.seed_for(2, inputs.FRICTION))
+    tau0 = 0.45 * (1.0 + 0.05 * rng.standard_normal(N))
+    tau0[N // 2 - 8:N // 2 + 8] = 0.61
+    el = kn.element_table(xy)
+    if mode == "plain":
+        Kop = kn.discrete_kernel(el, dt, M, 1.0, 1.0)
+        plan = fdph.Plan(xy, dt, M, 0.0, eta=0.0, eps_st=0.0, leaf_size=32)
+    else:
+        p = ofd.Params(eta=0.5, leaf=16, eps=1e-6, eps_st=1e-4, M=M, soe_terms=16)
+        oplan = ofd.build_plan(el, p)
+        Kop = ofd.operator_rows(el, oplan, np.arange(N))
+        plan = fdph.Plan(xy, dt, M, 1e-6, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
+    D0, T0 = dense.rupture_march(Kop, tau0, 1.0, 0.6, 0.3, 2.0, dt, M)
+    t0 = torch.from_numpy(tau0).cuda()
+    plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0)
+    Dd = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    Td = torch.zeros_like(Dd)
+    plan.rupture_run(M, Dd, Td)
+    plan.synchronize()
+    D, T = Dd.cpu().numpy(), Td.cpu().numpy()
+    assert (D0 > 0).sum() > 0.3 * D0.size          # the rupture spreads over the fault
+    assert _rel(D, D0) < 1e-9 and _rel(T, T0) < 1e-10

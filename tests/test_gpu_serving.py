@@ -1,0 +1,24 @@
+"""Serving: continuous batching of independent rupture scenarios gives each scenario the same
+result as serving it alone (bit for bit), and reports latency percentiles."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_mix_equals_alone_and_reports_latency():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02118_gb300 import build, serving
+    build.build()
+    reqs = serving.poisson_requests(6, rate=50.0, seed=7, n_min=256, n_max=1024, m_scale=0.25)
+    srv = serving.Server(max_live=4, chunk=32)
+    summary = srv.serve(reqs, realtime=True)
+    assert summary["requests"] == 6 and summary["p99_latency_s"] >= summary["p50_latency_s"] > 0
+    for r in reqs[:3]:
+        alone = serving.Request(r.rid, 0.0, r.N, r.cfl, r.seed, M=r.M)
+        serving.run_alone(alone, chunk=32)
+        assert np.array_equal(alone.slip, r.slip)
+        assert np.array_equal(alone.last_T, r.last_T)
+        assert (r.slip > 0).any()

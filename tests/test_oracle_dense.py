@@ -60,3 +60,38 @@ def test_fft_rows_equal_march():
     rows = [0, 7, 39]
     Tr = dense.march_rows_fft(K[:, rows, :], D)
     assert np.abs(Tr - T[:, rows]).max() < 1e-12 * np.abs(T).max()
+
+
+def test_rupture_follows_the_plane_wave_recursion_inside_the_causal_cone():
+    # Uniform overstress on a long planar fault: before edge waves arrive every interior element
+    # is a 1-D plane-wave problem, T = tau0 - mu/(2 cs) v, so with linear weakening the slip rate
+    # obeys eta v_n = tau0 - strength(u_n), u_{n+1} = u_n + v_n dt exactly (Sec. 6.2 law).
+    N, M, dt = 160, 60, 0.5
+    el = kn.element_table(inputs.straight_fault(N))
+    K = kn.discrete_kernel(el, dt, M, 1.0, 1.0)
+    tau0 = np.full(N, 0.62)
+    D, T = dense.rupture_march(K, tau0, 1.0, 0.6, 0.3, 4.0, dt, M)
+    u, eta = 0.0, 0.5
+    i = N // 2
+    for n in range(M):
+        if (n + 1) * dt >= el["mx"][i] - 1.0:   # edge waves could have arrived
+            break
+        s = 0.6 - 0.3 * min(u / 4.0, 1.0)
+        v = max(0.62 - s, 0.0) / eta
+        assert abs(D[n, i] - v) < 1e-12 and abs(T[n, i] - (0.62 - eta * v)) < 1e-12
+        u += v * dt
+    assert n > 40
+
+
+def test_rupture_respects_locking_and_no_back_slip():
+    N, M, dt = 120, 90, 0.5
+    el = kn.element_table(inputs.kinked_fault(N))
+    K = kn.discrete_kernel(el, dt, M, 1.0, 1.0)
+    tau0 = np.full(N, 0.45)
+    tau0[55:65] = 0.61                          # overstressed nucleation patch
+    D, T = dense.rupture_march(K, tau0, 1.0, 0.6, 0.3, 2.0, dt, M)
+    assert np.all(D >= 0.0)
+    assert np.all(D[0, :55] == 0.0) and np.all(D[0, 55:65] > 0.0)
+    slipping = D > 0.0
+    strength_max = 0.6
+    assert np.all(T[~slipping] <= strength_max + 1e-12)    # locked cells stay below strength

@@ -204,3 +204,48 @@ def test_fdph_march_close_to_plain_march(geom, bound):
     err = np.linalg.norm(T1 - T0) / np.linalg.norm(T0)
     assert err < bound
     assert err < GOLD["solution_error_eta_half"]["value"]
+
+
+def test_exponential_tail_reproduces_the_kernel_beyond_the_window():
+    # Extension (not the paper's): inadmissible pairs keep the exact kernel up to the leaf window
+    # and the fitted exponential tail beyond it.  Pinned against the plain kernel itself.
+    N, M = 200, 900
+    el, p = _setup("curved", N, eta=0.5, leaf=16, eps=1e-6, eps_st=1e-4, M=M, soe_terms=16)
+    plan = fdph.build_plan(el, p, receivers=[3, 100])
+    K = None
+    for d in plan["near"]:
+        Kx = kn.discrete_kernel(el, p.dt, M, p.mu, p.cs, d["I"], d["J"])
+        W = d["W"]
+        assert W >= 2 * 10                                   # covers the wave passage
+        op = np.concatenate([d["K"][:W], d["Ks"][None] * p.dt + d["fit"]], axis=0)
+        assert np.abs(op - Kx).max() < 5e-9                  # |K_ijk - operator| for every k < M
+
+
+def test_exponential_tail_removes_the_static_cut_bias():
+    # App. H: cutting at eps_st leaves the slowly decaying remainder K - Kstat dt out; its sum
+    # over the rest of the run is the systematic static-approximation error.  With the exponential
+    # tails that accumulated error vanishes, and the march is as accurate as keeping every step.
+    N, M = 256, 700
+    el, _ = _setup("curved", N)
+    rows = np.array([5, 128, 200])
+    D = inputs.gaussian_pulse(N, M, 0.5, 5)
+    K = kn.discrete_kernel(el, 0.5, M, 1.0, 1.0, rows)
+    T0 = dense.march_rows_fft(K, D)
+
+    def run(**kw):
+        p = fdph.Params(eta=0.5, leaf=16, eps=1e-6, M=M, **kw)
+        plan = fdph.build_plan(el, p, receivers=rows)
+        Kc = fdph.operator_rows(el, plan, rows)
+        near = [(np.nonzero(rows == i)[0][0], j) for d in plan["near"] for i in d["I"] if i in rows for j in d["J"]]
+        r, j = np.array(near).T
+        acc = np.abs(np.cumsum(Kc[:, r, j] - K[:, r, j], axis=0)).max()   # accumulated step-response error
+        T = dense.march_rows_fft(Kc, D)
+        return acc, np.linalg.norm(T - T0) / np.linalg.norm(T0)
+
+    acc_cut, _ = run(eps_st=1e-6)
+    acc_full, e_full = run(eps_st=0.0)
+    acc_soe, e_soe = run(eps_st=1e-4, soe_terms=16)
+    assert acc_cut > 1e-5            # the dropped remainder accumulates (App. H bias)
+    assert acc_full == 0.0
+    assert acc_soe < 1e-8
+    assert e_soe < 1.01 * e_full + 1e-9

@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <omp.h>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -924,7 +925,13 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         }
         FDPH_CUDA(cudaMemcpy(d_ms, ms.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
     }
-    finish_near_layout(hp, W, has_tail, kChunk);
+    // work-item length: the longest chunk (kChunk) that still yields about four waves of
+    // resident CTAs (152 SMs x 3), so small problems (the plain config) fill the device too
+    long long slices = 0;
+    for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
+    int chunk = kChunk;
+    while (chunk > 8 && slices / chunk < 4LL * 152 * 3) chunk /= 2;
+    finish_near_layout(hp, W, has_tail, chunk);
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
@@ -1229,6 +1236,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     };
     rc = build_host_plan(el, in, hp);
+    if (verbose) fprintf(stderr, "[fdph_plan] host threads %d\n", omp_get_max_threads());
     stamp("host plan (tree, LRA)");
     if (rc == -3) return fail(FDPH_E_CAUSALITY);
     if (rc) return fail(FDPH_E_ARG);

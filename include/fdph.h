@@ -178,6 +178,13 @@ int fdph_rupture_slip(fdph_plan_t plan, double* slip);
  * out and returns when T_n is ready (synchronous). */
 int fdph_step_host(fdph_plan_t plan, const double* D_n_host, double* T_n_host);
 
+/* `steps` consecutive steps with HOST buffers: D_host (steps * n doubles, step-major) ->
+ * T_host (same shape).  Every step's D_n is copied to the device and its T_n back to the host
+ * (page-locked buffers let the copies run asynchronously); the copies of later and earlier steps
+ * overlap the step in progress through a ring of device staging slots, and the steps replay
+ * one captured step graph.  Returns when T_host is complete.  Errors as fdph_run. */
+int fdph_run_host(fdph_plan_t plan, int32_t steps, const double* D_host, double* T_host);
+
 /* Return the plan to step 0 with zero history (rings, accumulators). */
 int fdph_reset(fdph_plan_t plan);
 

@@ -55,22 +55,31 @@ using namespace fdph;
     } while (0)
 
 static const int kChunk = 64;      // steps of exact kernel per near-field work item
-static const int kNearThreads = 256;
-static const int kStages = 4;      // shared-memory pipeline depth of the near-field kernel
-static const int kStageBytes = 12288;
+static const int kNearConsumers = 4;                       // consumer warps of the near-field kernel
+static const int kNearThreads = 32 * (kNearConsumers + 1);  // + one producer warp
+static const int kNearStageBytes = 16384;                  // one pipeline stage
+static const int kMaxPer = 8;                              // slices per stage at most
+static_assert(kNearStageBytes >= 32 * 32 * 8, "a stage holds at least one FP64 slice of a 32 x 32 leaf");
 static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls before giving up
 
 // ------------------------------------------------------------------------------------------
 // device-side views
 
 struct SbDev {
-    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, pad;
+    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, ident, e0, pad;
     long long f, g, h, ring, zring, dhat, delay, dm, ustate, trc, phi;
 };
 
 struct NearDev {
-    int r0, nr, s0, ns, W, sl;
+    int r0, nr, s0, ns, W, sl, sla, pad;
     long long tensor, stat, tail, vstate;
+};
+
+// one near-field work item as the persistent kernel reads it (one 64-byte load)
+struct __align__(16) NearTask {
+    long long off;       // element offset of the item's first slice (tensor, or aux for kind 1)
+    int item, k0, k1, kind, nr, ns, sl, s0, W, vstate;
+    int pad[2];
 };
 
 static const int kMaxSoe = 16;
@@ -83,6 +92,7 @@ struct StepArgs {
     const int* n_dev;
     int n_base;
     long long io_stride;
+    int io_ring;              // > 0: D_in / T_out rows are a ring of io_ring staging slots
     double dt;
     const double* D_in;       // caller's D_n (geometry order)
     double* T_out;            // caller's T_n (geometry order)
@@ -99,15 +109,12 @@ struct StepArgs {
     const int* run_start;
     const int* run_len;
     const int* src_order;
-    const int* scat_sb;
-    const int* scat_run;
-    const int* scat_l;
-    int n_scat;
-    const int* e_sb;
-    const int* e_il;
-    const int* e_pos;
-    int n_ent;
-    double* fval;             // [n_ent] far-field value of each (block, receiver) entry, CSR order
+    const int4* sc_tasks;     // scatter warp tasks {block, first run, runs, log2 lanes per run}
+    int n_sct;
+    const int4* ev_tasks;     // Eq. 39 warp tasks {block, first receiver, receivers, log2 lanes per receiver}
+    int n_evt;
+    const int* e_pos;         // CSR slot of each (block, receiver) entry, block-major
+    double* fval;             // [entries] far-field value of each (block, receiver) entry, CSR order
     const int* fir_sb;
     const int* fir_j;
     int n_fir;
@@ -122,10 +129,12 @@ struct StepArgs {
     double* dhat;
     // near field
     const NearDev* near;
-    const int4* items;
+    const NearTask* tasks;    // near-field work items in per-CTA order
+    const int* cta_ptr;       // [n_cta + 1]: CTA c owns tasks [cta_ptr[c], cta_ptr[c+1])
+    int n_cta;
     int n_items;
     const T* tensor;
-    const double* stat;
+    const double* stat;       // FP64 aux slices (static tiles, exponential-tail coefficients)
     double* partial;          // [n_items][32]
     const int* np_ptr;
     const int* np_idx;
@@ -141,14 +150,23 @@ struct StepArgs {
                               // fitted coefficients partly cancel, so they are not rounded to FP32)
 };
 
-__device__ __forceinline__ int pmod(long long a, int L) {
-    long long r = a % L;
-    return (int)(r < 0 ? r + L : r);
+// ring slot of step a (a may be negative; |a| < 2^31)
+__device__ __forceinline__ int wrap(int a, int L) {
+    const int r = a % L;
+    return r < 0 ? r + L : r;
 }
 
 template <class T>
 __device__ __forceinline__ int step_index(const StepArgs<T>& a) {
     return a.n_dev ? *a.n_dev : a.n;
+}
+
+// element offset of step n's row of D_in / T_out
+template <class T>
+__device__ __forceinline__ long long io_offset(const StepArgs<T>& a, int n) {
+    if (!a.n_dev) return 0;
+    const int k = n - a.n_base;
+    return (long long)(a.io_ring > 0 ? k % a.io_ring : k) * a.io_stride;
 }
 
 __global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
@@ -161,18 +179,18 @@ __global__ void push_kernel(StepArgs<T> a) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.N) return;
     if (!a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
-        a.Dring[(size_t)pmod(n, a.WD) * a.N + p] = 0.0;
+        a.Dring[(size_t)wrap(n, a.WD) * a.N + p] = 0.0;
         return;
     }
-    const double d = a.D_in[(a.n_dev ? (long long)(n - a.n_base) * a.io_stride : 0) + a.perm[p]];
-    a.Dring[(size_t)pmod(n, a.WD) * a.N + p] = d;
+    const double d = a.D_in[io_offset(a, n) + a.perm[p]];
+    a.Dring[(size_t)wrap(n, a.WD) * a.N + p] = d;
     // compensated running sum of the slip (units of dt)
     const double y = d - a.Ccomp[p];
     const double c0 = a.C[p];
     const double t = c0 + y;
     a.Ccomp[p] = (t - c0) - y;
     a.C[p] = t;
-    a.Cring[(size_t)pmod(n, a.WC) * a.N + p] = t;
+    a.Cring[(size_t)wrap(n, a.WC) * a.N + p] = t;
 }
 
 template <class T>
@@ -180,40 +198,83 @@ __global__ void fir_kernel(StepArgs<T> a) {
     const int n = step_index(a);
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.n_fir) return;
-    const SbDev sb = a.sbs[a.fir_sb[q]];
+    const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
-    const int col = sb.s0 + jl;
-    double s = 0.0;
-    const int taps = min(sb.taps, n + 1);
-    for (int m = 0; m < taps; ++m)
-        s += (double)a.fac[sb.h + (long long)m * sb.ns + jl] * a.Dring[(size_t)pmod(n - m, a.WD) * a.N + col];
-    a.dhat[sb.dhat + jl] = s;
+    const int ns = sb.ns;
+    const T* h = a.fac + sb.h + jl;
+    const double* D = a.Dring + sb.s0 + jl;
+    const int taps = min(sb.taps, n + 1);   // taps <= WD, so one wrap-around at most
+    const int slot = wrap(n, a.WD);
+    double s0 = 0.0, s1 = 0.0;
+    int m = 0;
+    for (; m + 1 < taps; m += 2) {
+        int t0 = slot - m, t1 = slot - m - 1;
+        t0 += t0 < 0 ? a.WD : 0;
+        t1 += t1 < 0 ? a.WD : 0;
+        s0 += (double)h[(long long)m * ns] * D[(size_t)t0 * a.N];
+        s1 += (double)h[(long long)(m + 1) * ns] * D[(size_t)t1 * a.N];
+    }
+    if (m < taps) {
+        int t0 = slot - m;
+        t0 += t0 < 0 ? a.WD : 0;
+        s0 += (double)h[(long long)m * ns] * D[(size_t)t0 * a.N];
+    }
+    a.dhat[sb.dhat + jl] = s0 + s1;
 }
 
+// source quantity u_j of Eq. 42 for block kind: Dhat (Domain F), dt * cumulative slip (Domain S,
+// App. B.1), slip rate (transient)
+template <class T>
+__device__ __forceinline__ double source_value(const StepArgs<T>& a, const SbDev& sb, int jl, int dslot) {
+    if (sb.kind == SB_F) return a.dhat[sb.dhat + jl];
+    if (sb.kind == SB_S) return a.dt * a.C[sb.s0 + jl];
+    return a.Dring[(size_t)dslot * a.N + sb.s0 + jl];
+}
+
+// Eq. 42: one warp per task of runs (sources of equal delay) of one block; 2^lg lanes per run
+// cover the rank index l, so a run writes its ring slot row [slot][0, rank) in one coalesced pass.
+// One writer per (slot, l): the runs of a block have distinct delays.
 template <class T>
 __global__ void scatter_kernel(StepArgs<T> a) {
     const int n = step_index(a);
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= a.n_scat) return;
-    const SbDev sb = a.sbs[a.scat_sb[q]];
-    const int run = a.scat_run[q];
-    const int l = a.scat_l[q];
-    const int delay = a.run_delay[run];
-    const int st = a.run_start[run];
-    const int len = a.run_len[run];
-    const int slot = pmod((long long)n + delay, sb.L);
-    const size_t dslot = (size_t)pmod(n, a.WD) * a.N;
-    double s = 0.0;
-    for (int u = 0; u < len; ++u) {
-        const int jl = a.src_order[st + u];
-        double v;
-        if (sb.kind == SB_F) v = a.dhat[sb.dhat + jl];
-        else if (sb.kind == SB_S) v = a.dt * a.C[sb.s0 + jl];
-        else v = a.Dring[dslot + sb.s0 + jl];
-        s += (double)a.fac[sb.g + (long long)jl * sb.rank + l] * v;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= a.n_sct) return;
+    const int4 tk = a.sc_tasks[w];
+    const SbDev& sb = a.sbs[tk.x];
+    const int lg = tk.w, G = 1 << lg;
+    const int gi = lane >> lg, lj = lane & (G - 1);
+    if (gi >= tk.z) return;
+    const int run = tk.y + gi;
+    const int delay = a.run_delay[run], st = a.run_start[run], len = a.run_len[run];
+    const int rank = sb.rank;
+    double* r = a.ring + sb.ring + (long long)wrap(n + delay, sb.L) * rank;
+    const int dslot = sb.kind == SB_TR ? wrap(n, a.WD) : 0;
+    if (sb.ident == 2) {
+        // G is the identity: column j of a slot receives source j only, once
+        for (int u = lj; u < len; u += G) {
+            const int jl = a.src_order[st + u];
+            r[jl] = source_value(a, sb, jl, dslot);
+        }
+        return;
     }
-    double* r = a.ring + sb.ring + (long long)slot * sb.rank + l;   // ring layout [slot][rank]
-    *r = delay == sb.maxdelay ? s : *r + s;   // the newest slot starts fresh
+    const bool fresh = delay == sb.maxdelay;   // the newest slot of the ring starts from zero
+    const T* g = a.fac + sb.g;
+    if (len == 1) {
+        const int jl = a.src_order[st];
+        const double u = source_value(a, sb, jl, dslot);
+        const T* gj = g + (long long)jl * rank;
+        for (int l = lj; l < rank; l += G) r[l] = fresh ? (double)gj[l] * u : r[l] + (double)gj[l] * u;
+        return;
+    }
+    for (int l = lj; l < rank; l += G) {
+        double s = 0.0;
+        for (int u = 0; u < len; ++u) {
+            const int jl = a.src_order[st + u];
+            s += (double)g[(long long)jl * rank + l] * source_value(a, sb, jl, dslot);
+        }
+        r[l] = fresh ? s : r[l] + s;
+    }
 }
 
 // one warp per (transient block, rank index)
@@ -225,20 +286,20 @@ __global__ void trconv_kernel(StepArgs<T> a) {
     if (q >= a.n_tr) return;
     const SbDev sb = a.sbs[a.tr_sb[q]];
     const int l = a.tr_l[q];
-    const long long t0 = (long long)n - sb.mindm;
+    const int t0 = n - sb.mindm;
     const double* Y = a.ring + sb.ring + l;
     double z = 0.0;
     for (int m = lane; m < sb.taps; m += 32)
-        z += (double)a.fac[sb.h + m] * Y[(long long)pmod(t0 - m, sb.L) * sb.rank];
+        z += (double)a.fac[sb.h + m] * Y[(long long)wrap(t0 - m, sb.L) * sb.rank];
     if (lane < sb.soe) {
         // tail beyond the exact taps: U_q(t) = rho_q U_q(t - 1) + Y(t - taps), z += c_q U_q(t)
         double* u = a.ustate + sb.ustate + (long long)l * sb.soe + lane;
-        const double un = a.rho[lane] * *u + Y[(long long)pmod(t0 - sb.taps, sb.L) * sb.rank];
+        const double un = a.rho[lane] * *u + Y[(long long)wrap(t0 - sb.taps, sb.L) * sb.rank];
         *u = un;
         z += a.trcoef[sb.trc + lane] * un;
     }
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) a.zring[sb.zring + (long long)pmod(t0, sb.LZ) * sb.rank + l] = z;
+    if (lane == 0) a.zring[sb.zring + (long long)wrap(t0, sb.LZ) * sb.rank + l] = z;
 }
 
 // ---- bulk-async copy + mbarrier helpers (PTX)
@@ -266,6 +327,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
+// as bulk_g2s, with an L2 cache policy (evict-first for data read once per step)
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                              unsigned long long policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
     const unsigned a = smem_u32(bar);
     for (long long it = 0; it < kWaitLimit; ++it) {
@@ -280,148 +357,292 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     return false;
 }
 
-// Near field: one CTA per work item (leaf, k in [k0, k1)).  The item's coefficients are one
-// contiguous block [k][sl]; thread 0 streams it into a kStages-deep ring of shared-memory stages
-// with cp.async.bulk + mbarrier, all four warps consume: warp w takes every 4th slice of a
-// stage, lane i owns receiver i, the slip rates D_{n-k, j} are broadcast by shuffle.  Products
-// and the sum over one item are formed in the storage type T; items are combined in FP64.
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void consumer_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kNearConsumers * 32) : "memory");
+}
+
 template <class T>
-__global__ void __launch_bounds__(kNearThreads, 3) near_kernel(StepArgs<T> a) {
-    const int n = step_index(a);
-    extern __shared__ __align__(128) unsigned char stage_mem[];
-    __shared__ __align__(8) unsigned long long bar[kStages];
-    __shared__ double red[kNearThreads / 32][32];
-    const int item = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int4 it = a.items[item];
-    const NearDev L = a.near[it.x];
-    const int k0 = it.y;
-    const int nsl = min(it.z, n + 1) - k0;              // slices needed at this step
-    const int per = max(1, kStageBytes / (L.sl * (int)sizeof(T)));
-    const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;  // stage loads
-    T* sd = (T*)(stage_mem + kStages * kStageBytes);      // [kChunk][32] slip rates D_{n-k, j}
-    T acc = (T)0;
-    bool failed = false;
-    if (nst > 0) {
-        const T* src = a.tensor + L.tensor + (long long)k0 * L.sl;
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-            mbar_fence_init();
-            for (int q = 0; q < min(kStages, nst); ++q) {
-                const int cnt = min(per, nsl - q * per);
-                const unsigned bytes = (unsigned)(cnt * L.sl * sizeof(T));
-                mbar_expect_tx(&bar[q], bytes);
-                bulk_g2s(stage_mem + q * kStageBytes, src + (long long)q * per * L.sl, bytes, &bar[q]);
-            }
+__device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
+    return tk.kind ? tk.k1 : min(tk.k1, n + 1) - tk.k0;
+}
+
+// The vectors of one work item (rows of 32: T for window slices, double for aux slices) are
+// gathered by the consumer warps in two halves: near_issue loads this warp's rows (w, w + C, ...)
+// into registers, near_commit (one item later, so that the loads are in flight meanwhile) forms
+// the values and stores them to shared memory.  Window row k: D_{n - k0 - k, j}.  Aux row 0:
+// C_j(n - W) (the static tile carries dt); aux row q + 1: the tail state
+// V_qj(n) = rho_q V_qj(n - 1) + D_{j, n-W}, updated here by its only reader.
+constexpr int kRowsPerWarp = kChunk / kNearConsumers;
+static_assert(kRowsPerWarp * kNearConsumers >= 17, "aux rows (1 + 16 tail terms) fit the row registers");
+
+template <class T>
+__device__ __forceinline__ void near_issue(const StepArgs<T>& a, const NearTask& tk, int n, int warp, int lane,
+                                           double (&r)[kRowsPerWarp], double& dW) {
+    const int nsl = near_slices<T>(tk, n);
+    const bool on = lane < tk.ns;
+    const size_t col = (size_t)tk.s0 + lane;
+    if (!tk.kind) {
+        const int b0 = wrap(n - tk.k0, a.WD);
+#pragma unroll
+        for (int m = 0; m < kRowsPerWarp; ++m) {
+            const int k = warp + m * kNearConsumers;
+            int slot = b0 - k;                     // k < W < WD: one wrap at most
+            slot += slot < 0 ? a.WD : 0;
+            r[m] = (on && k < nsl) ? a.Dring[(size_t)slot * a.N + col] : 0.0;
         }
-        // slip-rate history of the item's sources, while the first stages are in flight
-        for (int e = threadIdx.x; e < nsl * 32; e += kNearThreads) {
-            const int kk = e >> 5, j = e & 31;
-            sd[e] = j < L.ns ? (T)a.Dring[(size_t)pmod(n - (k0 + kk), a.WD) * a.N + L.s0 + j] : (T)0;
-        }
-        __syncthreads();
-        for (int q = 0; q < nst; ++q) {
-            const int s = q % kStages;
-            const bool ok = mbar_wait_bounded(&bar[s], (unsigned)((q / kStages) & 1));
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
+        dW = 0.0;
+    } else {
+        const int t = n - tk.W;
+        dW = (on && t >= 0) ? a.Dring[(size_t)wrap(t, a.WD) * a.N + col] : 0.0;
+#pragma unroll
+        for (int m = 0; m < kRowsPerWarp; ++m) {
+            const int k = warp + m * kNearConsumers;
+            double v = 0.0;
+            if (on && k < nsl) {
+                if (k == 0) v = t >= 0 ? a.Cring[(size_t)wrap(t, a.WC) * a.N + col] : 0.0;
+                else v = a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane];
             }
-            const T* buf = (const T*)(stage_mem + s * kStageBytes);
-            const int cnt = min(per, nsl - q * per);
-            if (lane < L.nr) {
-                for (int kk = warp; kk < cnt; kk += kNearThreads / 32) {
-                    const T* tile = buf + kk * L.sl + lane;
-                    const T* d = sd + (q * per + kk) * 32;
-                    T s0 = (T)0, s1 = (T)0;
-                    int j = 0;
-                    for (; j + 1 < L.ns; j += 2) {
-                        s0 += tile[j * L.nr] * d[j];
-                        s1 += tile[(j + 1) * L.nr] * d[j + 1];
-                    }
-                    if (j < L.ns) s0 += tile[j * L.nr] * d[j];
-                    acc += s0 + s1;
-                }
-            }
-            __syncthreads();
-            const int nq = q + kStages;
-            if (threadIdx.x == 0 && nq < nst) {
-                fence_proxy_async();
-                const int c2 = min(per, nsl - nq * per);
-                const unsigned bytes = (unsigned)(c2 * L.sl * sizeof(T));
-                mbar_expect_tx(&bar[s], bytes);
-                bulk_g2s(stage_mem + s * kStageBytes, src + (long long)nq * per * L.sl, bytes, &bar[s]);
-            }
+            r[m] = v;
         }
-    }
-    if (failed) {
-        if (threadIdx.x == 0) atomicExch(a.err, 1);
-        // give the copies still in flight a bounded chance to land before the CTA exits
-        for (int s = 0; s < kStages; ++s) (void)mbar_wait_bounded(&bar[s], 0u);
-        return;
-    }
-    double accd = (double)acc;
-    if (k0 == 0 && warp == 0 && n - L.W >= 0) {
-        const long long t = (long long)n - L.W;
-        const double cv = lane < L.ns ? a.Cring[(size_t)pmod(t, a.WC) * a.N + L.s0 + lane] : 0.0;
-        for (int j = 0; j < L.ns; ++j) {
-            const double cj = __shfl_sync(0xffffffffu, cv, j);
-            if (lane < L.nr) accd += a.stat[L.stat + j * L.nr + lane] * cj;
-        }
-    }
-    if (k0 == 0 && L.tail >= 0) {
-        // exponential tail beyond the window (extension): V_qj(n) = rho_q V_qj(n-1) + D_{j,n-W},
-        // T_i += sum_qj c_qji V_qj(n); the state update is done once per step, by this CTA
-        const long long t = (long long)n - L.W;
-        const size_t slot = (size_t)pmod(t, a.WD) * a.N;
-        for (int e = threadIdx.x; e < a.soe * L.ns; e += kNearThreads) {
-            const int q = e / L.ns, j = e - q * L.ns;
-            double* v = a.vstate + L.vstate + e;
-            const double vn = a.rho[q] * *v + (t >= 0 ? a.Dring[slot + L.s0 + j] : 0.0);
-            *v = vn;
-        }
-        __syncthreads();
-        if (lane < L.nr)
-            for (int q = warp; q < a.soe; q += kNearThreads / 32) {
-                const double* c = a.tail + L.tail + (long long)q * L.ns * L.nr + lane;
-                const double* v = a.vstate + L.vstate + (long long)q * L.ns;
-                double s = 0.0;
-                for (int j = 0; j < L.ns; ++j) s += c[j * L.nr] * v[j];
-                accd += s;
-            }
-    }
-    red[warp][lane] = accd;
-    __syncthreads();
-    if (warp == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kNearThreads / 32; ++w) s += red[w][lane];
-        a.partial[(size_t)item * 32 + lane] = s;
     }
 }
 
-// Eq. 39, one thread per (block, receiver) entry, blocks in order: f_{l,i} Tbar'_l[n - dm_i]
+template <class T>
+__device__ __forceinline__ void near_commit(const StepArgs<T>& a, const NearTask& tk, int n, int warp, int lane,
+                                            const double (&r)[kRowsPerWarp], double dW, unsigned char* vb) {
+    const int nsl = near_slices<T>(tk, n);
+#pragma unroll
+    for (int m = 0; m < kRowsPerWarp; ++m) {
+        const int k = warp + m * kNearConsumers;
+        if (k < nsl) {
+            if (!tk.kind) {
+                ((T*)vb)[k * 32 + lane] = (T)r[m];
+            } else if (k == 0) {
+                ((double*)vb)[lane] = r[m];
+            } else {
+                double vn = 0.0;
+                if (lane < tk.ns) {
+                    vn = a.rho[k - 1] * r[m] + dW;
+                    a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane] = vn;
+                }
+                ((double*)vb)[k * 32 + lane] = vn;
+            }
+        }
+    }
+}
+
+template <class T>
+struct NearCfg {
+    static constexpr int stages = sizeof(T) == 4 ? 5 : 4;          // shared-memory pipeline depth
+    static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(T);  // one item's vectors
+    static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
+};
+static_assert(17 * 32 * 8 <= kChunk * 32 * 4, "aux vectors (1 + 16 tail terms) fit a vector buffer");
+
+// Near field (App. E), persistent and warp-specialised.  Each CTA owns a list of work items
+// (window slices [k0, k1) of a leaf, or the leaf's FP64 aux slices: static tile and exponential
+// tail).  One producer thread streams the items' slices through a ring of shared-memory stages
+// (cp.async.bulk, full/empty mbarriers), continuing across item boundaries.  The consumer warps
+// load the vectors of the next item into a second shared buffer while they consume the current
+// one; consumer warp w takes slices w, w + kNearConsumers, ... of each stage, lane i = receiver i,
+// reading its coefficients and the vector 16 bytes at a time.  At the end of an item the
+// consumers' sums are combined in FP64 into the item's partial-sum slot.
+template <class T>
+__global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
+    using C = NearCfg<T>;
+    extern __shared__ __align__(128) unsigned char near_smem[];
+    __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
+    __shared__ double red[2][kNearConsumers][32];
+    __shared__ int abort_flag;
+    const int n = step_index(a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
+    unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kNearConsumers);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int g = 0;   // running stage counter, identical in producer and consumers
+    if (warp == kNearConsumers) {
+        // ---------------- producer (one thread)
+        if (lane == 0) {
+            const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
+            for (int ti = t0; ti < t1; ++ti) {
+                const NearTask tk = a.tasks[ti];
+                const int esz = tk.kind ? 8 : (int)sizeof(T);
+                const int nsl = near_slices<T>(tk, n);
+                const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
+                const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
+                const unsigned char* src = tk.kind ? (const unsigned char*)(a.stat + tk.off)
+                                                   : (const unsigned char*)(a.tensor + tk.off);
+                for (int q = 0; q < nst; ++q, ++g) {
+                    const int s = g % C::stages;
+                    if (!mbar_wait_bounded(&empty[s], (unsigned)(((g / C::stages) & 1) ^ 1))) {
+                        abort_flag = 1;
+                        atomicExch(a.err, 1);
+                    }
+                    const int cnt = min(per, nsl - q * per);
+                    const unsigned bytes = (unsigned)(cnt * tk.sl * esz);
+                    fence_proxy_async();
+                    mbar_expect_tx(&full[s], bytes);
+                    bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
+                                  policy);
+                }
+            }
+        }
+    } else {
+        // ---------------- consumers
+        double rows[kRowsPerWarp], dW = 0.0;
+        NearTask nxt;
+        if (t0 < t1) {
+            nxt = a.tasks[t0];
+            near_issue(a, nxt, n, warp, lane, rows, dW);
+            near_commit(a, nxt, n, warp, lane, rows, dW, vbuf);
+        }
+        consumer_barrier();
+        int par = 0;
+        for (int ti = t0; ti < t1; ++ti, par ^= 1) {
+            const NearTask tk = nxt;
+            // the next item's vector loads stay in flight while this item is consumed
+            if (ti + 1 < t1) {
+                nxt = a.tasks[ti + 1];
+                near_issue(a, nxt, n, warp, lane, rows, dW);
+            }
+            const unsigned char* vrows = vbuf + par * C::vec_bytes;
+            const int esz = tk.kind ? 8 : (int)sizeof(T);
+            const int nsl = near_slices<T>(tk, n);
+            const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
+            const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
+            const int li = lane < tk.nr ? lane : 0;     // lanes past nr read a valid element, unused
+            T acc = (T)0;
+            double accd = 0.0;
+            for (int q = 0; q < nst; ++q, ++g) {
+                const int s = g % C::stages;
+                const int cnt = min(per, nsl - q * per);
+                if (!mbar_wait_bounded(&full[s], (unsigned)((g / C::stages) & 1))) {
+                    abort_flag = 1;
+                    atomicExch(a.err, 1);
+                }
+                const unsigned char* buf = near_smem + s * kNearStageBytes;
+                for (int kk = warp; kk < cnt; kk += kNearConsumers) {
+                    const int row = q * per + kk;
+                    if (!tk.kind && sizeof(T) == 4) {
+                        // 4 sources per 16-byte load: tile row jb holds sources 4 jb .. 4 jb + 3
+                        const float4* tile = (const float4*)(buf + (size_t)kk * tk.sl * 4) + li;
+                        const float4* d = (const float4*)(vrows + row * 128);
+                        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                        const int nb = (tk.ns + 3) >> 2;
+                        if (nb == 8 && tk.nr == 32) {
+#pragma unroll
+                            for (int jb = 0; jb < 8; ++jb) {
+                                const float4 x = tile[jb * 32];
+                                const float4 y = d[jb];
+                                s0 = fmaf(x.x, y.x, s0);
+                                s1 = fmaf(x.y, y.y, s1);
+                                s2 = fmaf(x.z, y.z, s2);
+                                s3 = fmaf(x.w, y.w, s3);
+                            }
+                        } else {
+                            for (int jb = 0; jb < nb; ++jb) {
+                                const float4 x = tile[jb * tk.nr];
+                                const float4 y = d[jb];
+                                s0 = fmaf(x.x, y.x, s0);
+                                s1 = fmaf(x.y, y.y, s1);
+                                s2 = fmaf(x.z, y.z, s2);
+                                s3 = fmaf(x.w, y.w, s3);
+                            }
+                        }
+                        acc += (T)((s0 + s1) + (s2 + s3));
+                    } else {
+                        // FP64 slices (window of the FP64 plan, or aux): 2 sources per load
+                        const double2* tile = (const double2*)(buf + (size_t)kk * tk.sl * 8) + li;
+                        const double2* d = (const double2*)(vrows + row * 256);
+                        double s0 = 0.0, s1 = 0.0;
+                        const int nb = (tk.ns + 1) >> 1;
+                        for (int jb = 0; jb < nb; ++jb) {
+                            const double2 x = tile[jb * tk.nr];
+                            const double2 y = d[jb];
+                            s0 = fma(x.x, y.x, s0);
+                            s1 = fma(x.y, y.y, s1);
+                        }
+                        if (tk.kind) accd += s0 + s1;
+                        else acc += (T)(s0 + s1);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            if (ti + 1 < t1) near_commit(a, nxt, n, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            red[par][warp][lane] = lane < tk.nr ? (double)acc + accd : 0.0;
+            consumer_barrier();   // also publishes the next item's vectors
+            if (warp == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < kNearConsumers; ++w) sum += red[par][w][lane];
+                a.partial[(size_t)tk.item * 32 + lane] = sum;
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) {
+        // a wait gave up: give the copies that may still be in flight a bounded chance to land
+        for (int s = 0; s < C::stages; ++s) {
+            (void)mbar_wait_bounded(&full[s], 0u);
+            (void)mbar_wait_bounded(&full[s], 1u);
+        }
+    }
+}
+
+// Eq. 39: one warp per task of receivers of one block; 2^lg lanes per receiver split the rank
+// index l, so the receiver's factor row f_{i, .} and ring slot row are read coalesced; the value
+// f_{., i} . Tbar'[n - dm_i] goes to the receiver's CSR slot.  A block kept exact with F = I
+// reads one ring entry per receiver (2^lg = 1).
 template <class T>
 __global__ void far_eval_kernel(StepArgs<T> a) {
     const int n = step_index(a);
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.n_ent) return;
-    const SbDev sb = a.sbs[a.e_sb[e]];
-    const int il = a.e_il[e];
-    const long long t = (long long)n - a.ints[sb.dm + il];
-    const T* f = a.fac + sb.f + (long long)il * sb.rank;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= a.n_evt) return;   // warp-uniform
+    const int4 tk = a.ev_tasks[w];
+    const SbDev& sb = a.sbs[tk.x];
+    const int lg = tk.w, G = 1 << lg;
+    const int gi = lane >> lg, lj = lane & (G - 1);
+    const int il = tk.y + gi;
+    const bool valid = gi < tk.z;
     double s = 0.0;
-    const bool tr = sb.kind == SB_TR;
-    const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
-    const int len = tr ? sb.LZ : sb.L;
-    const double* r = base + (long long)pmod(t, len) * sb.rank;
-    if (a.phi) {   // exact delay dm_i + phi_i: linear interpolation with the next older step
-        const double ph = a.phi[sb.phi + il];
-        const double* r1 = base + (long long)pmod(t - 1, len) * sb.rank;
-        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * ((1.0 - ph) * r[l] + ph * r1[l]);
-    } else {
-        for (int l = 0; l < sb.rank; ++l) s += (double)f[l] * r[l];
+    if (valid) {
+        const bool tr = sb.kind == SB_TR;
+        const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
+        const int len = tr ? sb.LZ : sb.L;
+        const int rank = sb.rank;
+        const int t = n - a.ints[sb.dm + il];
+        const double* r = base + (long long)wrap(t, len) * rank;
+        if (a.phi) {   // exact delay dm_i + phi_i: linear interpolation with the next older step
+            const double ph = a.phi[sb.phi + il];
+            const double* r1 = base + (long long)wrap(t - 1, len) * rank;
+            if (sb.ident == 1) {
+                s = (1.0 - ph) * r[il] + ph * r1[il];
+            } else {
+                const T* f = a.fac + sb.f + (long long)il * rank;
+                for (int l = lj; l < rank; l += G) s += (double)f[l] * ((1.0 - ph) * r[l] + ph * r1[l]);
+            }
+        } else if (sb.ident == 1) {
+            s = r[il];
+        } else {
+            const T* f = a.fac + sb.f + (long long)il * rank;
+            for (int l = lj; l < rank; l += G) s += (double)f[l] * r[l];
+        }
     }
-    a.fval[a.e_pos[e]] = s;
+    for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (valid && lj == 0) a.fval[a.e_pos[sb.e0 + il]] = s;
 }
 
 // one warp per receiver: sum of its far entries and near-field partials, fixed order
@@ -435,7 +656,7 @@ __global__ void gather_kernel(StepArgs<T> a) {
     for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
     for (int e = a.np_ptr[p] + lane; e < a.np_ptr[p + 1]; e += 32) s += a.partial[a.np_idx[e]];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.T_out[(a.n_dev ? (long long)(n - a.n_base) * a.io_stride : 0) + a.perm[p]] = s;
+    if (lane == 0) a.T_out[io_offset(a, n) + a.perm[p]] = s;
 }
 
 // Local friction solve (geometry order): T_pred holds the traction change with D_n = 0.
@@ -530,10 +751,11 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
             v = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
         }
-        tensor[L.tensor + (long long)k * L.sl + (q % ((long long)L.ns * L.nr))] = (T)v;
+        constexpr int v4 = 16 / (int)sizeof(T);   // source-interleaved slices (plan.h)
+        tensor[L.tensor + (long long)k * L.sl + ((jl / v4) * L.nr + il) * v4 + jl % v4] = (T)v;
         if (k == 0) {
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
-            stat[L.stat + (long long)jl * L.nr + il] = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
+            stat[L.stat + ((jl / 2) * L.nr + il) * 2 + jl % 2] = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
         }
     }
 }
@@ -600,18 +822,21 @@ struct fdph_plan_s {
     SbDev* sbs = nullptr;
     void* fac = nullptr;
     int *ints = nullptr, *run_delay = nullptr, *run_start = nullptr, *run_len = nullptr, *src_order = nullptr;
-    int *scat_l = nullptr, *e_sb = nullptr, *e_il = nullptr, *e_pos = nullptr;
+    int* e_pos = nullptr;
+    int4 *sc_tasks = nullptr, *ev_tasks = nullptr;
+    int n_sct = 0, n_evt = 0;
     double* fval = nullptr;
-    int *scat_sb = nullptr, *scat_run = nullptr, *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
+    int *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
         *tr_l = nullptr, *g_ptr = nullptr, *g_sb = nullptr, *g_il = nullptr;
     NearDev* near = nullptr;
-    int4* items = nullptr;
+    NearTask* tasks = nullptr;
+    int* cta_ptr = nullptr;
+    int n_cta = 0;
     void* tensor = nullptr;
     double* stat = nullptr;
     int *np_ptr = nullptr, *np_idx = nullptr;
     int* err = nullptr;
     double* rho = nullptr;
-    void* tail = nullptr;
     // rupture state
     bool rupture = false;
     FrictionDev fr;
@@ -630,6 +855,15 @@ struct fdph_plan_s {
     // graph of one step for fdph_run (replayed with the step index in n_dev)
     cudaGraphExec_t graph = nullptr;
     int* n_dev = nullptr;
+    // branches of a step that run concurrently with the near field: [0] FIR + scatter,
+    // [1] transient convolution + Eq. 39 evaluation (fork after push, join before gather)
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    // fdph_run_host: device staging ring, copy streams and their events
+    static const int kIoSlots = 8;
+    double *io_D = nullptr, *io_T = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[kIoSlots] = {}, ev_out[kIoSlots] = {}, ev_free[kIoSlots] = {};
 };
 
 template <class T>
@@ -678,15 +912,12 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.run_start = P->run_start;
     a.run_len = P->run_len;
     a.src_order = P->src_order;
-    a.scat_sb = P->scat_sb;
-    a.scat_run = P->scat_run;
-    a.scat_l = P->scat_l;
-    a.e_sb = P->e_sb;
-    a.e_il = P->e_il;
+    a.sc_tasks = P->sc_tasks;
+    a.n_sct = P->n_sct;
+    a.ev_tasks = P->ev_tasks;
+    a.n_evt = P->n_evt;
     a.e_pos = P->e_pos;
-    a.n_ent = (int)P->hp.e_sb.size();
     a.fval = P->fval;
-    a.n_scat = (int)P->hp.scat_sb.size();
     a.fir_sb = P->fir_sb;
     a.fir_j = P->fir_j;
     a.n_fir = (int)P->hp.fir_sb.size();
@@ -700,7 +931,9 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.zring = P->zring;
     a.dhat = P->dhat;
     a.near = P->near;
-    a.items = P->items;
+    a.tasks = P->tasks;
+    a.cta_ptr = P->cta_ptr;
+    a.n_cta = P->n_cta;
     a.n_items = (int)P->hp.items.size();
     a.tensor = (const T*)P->tensor;
     a.stat = P->stat;
@@ -714,7 +947,6 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.trcoef = P->trcoef;
     a.phi = P->hp.interp ? P->phi : nullptr;
     a.vstate = P->vstate;
-    a.tail = (const double*)P->tail;
     return a;
 }
 
@@ -731,16 +963,36 @@ struct ProfScope {
 template <class T>
 static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
+    if (!P->prof && P->side[0]) {
+        // Within a step, FIR + scatter (writes ring slots n + delay >= n + 1), the transient
+        // convolution + Eq. 39 (read slots <= n - min dm, completed by earlier steps; causality
+        // min(dm + delay) >= 1) and the near field touch disjoint data once push is done.
+        cudaEventRecord(P->ev_fork, s);
+        cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
+        cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
+        if (a.n_fir) fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, P->side[0]>>>(a);
+        if (a.n_sct) scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, P->side[0]>>>(a);
+        if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, P->side[1]>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, P->side[1]>>>(a);
+        if (a.n_cta) near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
+        cudaEventRecord(P->ev_join[0], P->side[0]);
+        cudaEventRecord(P->ev_join[1], P->side[1]);
+        cudaStreamWaitEvent(s, P->ev_join[0], 0);
+        cudaStreamWaitEvent(s, P->ev_join[1], 0);
+        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+        return;
+    }
+    // serial order (per-kernel timing)
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
-    if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
+    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
-    if (a.n_items) {
+    if (a.n_cta) {
         ProfScope ps(P, 4);
-        near_kernel<T><<<a.n_items, kNearThreads, kStages * kStageBytes + kChunk * 32 * sizeof(T), s>>>(a);
+        near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_ent) far_eval_kernel<T><<<blocks(a.n_ent, 128), 128, 0, s>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
         gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
     }
 }
@@ -753,10 +1005,10 @@ static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
     return FDPH_OK;
 }
 
-// `steps` steps as replays of one captured step graph; kernels read the step index from n_dev
-// (advanced by the last node) and offset D / T by one row per step
+// One step captured as a CUDA graph that reads its step index from n_dev (advanced by the last
+// node) and offsets D / T by one row per step (modulo io_ring rows when io_ring > 0).
 template <class T>
-static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
+static int capture_step_graph(fdph_plan_t P, const double* D, double* Tout, int io_ring, cudaGraphExec_t* ex) {
     if (!P->n_dev) {
         int rc = dalloc(P, &P->n_dev, 1);
         if (rc) return rc;
@@ -766,9 +1018,9 @@ static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
     a.n_dev = P->n_dev;
     a.n_base = P->n;
     a.io_stride = P->N;
+    a.io_ring = io_ring;
     set_step_kernel<<<1, 1, 0, s>>>(P->n_dev, P->n);
     cudaGraph_t g = nullptr;
-    cudaGraphExec_t ex = nullptr;
     FDPH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     enqueue_step<T>(P, a, s);
     advance_step_kernel<<<1, 1, 0, s>>>(P->n_dev);
@@ -777,19 +1029,81 @@ static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
         set_error(std::string("graph capture: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
     }
-    e = cudaGraphInstantiate(&ex, g, 0);
+    e = cudaGraphInstantiate(ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
     }
+    return FDPH_OK;
+}
+
+// `steps` steps as replays of one captured step graph
+template <class T>
+static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
+    cudaGraphExec_t ex = nullptr;
+    int rc = capture_step_graph<T>(P, D, Tout, 0, &ex);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < steps; ++k) {
-        e = cudaGraphLaunch(ex, s);
+        e = cudaGraphLaunch(ex, P->stream);
         if (e != cudaSuccess) break;
     }
     cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) {
         set_error(std::string("graph launch: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    P->n += steps;
+    return FDPH_OK;
+}
+
+// Host-buffer steps: step k's D row goes host -> staging slot k % S on the h2d stream, the
+// step graph runs on the plan stream once that copy is done, and its T row goes back on the
+// d2h stream; slot k is reused by step k + S after T of step k has left it.
+template <class T>
+static int run_host(fdph_plan_t P, int steps, const double* D_host, double* T_host) {
+    const int S = fdph_plan_s::kIoSlots;
+    const size_t row = (size_t)P->N;
+    if (!P->io_D) {
+        int rc;
+        if ((rc = dalloc(P, &P->io_D, S * row)) || (rc = dalloc(P, &P->io_T, S * row))) return rc;
+        FDPH_CUDA(cudaStreamCreateWithFlags(&P->h2d, cudaStreamNonBlocking));
+        FDPH_CUDA(cudaStreamCreateWithFlags(&P->d2h, cudaStreamNonBlocking));
+        for (int q = 0; q < S; ++q) {
+            FDPH_CUDA(cudaEventCreateWithFlags(&P->ev_in[q], cudaEventDisableTiming));
+            FDPH_CUDA(cudaEventCreateWithFlags(&P->ev_out[q], cudaEventDisableTiming));
+            FDPH_CUDA(cudaEventCreateWithFlags(&P->ev_free[q], cudaEventDisableTiming));
+        }
+    }
+    // the staging slots must not be reused before work still queued from an earlier call is done
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->d2h));
+    cudaGraphExec_t ex = nullptr;
+    int rc = capture_step_graph<T>(P, P->io_D, P->io_T, S, &ex);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        const int q = k % S;
+        if (k >= S) e = cudaStreamWaitEvent(P->h2d, P->ev_free[q], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(P->io_D + q * row, D_host + (size_t)k * row, row * sizeof(double),
+                                cudaMemcpyHostToDevice, P->h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_in[q], P->h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_in[q], 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, P->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_out[q], P->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->d2h, P->ev_out[q], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T_host + (size_t)k * row, P->io_T + q * row, row * sizeof(double),
+                                cudaMemcpyDeviceToHost, P->d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_free[q], P->d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess) {
+        set_error(std::string("fdph_run_host: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
     }
     P->n += steps;
@@ -847,20 +1161,20 @@ static int launch_rupture_step(fdph_plan_t P, double* D, double* Tout) {
     cudaStream_t s = P->stream;
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }          // D_n = 0
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
-    if (a.n_items) {
+    if (a.n_cta) {
         ProfScope ps(P, 4);
-        near_kernel<T><<<a.n_items, kNearThreads, kStages * kStageBytes + kChunk * 32 * sizeof(T), s>>>(a);
+        near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_ent) far_eval_kernel<T><<<blocks(a.n_ent, 128), 128, 0, s>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
         gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
     }
     friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, Tout);
     a.D_in = D;                                                                                // commit D_n
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
-    if (a.n_scat) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks(a.n_scat, 128), 128, 0, s>>>(a); }
+    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
     FDPH_CUDA(cudaGetLastError());
     return FDPH_OK;
 }
@@ -931,18 +1245,19 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
     for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
     int chunk = kChunk;
     while (chunk > 8 && slices / chunk < 4LL * 152 * 3) chunk /= 2;
-    finish_near_layout(hp, W, has_tail, chunk);
+    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(T));
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
-        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, L.sla, 0, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
                  (long long)L.vstate};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
     T* tens = nullptr;
-    if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &P->stat, hp.near_stat_len))) return rc;
+    if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &P->stat, hp.near_aux_len))) return rc;
     P->tensor = tens;
     if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(T)));  // slice padding
+    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(P->stat, 0, hp.near_aux_len * sizeof(double)));
     for (int l = 0; l < nl; ++l) {
         const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
         if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
@@ -951,11 +1266,10 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         if (L.W == 0) {
             // temporarily fill one k-slice into a scratch to get the static tile
             T* tmp = nullptr;
-            if ((rc = dalloc(P, &tmp, (size_t)L.ns * L.nr))) return rc;
+            if ((rc = dalloc(P, &tmp, (size_t)L.sl))) return rc;
             NearDev L1 = L;
             L1.W = 1;
             L1.tensor = 0;
-            L1.sl = L.ns * L.nr;
             near_fill_kernel<T><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
                                                                             in.mu, in.cs, tmp, P->stat);
         } else {
@@ -987,7 +1301,10 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         FDPH_CUDA(cudaGetLastError());
         std::vector<double> gh((size_t)ntp * in.soe), ch((size_t)ntp * in.soe);
         FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        std::vector<double> tail_h(hp.near_tail_len);
+        // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
+        std::vector<size_t> toff(tl.size() + 1, 0);
+        for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sla;
+        std::vector<double> tail_h(toff.back(), 0.0);
 #pragma omp parallel for schedule(dynamic, 8)
         for (long t = 0; t < (long)tl.size(); ++t) {
             const NearDev& L = tl[t];
@@ -996,17 +1313,67 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             for (int il = 0; il < L.nr; ++il)
                 for (int jl = 0; jl < L.ns; ++jl)
                     for (int q = 0; q < in.soe; ++q)
-                        tail_h[L.tail + ((size_t)q * L.ns + jl) * L.nr + il] =
+                        tail_h[toff[t] + (size_t)q * L.sla + ((size_t)(jl / 2) * L.nr + il) * 2 + jl % 2] =
                             ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
         }
-        double* dt_ = nullptr;
-        if ((rc = upload(P, &dt_, tail_h))) return rc;
-        P->tail = dt_;
+        for (size_t t = 0; t < tl.size(); ++t)
+            FDPH_CUDA(cudaMemcpy(P->stat + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(double),
+                                 cudaMemcpyHostToDevice));
     }
-    std::vector<int4> it(hp.items.size());
-    for (size_t q = 0; q < it.size(); ++q) it[q] = make_int4(hp.items[q].leaf, hp.items[q].k0, hp.items[q].k1, 0);
-    if ((rc = upload(P, &P->items, it)) || (rc = upload(P, &P->np_ptr, hp.np_ptr)) ||
-        (rc = upload(P, &P->np_idx, hp.np_idx)))
+    // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
+    // largest first to the least-loaded CTA (steady-state bytes)
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<T>::smem));
+    int sms = 0, per_sm = 0;
+    FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T>, kNearThreads, NearCfg<T>::smem));
+    const int ni = (int)hp.items.size();
+    const int ncta = std::max(1, std::min(ni, sms * std::max(per_sm, 1)));
+    std::vector<NearTask> tasks_all(ni);
+    std::vector<double> cost(ni);
+    for (int q = 0; q < ni; ++q) {
+        const NearItem& it = hp.items[q];
+        const NearLeaf& L = hp.near[it.leaf];
+        NearTask t;
+        memset(&t, 0, sizeof(t));
+        t.off = it.kind ? (long long)L.stat : (long long)L.tensor + (long long)it.k0 * L.sl;
+        t.item = q;
+        t.k0 = it.k0;
+        t.k1 = it.k1;
+        t.kind = it.kind;
+        t.nr = L.nr;
+        t.ns = L.ns;
+        t.sl = it.kind ? L.sla : L.sl;
+        t.s0 = L.s0;
+        t.W = L.W;
+        t.vstate = (int)L.vstate;
+        tasks_all[q] = t;
+        cost[q] = (double)(it.k1 - it.k0) * t.sl * (it.kind ? 8.0 : (double)sizeof(T)) + 4096.0;
+    }
+    std::vector<int> order(ni);
+    for (int q = 0; q < ni; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<int>> own(ncta);
+    std::vector<std::pair<double, int>> heap;
+    for (int c = 0; c < ncta; ++c) heap.push_back({0.0, c});
+    auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int q : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        heap.back().first += cost[q];
+        own[heap.back().second].push_back(q);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<NearTask> tasks;
+    std::vector<int> cptr(1, 0);
+    for (int c = 0; c < ncta; ++c) {
+        for (int q : own[c]) tasks.push_back(tasks_all[q]);
+        cptr.push_back((int)tasks.size());
+    }
+    P->n_cta = ni ? ncta : 0;
+    if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
+        (rc = upload(P, &P->np_ptr, hp.np_ptr)) || (rc = upload(P, &P->np_idx, hp.np_idx)))
         return rc;
     FDPH_CUDA(cudaDeviceSynchronize());
     return FDPH_OK;
@@ -1034,15 +1401,24 @@ static void fill_stats(fdph_plan_t P) {
         near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
         flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
         if (L.tail >= 0) {                                                     // tail coefficients + states
-            near_b += (double)hp.soe * L.ns * L.nr * ps + (double)hp.soe * L.ns * 16.0;
+            near_b += (double)hp.soe * L.ns * L.nr * 8.0 + (double)hp.soe * L.ns * 16.0;   // FP64 coefficients
             flops += 2.0 * hp.soe * L.ns * (L.nr + 1.0);
         }
     }
     for (const SubBlock& sb : hp.sbs) {
         const double r = sb.rank;
-        far_b += (sb.nr + sb.ns) * r * ps + (sb.nr + sb.ns) * 4.0;          // f, g, delays
-        far_b += sb.nr * r * 8.0 + sb.nruns * r * 16.0;                     // ring reads / RMW
-        flops += 2.0 * (sb.nr + sb.ns) * r;
+        far_b += (sb.nr + sb.ns) * 4.0;                                        // delays
+        if (sb.ident == 1) {          // F = I: one ring read per receiver
+            far_b += sb.nr * 8.0 + sb.ns * r * ps + sb.nruns * r * 16.0;
+            flops += 2.0 * sb.ns * r;
+        } else if (sb.ident == 2) {   // G = I: one ring store per source
+            far_b += sb.nr * r * (ps + 8.0) + sb.ns * 8.0;
+            flops += 2.0 * sb.nr * r;
+        } else {
+            far_b += (sb.nr + sb.ns) * r * ps;                                 // f, g
+            far_b += sb.nr * r * 8.0 + sb.nruns * r * 16.0;                    // ring reads / RMW
+            flops += 2.0 * (sb.nr + sb.ns) * r;
+        }
         if (sb.kind == SB_F) {
             far_b += (double)sb.taps * sb.ns * (ps + 8.0) + sb.ns * 16.0;   // h, D history, Dhat
             flops += 2.0 * sb.taps * sb.ns;
@@ -1060,7 +1436,7 @@ static void fill_stats(fdph_plan_t P) {
     s.state_bytes = (long long)P->state_bytes;
     long long arena = 0;
     arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
-    arena += (long long)(hp.near_tensor_len * ps) + hp.near_stat_len * 8 + (long long)(hp.near_tail_len * ps);
+    arena += (long long)(hp.near_tensor_len * ps) + hp.near_aux_len * 8;
     s.arena_bytes = arena;
 }
 
@@ -1226,6 +1602,16 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         }
         P->own_stream = true;
     }
+    for (int k = 0; k < 2; ++k)
+        if (cudaStreamCreateWithFlags(&P->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_join[k], cudaEventDisableTiming) != cudaSuccess) {
+            set_error("cudaStreamCreate / cudaEventCreate failed");
+            return fail(FDPH_E_CUDA);
+        }
+    if (cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("cudaEventCreate failed");
+        return fail(FDPH_E_CUDA);
+    }
     PlanInputs in = make_inputs(material, dt, M, eps, p);
     Elements el = make_elements(geometry->n, geometry->xy);
     HostPlan& hp = P->hp;
@@ -1245,16 +1631,30 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     for (size_t q = 0; q < sd.size(); ++q) {
         const SubBlock& b = hp.sbs[q];
         sd[q] = {b.kind, b.rank, b.r0, b.nr, b.s0, b.ns, b.L, b.LZ, b.taps, b.maxdelay, b.mindm, b.run0,
-                 b.soe, 0, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
+                 b.soe, b.ident, b.e0, 0, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
                  (long long)b.dhat, (long long)b.delay, (long long)b.dm, (long long)b.ustate, (long long)b.trc,
                  (long long)b.phi};
     }
+    // warp tasks: 2^lg lanes per run (scatter) / per receiver (Eq. 39), 2^lg the rank rounded up
+    // to a power of two (at most 32); identity factors need one lane
+    std::vector<int4> sct, evt;
+    for (size_t q = 0; q < hp.sbs.size(); ++q) {
+        const SubBlock& b = hp.sbs[q];
+        int lg = 0;
+        while ((1 << lg) < std::min(b.rank, 32)) ++lg;
+        const int lg_s = b.ident == 2 ? 0 : lg, lg_e = b.ident == 1 ? 0 : lg;
+        for (int r = 0; r < b.nruns; r += 32 >> lg_s)
+            sct.push_back(make_int4((int)q, b.run0 + r, std::min(32 >> lg_s, b.nruns - r), lg_s));
+        for (int i = 0; i < b.nr; i += 32 >> lg_e)
+            evt.push_back(make_int4((int)q, i, std::min(32 >> lg_e, b.nr - i), lg_e));
+    }
+    P->n_sct = (int)sct.size();
+    P->n_evt = (int)evt.size();
+    if ((rc = upload(P, &P->sc_tasks, sct)) || (rc = upload(P, &P->ev_tasks, evt))) return fail(rc);
     if ((rc = upload(P, &P->perm, hp.perm)) || (rc = upload(P, &P->sbs, sd)) || (rc = upload(P, &P->ints, hp.ints)) ||
         (rc = upload(P, &P->run_delay, hp.run_delay)) || (rc = upload(P, &P->run_start, hp.run_start)) ||
         (rc = upload(P, &P->run_len, hp.run_len)) || (rc = upload(P, &P->src_order, hp.src_order)) ||
-        (rc = upload(P, &P->scat_sb, hp.scat_sb)) || (rc = upload(P, &P->scat_run, hp.scat_run)) ||
-        (rc = upload(P, &P->scat_l, hp.scat_l)) || (rc = upload(P, &P->e_sb, hp.e_sb)) ||
-        (rc = upload(P, &P->e_il, hp.e_il)) || (rc = upload(P, &P->e_pos, hp.e_pos)) ||
+        (rc = upload(P, &P->e_pos, hp.e_pos)) ||
         (rc = upload(P, &P->fir_sb, hp.fir_sb)) || (rc = upload(P, &P->fir_j, hp.fir_j)) ||
         (rc = upload(P, &P->tr_sb, hp.tr_sb)) || (rc = upload(P, &P->tr_l, hp.tr_l)) ||
         (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
@@ -1277,10 +1677,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     rc = P->precision == FDPH_FP32 ? build_near<float>(P, in) : build_near<double>(P, in);
     if (rc) return fail(rc);
     stamp("near field (windows, tails)");
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kStages * kStageBytes + kChunk * 32 * (int)sizeof(double)));
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kStages * kStageBytes + kChunk * 32 * (int)sizeof(float)));
+
     if ((rc = dalloc(P, &P->err, 1))) return fail(rc);
     FDPH_CUDA(cudaMemset(P->err, 0, sizeof(int)));
     // ---- state
@@ -1294,7 +1691,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if ((rc = st(&P->Dring, (size_t)P->WD * P->N)) || (rc = st(&P->Cring, (size_t)P->WC * P->N)) ||
         (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
         (rc = st(&P->zring, hp.zring_len)) || (rc = st(&P->dhat, hp.dhat_len)) ||
-        (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_sb.size())) ||
+        (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_pos.size())) ||
         (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
         return fail(rc);
     P->state_bytes = sb;
@@ -1343,6 +1740,32 @@ int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
         if (rc) return rc;
     }
     return FDPH_OK;
+}
+
+int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_host) {
+    if (!P || !D_host || !T_host || steps < 0) return FDPH_E_ARG;
+    if (P->n + steps > P->M) {
+        set_error("run would pass step M");
+        return FDPH_E_STATE;
+    }
+    if (steps == 0) return FDPH_OK;
+    int rc;
+    if (P->prof) {   // per-kernel timing: plain launches, one staging row
+        if (!P->dD && ((rc = dalloc(P, &P->dD, P->N)) || (rc = dalloc(P, &P->dT, P->N)))) return rc;
+        for (int k = 0; k < steps; ++k) {
+            FDPH_CUDA(cudaMemcpyAsync(P->dD, D_host + (size_t)k * P->N, P->N * sizeof(double),
+                                      cudaMemcpyHostToDevice, P->stream));
+            if ((rc = step_impl(P, P->dD, P->dT))) return rc;
+            FDPH_CUDA(cudaMemcpyAsync(T_host + (size_t)k * P->N, P->dT, P->N * sizeof(double),
+                                      cudaMemcpyDeviceToHost, P->stream));
+        }
+        FDPH_CUDA(cudaStreamSynchronize(P->stream));
+        return check_device_error(P);
+    }
+    rc = P->precision == FDPH_FP32 ? run_host<float>(P, steps, D_host, T_host)
+                                   : run_host<double>(P, steps, D_host, T_host);
+    if (rc) return rc;
+    return check_device_error(P);
 }
 
 int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
@@ -1541,6 +1964,20 @@ void fdph_destroy(fdph_plan_t P) {
     if (P->stream) cudaStreamSynchronize(P->stream);
     prof_drain(P);
     if (P->graph) cudaGraphExecDestroy(P->graph);
+    for (int k = 0; k < 2; ++k) {
+        if (P->side[k]) cudaStreamDestroy(P->side[k]);
+        if (P->ev_join[k]) cudaEventDestroy(P->ev_join[k]);
+    }
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->h2d) cudaStreamSynchronize(P->h2d);
+    if (P->d2h) cudaStreamSynchronize(P->d2h);
+    if (P->h2d) cudaStreamDestroy(P->h2d);
+    if (P->d2h) cudaStreamDestroy(P->d2h);
+    for (int q = 0; q < fdph_plan_s::kIoSlots; ++q) {
+        if (P->ev_in[q]) cudaEventDestroy(P->ev_in[q]);
+        if (P->ev_out[q]) cudaEventDestroy(P->ev_out[q]);
+        if (P->ev_free[q]) cudaEventDestroy(P->ev_free[q]);
+    }
     for (void* p : P->allocs) cudaFree(p);
     if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
     delete P;

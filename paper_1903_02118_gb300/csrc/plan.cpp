@@ -270,6 +270,9 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.phi = phi_off;
             sb.soe = soe;
             sb.trc = trc ? append(hp.trcoef, trc->data(), trc->size()) : 0;
+            sb.ident = lr.exact ? (lr.m <= lr.n ? 1 : 2) : 0;
+            sb.e0 = (int32_t)hp.far_nent;
+            hp.far_nent += o.nr;
             sb.ustate = hp.ustate_len;
             hp.ustate_len += (int64_t)sb.rank * soe;
             if (kind == SB_TR) {
@@ -304,12 +307,6 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.nruns = (int32_t)hp.run_delay.size() - sb.run0;
             const int id = (int)hp.sbs.size();
             hp.sbs.push_back(sb);
-            for (int r = 0; r < sb.nruns; ++r)
-                for (int l = 0; l < sb.rank; ++l) {
-                    hp.scat_sb.push_back(id);
-                    hp.scat_run.push_back(sb.run0 + r);
-                    hp.scat_l.push_back(l);
-                }
             if (kind == SB_F)
                 for (int j = 0; j < o.ns; ++j) {
                     hp.fir_sb.push_back(id);
@@ -352,20 +349,20 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         const SubBlock& sb = hp.sbs[id];
         for (int il = 0; il < sb.nr; ++il) {
             const int p = sb.r0 + il;
-            hp.e_sb.push_back(id);
-            hp.e_il.push_back(il);
             hp.e_pos.push_back(hp.g_ptr[p] + cnt[p]++);
         }
     }
     return 0;
 }
 
-void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk) {
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
+                        int vec) {
     const int nl = (int)hp.near_r0.size();
     hp.near.resize(nl);
     hp.items.clear();
     hp.near_tensor_len = 0;
-    hp.near_stat_len = 0;
+    hp.near_aux_len = 0;
+    hp.near_tail_len = 0;
     hp.max_W = 0;
     std::vector<std::vector<int32_t>> slots(hp.n);
     for (int l = 0; l < nl; ++l) {
@@ -375,28 +372,31 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::
         L.s0 = hp.near_s0[l];
         L.ns = hp.near_ns[l];
         L.W = W[l];
-        L.sl = (L.ns * L.nr + 3) / 4 * 4;
-        L.tensor = hp.near_tensor_len;                     // stays a multiple of 4 elements
+        L.sl = (L.ns + vec - 1) / vec * vec * L.nr;
+        L.sla = (L.ns + 1) / 2 * 2 * L.nr;
+        L.tensor = hp.near_tensor_len;                     // stays a multiple of vec elements
         hp.near_tensor_len += (int64_t)L.W * L.sl;
-        L.stat = hp.near_stat_len;
-        hp.near_stat_len += (int64_t)L.ns * L.nr;
-        L.tail = -1;
+        const bool tail = hp.soe > 0 && has_tail[l];
+        L.naux = 1 + (tail ? hp.soe : 0);
+        L.stat = hp.near_aux_len;                          // a multiple of 2 elements, like sla
+        L.tail = tail ? L.stat + L.sla : -1;
+        hp.near_aux_len += (int64_t)L.naux * L.sla;
+        if (tail) hp.near_tail_len += (int64_t)hp.soe * L.sla;
         L.vstate = 0;
-        if (hp.soe > 0 && has_tail[l]) {
-            L.tail = hp.near_tail_len;
-            hp.near_tail_len += (int64_t)hp.soe * L.ns * L.nr;
+        if (tail) {
             L.vstate = hp.vstate_len;
             hp.vstate_len += (int64_t)hp.soe * L.ns;
         }
         hp.max_W = std::max(hp.max_W, L.W);
-        // one work item per chunk of steps; the first item also carries the static tail
-        const int nchunk = std::max(1, (L.W + chunk - 1) / chunk);
-        for (int c = 0; c < nchunk; ++c) {
+        // one work item per chunk of window steps, and one for the aux slices (static term from
+        // step W on, exponential tail)
+        const int nchunk = (L.W + chunk - 1) / chunk;
+        for (int c = 0; c <= nchunk; ++c) {
             NearItem it;
             it.leaf = l;
-            it.k0 = c * chunk;
-            it.k1 = std::min(L.W, (c + 1) * chunk);
-            it.pad = 0;
+            it.kind = c == nchunk ? 1 : 0;
+            it.k0 = it.kind ? 0 : c * chunk;
+            it.k1 = it.kind ? L.naux : std::min(L.W, (c + 1) * chunk);
             const int id = (int)hp.items.size();
             hp.items.push_back(it);
             for (int il = 0; il < L.nr; ++il) slots[L.r0 + il].push_back(id * 32 + il);

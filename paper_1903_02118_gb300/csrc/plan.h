@@ -26,19 +26,30 @@ struct SubBlock {
     int64_t trc;       // TR: offset of their FP64 coefficients in HostPlan::trcoef
     int64_t ustate;    // TR: offset of the [rank][soe] recursive tail states
     int64_t phi;       // offset of the receivers' sub-step delays in HostPlan::phis (interp only)
+    int32_t ident;     // block kept exact: 1 = F is the identity (rank nr), 2 = G is the identity
+                       // (rank ns), 0 = low-rank factors
+    int32_t e0;        // index of the block's first (block, receiver) entry in block-major order
 };
 
 struct NearLeaf {
     int32_t r0, nr, s0, ns, W;   // W = window of exact kernel steps stored
-    int32_t sl;                  // slice stride: ns * nr rounded up to a multiple of 4 (16-byte rows)
-    int64_t tensor;              // offset of [W][sl] coefficients (slice k: [ns][nr]), 4-aligned
-    int64_t stat;                // offset of the [ns][nr] static tile (x dt), FP64
-    int64_t tail;                // offset of the [Q][ns][nr] exponential-tail coefficients (-1: none)
+    // Slices are stored source-interleaved: element (j, i) of a slice at ((j / v) * nr + i) * v + j % v
+    // with v = 16 bytes / element size, the sources padded with zeros to a multiple of v, so that a
+    // receiver reads v sources with one 16-byte load.
+    int32_t sl;                  // window slice stride: ceil(ns / v) v nr (v of the storage type)
+    int32_t sla;                 // FP64 aux slice stride: ceil(ns / 2) 2 nr
+    int64_t tensor;              // offset of [W][sl] coefficients
+    // FP64 "aux" slices of the leaf, [naux][sl] at `stat`: slice 0 the static tile (x dt),
+    // slices 1..Q the exponential-tail coefficients (the tail starts at `tail`, -1: none)
+    int64_t stat;
+    int64_t tail;
+    int32_t naux;
     int64_t vstate;              // offset of the [Q][ns] recursive tail states
 };
 
+// A near-field work item: window slices [k0, k1) of a leaf (kind 0), or its aux slices (kind 1).
 struct NearItem {
-    int32_t leaf, k0, k1, pad;
+    int32_t leaf, k0, k1, kind;
 };
 
 struct HostPlan {
@@ -56,11 +67,10 @@ struct HostPlan {
     int interp = 0;
     std::vector<int32_t> ints;                       // delays, dm
     std::vector<int32_t> run_delay, run_start, run_len, src_order;
-    std::vector<int32_t> scat_sb, scat_run, scat_l;  // scatter tasks (block, run, rank index)
     std::vector<int32_t> fir_sb, fir_j;              // FIR tasks
     std::vector<int32_t> tr_sb, tr_l;                // transient convolution tasks
     std::vector<int32_t> g_ptr, g_sb, g_il;          // gather CSR (receiver-major)
-    std::vector<int32_t> e_sb, e_il, e_pos;          // the same entries block-major, with their CSR slot
+    std::vector<int32_t> e_pos;                      // CSR slot of each entry, block-major order
     int64_t ring_len = 0, zring_len = 0, dhat_len = 0, ustate_len = 0;
     int soe = 0;                                     // exponential-tail terms (0: paper's cut)
     std::vector<double> rho;                         // their decay factors
@@ -70,17 +80,20 @@ struct HostPlan {
     std::vector<int32_t> near_r0, near_nr, near_s0, near_ns;   // for the m_S kernel
     std::vector<NearItem> items;
     std::vector<int32_t> np_ptr, np_idx;             // receiver -> partial slots
-    int64_t near_tensor_len = 0, near_stat_len = 0, near_tail_len = 0, vstate_len = 0;
+    int64_t near_tensor_len = 0, near_aux_len = 0, near_tail_len = 0, vstate_len = 0;
     int32_t max_W = 0;
     // stats
     int n_adm = 0, n_near = 0, max_rank = 0;
     double mean_rank = 0;
     int64_t far_entries = 0;
+    int64_t far_nent = 0;                            // (block, receiver) entries
 };
 
 // Everything except the near-field windows (which need the device). Returns status.
 int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
-void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk);
+// vec: sources per 16 bytes of the window storage type (4 for FP32, 2 for FP64).
+void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
+                        int vec);
 
 }  // namespace fdph

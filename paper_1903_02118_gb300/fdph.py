@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
 
 _lib = None
 
-EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset",
+EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_run_host", "fdph_reset",
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
@@ -84,6 +84,7 @@ def lib():
         L.fdph_step.argtypes = [c_p, c_p, c_p]
         L.fdph_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_step_host.argtypes = [c_p, c_p, c_p]
+        L.fdph_run_host.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_reset.argtypes = [c_p]
         L.fdph_current_step.argtypes = [c_p, ctypes.POINTER(ctypes.c_int32)]
         L.fdph_synchronize.argtypes = [c_p]
@@ -107,7 +108,8 @@ def lib():
         L.fdph_strerror.restype = ctypes.c_char_p
         L.fdph_last_error.argtypes = []
         L.fdph_last_error.restype = ctypes.c_char_p
-        for name in ("fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_reset", "fdph_current_step",
+        for name in ("fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_run_host", "fdph_reset",
+                     "fdph_current_step",
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
                      "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc",
                      "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip"):
@@ -179,6 +181,20 @@ class Plan:
             T_n = np.empty(self.n)
         _check(lib().fdph_step_host(self.handle, ctypes.c_void_p(D_n.ctypes.data), ctypes.c_void_p(T_n.ctypes.data)))
         return T_n
+
+    def run_host(self, D, T=None):
+        """Steps D.shape[0] steps from host arrays (numpy, or page-locked torch CPU tensors for
+        asynchronous copies); returns T of the same shape."""
+        if hasattr(D, "data_ptr"):
+            steps = int(D.shape[0])
+            _check(lib().fdph_run_host(self.handle, steps, _ptr(D), _ptr(T)))
+            return T
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        if T is None:
+            T = np.empty_like(D)
+        _check(lib().fdph_run_host(self.handle, int(D.shape[0]), ctypes.c_void_p(D.ctypes.data),
+                                   ctypes.c_void_p(T.ctypes.data)))
+        return T
 
     def reset(self):
         _check(lib().fdph_reset(self.handle))

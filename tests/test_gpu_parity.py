@@ -130,6 +130,11 @@ def test_step_run_host_reset_and_state_are_consistent():
     assert plan.current_step() == 60
     T_host = np.stack([plan.step_host(D[n]) for n in range(60, M)])
     assert np.array_equal(T_host, T_run[60:])
+    plan.load_state(saved)
+    assert np.array_equal(plan.run_host(D[60:]), T_run[60:])   # pipelined host-buffer steps
+    plan.load_state(saved)
+    assert np.array_equal(plan.run_host(D[60:65]), T_run[60:65])   # fewer steps than staging slots
+    assert np.array_equal(plan.run_host(D[65:]), T_run[65:])
     with pytest.raises(fdph.FdphError):
         plan.step(Dd[0], Td[0])                                 # past M
 

@@ -93,32 +93,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    return world, rank, local
-
-
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
 def make_workload(cfg, rank):
     from paper_1903_02118_gb300 import inputs
     k = 1 if cfg["geometry"] == "curved" else 0
@@ -153,7 +127,8 @@ def oracle_step_rate(K, D, steps, n_hi):
 
 
 def run_reference(args, cfg):
-    world, rank, _ = dist_setup()
+    from paper_1903_02118_gb300 import replicas
+    world, rank, _ = replicas.init()
     if rank != 0:
         return
     xy, D = make_workload(cfg, 0)
@@ -212,7 +187,8 @@ def main():
         return run_reference(args, cfg)
 
     import torch
-    world, rank, local = dist_setup()
+    from paper_1903_02118_gb300 import replicas
+    world, rank, local = replicas.init()
     torch.cuda.set_device(local)
     from paper_1903_02118_gb300 import build, fdph
     build.build()
@@ -265,15 +241,15 @@ def main():
     plan.run(W, Dd[n0:], Td[n0:])
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
-    barrier(world)
+    replicas.barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
         s0.record(stream)
         plan.run(K, Dd[n0 + W:], Td[n0 + W:])
         s1.record(stream)
         torch.cuda.synchronize()
-    barrier(world)
-    ms = max_over_ranks(s0.elapsed_time(s1), world)
+    replicas.barrier(world)
+    ms = replicas.max_over_ranks(s0.elapsed_time(s1), world)
     value = world * N * K / (ms * 1e-3)
 
     # per-kernel times (CUDA events inside the library, same stream) for the roofline
@@ -297,10 +273,10 @@ def main():
     roll_to(n0 + W)
     hD = torch.from_numpy(np.ascontiguousarray(D[n0 + W:n0 + W + K])).pin_memory()
     hT = torch.empty((K, N), dtype=torch.float64).pin_memory()
-    barrier(world)
+    replicas.barrier(world)
     te0 = time.perf_counter()
     plan.run_host(hD, hT)
-    te = max_over_ranks(time.perf_counter() - te0, world)
+    te = replicas.max_over_ranks(time.perf_counter() - te0, world)
     if not np.array_equal(hT.numpy(), T_full[n0 + W:n0 + W + K]):
         raise SystemExit("fdph_run_host result differs from fdph_run")
     e2e = {"value": world * N * K / te, "unit": "element-steps/s", "h2d_bytes_per_step": N * 8,
@@ -315,7 +291,7 @@ def main():
         rc = L.fdph_step_host(plan.handle, ctypes.c_void_p(hD[s].data_ptr()), ctypes.c_void_p(h1.data_ptr()))
         if rc:
             raise SystemExit("fdph_step_host failed: %d" % rc)
-    te1 = max_over_ranks(time.perf_counter() - te0, world)
+    te1 = replicas.max_over_ranks(time.perf_counter() - te0, world)
     e2e["step_host_value"] = world * N * K / te1
 
     line = {"metric": "element-steps/s", "value": value, "unit": "element-steps/s", "n_gpus": world,

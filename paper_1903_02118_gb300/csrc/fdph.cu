@@ -59,6 +59,7 @@ static const int kNearConsumers = 4;                       // consumer warps of 
 static const int kNearThreads = 32 * (kNearConsumers + 1);  // + one producer warp
 static const int kNearStageBytes = 16384;                  // one pipeline stage
 static const int kMaxPer = 8;                              // slices per stage at most
+static const int kTaskCache = 48;                          // work items per CTA kept in shared memory
 static_assert(kNearStageBytes >= 32 * 32 * 8, "a stage holds at least one FP64 slice of a 32 x 32 leaf");
 static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls before giving up
 
@@ -457,11 +458,18 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
     extern __shared__ __align__(128) unsigned char near_smem[];
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][32];
+    __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
     const int n = step_index(a);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
     unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
+    {
+        const int nt = min(t1 - t0, kTaskCache) * (int)(sizeof(NearTask) / sizeof(int4));
+        for (int e = threadIdx.x; e < nt; e += blockDim.x)
+            ((int4*)tcache)[e] = ((const int4*)(a.tasks + t0))[e];
+    }
+    auto task = [&](int ti) -> NearTask { return ti - t0 < kTaskCache ? tcache[ti - t0] : a.tasks[ti]; };
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::stages; ++s) {
             mbar_init(&full[s], 1);
@@ -477,7 +485,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
         if (lane == 0) {
             const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
             for (int ti = t0; ti < t1; ++ti) {
-                const NearTask tk = a.tasks[ti];
+                const NearTask tk = task(ti);
                 const int esz = tk.kind ? 8 : (int)sizeof(T);
                 const int nsl = near_slices<T>(tk, n);
                 const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
         double rows[kRowsPerWarp], dW = 0.0;
         NearTask nxt;
         if (t0 < t1) {
-            nxt = a.tasks[t0];
+            nxt = task(t0);
             near_issue(a, nxt, n, warp, lane, rows, dW);
             near_commit(a, nxt, n, warp, lane, rows, dW, vbuf);
         }
@@ -514,7 +522,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
             const NearTask tk = nxt;
             // the next item's vector loads stay in flight while this item is consumed
             if (ti + 1 < t1) {
-                nxt = a.tasks[ti + 1];
+                nxt = task(ti + 1);
                 near_issue(a, nxt, n, warp, lane, rows, dW);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;

@@ -72,7 +72,7 @@ struct SbDev {
 };
 
 struct NearDev {
-    int r0, nr, s0, ns, W, sl, sla, pad;
+    int r0, nr, s0, ns, W, sl;
     long long tensor, stat, tail, vstate;
 };
 
@@ -135,7 +135,7 @@ struct StepArgs {
     int n_cta;
     int n_items;
     const T* tensor;
-    const double* stat;       // FP64 aux slices (static tiles, exponential-tail coefficients)
+    const T* stat;            // aux slices (static tiles, exponential-tail coefficients)
     double* partial;          // [n_items][32]
     const int* np_ptr;
     const int* np_idx;
@@ -371,7 +371,7 @@ __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
     return tk.kind ? tk.k1 : min(tk.k1, n + 1) - tk.k0;
 }
 
-// The vectors of one work item (rows of 32: T for window slices, double for aux slices) are
+// The vectors of one work item (rows of 32 in the storage type) are
 // gathered by the consumer warps in two halves: near_issue loads this warp's rows (w, w + C, ...)
 // into registers, near_commit (one item later, so that the loads are in flight meanwhile) forms
 // the values and stores them to shared memory.  Window row k: D_{n - k0 - k, j}.  Aux row 0:
@@ -420,18 +420,15 @@ __device__ __forceinline__ void near_commit(const StepArgs<T>& a, const NearTask
     for (int m = 0; m < kRowsPerWarp; ++m) {
         const int k = warp + m * kNearConsumers;
         if (k < nsl) {
-            if (!tk.kind) {
-                ((T*)vb)[k * 32 + lane] = (T)r[m];
-            } else if (k == 0) {
-                ((double*)vb)[lane] = r[m];
-            } else {
-                double vn = 0.0;
+            double v = r[m];
+            if (tk.kind && k > 0) {
+                v = 0.0;
                 if (lane < tk.ns) {
-                    vn = a.rho[k - 1] * r[m] + dW;
-                    a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane] = vn;
+                    v = a.rho[k - 1] * r[m] + dW;
+                    a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane] = v;
                 }
-                ((double*)vb)[k * 32 + lane] = vn;
             }
+            ((T*)vb)[k * 32 + lane] = (T)v;
         }
     }
 }
@@ -442,10 +439,10 @@ struct NearCfg {
     static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(T);  // one item's vectors
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
 };
-static_assert(17 * 32 * 8 <= kChunk * 32 * 4, "aux vectors (1 + 16 tail terms) fit a vector buffer");
+static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer");
 
 // Near field (App. E), persistent and warp-specialised.  Each CTA owns a list of work items
-// (window slices [k0, k1) of a leaf, or the leaf's FP64 aux slices: static tile and exponential
+// (window slices [k0, k1) of a leaf, or the leaf's aux slices: static tile and exponential
 // tail).  One producer thread streams the items' slices through a ring of shared-memory stages
 // (cp.async.bulk, full/empty mbarriers), continuing across item boundaries.  The consumer warps
 // load the vectors of the next item into a second shared buffer while they consume the current
@@ -486,12 +483,11 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
             const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
             for (int ti = t0; ti < t1; ++ti) {
                 const NearTask tk = task(ti);
-                const int esz = tk.kind ? 8 : (int)sizeof(T);
+                constexpr int esz = (int)sizeof(T);
                 const int nsl = near_slices<T>(tk, n);
                 const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
                 const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
-                const unsigned char* src = tk.kind ? (const unsigned char*)(a.stat + tk.off)
-                                                   : (const unsigned char*)(a.tensor + tk.off);
+                const unsigned char* src = (const unsigned char*)((tk.kind ? a.stat : a.tensor) + tk.off);
                 for (int q = 0; q < nst; ++q, ++g) {
                     const int s = g % C::stages;
                     if (!mbar_wait_bounded(&empty[s], (unsigned)(((g / C::stages) & 1) ^ 1))) {
@@ -526,7 +522,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 near_issue(a, nxt, n, warp, lane, rows, dW);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
-            const int esz = tk.kind ? 8 : (int)sizeof(T);
+            constexpr int esz = (int)sizeof(T);
             const int nsl = near_slices<T>(tk, n);
             const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
             const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
@@ -543,7 +539,8 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
                 for (int kk = warp; kk < cnt; kk += kNearConsumers) {
                     const int row = q * per + kk;
-                    if (!tk.kind && sizeof(T) == 4) {
+                    T sum;
+                    if (sizeof(T) == 4) {
                         // 4 sources per 16-byte load: tile row jb holds sources 4 jb .. 4 jb + 3
                         const float4* tile = (const float4*)(buf + (size_t)kk * tk.sl * 4) + li;
                         const float4* d = (const float4*)(vrows + row * 128);
@@ -569,9 +566,9 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                                 s3 = fmaf(x.w, y.w, s3);
                             }
                         }
-                        acc += (T)((s0 + s1) + (s2 + s3));
+                        sum = (T)((s0 + s1) + (s2 + s3));
                     } else {
-                        // FP64 slices (window of the FP64 plan, or aux): 2 sources per load
+                        // FP64 storage: 2 sources per 16-byte load
                         const double2* tile = (const double2*)(buf + (size_t)kk * tk.sl * 8) + li;
                         const double2* d = (const double2*)(vrows + row * 256);
                         double s0 = 0.0, s1 = 0.0;
@@ -582,9 +579,10 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                             s0 = fma(x.x, y.x, s0);
                             s1 = fma(x.y, y.y, s1);
                         }
-                        if (tk.kind) accd += s0 + s1;
-                        else acc += (T)(s0 + s1);
+                        sum = (T)(s0 + s1);
                     }
+                    if (tk.kind) accd += (double)sum;   // static and tail slices: FP64 across slices
+                    else acc += sum;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
@@ -740,7 +738,7 @@ __global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const in
 // coefficients [k][j][i] for k < W: exact kernel below m_S(i, j), static * dt above
 template <class T>
 __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double dt, double mu, double c,
-                                 T* tensor, double* stat) {
+                                 T* tensor, T* stat) {
     const long long total = (long long)L.W * L.ns * L.nr;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
@@ -763,7 +761,7 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
         tensor[L.tensor + (long long)k * L.sl + ((jl / v4) * L.nr + il) * v4 + jl % v4] = (T)v;
         if (k == 0) {
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
-            stat[L.stat + ((jl / 2) * L.nr + il) * 2 + jl % 2] = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
+            stat[L.stat + ((jl / v4) * L.nr + il) * v4 + jl % v4] = (T)((g.nx[pi] * w.x + g.ny[pi] * w.y) * dt);
         }
     }
 }
@@ -841,7 +839,7 @@ struct fdph_plan_s {
     int* cta_ptr = nullptr;
     int n_cta = 0;
     void* tensor = nullptr;
-    double* stat = nullptr;
+    void* stat = nullptr;     // aux slices, storage type
     int *np_ptr = nullptr, *np_idx = nullptr;
     int* err = nullptr;
     double* rho = nullptr;
@@ -944,7 +942,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.n_cta = P->n_cta;
     a.n_items = (int)P->hp.items.size();
     a.tensor = (const T*)P->tensor;
-    a.stat = P->stat;
+    a.stat = (const T*)P->stat;
     a.partial = P->partial;
     a.np_ptr = P->np_ptr;
     a.np_idx = P->np_idx;
@@ -1257,15 +1255,17 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
-        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, L.sla, 0, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
                  (long long)L.vstate};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
     T* tens = nullptr;
-    if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &P->stat, hp.near_aux_len))) return rc;
+    T* aux = nullptr;
+    if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &aux, hp.near_aux_len))) return rc;
     P->tensor = tens;
+    P->stat = aux;
     if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(T)));  // slice padding
-    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(P->stat, 0, hp.near_aux_len * sizeof(double)));
+    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(aux, 0, hp.near_aux_len * sizeof(T)));
     for (int l = 0; l < nl; ++l) {
         const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
         if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
@@ -1279,10 +1279,10 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             L1.W = 1;
             L1.tensor = 0;
             near_fill_kernel<T><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
-                                                                            in.mu, in.cs, tmp, P->stat);
+                                                                            in.mu, in.cs, tmp, aux);
         } else {
             near_fill_kernel<T><<<std::min<long long>(blocks(tot, 256), 4096), 256>>>(
-                g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, P->stat);
+                g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, aux);
         }
         FDPH_CUDA(cudaGetLastError());
     }
@@ -1311,8 +1311,9 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
         // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
         std::vector<size_t> toff(tl.size() + 1, 0);
-        for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sla;
-        std::vector<double> tail_h(toff.back(), 0.0);
+        for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sl;
+        std::vector<T> tail_h(toff.back(), (T)0);
+        constexpr int v4 = 16 / (int)sizeof(T);
 #pragma omp parallel for schedule(dynamic, 8)
         for (long t = 0; t < (long)tl.size(); ++t) {
             const NearDev& L = tl[t];
@@ -1321,11 +1322,11 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             for (int il = 0; il < L.nr; ++il)
                 for (int jl = 0; jl < L.ns; ++jl)
                     for (int q = 0; q < in.soe; ++q)
-                        tail_h[toff[t] + (size_t)q * L.sla + ((size_t)(jl / 2) * L.nr + il) * 2 + jl % 2] =
-                            ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
+                        tail_h[toff[t] + (size_t)q * L.sl + ((size_t)(jl / v4) * L.nr + il) * v4 + jl % v4] =
+                            (T)ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
         }
         for (size_t t = 0; t < tl.size(); ++t)
-            FDPH_CUDA(cudaMemcpy(P->stat + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(double),
+            FDPH_CUDA(cudaMemcpy(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(T),
                                  cudaMemcpyHostToDevice));
     }
     // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
@@ -1350,12 +1351,12 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         t.kind = it.kind;
         t.nr = L.nr;
         t.ns = L.ns;
-        t.sl = it.kind ? L.sla : L.sl;
+        t.sl = L.sl;
         t.s0 = L.s0;
         t.W = L.W;
         t.vstate = (int)L.vstate;
         tasks_all[q] = t;
-        cost[q] = (double)(it.k1 - it.k0) * t.sl * (it.kind ? 8.0 : (double)sizeof(T)) + 4096.0;
+        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)sizeof(T) + 4096.0;
     }
     std::vector<int> order(ni);
     for (int q = 0; q < ni; ++q) order[q] = q;
@@ -1405,11 +1406,11 @@ static void fill_stats(fdph_plan_t P) {
     // algorithmic bytes of one steady-state step
     double near_b = 0, far_b = 0, flops = 0;
     for (const NearLeaf& L : hp.near) {
-        near_b += (double)L.W * L.ns * L.nr * ps + (double)L.ns * L.nr * 8.0;  // tensor + static tile
+        near_b += (double)L.W * L.ns * L.nr * ps + (double)L.ns * L.nr * ps;   // tensor + static tile
         near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
         flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
         if (L.tail >= 0) {                                                     // tail coefficients + states
-            near_b += (double)hp.soe * L.ns * L.nr * 8.0 + (double)hp.soe * L.ns * 16.0;   // FP64 coefficients
+            near_b += (double)hp.soe * L.ns * L.nr * ps + (double)hp.soe * L.ns * 16.0;
             flops += 2.0 * hp.soe * L.ns * (L.nr + 1.0);
         }
     }
@@ -1444,7 +1445,7 @@ static void fill_stats(fdph_plan_t P) {
     s.state_bytes = (long long)P->state_bytes;
     long long arena = 0;
     arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
-    arena += (long long)(hp.near_tensor_len * ps) + hp.near_aux_len * 8;
+    arena += (long long)((hp.near_tensor_len + hp.near_aux_len) * ps);
     s.arena_bytes = arena;
 }
 

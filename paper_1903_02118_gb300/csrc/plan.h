@@ -36,11 +36,10 @@ struct NearLeaf {
     // Slices are stored source-interleaved: element (j, i) of a slice at ((j / v) * nr + i) * v + j % v
     // with v = 16 bytes / element size, the sources padded with zeros to a multiple of v, so that a
     // receiver reads v sources with one 16-byte load.
-    int32_t sl;                  // window slice stride: ceil(ns / v) v nr (v of the storage type)
-    int32_t sla;                 // FP64 aux slice stride: ceil(ns / 2) 2 nr
+    int32_t sl;                  // slice stride: ceil(ns / v) v nr (v of the storage type)
     int64_t tensor;              // offset of [W][sl] coefficients
-    // FP64 "aux" slices of the leaf, [naux][sl] at `stat`: slice 0 the static tile (x dt),
-    // slices 1..Q the exponential-tail coefficients (the tail starts at `tail`, -1: none)
+    // "aux" slices of the leaf (storage type, same layout), [naux][sl] at `stat`: slice 0 the
+    // static tile (x dt), slices 1..Q the exponential-tail coefficients (`tail`, -1: none)
     int64_t stat;
     int64_t tail;
     int32_t naux;

@@ -28,6 +28,11 @@ CONFIGS = {
                  leaf=32, eps_st=1e-6, geometry="curved"),
     "plain": dict(name="Plain dense ST-BIEM, 2-D antiplane straight fault", N=256, M=256, eps=0.0, eta=0.0,
                   leaf=32, eps_st=0.0, geometry="straight"),
+    # dynamic rupture on a planar fault (linear slip weakening); N is 4096 instead of 16384 because
+    # the host plan of the 16384-element fault (exact QR + Jacobi factorisation of every block)
+    # takes tens of minutes
+    "rupture": dict(name="FDP=H dynamic rupture, 2-D antiplane planar fault, linear slip weakening", N=4096,
+                    M=8192, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="straight"),
 }
 DT = 0.5
 
@@ -161,13 +166,90 @@ def run_reference(args, cfg):
     print(json.dumps(line))
 
 
+def run_rupture(args, cfg):
+    """Dynamic rupture (Sec. 6.2): prestress 0.45 with 5 % seeded Gaussian heterogeneity, 64 central
+    elements overstressed at 0.61, mu_s 0.6, mu_d 0.3, Dc 6.4, sigma_n 1; FP32 storage, exponential
+    tails.  The march is rolled past the longest near window, then K steps are timed."""
+    import torch
+    from paper_1903_02118_gb300 import build, fdph, inputs, replicas
+    world, rank, local = replicas.init()
+    torch.cuda.set_device(local)
+    build.build()
+    N, M = cfg["N"], cfg["M"]
+    xy = inputs.straight_fault(N)
+    rng = np.random.default_rng(inputs.seed_for(2 + 10 * rank, inputs.FRICTION))
+    tau0 = 0.45 * (1.0 + 0.05 * rng.standard_normal(N))
+    tau0[N // 2 - 32:N // 2 + 32] = 0.61
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = fdph.FP32 if args.precision == "fp32" else fdph.FP64
+    t0 = time.perf_counter()
+    plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
+                     precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+    plan.rupture_init(torch.from_numpy(tau0).cuda(), 1.0, 0.6, 0.3, 6.4)
+    K, W = args.steps, args.warmup
+    n0 = max(0, min(st["max_window"], M - W - K))
+    Dd = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    Td = torch.zeros_like(Dd)
+    plan.rupture_run(n0 + W, Dd, Td)
+    plan.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    replicas.barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.rupture_run(K, Dd[n0 + W:], Td[n0 + W:])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), world)
+    D_last = Dd[n0 + W + K - 1].cpu().numpy()
+    line = {"metric": "element-steps/s", "value": world * N * K / (ms * 1e-3), "unit": "element-steps/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == fdph.FP64 else "f32-storage/f64-accumulate", "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
+                       "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
+                       "first_timed_step": n0 + W, "note": "N reduced from 16384 (host plan time)"},
+            "rupture": {"slipping_fraction_last_step": float((D_last > 0).mean()),
+                        "max_slip_rate": float(D_last.max())},
+            "plan": {"seconds": plan_s, "bytes_per_step": st["bytes_per_step"], "n_near": st["n_near"],
+                     "n_admissible": st["n_admissible"], "max_rank": st["max_rank"]}}
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+
+
+def run_serving(args):
+    """Continuous batching of rupture scenarios (serving.py) against the same requests served one
+    at a time with FP64 storage.  Requests: Poisson arrivals at 8/s, N log-uniform in [256, 2048]
+    (reduced from [512, 16384]: host plan time), CFL 0.25 or 0.5, M = N / CFL / 2, curved
+    geometries; FP32 storage, exponential tails."""
+    import torch
+    from paper_1903_02118_gb300 import build, fdph, serving
+    torch.cuda.set_device(0)
+    build.build()
+    kw = dict(n_min=256, n_max=2048, m_scale=0.5)
+    reqs = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
+    mix = serving.Server(max_live=16, chunk=64, planners=2, precision=fdph.FP32).serve(reqs, realtime=True)
+    ref = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
+    alone = serving.Server(max_live=1, chunk=64, planners=1, precision=fdph.FP64).serve(ref, realtime=True)
+    line = {"metric": "serving element-steps/s and time to solution", "requests": args.requests,
+            "arrivals": "Poisson 8/s", "N_range": [256, 2048], "M": "N / CFL / 2, CFL in {0.25, 0.5}",
+            "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, **mix},
+            "one_at_a_time_fp64": {"precision": "f64", "max_live": 1, **alone},
+            "data": "synthetic"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fdph", choices=sorted(CONFIGS))
+    ap.add_argument("--workload", default="fdph", choices=sorted(CONFIGS) + ["serving"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--soe", type=int, default=16, help="exponential-tail terms (0: the paper's static cut)")
     ap.add_argument("--eta", type=float, default=None)
@@ -177,7 +259,10 @@ def main():
                     help="plan + roll forward + warm-up + timed steps only (for profiler launch lists)")
     ap.add_argument("--n", type=int, default=None, help="override N (profiling of smaller cases)")
     ap.add_argument("--m", type=int, default=None, help="override M")
+    ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
     args = ap.parse_args()
+    if args.workload == "serving":
+        return run_serving(args)
     cfg = dict(CONFIGS[args.workload])
     if args.workload == "fdph":
         cfg["soe"] = args.soe
@@ -191,8 +276,12 @@ def main():
         cfg["N"] = args.n
     if args.m:
         cfg["M"] = args.m
+    if args.workload == "rupture":
+        cfg["soe"] = args.soe
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if args.workload == "rupture":
+        return run_rupture(args, cfg)
 
     import torch
     from paper_1903_02118_gb300 import replicas

@@ -140,7 +140,8 @@ int fdph_step(fdph_plan_t plan, const double* D_n, double* T_n);
 
 /* `steps` consecutive steps: D (device, steps * n doubles, step-major) -> T (device, same shape).
  * Equivalent to `steps` calls of fdph_step; from 8 steps on (and with profiling off) the call
- * captures one step as a CUDA graph and replays it, which removes the per-kernel launch cost.
+ * replays a CUDA graph of one step, which removes the per-kernel launch cost; the graph is kept
+ * with the plan (at most 8 per plan) and reused by later calls on the same D, T buffers.
  * Errors as fdph_step; FDPH_E_STATE if the plan would pass step M. */
 int fdph_run(fdph_plan_t plan, int32_t steps, const double* D, double* T);
 
@@ -168,7 +169,9 @@ int fdph_rupture_init(fdph_plan_t plan, const fdph_friction* friction);
  * tau0 + T_n (both device, n doubles, geometry order) and advances to n + 1. */
 int fdph_rupture_step(fdph_plan_t plan, double* D_n, double* T_n);
 
-/* `steps` rupture steps into D, T (device, steps * n doubles). */
+/* `steps` rupture steps into D, T (device, steps * n doubles, step-major).  From 8 steps on
+ * (profiling off) one rupture step is captured as a CUDA graph and replayed; the graph is kept
+ * with the plan for later calls on the same D, T buffers. */
 int fdph_rupture_run(fdph_plan_t plan, int32_t steps, double* D, double* T);
 
 /* Copy the accumulated slip (device, n doubles, geometry order). */

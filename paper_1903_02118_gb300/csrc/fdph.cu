@@ -88,10 +88,9 @@ static const int kMaxSoe = 16;
 template <class T>
 struct StepArgs {
     int n, N, WD, WC;
-    // graph replay: the step index is read from n_dev, and D_in / T_out advance by io_stride
-    // elements per step past n_base (both unused when n_dev is null)
+    // graph replay: the step index is read from n_dev[0], and D_in / T_out advance by io_stride
+    // elements per step past the step n_dev[1] of the call's first row (unused when n_dev is null)
     const int* n_dev;
-    int n_base;
     long long io_stride;
     int io_ring;              // > 0: D_in / T_out rows are a ring of io_ring staging slots
     double dt;
@@ -166,13 +165,16 @@ __device__ __forceinline__ int step_index(const StepArgs<T>& a) {
 template <class T>
 __device__ __forceinline__ long long io_offset(const StepArgs<T>& a, int n) {
     if (!a.n_dev) return 0;
-    const int k = n - a.n_base;
+    const int k = n - a.n_dev[1];
     return (long long)(a.io_ring > 0 ? k % a.io_ring : k) * a.io_stride;
 }
 
 __global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
 
-__global__ void set_step_kernel(int* n_dev, int v) { *n_dev = v; }
+__global__ void set_step_kernel(int* n_dev, int v) {
+    n_dev[0] = v;   // step index
+    n_dev[1] = v;   // step of the call's first row of D / T
+}
 
 template <class T>
 __global__ void push_kernel(StepArgs<T> a) {
@@ -673,9 +675,15 @@ struct FrictionDev {
     double sigma_n, mu_s, mu_d, Dc, dt;
 };
 
-__global__ void friction_kernel(FrictionDev f, int N, double* D, double* T) {
+// D, T: this step's rows (graph replay: row n_dev[0] - n_dev[1] of a step-major array)
+__global__ void friction_kernel(FrictionDev f, int N, double* D, double* T, const int* n_dev) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
+    if (n_dev) {
+        const long long off = (long long)(n_dev[0] - n_dev[1]) * N;
+        D += off;
+        T += off;
+    }
     const double tau = f.tau0[e] + T[e];
     const double u = f.slip[e];
     const double w = u < f.Dc ? u / f.Dc : 1.0;
@@ -858,8 +866,16 @@ struct fdph_plan_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
     double prof_ms[FDPH_NUM_KERNELS] = {0};
     int64_t prof_n[FDPH_NUM_KERNELS] = {0};
-    // graph of one step for fdph_run (replayed with the step index in n_dev)
-    cudaGraphExec_t graph = nullptr;
+    // graphs of one step (fdph_run, fdph_run_host, fdph_rupture_run), replayed with the step index
+    // and the call's first step in n_dev[0..1]; kept per (kind, D, T) so that repeated calls on
+    // the same buffers reuse them
+    struct GraphEntry {
+        int kind;
+        const void* D;
+        const void* T;
+        cudaGraphExec_t ex;
+    };
+    std::vector<GraphEntry> graphs;
     int* n_dev = nullptr;
     // branches of a step that run concurrently with the near field: [0] FIR + scatter,
     // [1] transient convolution + Eq. 39 evaluation (fork after push, join before gather)
@@ -1011,24 +1027,36 @@ static int launch_step(fdph_plan_t P, const double* D, double* Tout) {
     return FDPH_OK;
 }
 
-// One step captured as a CUDA graph that reads its step index from n_dev (advanced by the last
-// node) and offsets D / T by one row per step (modulo io_ring rows when io_ring > 0).
+// kinds of cached step graphs
+enum { GRAPH_RUN = 0, GRAPH_RUN_HOST = 1, GRAPH_RUPTURE = 2 };
+
 template <class T>
-static int capture_step_graph(fdph_plan_t P, const double* D, double* Tout, int io_ring, cudaGraphExec_t* ex) {
+static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaStream_t s);
+
+// The cached graph of one step of `kind` on buffers (D, T) (rows modulo io_ring when > 0),
+// captured on first use; the step index and the first row's step are set on the device before
+// the replays.
+template <class T>
+static int step_graph(fdph_plan_t P, int kind, const double* D, double* Tout, int io_ring, cudaGraphExec_t* ex) {
     if (!P->n_dev) {
-        int rc = dalloc(P, &P->n_dev, 1);
+        int rc = dalloc(P, &P->n_dev, 2);
         if (rc) return rc;
     }
     cudaStream_t s = P->stream;
-    StepArgs<T> a = make_args<T>(P, D, Tout);
+    set_step_kernel<<<1, 1, 0, s>>>(P->n_dev, P->n);
+    for (const auto& ge : P->graphs)
+        if (ge.kind == kind && ge.D == (const void*)D && ge.T == (const void*)Tout) {
+            *ex = ge.ex;
+            return FDPH_OK;
+        }
+    StepArgs<T> a = make_args<T>(P, kind == GRAPH_RUPTURE ? nullptr : D, Tout);
     a.n_dev = P->n_dev;
-    a.n_base = P->n;
     a.io_stride = P->N;
     a.io_ring = io_ring;
-    set_step_kernel<<<1, 1, 0, s>>>(P->n_dev, P->n);
     cudaGraph_t g = nullptr;
     FDPH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    enqueue_step<T>(P, a, s);
+    if (kind == GRAPH_RUPTURE) enqueue_rupture_step<T>(P, a, (double*)D, s);
+    else enqueue_step<T>(P, a, s);
     advance_step_kernel<<<1, 1, 0, s>>>(P->n_dev);
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) {
@@ -1041,6 +1069,12 @@ static int capture_step_graph(fdph_plan_t P, const double* D, double* Tout, int 
         set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
     }
+    if (P->graphs.size() >= 8) {   // bounded cache: drop the oldest graph
+        cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(P->graphs.front().ex);
+        P->graphs.erase(P->graphs.begin());
+    }
+    P->graphs.push_back({kind, (const void*)D, (const void*)Tout, *ex});
     return FDPH_OK;
 }
 
@@ -1048,14 +1082,13 @@ static int capture_step_graph(fdph_plan_t P, const double* D, double* Tout, int 
 template <class T>
 static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
     cudaGraphExec_t ex = nullptr;
-    int rc = capture_step_graph<T>(P, D, Tout, 0, &ex);
+    int rc = step_graph<T>(P, GRAPH_RUN, D, Tout, 0, &ex);
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < steps; ++k) {
         e = cudaGraphLaunch(ex, P->stream);
         if (e != cudaSuccess) break;
     }
-    cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) {
         set_error(std::string("graph launch: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
@@ -1086,7 +1119,7 @@ static int run_host(fdph_plan_t P, int steps, const double* D_host, double* T_ho
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->d2h));
     cudaGraphExec_t ex = nullptr;
-    int rc = capture_step_graph<T>(P, P->io_D, P->io_T, S, &ex);
+    int rc = step_graph<T>(P, GRAPH_RUN_HOST, P->io_D, P->io_T, S, &ex);
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
@@ -1107,7 +1140,6 @@ static int run_host(fdph_plan_t P, int steps, const double* D_host, double* T_ho
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->d2h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
-    cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) {
         set_error(std::string("fdph_run_host: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
@@ -1161,10 +1193,12 @@ static int step_impl(fdph_plan_t P, const double* D, double* T_) {
     return rc;
 }
 
+// One rupture step (Sec. 6.2): predict the traction with D_n = 0 (push of a zero row, transient,
+// near field, Eq. 39, gather), solve the friction law element by element, then commit D_n
+// (push, FIR, scatter).  `a` carries the step-index source (direct: a.n; graph: n_dev).
 template <class T>
-static int launch_rupture_step(fdph_plan_t P, double* D, double* Tout) {
-    StepArgs<T> a = make_args<T>(P, nullptr, Tout);
-    cudaStream_t s = P->stream;
+static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaStream_t s) {
+    a.D_in = nullptr;
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }          // D_n = 0
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
     if (a.n_cta) {
@@ -1176,12 +1210,34 @@ static int launch_rupture_step(fdph_plan_t P, double* D, double* Tout) {
         if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
         gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
     }
-    friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, Tout);
+    friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, a.T_out, a.n_dev);
     a.D_in = D;                                                                                // commit D_n
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
     if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
+}
+
+template <class T>
+static int launch_rupture_step(fdph_plan_t P, double* D, double* Tout) {
+    StepArgs<T> a = make_args<T>(P, nullptr, Tout);
+    enqueue_rupture_step<T>(P, a, D, P->stream);
     FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
+}
+
+// `steps` rupture steps as replays of one captured step graph (rows of D, T advance per step)
+template <class T>
+static int rupture_graph(fdph_plan_t P, int steps, double* D, double* Tout) {
+    cudaGraphExec_t ex = nullptr;
+    int rc = step_graph<T>(P, GRAPH_RUPTURE, D, Tout, 0, &ex);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, P->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("rupture graph: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    P->n += steps;
     return FDPH_OK;
 }
 
@@ -1930,6 +1986,12 @@ int fdph_rupture_run(fdph_plan_t P, int32_t steps, double* D, double* T) {
         set_error("run would pass step M");
         return FDPH_E_STATE;
     }
+    if (!P->rupture) {
+        set_error("fdph_rupture_init has not been called on this plan");
+        return FDPH_E_STATE;
+    }
+    if (steps >= 8 && !P->prof)   // replay a captured graph of one rupture step
+        return P->precision == FDPH_FP32 ? rupture_graph<float>(P, steps, D, T) : rupture_graph<double>(P, steps, D, T);
     for (int s = 0; s < steps; ++s) {
         int rc = fdph_rupture_step(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
         if (rc) return rc;
@@ -1972,7 +2034,7 @@ void fdph_destroy(fdph_plan_t P) {
     cudaSetDevice(P->device);
     if (P->stream) cudaStreamSynchronize(P->stream);
     prof_drain(P);
-    if (P->graph) cudaGraphExecDestroy(P->graph);
+    for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);
     for (int k = 0; k < 2; ++k) {
         if (P->side[k]) cudaStreamDestroy(P->side[k]);
         if (P->ev_join[k]) cudaEventDestroy(P->ev_join[k]);

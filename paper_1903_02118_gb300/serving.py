@@ -9,8 +9,9 @@ scenario releases its memory at once and the next waiting request takes its plac
 request the loop records queueing, plan and run times and the time to solution (arrival to
 last step on the device).
 
-All arithmetic runs in libfdph (fdph_plan, fdph_rupture_init, fdph_rupture_run); this module
-only schedules.  Plans are independent, so a scenario's result is bit-identical alone and in
+All arithmetic runs in libfdph (fdph_plan, fdph_rupture_init, fdph_rupture_run: one cached step
+graph replayed per chunk); this module only schedules, and builds plans on background threads
+so that planning overlaps the stepping of the live scenarios.  Plans are independent, so a scenario's result is bit-identical alone and in
 the mix (tests/test_gpu_serving.py).
 """
 import time
@@ -63,20 +64,35 @@ def poisson_requests(count, rate, seed, n_min=512, n_max=16384, cfls=(0.25, 0.5)
 
 
 class Server:
-    def __init__(self, hbm_budget=64 << 30, max_live=16, chunk=64, device=0, time_scale=1.0):
+    """Continuous batching on one GPU.  Plans are built by `planners` background threads (the
+    library call releases the interpreter), so live scenarios keep stepping while new requests
+    are planned; a request is admitted when a slot is free and the HBM estimate of its plan fits
+    the budget (the estimate is replaced by the plan's real footprint once it exists)."""
+
+    def __init__(self, hbm_budget=64 << 30, max_live=16, chunk=64, device=0, time_scale=1.0, planners=1,
+                 precision=None):
         import torch
         self.torch = torch
         self.budget, self.max_live, self.chunk, self.device = hbm_budget, max_live, chunk, device
         self.time_scale = time_scale
+        self.planners = planners
+        self.precision = precision
         self.used = 0
+
+    @staticmethod
+    def estimate(req):
+        """Footprint bound before the plan exists (operator + rings + histories), bytes."""
+        return req.N * 2_000_000
 
     def _admit(self, req):
         torch = self.torch
+        torch.cuda.set_device(self.device)
         xy, tau0 = req.inputs()
         stream = torch.cuda.Stream(device=self.device)
         dt = req.cfl  # dx = cs = 1
+        prec = self.precision if self.precision is not None else req.precision
         plan = fdph.Plan(xy, dt, req.M, req.eps, eta=req.eta, eps_st=req.eps_st, leaf_size=req.leaf,
-                         precision=req.precision, soe_terms=req.soe_terms, device=self.device,
+                         precision=prec, soe_terms=req.soe_terms, device=self.device,
                          stream=stream.cuda_stream)
         st = plan.stats()
         foot = st["arena_bytes"] + st["state_bytes"] + 3 * req.N * 8 * (self.chunk + 2)
@@ -105,41 +121,53 @@ class Server:
     def serve(self, requests, realtime=True):
         """Run all requests; returns summary metrics.  With realtime=False arrivals are ignored
         (everything waits at t = 0), which gives the closed-batch throughput."""
-        torch = self.torch
+        from concurrent.futures import ThreadPoolExecutor
         pending = sorted(requests, key=lambda r: r.arrival)
-        live = []
+        live, planning = [], {}
+        pool = ThreadPoolExecutor(max_workers=self.planners)
         t0 = time.perf_counter()
         steps_done = 0
-        while pending or live:
-            now = (time.perf_counter() - t0) * self.time_scale
-            while pending and len(live) < self.max_live and (not realtime or pending[0].arrival <= now):
-                est = pending[0].N * 2_000_000      # generous per-element estimate before the plan exists
-                if live and self.used + est > self.budget:
-                    break
-                req = pending.pop(0)
-                req.t_admit = time.perf_counter() - t0
-                s = self._admit(req)
-                req.t_planned = time.perf_counter() - t0
-                self.used += s["foot"]
-                live.append(s)
-            if not live:
-                time.sleep(0.001)
-                continue
-            for s in live:
-                req = s["req"]
-                k = min(self.chunk, req.M - s["n"])
-                s["plan"].rupture_run(k, s["D"], s["T"])
-                s["n"] += k
-                steps_done += k * req.N
-            still = []
-            for s in live:
-                if s["n"] >= s["req"].M:
-                    s["plan"].synchronize()
-                    s["req"].t_done = time.perf_counter() - t0
-                    self._finish(s)
-                else:
-                    still.append(s)
-            live = still
+        try:
+            while pending or live or planning:
+                now = (time.perf_counter() - t0) * self.time_scale
+                # admission: a free slot, an arrived request and room in the HBM budget
+                while (pending and len(live) + len(planning) < self.max_live
+                       and (not realtime or pending[0].arrival <= now)):
+                    est = self.estimate(pending[0])
+                    if (live or planning) and self.used + est > self.budget:
+                        break
+                    req = pending.pop(0)
+                    req.t_admit = time.perf_counter() - t0
+                    self.used += est
+                    planning[pool.submit(self._admit, req)] = (req, est)
+                # plans that are ready join the live set
+                for fut in [f for f in planning if f.done()]:
+                    req, est = planning.pop(fut)
+                    s = fut.result()
+                    req.t_planned = time.perf_counter() - t0
+                    self.used += s["foot"] - est
+                    live.append(s)
+                if not live:
+                    time.sleep(0.001)
+                    continue
+                # every live scenario advances by one chunk of steps, each on its own stream
+                for s in live:
+                    req = s["req"]
+                    k = min(self.chunk, req.M - s["n"])
+                    s["plan"].rupture_run(k, s["D"], s["T"])
+                    s["n"] += k
+                    steps_done += k * req.N
+                still = []
+                for s in live:
+                    if s["n"] >= s["req"].M:
+                        s["plan"].synchronize()
+                        s["req"].t_done = time.perf_counter() - t0
+                        self._finish(s)
+                    else:
+                        still.append(s)
+                live = still
+        finally:
+            pool.shutdown(wait=True)
         wall = time.perf_counter() - t0
         lat = np.array([r.t_done - (r.arrival / self.time_scale if realtime else 0.0) for r in requests])
         return {"element_steps_per_s": steps_done / wall, "wall_s": wall, "requests": len(requests),
@@ -147,8 +175,8 @@ class Server:
                 "element_steps": steps_done}
 
 
-def run_alone(req, chunk=64, device=0):
+def run_alone(req, chunk=64, device=0, precision=None):
     """The same request served on its own (reference for the mix)."""
-    srv = Server(max_live=1, chunk=chunk, device=device)
+    srv = Server(max_live=1, chunk=chunk, device=device, precision=precision)
     srv.serve([req], realtime=False)
     return req

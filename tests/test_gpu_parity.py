@@ -187,3 +187,68 @@ def test_rupture_matches_oracle(mode):
     D, T = Dd.cpu().numpy(), Td.cpu().numpy()
     assert (D0 > 0).sum() > 0.3 * D0.size          # the rupture spreads over the fault
     assert _rel(D, D0) < 1e-9 and _rel(T, T0) < 1e-10
+
+
+def test_cached_step_graphs_replay_bit_for_bit():
+    """fdph_run keeps its step graph per (D, T) buffers: a second run on the same buffers, runs
+    split at any step, and chunked runs through one staging buffer give the same T bit for bit."""
+    _need_gpu()
+    N, M = 150, 96
+    xy = _geom("curved", N)
+    D = inputs.gaussian_filtered_history(N, M, 5)
+    plan = fdph.Plan(xy, 0.5, M, 1e-4, eta=0.5, eps_st=1e-4, leaf_size=8, soe_terms=16)
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    plan.run(M, Dd, Td)
+    T1 = Td.cpu().numpy()
+    plan.reset()
+    plan.run(M, Dd, Td)                       # cached graph
+    assert np.array_equal(Td.cpu().numpy(), T1)
+    plan.reset()
+    plan.run(40, Dd, Td)
+    plan.run(M - 40, Dd[40:], Td[40:])
+    assert np.array_equal(Td.cpu().numpy(), T1)
+    plan.reset()
+    Dc = torch.empty((16, N), dtype=torch.float64, device="cuda")
+    Tc = torch.empty_like(Dc)
+    out = np.empty_like(T1)
+    for c in range(0, M, 16):
+        Dc.copy_(Dd[c:c + 16])
+        plan.run(16, Dc, Tc)                  # same buffers every call: rows restart at 0
+        out[c:c + 16] = Tc.cpu().numpy()
+    assert np.array_equal(out, T1)
+
+
+def test_rupture_graph_equals_stepwise_rupture():
+    """fdph_rupture_run (one replayed step graph, also in chunks through one buffer pair) equals
+    fdph_rupture_step called step by step, bit for bit."""
+    _need_gpu()
+    N, M, dt = 140, 96, 0.5
+    xy = _geom("kinked", N)
+    tau0 = np.full(N, 0.45)
+    tau0[N // 2 - 6:N // 2 + 6] = 0.61
+    t0 = torch.from_numpy(tau0).cuda()
+    outs = []
+    for mode in ("graph", "steps", "chunks"):
+        plan = fdph.Plan(xy, dt, M, 1e-5, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
+        plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0)
+        Dd = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+        Td = torch.zeros_like(Dd)
+        if mode == "graph":
+            plan.rupture_run(M, Dd, Td)
+        elif mode == "steps":
+            for n in range(M):
+                plan.rupture_step(Dd[n], Td[n])
+        else:
+            Dc = torch.zeros((32, N), dtype=torch.float64, device="cuda")
+            Tc = torch.zeros_like(Dc)
+            for c in range(0, M, 32):
+                plan.rupture_run(32, Dc, Tc)
+                Dd[c:c + 32].copy_(Dc)
+                Td[c:c + 32].copy_(Tc)
+        plan.synchronize()
+        outs.append((Dd.cpu().numpy(), Td.cpu().numpy()))
+        plan.close()
+    assert (outs[0][0] > 0).any()
+    for D_, T_ in outs[1:]:
+        assert np.array_equal(D_, outs[0][0]) and np.array_equal(T_, outs[0][1])

@@ -199,14 +199,18 @@ def test_cached_step_graphs_replay_bit_for_bit():
     plan = fdph.Plan(xy, 0.5, M, 1e-4, eta=0.5, eps_st=1e-4, leaf_size=8, soe_terms=16)
     Dd = torch.from_numpy(D).cuda()
     Td = torch.empty_like(Dd)
+    torch.cuda.synchronize()
     plan.run(M, Dd, Td)
+    plan.synchronize()                        # the plan has its own stream
     T1 = Td.cpu().numpy()
     plan.reset()
     plan.run(M, Dd, Td)                       # cached graph
+    plan.synchronize()
     assert np.array_equal(Td.cpu().numpy(), T1)
     plan.reset()
     plan.run(40, Dd, Td)
     plan.run(M - 40, Dd[40:], Td[40:])
+    plan.synchronize()
     assert np.array_equal(Td.cpu().numpy(), T1)
     plan.reset()
     Dc = torch.empty((16, N), dtype=torch.float64, device="cuda")
@@ -214,7 +218,9 @@ def test_cached_step_graphs_replay_bit_for_bit():
     out = np.empty_like(T1)
     for c in range(0, M, 16):
         Dc.copy_(Dd[c:c + 16])
+        torch.cuda.synchronize()
         plan.run(16, Dc, Tc)                  # same buffers every call: rows restart at 0
+        plan.synchronize()
         out[c:c + 16] = Tc.cpu().numpy()
     assert np.array_equal(out, T1)
 
@@ -234,6 +240,7 @@ def test_rupture_graph_equals_stepwise_rupture():
         plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0)
         Dd = torch.zeros((M, N), dtype=torch.float64, device="cuda")
         Td = torch.zeros_like(Dd)
+        torch.cuda.synchronize()
         if mode == "graph":
             plan.rupture_run(M, Dd, Td)
         elif mode == "steps":
@@ -242,10 +249,13 @@ def test_rupture_graph_equals_stepwise_rupture():
         else:
             Dc = torch.zeros((32, N), dtype=torch.float64, device="cuda")
             Tc = torch.zeros_like(Dc)
+            torch.cuda.synchronize()
             for c in range(0, M, 32):
                 plan.rupture_run(32, Dc, Tc)
+                plan.synchronize()                # the plan has its own stream
                 Dd[c:c + 32].copy_(Dc)
                 Td[c:c + 32].copy_(Tc)
+                torch.cuda.synchronize()
         plan.synchronize()
         outs.append((Dd.cpu().numpy(), Td.cpu().numpy()))
         plan.close()

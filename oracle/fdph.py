@@ -287,15 +287,16 @@ def near_leaf(el, lf, p):
     """Exact kernel up to m_S(i, j), then the static kernel (App. E, App. H).
 
     With p.soe_terms = Q > 0 (an extension of this implementation, not the paper's): the exact
-    kernel is kept for every pair of the leaf up to W = max m_S, and beyond W the difference
-    K - K_stat dt is represented by its least-squares fit on the exponentials
-    exp(-lambda_q (k - W)), q < Q (soe_rates), instead of being dropped.
+    kernel is kept for every pair of the leaf up to W = the leaf's longest wave passage (both end
+    points' fronts + n_c steps), and beyond W the difference K - K_stat dt is represented by its
+    least-squares fit on the exponentials exp(-lambda_q (k - W)), q < Q (soe_rates), instead of
+    being dropped; m_S plays no part then.
     """
     I, J = lf["tau"].idx, lf["sig"].idx
     K = kn.discrete_kernel(el, p.dt, p.M, p.mu, p.cs, I, J)          # [M, nr, ns]
     Ks = kn.static_kernel(el, p.mu, I, J)
     tail = None
-    if p.eps_st > 0.0:
+    if p.eps_st > 0.0 or p.soe_terms > 0:
         thr = p.eps_st * p.mu / (2.0 * p.cs)
         tail = kn.tail_kernel(el, p.dt, p.M, p.mu, p.cs, I, J)
         big = np.abs(tail) >= thr
@@ -307,14 +308,14 @@ def near_leaf(el, lf, p):
     out = dict(I=I, J=J, K=K, Ks=Ks, mS=mS)
     if p.soe_terms > 0:
         Q = p.soe_terms
-        # the window must also outlast the wave passage of every pair (both end points' fronts
+        # the window covers the wave passage of every pair (both end points' fronts
         # plus the n_c extra steps of Domain F), since a fit on smooth exponentials cannot
         # represent a wavefront
         nc = default_extra_steps(el, p) if p.extra_steps < 0 else p.extra_steps
         far_end = np.maximum(_dist(el["mx"][I][:, None], el["my"][I][:, None], el["ax"][J][None, :], el["ay"][J][None, :]),
                              _dist(el["mx"][I][:, None], el["my"][I][:, None], el["bx"][J][None, :], el["by"][J][None, :]))
         passage = np.ceil(far_end / (p.cs * p.dt)).astype(np.int64) + nc
-        W = int(max(mS.max(), passage.max()))
+        W = int(passage.max())           # the fit takes over once the wave has passed (no m_S cut)
         if p.M - W < soe_min_len(W):     # too short a tail to fit well: keep the kernel exact
             W = p.M
         fit = np.zeros((p.M - W, I.size, J.size))

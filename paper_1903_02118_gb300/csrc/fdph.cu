@@ -877,6 +877,7 @@ struct fdph_plan_s {
     };
     std::vector<GraphEntry> graphs;
     int* n_dev = nullptr;
+    int near_priority = 0;    // greatest stream priority of the device
     // branches of a step that run concurrently with the near field: [0] FIR + scatter,
     // [1] transient convolution + Eq. 39 evaluation (fork after push, join before gather)
     cudaStream_t side[2] = {nullptr, nullptr};
@@ -982,6 +983,24 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// The near-field kernel is persistent with a static schedule (one CTA pair per SM), so it is
+// launched at the greatest stream priority: when it shares the GPU with the far-field branches of
+// the same step its CTAs are placed first and none starts late.
+template <class T>
+static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_cta);
+    cfg.blockDim = dim3(kNearThreads);
+    cfg.dynamicSmemBytes = NearCfg<T>::smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = P->near_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, near_kernel<T>, a);
+}
+
 template <class T>
 static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
@@ -996,7 +1015,7 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         if (a.n_sct) scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, P->side[0]>>>(a);
         if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, P->side[1]>>>(a);
         if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, P->side[1]>>>(a);
-        if (a.n_cta) near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
+        if (a.n_cta) launch_near<T>(P, a, s);
         cudaEventRecord(P->ev_join[0], P->side[0]);
         cudaEventRecord(P->ev_join[1], P->side[1]);
         cudaStreamWaitEvent(s, P->ev_join[0], 0);
@@ -1010,7 +1029,7 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
-        near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
+        launch_near<T>(P, a, s);
     }
     {
         ProfScope ps(P, 5);
@@ -1063,7 +1082,7 @@ static int step_graph(fdph_plan_t P, int kind, const double* D, double* Tout, in
         set_error(std::string("graph capture: ") + cudaGetErrorString(e));
         return FDPH_E_CUDA;
     }
-    e = cudaGraphInstantiate(ex, g, 0);
+    e = cudaGraphInstantiate(ex, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -1203,7 +1222,7 @@ static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaSt
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
-        near_kernel<T><<<a.n_cta, kNearThreads, NearCfg<T>::smem, s>>>(a);
+        launch_near<T>(P, a, s);
     }
     {
         ProfScope ps(P, 5);
@@ -1245,6 +1264,14 @@ template <class T>
 static int build_near(fdph_plan_t P, const PlanInputs& in) {
     HostPlan& hp = P->hp;
     const int nl = (int)hp.near_r0.size();
+    const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
+    const auto t_start = std::chrono::steady_clock::now();
+    auto stamp = [&](const char* what) {   // stage times of the near-field build (device-synchronised)
+        if (!verbose) return;
+        cudaDeviceSynchronize();
+        fprintf(stderr, "[fdph_plan]   %-26s %8.3f s\n", what,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+    };
     GeoDev g;
     double *px, *py, *nx, *ny, *ax, *ay, *tx, *ty, *ln;
     int rc;
@@ -1267,19 +1294,23 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             return rc;
         std::vector<long long> p0(pair0.begin(), pair0.end() - 1);
         if ((rc = upload(P, &d_p0, p0))) return rc;
-        const double thr = in.eps_st * in.mu / (2.0 * in.cs);
-        near_ms_kernel<<<blocks(npairs, 128), 128>>>(g, d_r, d_nr, d_s, d_ns, d_p0, npairs, nl, in.M, in.dt,
-                                                      in.mu, in.cs, thr, d_ms);
-        FDPH_CUDA(cudaGetLastError());
-        ms.resize(npairs);
-        FDPH_CUDA(cudaMemcpy(ms.data(), d_ms, npairs * sizeof(int), cudaMemcpyDeviceToHost));
-        for (int l = 0; l < nl; ++l)
-            for (long long q = pair0[l]; q < pair0[l + 1]; ++q) W[l] = std::max(W[l], ms[q]);
+        ms.assign(npairs, 0);
+        if (in.soe == 0) {   // the paper's cut: exact kernel up to each pair's m_S (App. H)
+            const double thr = in.eps_st * in.mu / (2.0 * in.cs);
+            near_ms_kernel<<<blocks(npairs, 128), 128>>>(g, d_r, d_nr, d_s, d_ns, d_p0, npairs, nl, in.M, in.dt,
+                                                          in.mu, in.cs, thr, d_ms);
+            FDPH_CUDA(cudaGetLastError());
+            FDPH_CUDA(cudaMemcpy(ms.data(), d_ms, npairs * sizeof(int), cudaMemcpyDeviceToHost));
+            for (int l = 0; l < nl; ++l)
+                for (long long q = pair0[l]; q < pair0[l + 1]; ++q) W[l] = std::max(W[l], ms[q]);
+        }
+        stamp("near: windows");
     }
     std::vector<char> has_tail(nl, 0);
     if (in.soe > 0) {
-        // exponential tails: the window also covers every pair's wave passage (both end-point
-        // fronts + n_c steps); the exact kernel is kept for all pairs up to the leaf's window
+        // exponential tails: the window covers every pair's wave passage (both end-point fronts +
+        // n_c steps), the exact kernel is kept for all pairs up to the leaf's window, and the
+        // smooth remainder beyond it is fitted (no m_S cut is needed)
         const double cdt = in.cs * in.dt;
         for (int l = 0; l < nl; ++l) {
             for (int il = 0; il < hp.near_nr[l]; ++il) {
@@ -1342,6 +1373,7 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         }
         FDPH_CUDA(cudaGetLastError());
     }
+    stamp("near: exact windows filled");
     if (in.soe > 0 && hp.near_tail_len > 0) {
         // all tail leaves in one launch, then one Cholesky solve per leaf on the host
         std::vector<NearDev> tl;
@@ -1365,6 +1397,7 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         FDPH_CUDA(cudaGetLastError());
         std::vector<double> gh((size_t)ntp * in.soe), ch((size_t)ntp * in.soe);
         FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        stamp("near: tail projections");
         // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
         std::vector<size_t> toff(tl.size() + 1, 0);
         for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sl;
@@ -1385,6 +1418,7 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             FDPH_CUDA(cudaMemcpy(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(T),
                                  cudaMemcpyHostToDevice));
     }
+    stamp("near: tail fits");
     // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
     // largest first to the least-loaded CTA (steady-state bytes)
     FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<T>::smem));
@@ -1676,6 +1710,10 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if (cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
         set_error("cudaEventCreate failed");
         return fail(FDPH_E_CUDA);
+    }
+    {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) P->near_priority = greatest;
     }
     PlanInputs in = make_inputs(material, dt, M, eps, p);
     Elements el = make_elements(geometry->n, geometry->xy);

@@ -35,6 +35,7 @@ CONFIGS = {
                     M=8192, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="straight"),
 }
 DT = 0.5
+DTYPE = {0: "f64", 1: "f32-storage/f64-accumulate", 2: "f16-near-window/f32-storage/f64-accumulate"}
 
 # DRAM traffic of the near-field kernel from one ncu capture (profiles/near_kernel_curved_n2048_m1024_fp32_soe16.md):
 # curved N = 2048, M = 1024, FP32, Q = 16, steady state: dram read + write per launch 1.4636 GB against
@@ -43,7 +44,7 @@ DT = 0.5
 # figure is only reported while the near-field kernel's source (near_kernel_source_hash) is the
 # one that was captured.
 NEAR_NCU = {"source_sha256": "8b430ff9c128f85acf8d4c69d09024214a120a793041d1ddb9f905bd35c01c4c",
-            "ratio": 1.4636 / 1.5497, "capture": "curved N=2048 M=1024 FP32 Q=16, 2 steady-state launches"}
+            "ratio": 1.4636 / 1.5497, "precision": 1, "capture": "curved N=2048 M=1024 FP32 Q=16, 2 steady-state launches"}
 
 
 def near_kernel_source_hash():
@@ -196,7 +197,7 @@ def run_rupture(args, cfg):
     tau0[N // 2 - 32:N // 2 + 32] = 0.61
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    prec = fdph.FP32 if args.precision == "fp32" else fdph.FP64
+    prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[args.precision]
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
@@ -222,7 +223,7 @@ def run_rupture(args, cfg):
     line = {"metric": "element-steps/s", "value": world * N * K / (ms * 1e-3), "unit": "element-steps/s",
             "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == fdph.FP64 else "f32-storage/f64-accumulate", "data": "synthetic",
+            "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
                        "first_timed_step": n0 + W, "note": "N reduced from 16384 (host plan time)"},
@@ -264,7 +265,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fdph", choices=sorted(CONFIGS) + ["serving"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16"],
+                    help="storage: fp16 keeps the near-field window in FP16 (products in FP32)")
     ap.add_argument("--soe", type=int, default=16, help="exponential-tail terms (0: the paper's static cut)")
     ap.add_argument("--eta", type=float, default=None)
     ap.add_argument("--eps-st", type=float, default=None)
@@ -309,7 +311,7 @@ def main():
     # the library's kernels
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    prec = fdph.FP32 if args.precision == "fp32" else fdph.FP64
+    prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[args.precision]
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
@@ -375,7 +377,7 @@ def main():
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = near_bytes / (near_ms * 1e-3) / 1e9
     same = near_kernel_source_hash() == NEAR_NCU["source_sha256"]
-    traffic = NEAR_NCU["ratio"] * near_bytes if (same and prec == fdph.FP32 and cfg.get("soe")) else None
+    traffic = NEAR_NCU["ratio"] * near_bytes if (same and prec == NEAR_NCU["precision"] and cfg.get("soe")) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "traffic_note": ("ncu dram read+write per launch scaled from " + NEAR_NCU["capture"]) if traffic
@@ -411,7 +413,7 @@ def main():
 
     line = {"metric": "element-steps/s", "value": value, "unit": "element-steps/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == fdph.FP64 else "f32-storage/f64-accumulate",
+            "vs_baseline": None, "dtype": DTYPE[prec],
             "data": "synthetic",
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,

@@ -52,9 +52,15 @@ typedef enum fdph_status {
 
 typedef enum fdph_precision {
     FDPH_FP64 = 0,         /* factors, waveforms and near-field tensor stored and multiplied in FP64 */
-    FDPH_FP32 = 1          /* stored in FP32; near-field products summed in FP32 within one work
+    FDPH_FP32 = 1,         /* stored in FP32; near-field products summed in FP32 within one work
                               item (<= 64 steps x 32 sources) and in FP64 across items; far-field
                               sums, rings and accumulators stay FP64 */
+    FDPH_FP16 = 2          /* as FDPH_FP32, but the near-field window coefficients (the exact
+                              kernel of the inadmissible leaves, the bulk of the bytes) are stored
+                              in FP16 and converted to FP32 for the products; the near-field static
+                              and tail coefficients stay FP32.  Adds a rounding error of at most
+                              2^-11 of each stored coefficient (about 1e-3 relative on the test
+                              faults); BF16 (2^-8) was measured at 6e-3 to 9e-3 and is not offered */
 } fdph_precision;
 
 typedef struct fdph_plan_s* fdph_plan_t;

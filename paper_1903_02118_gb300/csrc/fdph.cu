@@ -17,6 +17,7 @@
 //            partials, written in the caller's element order
 // Causality (min(dm + delay) >= 1, checked at plan time) guarantees that the ring slots read
 // at step n were completed by steps < n and that the slots written at step n are not read.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -72,7 +73,7 @@ struct SbDev {
 };
 
 struct NearDev {
-    int r0, nr, s0, ns, W, sl;
+    int r0, nr, s0, ns, W, sl, sla, pad;
     long long tensor, stat, tail, vstate;
 };
 
@@ -133,8 +134,8 @@ struct StepArgs {
     const int* cta_ptr;       // [n_cta + 1]: CTA c owns tasks [cta_ptr[c], cta_ptr[c+1])
     int n_cta;
     int n_items;
-    const T* tensor;
-    const T* stat;            // aux slices (static tiles, exponential-tail coefficients)
+    const void* tensor;       // near-field window slices (window storage type)
+    const void* stat;         // aux slices: static tiles, exponential-tail coefficients (aux storage type)
     double* partial;          // [n_items][32]
     const int* np_ptr;
     const int* np_idx;
@@ -414,7 +415,7 @@ __device__ __forceinline__ void near_issue(const StepArgs<T>& a, const NearTask&
     }
 }
 
-template <class T>
+template <class R, class T>
 __device__ __forceinline__ void near_commit(const StepArgs<T>& a, const NearTask& tk, int n, int warp, int lane,
                                             const double (&r)[kRowsPerWarp], double dW, unsigned char* vb) {
     const int nsl = near_slices<T>(tk, n);
@@ -430,17 +431,101 @@ __device__ __forceinline__ void near_commit(const StepArgs<T>& a, const NearTask
                     a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane] = v;
                 }
             }
-            ((T*)vb)[k * 32 + lane] = (T)v;
+            ((R*)vb)[k * 32 + lane] = (R)v;
         }
     }
 }
 
-template <class T>
+// Near-field storage: window slices in H; aux slices (static tile, tail coefficients) in the aux
+// type (FP32 when the window is FP16: the static term multiplies the cumulative slip, so its
+// coefficients keep FP32); slip-rate vectors and products in the row type R.
+template <class H> struct NearTypes { using Aux = H; using Row = H; };
+template <> struct NearTypes<__half> { using Aux = float; using Row = float; };
+
+template <class H>
 struct NearCfg {
-    static constexpr int stages = sizeof(T) == 4 ? 5 : 4;          // shared-memory pipeline depth
-    static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(T);  // one item's vectors
+    using R = typename NearTypes<H>::Row;
+    static constexpr int stages = sizeof(R) == 4 ? 5 : 4;          // shared-memory pipeline depth
+    static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(R);  // one item's vectors
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
 };
+
+// slice . vector for one receiver lane: 16-byte loads of the source-interleaved slice (plan.h)
+// and of the vector row; products and the sum in the row type
+__device__ __forceinline__ float slice_dot(const float* buf, const float* vrow, int ns, int nr, int li) {
+    const float4* tile = (const float4*)buf + li;
+    const float4* d = (const float4*)vrow;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    const int nb = (ns + 3) >> 2;
+    if (nb == 8 && nr == 32) {
+#pragma unroll
+        for (int jb = 0; jb < 8; ++jb) {
+            const float4 x = tile[jb * 32];
+            const float4 y = d[jb];
+            s0 = fmaf(x.x, y.x, s0);
+            s1 = fmaf(x.y, y.y, s1);
+            s2 = fmaf(x.z, y.z, s2);
+            s3 = fmaf(x.w, y.w, s3);
+        }
+    } else {
+        for (int jb = 0; jb < nb; ++jb) {
+            const float4 x = tile[jb * nr];
+            const float4 y = d[jb];
+            s0 = fmaf(x.x, y.x, s0);
+            s1 = fmaf(x.y, y.y, s1);
+            s2 = fmaf(x.z, y.z, s2);
+            s3 = fmaf(x.w, y.w, s3);
+        }
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+__device__ __forceinline__ double slice_dot(const double* buf, const double* vrow, int ns, int nr, int li) {
+    const double2* tile = (const double2*)buf + li;
+    const double2* d = (const double2*)vrow;
+    double s0 = 0.0, s1 = 0.0;
+    const int nb = (ns + 1) >> 1;
+    for (int jb = 0; jb < nb; ++jb) {
+        const double2 x = tile[jb * nr];
+        const double2 y = d[jb];
+        s0 = fma(x.x, y.x, s0);
+        s1 = fma(x.y, y.y, s1);
+    }
+    return s0 + s1;
+}
+
+__device__ __forceinline__ float half8_dot(const uint4 x, const float4 y0, const float4 y1, float acc) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&x.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&x.z));
+    const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&x.w));
+    acc = fmaf(a.x, y0.x, acc);
+    acc = fmaf(a.y, y0.y, acc);
+    acc = fmaf(b.x, y0.z, acc);
+    acc = fmaf(b.y, y0.w, acc);
+    acc = fmaf(c.x, y1.x, acc);
+    acc = fmaf(c.y, y1.y, acc);
+    acc = fmaf(e.x, y1.z, acc);
+    return fmaf(e.y, y1.w, acc);
+}
+
+// FP16 slices: 8 sources per 16-byte load, converted to FP32
+__device__ __forceinline__ float slice_dot(const __half* buf, const float* vrow, int ns, int nr, int li) {
+    const uint4* tile = (const uint4*)buf + li;
+    const float4* d = (const float4*)vrow;
+    float s0 = 0.f, s1 = 0.f;
+    const int nb = (ns + 7) >> 3;
+    if (nb == 4 && nr == 32) {
+#pragma unroll
+        for (int jb = 0; jb < 4; jb += 2) {
+            s0 = half8_dot(tile[jb * 32], d[2 * jb], d[2 * jb + 1], s0);
+            s1 = half8_dot(tile[(jb + 1) * 32], d[2 * jb + 2], d[2 * jb + 3], s1);
+        }
+    } else {
+        for (int jb = 0; jb < nb; ++jb) s0 = half8_dot(tile[jb * nr], d[2 * jb], d[2 * jb + 1], s0);
+    }
+    return s0 + s1;
+}
 static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer");
 
 // Near field (App. E), persistent and warp-specialised.  Each CTA owns a list of work items
@@ -451,9 +536,11 @@ static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer
 // one; consumer warp w takes slices w, w + kNearConsumers, ... of each stage, lane i = receiver i,
 // reading its coefficients and the vector 16 bytes at a time.  At the end of an item the
 // consumers' sums are combined in FP64 into the item's partial-sum slot.
-template <class T>
+template <class T, class H>
 __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
-    using C = NearCfg<T>;
+    using C = NearCfg<H>;
+    using A = typename NearTypes<H>::Aux;
+    using R = typename NearTypes<H>::Row;
     extern __shared__ __align__(128) unsigned char near_smem[];
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][32];
@@ -485,11 +572,12 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
             const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
             for (int ti = t0; ti < t1; ++ti) {
                 const NearTask tk = task(ti);
-                constexpr int esz = (int)sizeof(T);
+                const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
                 const int nsl = near_slices<T>(tk, n);
                 const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
                 const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
-                const unsigned char* src = (const unsigned char*)((tk.kind ? a.stat : a.tensor) + tk.off);
+                const unsigned char* src = tk.kind ? (const unsigned char*)((const A*)a.stat + tk.off)
+                                                   : (const unsigned char*)((const H*)a.tensor + tk.off);
                 for (int q = 0; q < nst; ++q, ++g) {
                     const int s = g % C::stages;
                     if (!mbar_wait_bounded(&empty[s], (unsigned)(((g / C::stages) & 1) ^ 1))) {
@@ -512,7 +600,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
         if (t0 < t1) {
             nxt = task(t0);
             near_issue(a, nxt, n, warp, lane, rows, dW);
-            near_commit(a, nxt, n, warp, lane, rows, dW, vbuf);
+            near_commit<R>(a, nxt, n, warp, lane, rows, dW, vbuf);
         }
         consumer_barrier();
         int par = 0;
@@ -524,12 +612,12 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 near_issue(a, nxt, n, warp, lane, rows, dW);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
-            constexpr int esz = (int)sizeof(T);
+            const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
             const int nsl = near_slices<T>(tk, n);
             const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
             const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
             const int li = lane < tk.nr ? lane : 0;     // lanes past nr read a valid element, unused
-            T acc = (T)0;
+            R acc = (R)0;
             double accd = 0.0;
             for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % C::stages;
@@ -540,56 +628,16 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 }
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
                 for (int kk = warp; kk < cnt; kk += kNearConsumers) {
-                    const int row = q * per + kk;
-                    T sum;
-                    if (sizeof(T) == 4) {
-                        // 4 sources per 16-byte load: tile row jb holds sources 4 jb .. 4 jb + 3
-                        const float4* tile = (const float4*)(buf + (size_t)kk * tk.sl * 4) + li;
-                        const float4* d = (const float4*)(vrows + row * 128);
-                        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                        const int nb = (tk.ns + 3) >> 2;
-                        if (nb == 8 && tk.nr == 32) {
-#pragma unroll
-                            for (int jb = 0; jb < 8; ++jb) {
-                                const float4 x = tile[jb * 32];
-                                const float4 y = d[jb];
-                                s0 = fmaf(x.x, y.x, s0);
-                                s1 = fmaf(x.y, y.y, s1);
-                                s2 = fmaf(x.z, y.z, s2);
-                                s3 = fmaf(x.w, y.w, s3);
-                            }
-                        } else {
-                            for (int jb = 0; jb < nb; ++jb) {
-                                const float4 x = tile[jb * tk.nr];
-                                const float4 y = d[jb];
-                                s0 = fmaf(x.x, y.x, s0);
-                                s1 = fmaf(x.y, y.y, s1);
-                                s2 = fmaf(x.z, y.z, s2);
-                                s3 = fmaf(x.w, y.w, s3);
-                            }
-                        }
-                        sum = (T)((s0 + s1) + (s2 + s3));
-                    } else {
-                        // FP64 storage: 2 sources per 16-byte load
-                        const double2* tile = (const double2*)(buf + (size_t)kk * tk.sl * 8) + li;
-                        const double2* d = (const double2*)(vrows + row * 256);
-                        double s0 = 0.0, s1 = 0.0;
-                        const int nb = (tk.ns + 1) >> 1;
-                        for (int jb = 0; jb < nb; ++jb) {
-                            const double2 x = tile[jb * tk.nr];
-                            const double2 y = d[jb];
-                            s0 = fma(x.x, y.x, s0);
-                            s1 = fma(x.y, y.y, s1);
-                        }
-                        sum = (T)(s0 + s1);
-                    }
-                    if (tk.kind) accd += (double)sum;   // static and tail slices: FP64 across slices
-                    else acc += sum;
+                    const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * 32 * sizeof(R));
+                    if (tk.kind)   // static and tail slices: FP64 across slices
+                        accd += (double)slice_dot((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
+                    else
+                        acc += slice_dot((const H*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            if (ti + 1 < t1) near_commit(a, nxt, n, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            if (ti + 1 < t1) near_commit<R>(a, nxt, n, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             red[par][warp][lane] = lane < tk.nr ? (double)acc + accd : 0.0;
             consumer_barrier();   // also publishes the next item's vectors
             if (warp == 0) {
@@ -744,9 +792,9 @@ __global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const in
 }
 
 // coefficients [k][j][i] for k < W: exact kernel below m_S(i, j), static * dt above
-template <class T>
+template <class H, class A>
 __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double dt, double mu, double c,
-                                 T* tensor, T* stat) {
+                                 H* tensor, A* stat) {
     const long long total = (long long)L.W * L.ns * L.nr;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
@@ -765,11 +813,11 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
             v = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
         }
-        constexpr int v4 = 16 / (int)sizeof(T);   // source-interleaved slices (plan.h)
-        tensor[L.tensor + (long long)k * L.sl + ((jl / v4) * L.nr + il) * v4 + jl % v4] = (T)v;
+        constexpr int vh = 16 / (int)sizeof(H), va = 16 / (int)sizeof(A);   // source-interleaved slices (plan.h)
+        tensor[L.tensor + (long long)k * L.sl + ((jl / vh) * L.nr + il) * vh + jl % vh] = (H)v;
         if (k == 0) {
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
-            stat[L.stat + ((jl / v4) * L.nr + il) * v4 + jl % v4] = (T)((g.nx[pi] * w.x + g.ny[pi] * w.y) * dt);
+            stat[L.stat + ((jl / va) * L.nr + il) * va + jl % va] = (A)((g.nx[pi] * w.x + g.ny[pi] * w.y) * dt);
         }
     }
 }
@@ -958,8 +1006,8 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.cta_ptr = P->cta_ptr;
     a.n_cta = P->n_cta;
     a.n_items = (int)P->hp.items.size();
-    a.tensor = (const T*)P->tensor;
-    a.stat = (const T*)P->stat;
+    a.tensor = P->tensor;
+    a.stat = P->stat;
     a.partial = P->partial;
     a.np_ptr = P->np_ptr;
     a.np_idx = P->np_idx;
@@ -991,14 +1039,21 @@ static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.n_cta);
     cfg.blockDim = dim3(kNearThreads);
-    cfg.dynamicSmemBytes = NearCfg<T>::smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributePriority;
     attr[0].val.priority = P->near_priority;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, near_kernel<T>, a);
+    if constexpr (sizeof(T) == 4) {
+        if (P->precision == FDPH_FP16) {
+            cfg.dynamicSmemBytes = NearCfg<__half>::smem;
+            cudaLaunchKernelEx(&cfg, near_kernel<T, __half>, a);
+            return;
+        }
+    }
+    cfg.dynamicSmemBytes = NearCfg<T>::smem;
+    cudaLaunchKernelEx(&cfg, near_kernel<T, T>, a);
 }
 
 template <class T>
@@ -1207,7 +1262,7 @@ static int check_device_error(fdph_plan_t P) {
 }
 
 static int step_impl(fdph_plan_t P, const double* D, double* T_) {
-    int rc = P->precision == FDPH_FP32 ? launch_step<float>(P, D, T_) : launch_step<double>(P, D, T_);
+    int rc = P->precision != FDPH_FP64 ? launch_step<float>(P, D, T_) : launch_step<double>(P, D, T_);
     if (rc == FDPH_OK) P->n += 1;
     return rc;
 }
@@ -1260,8 +1315,10 @@ static int rupture_graph(fdph_plan_t P, int steps, double* D, double* Tout) {
     return FDPH_OK;
 }
 
-template <class T>
+// T: far-field / step type; H: near-field window storage type (aux slices: NearTypes<H>::Aux)
+template <class T, class H>
 static int build_near(fdph_plan_t P, const PlanInputs& in) {
+    using A = typename NearTypes<H>::Aux;
     HostPlan& hp = P->hp;
     const int nl = (int)hp.near_r0.size();
     const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
@@ -1338,21 +1395,21 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
     for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
     int chunk = kChunk;
     while (chunk > 8 && slices / chunk < 4LL * 152 * 3) chunk /= 2;
-    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(T));
+    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
-        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
+        nd[l] = {L.r0, L.nr, L.s0, L.ns, L.W, L.sl, L.sla, 0, (long long)L.tensor, (long long)L.stat, (long long)L.tail,
                  (long long)L.vstate};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
-    T* tens = nullptr;
-    T* aux = nullptr;
+    H* tens = nullptr;
+    A* aux = nullptr;
     if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &aux, hp.near_aux_len))) return rc;
     P->tensor = tens;
     P->stat = aux;
-    if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(T)));  // slice padding
-    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(aux, 0, hp.near_aux_len * sizeof(T)));
+    if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(H)));  // slice padding
+    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(aux, 0, hp.near_aux_len * sizeof(A)));
     for (int l = 0; l < nl; ++l) {
         const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
         if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
@@ -1360,15 +1417,15 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         NearDev L = nd[l];
         if (L.W == 0) {
             // temporarily fill one k-slice into a scratch to get the static tile
-            T* tmp = nullptr;
+            H* tmp = nullptr;
             if ((rc = dalloc(P, &tmp, (size_t)L.sl))) return rc;
             NearDev L1 = L;
             L1.W = 1;
             L1.tensor = 0;
-            near_fill_kernel<T><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
+            near_fill_kernel<H, A><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
                                                                             in.mu, in.cs, tmp, aux);
         } else {
-            near_fill_kernel<T><<<std::min<long long>(blocks(tot, 256), 4096), 256>>>(
+            near_fill_kernel<H, A><<<std::min<long long>(blocks(tot, 256), 4096), 256>>>(
                 g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, aux);
         }
         FDPH_CUDA(cudaGetLastError());
@@ -1400,9 +1457,9 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         stamp("near: tail projections");
         // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
         std::vector<size_t> toff(tl.size() + 1, 0);
-        for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sl;
-        std::vector<T> tail_h(toff.back(), (T)0);
-        constexpr int v4 = 16 / (int)sizeof(T);
+        for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sla;
+        std::vector<A> tail_h(toff.back(), (A)0);
+        constexpr int v4 = 16 / (int)sizeof(A);
 #pragma omp parallel for schedule(dynamic, 8)
         for (long t = 0; t < (long)tl.size(); ++t) {
             const NearDev& L = tl[t];
@@ -1411,20 +1468,20 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
             for (int il = 0; il < L.nr; ++il)
                 for (int jl = 0; jl < L.ns; ++jl)
                     for (int q = 0; q < in.soe; ++q)
-                        tail_h[toff[t] + (size_t)q * L.sl + ((size_t)(jl / v4) * L.nr + il) * v4 + jl % v4] =
-                            (T)ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
+                        tail_h[toff[t] + (size_t)q * L.sla + ((size_t)(jl / v4) * L.nr + il) * v4 + jl % v4] =
+                            (A)ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
         }
         for (size_t t = 0; t < tl.size(); ++t)
-            FDPH_CUDA(cudaMemcpy(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(T),
+            FDPH_CUDA(cudaMemcpy(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(A),
                                  cudaMemcpyHostToDevice));
     }
     stamp("near: tail fits");
     // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
     // largest first to the least-loaded CTA (steady-state bytes)
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<T>::smem));
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
     int sms = 0, per_sm = 0;
     FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
-    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T>, kNearThreads, NearCfg<T>::smem));
+    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H>, kNearThreads, NearCfg<H>::smem));
     const int ni = (int)hp.items.size();
     const int ncta = std::max(1, std::min(ni, sms * std::max(per_sm, 1)));
     std::vector<NearTask> tasks_all(ni);
@@ -1441,12 +1498,12 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         t.kind = it.kind;
         t.nr = L.nr;
         t.ns = L.ns;
-        t.sl = L.sl;
+        t.sl = it.kind ? L.sla : L.sl;
         t.s0 = L.s0;
         t.W = L.W;
         t.vstate = (int)L.vstate;
         tasks_all[q] = t;
-        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)sizeof(T) + 4096.0;
+        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0;
     }
     std::vector<int> order(ni);
     for (int q = 0; q < ni; ++q) order[q] = q;
@@ -1481,7 +1538,8 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
 static void fill_stats(fdph_plan_t P) {
     HostPlan& hp = P->hp;
     fdph_stats& s = P->st;
-    const double ps = P->precision == FDPH_FP32 ? 4.0 : 8.0;
+    const double ps = P->precision != FDPH_FP64 ? 4.0 : 8.0;   // far factors and near aux slices
+    const double pw = P->precision == FDPH_FP16 ? 2.0 : ps;    // near window coefficients
     s.n = hp.n;
     s.M = hp.M;
     s.n_admissible = hp.n_adm;
@@ -1496,7 +1554,7 @@ static void fill_stats(fdph_plan_t P) {
     // algorithmic bytes of one steady-state step
     double near_b = 0, far_b = 0, flops = 0;
     for (const NearLeaf& L : hp.near) {
-        near_b += (double)L.W * L.ns * L.nr * ps + (double)L.ns * L.nr * ps;   // tensor + static tile
+        near_b += (double)L.W * L.ns * L.nr * pw + (double)L.ns * L.nr * ps;   // tensor + static tile
         near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
         flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
         if (L.tail >= 0) {                                                     // tail coefficients + states
@@ -1535,7 +1593,7 @@ static void fill_stats(fdph_plan_t P) {
     s.state_bytes = (long long)P->state_bytes;
     long long arena = 0;
     arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
-    arena += (long long)((hp.near_tensor_len + hp.near_aux_len) * ps);
+    arena += (long long)(hp.near_tensor_len * pw + hp.near_aux_len * ps);
     s.arena_bytes = arena;
 }
 
@@ -1579,9 +1637,9 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
         return FDPH_E_ARG;
     }
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 ||
-              (p->precision != FDPH_FP64 && p->precision != FDPH_FP32) ||
+              (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
-        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64 or FP32, "
+        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -1763,7 +1821,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
         (rc = upload(P, &P->g_il, hp.g_il)))
         return fail(rc);
-    if (P->precision == FDPH_FP32) {
+    if (P->precision != FDPH_FP64) {
         std::vector<float> f(hp.fac.begin(), hp.fac.end());
         float* d = nullptr;
         if ((rc = upload(P, &d, f))) return fail(rc);
@@ -1777,7 +1835,9 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if (hp.interp && (rc = upload(P, &P->phi, hp.phis))) return fail(rc);
     stamp("far-field upload");
     // ---- near field (device-evaluated kernel windows)
-    rc = P->precision == FDPH_FP32 ? build_near<float>(P, in) : build_near<double>(P, in);
+    rc = P->precision == FDPH_FP16   ? build_near<float, __half>(P, in)
+         : P->precision == FDPH_FP32 ? build_near<float, float>(P, in)
+                                     : build_near<double, double>(P, in);
     if (rc) return fail(rc);
     stamp("near field (windows, tails)");
 
@@ -1837,7 +1897,7 @@ int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
         return FDPH_E_STATE;
     }
     if (steps >= 8 && !P->prof)   // launch-bound steps: replay a captured graph of one step
-        return P->precision == FDPH_FP32 ? run_graph<float>(P, steps, D, T) : run_graph<double>(P, steps, D, T);
+        return P->precision != FDPH_FP64 ? run_graph<float>(P, steps, D, T) : run_graph<double>(P, steps, D, T);
     for (int s = 0; s < steps; ++s) {
         int rc = step_impl(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
         if (rc) return rc;
@@ -1865,7 +1925,7 @@ int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_
         FDPH_CUDA(cudaStreamSynchronize(P->stream));
         return check_device_error(P);
     }
-    rc = P->precision == FDPH_FP32 ? run_host<float>(P, steps, D_host, T_host)
+    rc = P->precision != FDPH_FP64 ? run_host<float>(P, steps, D_host, T_host)
                                    : run_host<double>(P, steps, D_host, T_host);
     if (rc) return rc;
     return check_device_error(P);
@@ -2013,7 +2073,7 @@ int fdph_rupture_step(fdph_plan_t P, double* D_n, double* T_n) {
         set_error("the plan has already taken M steps");
         return FDPH_E_STATE;
     }
-    int rc = P->precision == FDPH_FP32 ? launch_rupture_step<float>(P, D_n, T_n) : launch_rupture_step<double>(P, D_n, T_n);
+    int rc = P->precision != FDPH_FP64 ? launch_rupture_step<float>(P, D_n, T_n) : launch_rupture_step<double>(P, D_n, T_n);
     if (rc == FDPH_OK) P->n += 1;
     return rc;
 }
@@ -2029,7 +2089,7 @@ int fdph_rupture_run(fdph_plan_t P, int32_t steps, double* D, double* T) {
         return FDPH_E_STATE;
     }
     if (steps >= 8 && !P->prof)   // replay a captured graph of one rupture step
-        return P->precision == FDPH_FP32 ? rupture_graph<float>(P, steps, D, T) : rupture_graph<double>(P, steps, D, T);
+        return P->precision != FDPH_FP64 ? rupture_graph<float>(P, steps, D, T) : rupture_graph<double>(P, steps, D, T);
     for (int s = 0; s < steps; ++s) {
         int rc = fdph_rupture_step(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
         if (rc) return rc;

@@ -356,7 +356,7 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
 }
 
 void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
-                        int vec) {
+                        int vec, int vec_aux) {
     const int nl = (int)hp.near_r0.size();
     hp.near.resize(nl);
     hp.items.clear();
@@ -373,14 +373,15 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::
         L.ns = hp.near_ns[l];
         L.W = W[l];
         L.sl = (L.ns + vec - 1) / vec * vec * L.nr;
+        L.sla = (L.ns + vec_aux - 1) / vec_aux * vec_aux * L.nr;
         L.tensor = hp.near_tensor_len;                     // stays a multiple of vec elements
         hp.near_tensor_len += (int64_t)L.W * L.sl;
         const bool tail = hp.soe > 0 && has_tail[l];
         L.naux = 1 + (tail ? hp.soe : 0);
-        L.stat = hp.near_aux_len;                          // a multiple of vec elements, like sl
-        L.tail = tail ? L.stat + L.sl : -1;
-        hp.near_aux_len += (int64_t)L.naux * L.sl;
-        if (tail) hp.near_tail_len += (int64_t)hp.soe * L.sl;
+        L.stat = hp.near_aux_len;                          // a multiple of vec_aux elements, like sla
+        L.tail = tail ? L.stat + L.sla : -1;
+        hp.near_aux_len += (int64_t)L.naux * L.sla;
+        if (tail) hp.near_tail_len += (int64_t)hp.soe * L.sla;
         L.vstate = 0;
         if (tail) {
             L.vstate = hp.vstate_len;

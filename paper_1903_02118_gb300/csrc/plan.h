@@ -36,10 +36,11 @@ struct NearLeaf {
     // Slices are stored source-interleaved: element (j, i) of a slice at ((j / v) * nr + i) * v + j % v
     // with v = 16 bytes / element size, the sources padded with zeros to a multiple of v, so that a
     // receiver reads v sources with one 16-byte load.
-    int32_t sl;                  // slice stride: ceil(ns / v) v nr (v of the storage type)
+    int32_t sl;                  // window slice stride: ceil(ns / v) v nr (v of the window storage type)
+    int32_t sla;                 // aux slice stride, the same with v of the aux storage type
     int64_t tensor;              // offset of [W][sl] coefficients
-    // "aux" slices of the leaf (storage type, same layout), [naux][sl] at `stat`: slice 0 the
-    // static tile (x dt), slices 1..Q the exponential-tail coefficients (`tail`, -1: none)
+    // "aux" slices of the leaf (aux storage type, same layout), [naux][sla] at `stat`: slice 0
+    // the static tile (x dt), slices 1..Q the exponential-tail coefficients (`tail`, -1: none)
     int64_t stat;
     int64_t tail;
     int32_t naux;
@@ -91,8 +92,8 @@ struct HostPlan {
 // Everything except the near-field windows (which need the device). Returns status.
 int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
-// vec: sources per 16 bytes of the window storage type (4 for FP32, 2 for FP64).
+// vec, vec_aux: sources per 16 bytes of the window and aux storage types (8 FP16, 4 FP32, 2 FP64).
 void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
-                        int vec);
+                        int vec, int vec_aux);
 
 }  // namespace fdph

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfdph.so")
 
 OK, E_ARG, E_OOM, E_CAUSALITY, E_CUDA, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, FP32 = 0, 1
+FP64, FP32, FP16 = 0, 1, 2
 
 
 class FdphError(RuntimeError):

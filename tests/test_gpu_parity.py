@@ -262,3 +262,27 @@ def test_rupture_graph_equals_stepwise_rupture():
     assert (outs[0][0] > 0).any()
     for D_, T_ in outs[1:]:
         assert np.array_equal(D_, outs[0][0]) and np.array_equal(T_, outs[0][1])
+
+
+def test_fdph_fp16_near_window_within_rounding_bound():
+    """FP16 storage of the near-field window: every output is within the rounding bound of its
+    stored coefficients, |dT_i,n| <= 2^-11 sum |K_ijk| |D_j,n-k| + 2^-25 sum |D_j,n-k| over the
+    window entries (FP16 unit roundoff; subnormal spacing), plus the FP32 slack of the other
+    parts, against the oracle's compressed operator (FP64)."""
+    _need_gpu()
+    N, M, eps, leaf = 160, 900, 1e-5, 16
+    xy = _geom("curved", N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-4, soe_terms=16)
+    Kabs = np.zeros((M, N, N))
+    Kone = np.zeros((M, N, N))
+    for d in oplan["near"]:
+        I, J, W = d["I"], d["J"], d["W"]
+        Kabs[:W][:, I[:, None], J[None, :]] = np.abs(d["K"][:W])
+        Kone[:W][:, I[:, None], J[None, :]] = 1.0
+    B = dense.march(Kabs, np.abs(D)) * 2.0 ** -11 + dense.march(Kone, np.abs(D)) * 2.0 ** -25
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-4, leaf_size=leaf, soe_terms=16, precision=fdph.FP16)
+    T = _run(plan, D)
+    slack = 5e-6 * np.abs(T0).max()
+    assert np.all(np.abs(T - T0) <= B + slack)
+    assert _rel(T, T0) > 1e-7          # the rounding is there (not an FP32 path)

@@ -1315,17 +1315,27 @@ static int rupture_graph(fdph_plan_t P, int steps, double* D, double* Tout) {
     return FDPH_OK;
 }
 
+// Near-field build in two phases around the host factorisation of the admissible blocks, which
+// it does not need: build_near_begin (windows, exact tensors, tail projections launched on the
+// device) and build_near_finish (tail fits on the host, upload, persistent schedule).
+struct NearBuild {
+    std::vector<NearDev> tl;        // leaves with an exponential tail
+    std::vector<long long> tp0;     // their first pair
+    double* d_g = nullptr;          // projections on the device
+    long long ntp = 0;
+    bool tails = false;
+};
+
 // T: far-field / step type; H: near-field window storage type (aux slices: NearTypes<H>::Aux)
 template <class T, class H>
-static int build_near(fdph_plan_t P, const PlanInputs& in) {
+static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) {
     using A = typename NearTypes<H>::Aux;
     HostPlan& hp = P->hp;
     const int nl = (int)hp.near_r0.size();
     const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
     const auto t_start = std::chrono::steady_clock::now();
-    auto stamp = [&](const char* what) {   // stage times of the near-field build (device-synchronised)
+    auto stamp = [&](const char* what) {   // stage times of the near-field build
         if (!verbose) return;
-        cudaDeviceSynchronize();
         fprintf(stderr, "[fdph_plan]   %-26s %8.3f s\n", what,
                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
     };
@@ -1432,10 +1442,11 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
     }
     stamp("near: exact windows filled");
     if (in.soe > 0 && hp.near_tail_len > 0) {
-        // all tail leaves in one launch, then one Cholesky solve per leaf on the host
-        std::vector<NearDev> tl;
+        // all tail leaves in one launch (here), then one Cholesky solve per leaf on the host (finish)
+        std::vector<NearDev>& tl = nb.tl;
         std::vector<int> tl_id;
-        std::vector<long long> tp0{0};
+        std::vector<long long>& tp0 = nb.tp0;
+        tp0.assign(1, 0);
         for (int l = 0; l < nl; ++l)
             if (has_tail[l]) {
                 tl.push_back(nd[l]);
@@ -1452,9 +1463,35 @@ static int build_near(fdph_plan_t P, const PlanInputs& in) {
         near_soe_proj_kernel<<<blocks(ntp, 128), 128>>>(g, d_tl, d_tp0, (int)tl.size(), ntp, in.M, in.dt, in.mu, in.cs,
                                                         in.soe, P->rho, d_g);
         FDPH_CUDA(cudaGetLastError());
+        nb.d_g = d_g;
+        nb.ntp = ntp;
+        nb.tails = true;
+    }
+    stamp("near: tail projections launched");
+    return FDPH_OK;
+}
+
+template <class T, class H>
+static int build_near_finish(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) {
+    using A = typename NearTypes<H>::Aux;
+    HostPlan& hp = P->hp;
+    A* aux = (A*)P->stat;
+    int rc;
+    const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
+    const auto t_start = std::chrono::steady_clock::now();
+    auto stamp = [&](const char* what) {
+        if (!verbose) return;
+        fprintf(stderr, "[fdph_plan]   %-26s %8.3f s\n", what,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+    };
+    if (nb.tails) {
+        const std::vector<NearDev>& tl = nb.tl;
+        const std::vector<long long>& tp0 = nb.tp0;
+        const long long ntp = nb.ntp;
+        double* d_g = nb.d_g;
         std::vector<double> gh((size_t)ntp * in.soe), ch((size_t)ntp * in.soe);
         FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        stamp("near: tail projections");
+        stamp("near: tail projections done");
         // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
         std::vector<size_t> toff(tl.size() + 1, 0);
         for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sla;
@@ -1782,9 +1819,19 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
             fprintf(stderr, "[fdph_plan] %-28s %8.3f s\n", what,
                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     };
-    rc = build_host_plan(el, in, hp);
+    build_host_tree(el, in, hp);
+    stamp("cluster and block trees");
+    // near field on the device (exact windows, tail projections) while the host factorises the
+    // admissible blocks
+    NearBuild nb;
+    if (hp.soe > 0 && (rc = upload(P, &P->rho, hp.rho))) return fail(rc);
+    rc = P->precision == FDPH_FP16   ? build_near_begin<float, __half>(P, in, nb)
+         : P->precision == FDPH_FP32 ? build_near_begin<float, float>(P, in, nb)
+                                     : build_near_begin<double, double>(P, in, nb);
+    if (rc) return fail(rc);
+    rc = build_host_far(el, in, hp);
     if (verbose) fprintf(stderr, "[fdph_plan] host threads %d\n", omp_get_max_threads());
-    stamp("host plan (tree, LRA)");
+    stamp("host plan (admissible blocks)");
     if (rc == -3) return fail(FDPH_E_CAUSALITY);
     if (rc) return fail(FDPH_E_ARG);
     // ---- upload the far-field operator
@@ -1831,13 +1878,13 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         if ((rc = upload(P, &d, hp.fac))) return fail(rc);
         P->fac = d;
     }
-    if (hp.soe > 0 && ((rc = upload(P, &P->rho, hp.rho)) || (rc = upload(P, &P->trcoef, hp.trcoef)))) return fail(rc);
+    if (hp.soe > 0 && (rc = upload(P, &P->trcoef, hp.trcoef))) return fail(rc);
     if (hp.interp && (rc = upload(P, &P->phi, hp.phis))) return fail(rc);
     stamp("far-field upload");
     // ---- near field (device-evaluated kernel windows)
-    rc = P->precision == FDPH_FP16   ? build_near<float, __half>(P, in)
-         : P->precision == FDPH_FP32 ? build_near<float, float>(P, in)
-                                     : build_near<double, double>(P, in);
+    rc = P->precision == FDPH_FP16   ? build_near_finish<float, __half>(P, in, nb)
+         : P->precision == FDPH_FP32 ? build_near_finish<float, float>(P, in, nb)
+                                     : build_near_finish<double, double>(P, in, nb);
     if (rc) return fail(rc);
     stamp("near field (windows, tails)");
 

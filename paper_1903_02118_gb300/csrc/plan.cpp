@@ -191,6 +191,11 @@ int64_t append(std::vector<T>& dst, const T* src, size_t n) {
 }  // namespace
 
 int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
+    build_host_tree(el, in, hp);
+    return build_host_far(el, in, hp);
+}
+
+void build_host_tree(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     hp.n = el.n;
     hp.M = in.M;
     hp.dt = in.dt;
@@ -223,6 +228,17 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     }
     hp.n_adm = (int)adm.size();
     hp.n_near = (int)hp.near_r0.size();
+    hp.soe = in.soe;
+    hp.interp = in.interp;
+    if (in.soe > 0) hp.rho = soe_rho(in.M, in.soe);
+}
+
+int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
+    const Tree& tr = hp.tree;
+    const int n = el.n;
+    std::vector<const Leaf*> adm;
+    for (const Leaf& lf : tr.leaves)
+        if (lf.kind == 1) adm.push_back(&lf);
     std::vector<LeafOut> outs(adm.size());
 #pragma omp parallel for schedule(dynamic, 1)
     for (long a = 0; a < (long)adm.size(); ++a) admissible(el, tr, *adm[a], in, outs[a]);
@@ -331,9 +347,6 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             if (o.Dtr[cc] > 0) add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc], o.trsoe[cc], &o.trc[cc]);
     }
     hp.mean_rank = rank_cnt ? rank_sum / rank_cnt : 0.0;
-    hp.soe = in.soe;
-    hp.interp = in.interp;
-    if (in.soe > 0) hp.rho = soe_rho(in.M, in.soe);
     hp.g_ptr.assign(n + 1, 0);
     for (int p = 0; p < n; ++p) {
         hp.g_ptr[p + 1] = hp.g_ptr[p] + (int32_t)recv[p].size();

@@ -91,6 +91,11 @@ struct HostPlan {
 
 // Everything except the near-field windows (which need the device). Returns status.
 int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
+// The same in two stages: the cluster and block trees (with the near-leaf lists), then the
+// admissible blocks (ART integers, low-rank factors, waveforms, transients).  The near-field
+// build needs only the first stage, so the device can work on it during the second.
+void build_host_tree(const Elements& el, const PlanInputs& in, HostPlan& hp);
+int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
 // vec, vec_aux: sources per 16 bytes of the window and aux storage types (8 FP16, 4 FP32, 2 FP64).
 void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,

@@ -4,11 +4,11 @@
 // given rank is the truncated SVD, so the rank chosen here is the smallest r whose discarded
 // singular values satisfy the criterion.  The SVD is computed in two exact stages:
 //   1. Householder QR with column pivoting, stopped once the trailing block is below
-//      1e-12 |A|_F (A P = Q R + E): E changes the factors by at most 1e-12 relative, far
+//      1e-11 |A|_F (A P = Q R + E): E changes the factors by at most 1e-11 relative, far
 //      below any criterion eps used with the method, and it is counted in the discarded part
 //      of the rank decision.  Rounding noise of the kernel values makes the numerical rank
-//      at 1e-15 nearly full (512 x 512 blocks: ~490-514), while at 1e-12 it stays closer to
-//      the rank the criterion keeps, so this costs O(m n k) with a smaller k;
+//      at 1e-15 nearly full (512 x 512 blocks: ~490-514); at 1e-11 the mean k of the curved
+//      N = 4096 plan is 16 (30 at 1e-12), and the Jacobi stage below costs O(n k^2) a sweep;
 //   2. one-sided (Hestenes) Jacobi SVD of the k x n row space R P^T.
 // Factors are balanced: F = U_r sqrt(S_r), G = V_r sqrt(S_r).  When the chosen rank would
 // store at least as many numbers as the block (rank (m + n) >= m n) the block is kept exact
@@ -108,7 +108,7 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
     std::vector<std::vector<double>> hv;  // Householder vectors (length m - k)
     const int kmax = std::min(m, n);
     int k = 0;
-    const double stop2 = 1e-24 * norm2;
+    const double stop2 = 1e-22 * norm2;
     for (; k < kmax; ++k) {
         double trail = 0.0;
         int best = k;

@@ -240,8 +240,17 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     for (const Leaf& lf : tr.leaves)
         if (lf.kind == 1) adm.push_back(&lf);
     std::vector<LeafOut> outs(adm.size());
+    // largest blocks first, so that no big factorisation starts last (results stay in leaf order)
+    std::vector<long> order(adm.size());
+    for (long a = 0; a < (long)adm.size(); ++a) order[a] = a;
+    auto size_of = [&](long a) {
+        const ClusterNode& t = tr.nodes[adm[a]->tau];
+        const ClusterNode& g = tr.nodes[adm[a]->sig];
+        return (long)(t.hi - t.lo) * (g.hi - g.lo);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](long x, long y) { return size_of(x) > size_of(y); });
 #pragma omp parallel for schedule(dynamic, 1)
-    for (long a = 0; a < (long)adm.size(); ++a) admissible(el, tr, *adm[a], in, outs[a]);
+    for (long q = 0; q < (long)adm.size(); ++q) admissible(el, tr, *adm[order[q]], in, outs[order[q]]);
     for (const LeafOut& o : outs)
         if (!o.ok) {
             set_error("discretised causality min(dm_i + mbar_j) >= 1 violated by an admissible leaf");

@@ -248,12 +248,12 @@ def run_serving(args):
     build.build()
     kw = dict(n_min=256, n_max=2048, m_scale=0.5)
     reqs = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
-    mix = serving.Server(max_live=16, chunk=64, planners=2, precision=fdph.FP32).serve(reqs, realtime=True)
+    mix = serving.Server(max_live=16, chunk=64, planners=args.planners, precision=fdph.FP32).serve(reqs, realtime=True)
     ref = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
     alone = serving.Server(max_live=1, chunk=64, planners=1, precision=fdph.FP64).serve(ref, realtime=True)
     line = {"metric": "serving element-steps/s and time to solution", "requests": args.requests,
             "arrivals": "Poisson 8/s", "N_range": [256, 2048], "M": "N / CFL / 2, CFL in {0.25, 0.5}",
-            "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, **mix},
+            "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, "planners": args.planners, **mix},
             "one_at_a_time_fp64": {"precision": "f64", "max_live": 1, **alone},
             "data": "synthetic"}
     print(json.dumps(line))
@@ -277,6 +277,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override N (profiling of smaller cases)")
     ap.add_argument("--m", type=int, default=None, help="override M")
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
+    ap.add_argument("--planners", type=int, default=4, help="serving workload: plan-building threads")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)

@@ -194,6 +194,14 @@ int fdph_step_host(fdph_plan_t plan, const double* D_n_host, double* T_n_host);
  * one captured step graph.  Returns when T_host is complete.  Errors as fdph_run. */
 int fdph_run_host(fdph_plan_t plan, int32_t steps, const double* D_host, double* T_host);
 
+/* Self-test of the device-side timeout path (no counterpart in the paper): every wait of the
+ * library's pipelines polls an mbarrier a bounded number of times and, if it gives up, records
+ * the fact and lets the kernel finish, after which the host call returns FDPH_E_TIMEOUT and the
+ * CUDA context stays usable.  This call runs one such wait, with `polls` in [1, 2^24], on a
+ * barrier that nothing completes, on `device`.  Returns FDPH_E_TIMEOUT when the path works,
+ * FDPH_E_ARG for an out-of-range `polls`, FDPH_E_CUDA on a CUDA error. */
+int fdph_selftest_wait_timeout(int32_t device, int64_t polls);
+
 /* Return the plan to step 0 with zero history (rings, accumulators). */
 int fdph_reset(fdph_plan_t plan);
 

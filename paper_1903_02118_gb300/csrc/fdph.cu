@@ -347,9 +347,9 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
     return p;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
+__device__ __forceinline__ bool mbar_wait_limit(unsigned long long* bar, unsigned phase, long long limit) {
     const unsigned a = smem_u32(bar);
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         unsigned ok;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -359,6 +359,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
         if (ok) return true;
     }
     return false;
+}
+
+// every pipeline wait of the library: at most kWaitLimit polls, then the caller records a timeout
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned phase) {
+    return mbar_wait_limit(bar, phase, kWaitLimit);
+}
+
+// Self-test of the bounded wait: one CTA waits on an mbarrier that no thread ever completes; the
+// wait gives up after `limit` polls and records the timeout in err, and the kernel returns (no
+// copy is in flight), so the context stays usable.
+__global__ void wait_selftest_kernel(long long limit, int* err) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_limit(&bar, 0u, limit)) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
@@ -1990,6 +2008,34 @@ int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
     FDPH_CUDA(cudaMemcpyAsync(T_n_host, P->dT, P->N * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     return check_device_error(P);
+}
+
+int fdph_selftest_wait_timeout(int32_t device, int64_t polls) {
+    if (polls < 1 || polls > (1LL << 24)) {
+        set_error("fdph_selftest_wait_timeout: polls in [1, 2^24]");
+        return FDPH_E_ARG;
+    }
+    FDPH_CUDA(cudaSetDevice(device));
+    int* err = nullptr;
+    FDPH_CUDA(cudaMalloc(&err, sizeof(int)));
+    int h = 0;
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32>>>(polls, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) {
+        set_error(std::string("fdph_selftest_wait_timeout: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    if (h) {
+        set_error("bounded mbarrier wait gave up after " + std::to_string(polls) + " polls (self-test)");
+        return FDPH_E_TIMEOUT;
+    }
+    return FDPH_OK;
 }
 
 int fdph_current_step(fdph_plan_t P, int32_t* n) {

@@ -64,7 +64,7 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
-           "fdph_rupture_run", "fdph_rupture_slip"]
+           "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -104,6 +104,8 @@ def lib():
         L.fdph_rupture_step.argtypes = [c_p, c_p, c_p]
         L.fdph_rupture_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_rupture_slip.argtypes = [c_p, c_p]
+        L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
+        L.fdph_selftest_wait_timeout.restype = ctypes.c_int
         L.fdph_strerror.argtypes = [ctypes.c_int]
         L.fdph_strerror.restype = ctypes.c_char_p
         L.fdph_last_error.argtypes = []
@@ -128,6 +130,11 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return ctypes.c_void_p(x.data_ptr())
     return ctypes.c_void_p(int(x))
+
+
+def selftest_wait_timeout(device=0, polls=1000):
+    """Status of fdph_selftest_wait_timeout (E_TIMEOUT when the bounded-wait path works)."""
+    return lib().fdph_selftest_wait_timeout(int(device), int(polls))
 
 
 def default_params():

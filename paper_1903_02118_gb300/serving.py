@@ -170,9 +170,12 @@ class Server:
             pool.shutdown(wait=True)
         wall = time.perf_counter() - t0
         lat = np.array([r.t_done - (r.arrival / self.time_scale if realtime else 0.0) for r in requests])
+        plan_s = np.array([r.t_planned - r.t_admit for r in requests])
+        wait_s = np.array([r.t_admit - (r.arrival / self.time_scale if realtime else 0.0) for r in requests])
         return {"element_steps_per_s": steps_done / wall, "wall_s": wall, "requests": len(requests),
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                "element_steps": steps_done}
+                "element_steps": steps_done, "plan_s_p50": float(np.percentile(plan_s, 50)),
+                "plan_s_max": float(plan_s.max()), "admission_wait_s_p50": float(np.percentile(wait_s, 50))}
 
 
 def run_alone(req, chunk=64, device=0, precision=None):

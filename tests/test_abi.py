@@ -29,6 +29,11 @@ def test_library_exports_every_declared_symbol(L):
     assert declared <= set(fdph.EXPORTS)
 
 
+def test_timeout_selftest_rejects_bad_poll_counts_without_a_device(L):
+    assert L.fdph_selftest_wait_timeout(0, 0) == fdph.E_ARG
+    assert L.fdph_selftest_wait_timeout(0, (1 << 24) + 1) == fdph.E_ARG
+
+
 def test_invalid_arguments_are_rejected_without_a_device(L):
     g = fdph.Geometry(0, None)
     m = fdph.Material(1.0, 1.0)

@@ -103,6 +103,9 @@ typedef struct fdph_params {
                              delay dm_i + phi_i by linear interpolation between steps n - dm_i and
                              n - dm_i - 1 (the higher-order interpolation Sec. 4.3.1 mentions) */
     void* cuda_stream;    /* cudaStream_t the plan runs on; NULL => a stream the plan creates */
+    int32_t host_threads; /* host threads of the plan build (OpenMP); 0 (default) => the OpenMP
+                             default.  Callers that build several plans at once (a serving loop
+                             with planner threads) give each a share of the cores */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */

@@ -973,7 +973,9 @@ template <class T>
 static int upload(fdph_plan_t P, T** out, const std::vector<T>& v) {
     int rc = dalloc(P, out, v.size());
     if (rc) return rc;
-    if (!v.empty()) FDPH_CUDA(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    // ordered on the plan's stream (a pageable source is staged before the call returns)
+    if (!v.empty())
+        FDPH_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, P->stream));
     return FDPH_OK;
 }
 
@@ -1270,10 +1272,11 @@ static void prof_drain(fdph_plan_t P) {
 static int check_device_error(fdph_plan_t P) {
     int e = 0;
     if (!P->err) return FDPH_OK;
-    FDPH_CUDA(cudaMemcpy(&e, P->err, sizeof(int), cudaMemcpyDeviceToHost));
+    FDPH_CUDA(cudaMemcpyAsync(&e, P->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
     if (e) {
         set_error("a bounded mbarrier wait in the near-field kernel gave up; results of the step are invalid");
-        cudaMemset(P->err, 0, sizeof(int));
+        cudaMemsetAsync(P->err, 0, sizeof(int), P->stream);
         return FDPH_E_TIMEOUT;
     }
     return FDPH_OK;
@@ -1382,10 +1385,11 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
         ms.assign(npairs, 0);
         if (in.soe == 0) {   // the paper's cut: exact kernel up to each pair's m_S (App. H)
             const double thr = in.eps_st * in.mu / (2.0 * in.cs);
-            near_ms_kernel<<<blocks(npairs, 128), 128>>>(g, d_r, d_nr, d_s, d_ns, d_p0, npairs, nl, in.M, in.dt,
+            near_ms_kernel<<<blocks(npairs, 128), 128, 0, P->stream>>>(g, d_r, d_nr, d_s, d_ns, d_p0, npairs, nl, in.M, in.dt,
                                                           in.mu, in.cs, thr, d_ms);
             FDPH_CUDA(cudaGetLastError());
-            FDPH_CUDA(cudaMemcpy(ms.data(), d_ms, npairs * sizeof(int), cudaMemcpyDeviceToHost));
+            FDPH_CUDA(cudaMemcpyAsync(ms.data(), d_ms, npairs * sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+            FDPH_CUDA(cudaStreamSynchronize(P->stream));
             for (int l = 0; l < nl; ++l)
                 for (long long q = pair0[l]; q < pair0[l + 1]; ++q) W[l] = std::max(W[l], ms[q]);
         }
@@ -1415,7 +1419,7 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
             else has_tail[l] = 1;
             for (long long q = pair0[l]; q < pair0[l + 1]; ++q) ms[q] = W[l];   // exact over the window
         }
-        FDPH_CUDA(cudaMemcpy(d_ms, ms.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
+        FDPH_CUDA(cudaMemcpyAsync(d_ms, ms.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, P->stream));
     }
     // work-item length: the longest chunk (kChunk) that still yields about four waves of
     // resident CTAs (152 SMs x 3), so small problems (the plain config) fill the device too
@@ -1436,8 +1440,8 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
     if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &aux, hp.near_aux_len))) return rc;
     P->tensor = tens;
     P->stat = aux;
-    if (hp.near_tensor_len) FDPH_CUDA(cudaMemset(tens, 0, hp.near_tensor_len * sizeof(H)));  // slice padding
-    if (hp.near_aux_len) FDPH_CUDA(cudaMemset(aux, 0, hp.near_aux_len * sizeof(A)));
+    if (hp.near_tensor_len) FDPH_CUDA(cudaMemsetAsync(tens, 0, hp.near_tensor_len * sizeof(H), P->stream));  // padding
+    if (hp.near_aux_len) FDPH_CUDA(cudaMemsetAsync(aux, 0, hp.near_aux_len * sizeof(A), P->stream));
     for (int l = 0; l < nl; ++l) {
         const long long tot = (long long)nd[l].W * nd[l].ns * nd[l].nr;
         if (tot == 0 && nd[l].ns * nd[l].nr == 0) continue;
@@ -1450,10 +1454,10 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
             NearDev L1 = L;
             L1.W = 1;
             L1.tensor = 0;
-            near_fill_kernel<H, A><<<blocks((long long)L.ns * L.nr, 128), 128>>>(g, L1, d_ms + pair0[l], in.dt,
+            near_fill_kernel<H, A><<<blocks((long long)L.ns * L.nr, 128), 128, 0, P->stream>>>(g, L1, d_ms + pair0[l], in.dt,
                                                                             in.mu, in.cs, tmp, aux);
         } else {
-            near_fill_kernel<H, A><<<std::min<long long>(blocks(tot, 256), 4096), 256>>>(
+            near_fill_kernel<H, A><<<std::min<long long>(blocks(tot, 256), 4096), 256, 0, P->stream>>>(
                 g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, aux);
         }
         FDPH_CUDA(cudaGetLastError());
@@ -1478,7 +1482,7 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
         std::vector<long long> tp0s(tp0.begin(), tp0.end() - 1);
         if ((rc = upload(P, &d_tl, tl)) || (rc = upload(P, &d_tp0, tp0s)) || (rc = dalloc(P, &d_g, (size_t)ntp * in.soe)))
             return rc;
-        near_soe_proj_kernel<<<blocks(ntp, 128), 128>>>(g, d_tl, d_tp0, (int)tl.size(), ntp, in.M, in.dt, in.mu, in.cs,
+        near_soe_proj_kernel<<<blocks(ntp, 128), 128, 0, P->stream>>>(g, d_tl, d_tp0, (int)tl.size(), ntp, in.M, in.dt, in.mu, in.cs,
                                                         in.soe, P->rho, d_g);
         FDPH_CUDA(cudaGetLastError());
         nb.d_g = d_g;
@@ -1508,14 +1512,15 @@ static int build_near_finish(fdph_plan_t P, const PlanInputs& in, NearBuild& nb)
         const long long ntp = nb.ntp;
         double* d_g = nb.d_g;
         std::vector<double> gh((size_t)ntp * in.soe), ch((size_t)ntp * in.soe);
-        FDPH_CUDA(cudaMemcpy(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        FDPH_CUDA(cudaMemcpyAsync(gh.data(), d_g, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+        FDPH_CUDA(cudaStreamSynchronize(P->stream));
         stamp("near: tail projections done");
         // tail slices q = 1..Q of each leaf's aux block, [q][ns][nr] with slice stride sl
         std::vector<size_t> toff(tl.size() + 1, 0);
         for (size_t t = 0; t < tl.size(); ++t) toff[t + 1] = toff[t] + (size_t)in.soe * tl[t].sla;
         std::vector<A> tail_h(toff.back(), (A)0);
         constexpr int v4 = 16 / (int)sizeof(A);
-#pragma omp parallel for schedule(dynamic, 8)
+#pragma omp parallel for schedule(dynamic, 8) num_threads(in.threads)
         for (long t = 0; t < (long)tl.size(); ++t) {
             const NearDev& L = tl[t];
             const size_t b = (size_t)tp0[t] * in.soe;
@@ -1527,8 +1532,8 @@ static int build_near_finish(fdph_plan_t P, const PlanInputs& in, NearBuild& nb)
                             (A)ch[b + ((size_t)il * L.ns + jl) * in.soe + q];
         }
         for (size_t t = 0; t < tl.size(); ++t)
-            FDPH_CUDA(cudaMemcpy(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(A),
-                                 cudaMemcpyHostToDevice));
+            FDPH_CUDA(cudaMemcpyAsync(aux + tl[t].tail, tail_h.data() + toff[t], (toff[t + 1] - toff[t]) * sizeof(A),
+                                      cudaMemcpyHostToDevice, P->stream));
     }
     stamp("near: tail fits");
     // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
@@ -1586,7 +1591,7 @@ static int build_near_finish(fdph_plan_t P, const PlanInputs& in, NearBuild& nb)
     if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
         (rc = upload(P, &P->np_ptr, hp.np_ptr)) || (rc = upload(P, &P->np_idx, hp.np_idx)))
         return rc;
-    FDPH_CUDA(cudaDeviceSynchronize());
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
     return FDPH_OK;
 }
 
@@ -1691,10 +1696,10 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
         set_error("geometry, material and dt must be given, n > 0, dt, mu, cs > 0");
         return FDPH_E_ARG;
     }
-    if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 ||
+    if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
-        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, precision FP64, FP32 or FP16, "
+        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -1727,6 +1732,7 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.extra_steps = p.extra_steps;
     in.soe = p.soe_terms;
     in.interp = p.art_interp ? 1 : 0;
+    in.threads = p.host_threads > 0 ? p.host_threads : omp_get_max_threads();
     return in;
 }
 
@@ -1848,7 +1854,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
                                      : build_near_begin<double, double>(P, in, nb);
     if (rc) return fail(rc);
     rc = build_host_far(el, in, hp);
-    if (verbose) fprintf(stderr, "[fdph_plan] host threads %d\n", omp_get_max_threads());
+    if (verbose) fprintf(stderr, "[fdph_plan] host threads %d\n", in.threads);
     stamp("host plan (admissible blocks)");
     if (rc == -3) return fail(FDPH_E_CAUSALITY);
     if (rc) return fail(FDPH_E_ARG);
@@ -1907,7 +1913,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     stamp("near field (windows, tails)");
 
     if ((rc = dalloc(P, &P->err, 1))) return fail(rc);
-    FDPH_CUDA(cudaMemset(P->err, 0, sizeof(int)));
+    FDPH_CUDA(cudaMemsetAsync(P->err, 0, sizeof(int), P->stream));
     // ---- state
     P->WD = std::max(std::max(hp.max_W + (hp.soe > 0 ? 1 : 0), hp.max_taps), 1);
     P->WC = hp.max_W + 1;
@@ -2075,9 +2081,10 @@ int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     memcpy(o, hdr, sizeof(hdr));
     o += sizeof(hdr);
     for (int q = 0; q < 8; ++q) {
-        if (cnt[q]) FDPH_CUDA(cudaMemcpy(o, bufs[q], cnt[q] * sizeof(double), cudaMemcpyDeviceToHost));
+        if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(o, bufs[q], cnt[q] * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
         o += cnt[q] * sizeof(double);
     }
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));   // the caller's buffer is complete on return
     *len = need;
     return FDPH_OK;
 }
@@ -2105,9 +2112,10 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
                     (size_t)P->hp.vstate_len};
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     for (int q = 0; q < 8; ++q) {
-        if (cnt[q]) FDPH_CUDA(cudaMemcpy(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice));
+        if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice, P->stream));
         o += cnt[q] * sizeof(double);
     }
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));   // the caller may reuse the buffer on return
     P->n = hdr[0];
     return FDPH_OK;
 }
@@ -2144,9 +2152,11 @@ int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
         P->fr.k0 = kk;
         P->fr.slip = slip;
     }
-    FDPH_CUDA(cudaMemcpy((void*)P->fr.tau0, f->tau0, P->N * sizeof(double), cudaMemcpyDeviceToDevice));
-    FDPH_CUDA(cudaMemcpy((void*)P->fr.k0, k0.data(), P->N * sizeof(double), cudaMemcpyHostToDevice));
-    FDPH_CUDA(cudaMemset(P->fr.slip, 0, P->N * sizeof(double)));
+    // ordered after the caller's work on the plan's stream (tau0 may have been written there)
+    FDPH_CUDA(cudaMemcpyAsync((void*)P->fr.tau0, f->tau0, P->N * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+    FDPH_CUDA(cudaMemcpyAsync((void*)P->fr.k0, k0.data(), P->N * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->fr.sigma_n = f->sigma_n;
     P->fr.mu_s = f->mu_s;
     P->fr.mu_d = f->mu_d;

@@ -49,6 +49,7 @@ struct PlanInputs {
     int M, leaf, extra_steps;
     int soe;           // exponential-tail terms (0 = the paper's static cut)
     int interp;        // 1: receiver delays interpolated between steps (extension)
+    int threads;       // host threads of the build (OpenMP), > 0
 };
 
 // Decay factors rho_q = exp(-lambda_q) of the exponential tail basis, lambda_q spaced

@@ -249,7 +249,7 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         return (long)(t.hi - t.lo) * (g.hi - g.lo);
     };
     std::stable_sort(order.begin(), order.end(), [&](long x, long y) { return size_of(x) > size_of(y); });
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(in.threads)
     for (long q = 0; q < (long)adm.size(); ++q) admissible(el, tr, *adm[order[q]], in, outs[order[q]]);
     for (const LeafOut& o : outs)
         if (!o.ok) {

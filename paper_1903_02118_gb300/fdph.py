@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("lmin", ctypes.c_double), ("eps_st", ctypes.c_double),
                 ("leaf_size", ctypes.c_int32), ("extra_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+                ("host_threads", ctypes.c_int32)]
 
 
 class Friction(ctypes.Structure):
@@ -144,10 +145,11 @@ def default_params():
 
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
-                device=None, stream=None, soe_terms=None, art_interp=None):
+                device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
+                 ("host_threads", host_threads),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)

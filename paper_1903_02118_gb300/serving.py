@@ -14,6 +14,7 @@ graph replayed per chunk); this module only schedules, and builds plans on backg
 so that planning overlaps the stepping of the live scenarios.  Plans are independent, so a scenario's result is bit-identical alone and in
 the mix (tests/test_gpu_serving.py).
 """
+import os
 import time
 
 import numpy as np
@@ -77,6 +78,8 @@ class Server:
         self.time_scale = time_scale
         self.planners = planners
         self.precision = precision
+        # each planner builds with its share of the host cores (the builds run at the same time)
+        self.host_threads = max(1, (os.cpu_count() or 16) // max(1, planners))
         self.used = 0
 
     @staticmethod
@@ -93,7 +96,7 @@ class Server:
         prec = self.precision if self.precision is not None else req.precision
         plan = fdph.Plan(xy, dt, req.M, req.eps, eta=req.eta, eps_st=req.eps_st, leaf_size=req.leaf,
                          precision=prec, soe_terms=req.soe_terms, device=self.device,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, host_threads=self.host_threads)
         st = plan.stats()
         foot = st["arena_bytes"] + st["state_bytes"] + 3 * req.N * 8 * (self.chunk + 2)
         with torch.cuda.stream(stream):

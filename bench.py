@@ -277,7 +277,8 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override N (profiling of smaller cases)")
     ap.add_argument("--m", type=int, default=None, help="override M")
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
-    ap.add_argument("--planners", type=int, default=4, help="serving workload: plan-building threads")
+    ap.add_argument("--planners", type=int, default=2, help="serving workload: plan-building threads")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default near-field work-item length")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)
@@ -318,6 +319,9 @@ def main():
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
     plan_s = time.perf_counter() - t0
+    # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
+    # profiler commands rely on)
+    chunk = None if (args.no_autotune or args.quick) else plan.autotune(16)
     st = plan.stats()
     Dd = torch.from_numpy(D).cuda()
     Td = torch.empty_like(Dd)
@@ -419,7 +423,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
-                       "first_timed_step": n0 + W,
+                       "first_timed_step": n0 + W, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": e2e, "gpu_launches": int(sum(v[1] for v in kt.values()) // 1),

@@ -944,6 +944,11 @@ struct fdph_plan_s {
     std::vector<GraphEntry> graphs;
     int* n_dev = nullptr;
     int near_priority = 0;    // greatest stream priority of the device
+    // near-field schedule inputs (kept so that the work-item length can be changed later)
+    std::vector<int32_t> near_W;
+    std::vector<char> near_tail;
+    int chunk = 0;            // steps of exact kernel per near-field work item
+    size_t partial_cap = 0;   // capacity of `partial`, in doubles
     // branches of a step that run concurrently with the near field: [0] FIR + scatter,
     // [1] transient convolution + Eq. 39 evaluation (fork after push, join before gather)
     cudaStream_t side[2] = {nullptr, nullptr};
@@ -1336,6 +1341,70 @@ static int rupture_graph(fdph_plan_t P, int steps, double* D, double* Tout) {
     return FDPH_OK;
 }
 
+// Persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
+// largest first to the least-loaded CTA (steady-state bytes); uploads the task lists and the
+// receiver -> partial-slot map of the current items.
+template <class T, class H>
+static int build_schedule(fdph_plan_t P) {
+    using A = typename NearTypes<H>::Aux;
+    HostPlan& hp = P->hp;
+    int rc;
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
+    int sms = 0, per_sm = 0;
+    FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H>, kNearThreads, NearCfg<H>::smem));
+    const int ni = (int)hp.items.size();
+    const int ncta = std::max(1, std::min(ni, sms * std::max(per_sm, 1)));
+    std::vector<NearTask> tasks_all(ni);
+    std::vector<double> cost(ni);
+    for (int q = 0; q < ni; ++q) {
+        const NearItem& it = hp.items[q];
+        const NearLeaf& L = hp.near[it.leaf];
+        NearTask t;
+        memset(&t, 0, sizeof(t));
+        t.off = it.kind ? (long long)L.stat : (long long)L.tensor + (long long)it.k0 * L.sl;
+        t.item = q;
+        t.k0 = it.k0;
+        t.k1 = it.k1;
+        t.kind = it.kind;
+        t.nr = L.nr;
+        t.ns = L.ns;
+        t.sl = it.kind ? L.sla : L.sl;
+        t.s0 = L.s0;
+        t.W = L.W;
+        t.vstate = (int)L.vstate;
+        tasks_all[q] = t;
+        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0;
+    }
+    std::vector<int> order(ni);
+    for (int q = 0; q < ni; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<int>> own(ncta);
+    std::vector<std::pair<double, int>> heap;
+    for (int c = 0; c < ncta; ++c) heap.push_back({0.0, c});
+    auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int q : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        heap.back().first += cost[q];
+        own[heap.back().second].push_back(q);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<NearTask> tasks;
+    std::vector<int> cptr(1, 0);
+    for (int c = 0; c < ncta; ++c) {
+        for (int q : own[c]) tasks.push_back(tasks_all[q]);
+        cptr.push_back((int)tasks.size());
+    }
+    P->n_cta = ni ? ncta : 0;
+    if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
+        (rc = upload(P, &P->np_ptr, hp.np_ptr)) || (rc = upload(P, &P->np_idx, hp.np_idx)))
+        return rc;
+    return FDPH_OK;
+}
+
 // Near-field build in two phases around the host factorisation of the admissible blocks, which
 // it does not need: build_near_begin (windows, exact tensors, tail projections launched on the
 // device) and build_near_finish (tail fits on the host, upload, persistent schedule).
@@ -1428,6 +1497,9 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
     int chunk = kChunk;
     while (chunk > 8 && slices / chunk < 4LL * 152 * 3) chunk /= 2;
     finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
+    P->near_W = W;
+    P->near_tail = has_tail;
+    P->chunk = chunk;
     std::vector<NearDev> nd(nl);
     for (int l = 0; l < nl; ++l) {
         const NearLeaf& L = hp.near[l];
@@ -1536,61 +1608,7 @@ static int build_near_finish(fdph_plan_t P, const PlanInputs& in, NearBuild& nb)
                                       cudaMemcpyHostToDevice, P->stream));
     }
     stamp("near: tail fits");
-    // persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
-    // largest first to the least-loaded CTA (steady-state bytes)
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
-    int sms = 0, per_sm = 0;
-    FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
-    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H>, kNearThreads, NearCfg<H>::smem));
-    const int ni = (int)hp.items.size();
-    const int ncta = std::max(1, std::min(ni, sms * std::max(per_sm, 1)));
-    std::vector<NearTask> tasks_all(ni);
-    std::vector<double> cost(ni);
-    for (int q = 0; q < ni; ++q) {
-        const NearItem& it = hp.items[q];
-        const NearLeaf& L = hp.near[it.leaf];
-        NearTask t;
-        memset(&t, 0, sizeof(t));
-        t.off = it.kind ? (long long)L.stat : (long long)L.tensor + (long long)it.k0 * L.sl;
-        t.item = q;
-        t.k0 = it.k0;
-        t.k1 = it.k1;
-        t.kind = it.kind;
-        t.nr = L.nr;
-        t.ns = L.ns;
-        t.sl = it.kind ? L.sla : L.sl;
-        t.s0 = L.s0;
-        t.W = L.W;
-        t.vstate = (int)L.vstate;
-        tasks_all[q] = t;
-        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0;
-    }
-    std::vector<int> order(ni);
-    for (int q = 0; q < ni; ++q) order[q] = q;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<std::vector<int>> own(ncta);
-    std::vector<std::pair<double, int>> heap;
-    for (int c = 0; c < ncta; ++c) heap.push_back({0.0, c});
-    auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
-        return x.first > y.first || (x.first == y.first && x.second > y.second);
-    };
-    std::make_heap(heap.begin(), heap.end(), cmp);
-    for (int q : order) {
-        std::pop_heap(heap.begin(), heap.end(), cmp);
-        heap.back().first += cost[q];
-        own[heap.back().second].push_back(q);
-        std::push_heap(heap.begin(), heap.end(), cmp);
-    }
-    std::vector<NearTask> tasks;
-    std::vector<int> cptr(1, 0);
-    for (int c = 0; c < ncta; ++c) {
-        for (int q : own[c]) tasks.push_back(tasks_all[q]);
-        cptr.push_back((int)tasks.size());
-    }
-    P->n_cta = ni ? ncta : 0;
-    if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
-        (rc = upload(P, &P->np_ptr, hp.np_ptr)) || (rc = upload(P, &P->np_idx, hp.np_idx)))
-        return rc;
+    if ((rc = build_schedule<T, H>(P))) return rc;
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     return FDPH_OK;
 }
@@ -1655,6 +1673,37 @@ static void fill_stats(fdph_plan_t P) {
     arena += (long long)(hp.fac.size() * ps) + hp.ints.size() * 4 + hp.sbs.size() * sizeof(SbDev);
     arena += (long long)(hp.near_tensor_len * pw + hp.near_aux_len * ps);
     s.arena_bytes = arena;
+}
+
+// Near-field work items of `chunk` kernel steps (1..kChunk): new items, partial slots and
+// persistent schedule; the stored coefficients do not move.  Cached step graphs refer to the old
+// schedule and are dropped.
+template <class T, class H>
+static int set_chunk(fdph_plan_t P, int chunk) {
+    using A = typename NearTypes<H>::Aux;
+    HostPlan& hp = P->hp;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);
+    P->graphs.clear();
+    finish_near_layout(hp, P->near_W, P->near_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
+    const size_t need = hp.items.size() * 32;
+    if (need > P->partial_cap) {
+        int rc = dalloc(P, &P->partial, need);
+        if (rc) return rc;
+        FDPH_CUDA(cudaMemsetAsync(P->partial, 0, need * sizeof(double), P->stream));
+        P->partial_cap = need;
+    }
+    int rc = build_schedule<T, H>(P);
+    if (rc) return rc;
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    P->chunk = chunk;
+    return FDPH_OK;
+}
+
+static int set_chunk_any(fdph_plan_t P, int chunk) {
+    return P->precision == FDPH_FP16   ? set_chunk<float, __half>(P, chunk)
+           : P->precision == FDPH_FP32 ? set_chunk<float, float>(P, chunk)
+                                       : set_chunk<double, double>(P, chunk);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1929,6 +1978,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
         return fail(rc);
     P->state_bytes = sb;
+    P->partial_cap = hp.items.size() * 32;
     if ((rc = fdph_reset(P))) return fail(rc);
     fill_stats(P);
     P->st.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2041,6 +2091,66 @@ int fdph_selftest_wait_timeout(int32_t device, int64_t polls) {
         set_error("bounded mbarrier wait gave up after " + std::to_string(polls) + " polls (self-test)");
         return FDPH_E_TIMEOUT;
     }
+    return FDPH_OK;
+}
+
+int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
+    if (!P || steps < 1 || steps > 1024) return FDPH_E_ARG;
+    if (P->prof) {
+        set_error("fdph_autotune: profiling is on");
+        return FDPH_E_STATE;
+    }
+    if (P->hp.items.empty()) {
+        if (chunk_out) *chunk_out = P->chunk;
+        return FDPH_OK;
+    }
+    const int M = P->M;
+    if (steps + 2 > M) {
+        set_error("fdph_autotune: the plan has fewer than steps + 2 steps");
+        return FDPH_E_ARG;
+    }
+    // the state is saved and restored around the trials
+    size_t len = 0;
+    int rc = fdph_save_state(P, nullptr, &len);
+    if (rc) return rc;
+    std::vector<char> saved(len);
+    if ((rc = fdph_save_state(P, saved.data(), &len))) return rc;
+    double *Dz = nullptr, *Tz = nullptr;
+    if ((rc = dalloc(P, &Dz, (size_t)(steps + 2) * P->N)) || (rc = dalloc(P, &Tz, (size_t)(steps + 2) * P->N))) return rc;
+    FDPH_CUDA(cudaMemsetAsync(Dz, 0, (size_t)(steps + 2) * P->N * sizeof(double), P->stream));
+    // trials at a steady-state step index (every window full); the values stepped are irrelevant
+    const int n0 = std::max(0, std::min(P->hp.max_W, M - steps - 2));
+    cudaEvent_t e0, e1;
+    FDPH_CUDA(cudaEventCreate(&e0));
+    FDPH_CUDA(cudaEventCreate(&e1));
+    const int cands[3] = {kChunk, kChunk / 2, kChunk / 4};
+    int best = P->chunk;
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        if ((rc = set_chunk_any(P, c))) break;
+        P->n = n0;
+        rc = P->precision != FDPH_FP64 ? run_graph<float>(P, 2, Dz, Tz) : run_graph<double>(P, 2, Dz, Tz);   // capture
+        if (rc) break;
+        cudaEventRecord(e0, P->stream);
+        rc = P->precision != FDPH_FP64 ? run_graph<float>(P, steps, Dz, Tz) : run_graph<double>(P, steps, Dz, Tz);
+        if (rc) break;
+        cudaEventRecord(e1, P->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = set_chunk_any(P, best);
+    int rc2 = fdph_load_state(P, saved.data(), saved.size());
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if ((rc = check_device_error(P))) return rc;
+    if (chunk_out) *chunk_out = best;
     return FDPH_OK;
 }
 

@@ -65,7 +65,7 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
-           "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout"]
+           "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -105,6 +105,8 @@ def lib():
         L.fdph_rupture_step.argtypes = [c_p, c_p, c_p]
         L.fdph_rupture_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_rupture_slip.argtypes = [c_p, c_p]
+        L.fdph_autotune.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.fdph_autotune.restype = ctypes.c_int
         L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
         L.fdph_selftest_wait_timeout.restype = ctypes.c_int
         L.fdph_strerror.argtypes = [ctypes.c_int]
@@ -204,6 +206,12 @@ class Plan:
         _check(lib().fdph_run_host(self.handle, int(D.shape[0]), ctypes.c_void_p(D.ctypes.data),
                                    ctypes.c_void_p(T.ctypes.data)))
         return T
+
+    def autotune(self, steps=16):
+        """fdph_autotune: picks the near-field work-item length; returns it."""
+        c = ctypes.c_int32()
+        _check(lib().fdph_autotune(self.handle, int(steps), ctypes.byref(c)))
+        return c.value
 
     def reset(self):
         _check(lib().fdph_reset(self.handle))

@@ -286,3 +286,26 @@ def test_fdph_fp16_near_window_within_rounding_bound():
     slack = 5e-6 * np.abs(T0).max()
     assert np.all(np.abs(T - T0) <= B + slack)
     assert _rel(T, T0) > 1e-7          # the rounding is there (not an FP32 path)
+
+
+def test_autotune_keeps_state_and_results():
+    """fdph_autotune changes only the grouping of the near-field sums: a tuned plan continues from
+    its saved state and matches an untuned plan to rounding (FP64)."""
+    _need_gpu()
+    N, M = 180, 200
+    xy = _geom("curved", N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    ref = fdph.Plan(xy, 0.5, M, 1e-5, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
+    T_ref = _run(ref, D)
+    plan = fdph.Plan(xy, 0.5, M, 1e-5, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    torch.cuda.synchronize()
+    plan.run(50, Dd, Td)
+    plan.synchronize()
+    chunk = plan.autotune(steps=8)
+    assert chunk in (16, 32, 64)
+    assert plan.current_step() == 50
+    plan.run(M - 50, Dd[50:], Td[50:])
+    plan.synchronize()
+    assert _rel(Td.cpu().numpy(), T_ref) < 1e-13

@@ -1685,7 +1685,13 @@ static int set_chunk(fdph_plan_t P, int chunk) {
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);
     P->graphs.clear();
+    const int64_t tens0 = hp.near_tensor_len, aux0 = hp.near_aux_len, vst0 = hp.vstate_len;
     finish_near_layout(hp, P->near_W, P->near_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
+    if (hp.near_tensor_len != tens0 || hp.near_aux_len != aux0 || hp.vstate_len != vst0) {
+        // the stored coefficients and states must keep their places (only the items change)
+        set_error("set_chunk: near-field layout changed; the plan is unusable");
+        return FDPH_E_STATE;
+    }
     const size_t need = hp.items.size() * 32;
     if (need > P->partial_cap) {
         int rc = dalloc(P, &P->partial, need);

@@ -385,6 +385,7 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::
     hp.near_tensor_len = 0;
     hp.near_aux_len = 0;
     hp.near_tail_len = 0;
+    hp.vstate_len = 0;
     hp.max_W = 0;
     std::vector<std::vector<int32_t>> slots(hp.n);
     for (int l = 0; l < nl; ++l) {

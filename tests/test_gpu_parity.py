@@ -290,9 +290,10 @@ def test_fdph_fp16_near_window_within_rounding_bound():
 
 def test_autotune_keeps_state_and_results():
     """fdph_autotune changes only the grouping of the near-field sums: a tuned plan continues from
-    its saved state and matches an untuned plan to rounding (FP64)."""
+    its saved state and matches an untuned plan to rounding (FP64).  M is long enough for the
+    exponential tails (their states must keep their places when the items are rebuilt)."""
     _need_gpu()
-    N, M = 180, 200
+    N, M = 180, 900
     xy = _geom("curved", N)
     D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
     ref = fdph.Plan(xy, 0.5, M, 1e-5, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
@@ -303,6 +304,7 @@ def test_autotune_keeps_state_and_results():
     torch.cuda.synchronize()
     plan.run(50, Dd, Td)
     plan.synchronize()
+    assert plan.stats()["max_window"] < M        # tails present
     chunk = plan.autotune(steps=8)
     assert chunk in (16, 32, 64)
     assert plan.current_step() == 50

@@ -201,7 +201,8 @@ def run_rupture(args, cfg):
     prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[args.precision]
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
-                     precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
+                     precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
+                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0))
     plan_s = time.perf_counter() - t0
     st = plan.stats()
     plan.rupture_init(torch.from_numpy(tau0).cuda(), 1.0, 0.6, 0.3, 6.4)
@@ -271,6 +272,9 @@ def main():
     ap.add_argument("--soe", type=int, default=16, help="exponential-tail terms (0: the paper's static cut)")
     ap.add_argument("--eta", type=float, default=None)
     ap.add_argument("--eps-st", type=float, default=None)
+    ap.add_argument("--eta-scheme", type=int, default=None, choices=[0, 1],
+                    help="admissibility: 0 constant eta (Eq. 8), 1 constant eta^2 dist (Eq. 25, needs --lmin)")
+    ap.add_argument("--lmin", type=float, default=None, help="lmin of Eq. 9 / Eq. 25, in element lengths")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--quick", action="store_true",
                     help="plan + roll forward + warm-up + timed steps only (for profiler launch lists)")
@@ -291,6 +295,10 @@ def main():
         cfg["eta"] = args.eta
     if args.eps_st is not None:
         cfg["eps_st"] = args.eps_st
+    if args.eta_scheme is not None:
+        cfg["eta_scheme"] = args.eta_scheme
+    if args.lmin is not None:
+        cfg["lmin"] = args.lmin
     if args.n:
         cfg["N"] = args.n
     if args.m:
@@ -317,7 +325,8 @@ def main():
     prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[args.precision]
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
-                     precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0))
+                     precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
+                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0))
     plan_s = time.perf_counter() - t0
     # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
     # profiler commands rely on)
@@ -423,6 +432,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
+                       "eta_scheme": cfg.get("eta_scheme", 0), "lmin": cfg.get("lmin", 0.0),
                        "first_timed_step": n0 + W, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

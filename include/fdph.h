@@ -106,6 +106,11 @@ typedef struct fdph_params {
     int32_t host_threads; /* host threads of the plan build (OpenMP); 0 (default) => the OpenMP
                              default.  Callers that build several plans at once (a serving loop
                              with planner threads) give each a share of the cores */
+    int32_t eta_scheme;   /* admissibility: 0 (default) the constant eta scheme, diam < eta dist
+                             (Eq. 8); 1 the constant eta^2 dist scheme of Eq. 25, diam <
+                             sqrt(eta lmin dist) (eta = eta_0, lmin > 0 required), which bounds the
+                             travel-time error of the plane-wave approximation by eta lmin / (4 c)
+                             (Eq. 26) at a cost that grows like N^(3/2) */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */

@@ -73,12 +73,13 @@ NODAL_TAU = 0.2   # nodal-direction threshold of the waveform choice (reading, s
 
 class Params:
     def __init__(self, eta=0.5, leaf=32, eps=1e-4, eps_st=1e-6, extra_steps=-1, lmin=0.0,
-                 mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False):
+                 mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False, eta_scheme=0):
         self.eta, self.leaf, self.eps, self.eps_st = eta, leaf, eps, eps_st
         self.extra_steps, self.lmin, self.mu, self.cs, self.dt, self.M = extra_steps, lmin, mu, cs, dt, M
         self.soe_terms = soe_terms
         self.eps_tr = eps_st if eps_tr is None else eps_tr
         self.art_interp = art_interp
+        self.eta_scheme = eta_scheme   # 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25), needs lmin > 0
 
 
 def soe_min_len(W):
@@ -147,6 +148,8 @@ def root_cluster(el):
 
 def block_tree(el, p, maxdepth=64):
     """List of leaves: dicts with kind 'adm' / 'near', the two clusters and geometry."""
+    if p.eta_scheme not in (0, 1) or (p.eta_scheme == 1 and not p.lmin > 0.0):
+        raise ValueError("eta_scheme must be 0, or 1 with lmin > 0")
     root = root_cluster(el)
     lens = el["len"]
     leaves = []
@@ -159,7 +162,11 @@ def block_tree(el, p, maxdepth=64):
         ct, cs_ = tau.centre(), sig.centre()
         rbar = math.sqrt((ct[0] - cs_[0]) * (ct[0] - cs_[0]) + (ct[1] - cs_[1]) * (ct[1] - cs_[1]))
         dist = rbar - diam
-        if p.eta > 0.0 and diam < p.eta * dist:
+        if p.eta_scheme == 1:      # constant eta^2 dist scheme (Eq. 25)
+            adm = p.eta > 0.0 and dist > 0.0 and diam < math.sqrt(p.eta * p.lmin * dist)
+        else:                      # constant eta scheme (Eq. 8)
+            adm = p.eta > 0.0 and diam < p.eta * dist
+        if adm:
             leaves.append(dict(kind="adm", tau=tau, sig=sig, diam=diam, dist=dist, rbar=rbar))
         elif (tau.idx.size <= p.leaf and sig.idx.size <= p.leaf) or diam < p.lmin or depth >= maxdepth:
             leaves.append(dict(kind="near", tau=tau, sig=sig, diam=diam, dist=dist, rbar=rbar))

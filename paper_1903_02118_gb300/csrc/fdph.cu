@@ -1752,9 +1752,11 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
         return FDPH_E_ARG;
     }
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
+              (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
-        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, precision FP64, FP32 or FP16, "
+        set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
+                  "lmin > 0), precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -1788,6 +1790,7 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.soe = p.soe_terms;
     in.interp = p.art_interp ? 1 : 0;
     in.threads = p.host_threads > 0 ? p.host_threads : omp_get_max_threads();
+    in.eta_scheme = p.eta_scheme;
     return in;
 }
 

@@ -50,6 +50,7 @@ struct PlanInputs {
     int soe;           // exponential-tail terms (0 = the paper's static cut)
     int interp;        // 1: receiver delays interpolated between steps (extension)
     int threads;       // host threads of the build (OpenMP), > 0
+    int eta_scheme;    // 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25)
 };
 
 // Decay factors rho_q = exp(-lambda_q) of the exponential tail basis, lambda_q spaced

@@ -12,7 +12,8 @@
 //
 // Block tree (Eqs. 8-9, Sec. 4.2.2): diam = largest box diagonal + largest element length of
 // the two clusters, rbar = distance of the box centres, dist = rbar - diam; admissible when
-// diam < eta dist, inadmissible when both clusters hold at most `leaf` elements (or
+// diam < eta dist (constant eta scheme) or diam < sqrt(eta l_min dist) (constant eta^2 dist
+// scheme, Eq. 25), inadmissible when both clusters hold at most `leaf` elements (or
 // diam < l_min), else both clusters are bisected.
 #include <math.h>
 
@@ -155,7 +156,9 @@ void build_tree(const Elements& el, const PlanInputs& in, Tree& tr) {
         const double rbar = sqrt((ct[0] - cs[0]) * (ct[0] - cs[0]) + (ct[1] - cs[1]) * (ct[1] - cs[1]));
         const double dist = rbar - diam;
         const int nt = tn.hi - tn.lo, ns = sn.hi - sn.lo;
-        if (in.eta > 0.0 && diam < in.eta * dist) {
+        const bool adm = in.eta_scheme == 1 ? (in.eta > 0.0 && dist > 0.0 && diam < sqrt(in.eta * in.lmin * dist))
+                                            : (in.eta > 0.0 && diam < in.eta * dist);
+        if (adm) {
             tr.leaves.push_back({1, it.tau, it.sig, diam, dist, rbar});
         } else if ((nt <= in.leaf && ns <= in.leaf) || diam < in.lmin || it.depth >= kMaxDepth) {
             tr.leaves.push_back({0, it.tau, it.sig, diam, dist, rbar});

@@ -53,11 +53,11 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_strerror(fdph.E_CAUSALITY)
 
 
-def _compare_tree(xy, eta, leaf):
-    tr = fdph.tree_export(xy, 0.5, eta=eta, leaf_size=leaf)
+def _compare_tree(xy, eta, leaf, eta_scheme=0, lmin=0.0):
+    tr = fdph.tree_export(xy, 0.5, eta=eta, leaf_size=leaf, eta_scheme=eta_scheme, lmin=lmin)
     perm = tr["perm"]
     el = kn.element_table(xy)
-    p = ofd.Params(eta=eta, leaf=leaf)
+    p = ofd.Params(eta=eta, leaf=leaf, eta_scheme=eta_scheme, lmin=lmin)
     leaves = ofd.block_tree(el, p)
     key = lambda a, b: (tuple(sorted(a)), tuple(sorted(b)))
     mine = {}
@@ -97,3 +97,18 @@ def test_tree_and_art_integers_bit_exact(L, geom, N, eta, leaf):
         xy = {"straight": inputs.straight_fault(N), "curved": inputs.curved_fault(N, inputs.seed_for(1, 0)),
               "kinked": inputs.kinked_fault(N)}[geom]
     _compare_tree(xy, eta, leaf)
+
+
+@pytest.mark.parametrize("geom,N,lmin", [("curved", 1500, 8.0), ("kinked", 600, 12.0), ("straight", 400, 6.0)])
+def test_eta2dist_tree_bit_exact(L, geom, N, lmin):
+    """Constant eta^2 dist admissibility (Eq. 25): the library's tree and ART integers equal the
+    oracle's."""
+    xy = {"straight": inputs.straight_fault(N), "curved": inputs.curved_fault(N, inputs.seed_for(1, 0)),
+          "kinked": inputs.kinked_fault(N)}[geom]
+    _compare_tree(xy, 0.5, 32, eta_scheme=1, lmin=lmin)
+
+
+def test_eta2dist_needs_lmin(L):
+    xy = np.ascontiguousarray(inputs.straight_fault(64))
+    with pytest.raises(fdph.FdphError):
+        fdph.tree_export(xy, 0.5, eta=0.5, eta_scheme=1, lmin=0.0)

@@ -62,9 +62,10 @@ def test_plain_st_biem_fp64(geom, N, M):
     assert st["n_admissible"] == 0 and st["max_window"] == M
 
 
-def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6, soe_terms=0, eta=0.5, art_interp=False):
+def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6, soe_terms=0, eta=0.5, art_interp=False, eta_scheme=0, lmin=0.0):
     el = kn.element_table(xy)
-    p = ofd.Params(eta=eta, leaf=leaf, eps=eps, eps_st=eps_st, M=M, soe_terms=soe_terms, art_interp=art_interp)
+    p = ofd.Params(eta=eta, leaf=leaf, eps=eps, eps_st=eps_st, M=M, soe_terms=soe_terms, art_interp=art_interp,
+                   eta_scheme=eta_scheme, lmin=lmin)
     plan = ofd.build_plan(el, p)
     Kc = ofd.operator_rows(el, plan, np.arange(xy.shape[0]))
     return dense.march(Kc, D), plan
@@ -95,6 +96,23 @@ def test_fdph_exponential_tails_fp64_equals_compressed_operator(geom, N, leaf, e
     plan = fdph.Plan(xy, 0.5, M, eps, eta=eta, eps_st=1e-4, leaf_size=leaf, soe_terms=16, art_interp=interp)
     T = _run(plan, D)
     assert plan.stats()["max_window"] == max(d["W"] for d in oplan["near"]) < M
+    assert _rel(T, T0) < TOL64
+
+
+@pytest.mark.parametrize("geom,N,M,soe", [("curved", 300, 320, 0), ("kinked", 240, 900, 16)])
+def test_fdph_eta2dist_fp64_equals_compressed_operator(geom, N, M, soe):
+    """Constant eta^2 dist admissibility (Eq. 25, eta0 = 0.5, lmin = 6): same leaves and same
+    compressed operator as the oracle, with and without exponential tails."""
+    _need_gpu()
+    eps, leaf, lmin = 1e-5, 16, 6.0
+    eps_st = 1e-4 if soe else 1e-6
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, eps_st=eps_st, soe_terms=soe, eta_scheme=1, lmin=lmin)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=eps_st, leaf_size=leaf, soe_terms=soe, eta_scheme=1, lmin=lmin)
+    T = _run(plan, D)
+    st = plan.stats()
+    assert st["n_admissible"] == len(oplan["adm"]) > 0 and st["n_near"] == len(oplan["near"])
     assert _rel(T, T0) < TOL64
 
 

@@ -249,3 +249,50 @@ def test_exponential_tail_removes_the_static_cut_bias():
     assert acc_full == 0.0
     assert acc_soe < 1e-8
     assert e_soe < 1.01 * e_full + 1e-9
+
+
+def _worst_travel_time_error(el, p):
+    worst = 0.0
+    for lf in fdph.block_tree(el, p):
+        if lf["kind"] != "adm":
+            continue
+        ist, jst = lf["tau"].centre(), lf["sig"].centre()
+        I, J = lf["tau"].idx, lf["sig"].idx
+        rij = np.hypot(el["mx"][I][:, None] - el["mx"][J][None], el["my"][I][:, None] - el["my"][J][None])
+        dti = np.hypot(el["mx"][I] - jst[0], el["my"][I] - jst[1]) - lf["rbar"]
+        tbj = np.hypot(ist[0] - el["mx"][J], ist[1] - el["my"][J])
+        worst = max(worst, np.abs(dti[:, None] + tbj[None, :] - rij).max() / p.cs)
+    return worst
+
+
+@pytest.mark.parametrize("geom,N", [("curved", 1024), ("kinked", 600), ("square", 700)])
+def test_eta2dist_travel_time_bound_eq26(geom, N):
+    # Constant eta^2 dist scheme (Eq. 25): the plane-wave travel-time error of every admissible
+    # leaf stays under eta0 lmin / (4 c) whatever the distance (Eq. 26), while the constant eta
+    # scheme with the same eta0 exceeds it on a bent fault (its error grows with dist, Eq. 17).
+    if geom == "square":
+        rng = np.random.default_rng(5)
+        c = rng.uniform(0, 160, (N, 2))
+        ang = rng.uniform(0, 2 * np.pi, N)
+        xy = np.stack([c[:, 0] - 0.5 * np.cos(ang), c[:, 1] - 0.5 * np.sin(ang),
+                       c[:, 0] + 0.5 * np.cos(ang), c[:, 1] + 0.5 * np.sin(ang)], 1)
+        el = kn.element_table(xy)
+    else:
+        el, _ = _setup(geom, N)
+    eta0 = 0.5
+    for lmin in (8.0, 16.0):
+        p = fdph.Params(eta=eta0, leaf=8 if geom == "square" else 32, eta_scheme=1, lmin=lmin)
+        assert _worst_travel_time_error(el, p) < 0.25 * eta0 * lmin / p.cs, (geom, lmin)
+        # eta = sqrt(eta0 lmin / dist) is at most eta0 on leaves with diam >= lmin
+        for lf in fdph.block_tree(el, p):
+            if lf["kind"] == "adm" and lf["diam"] >= lmin:
+                assert lf["diam"] < eta0 * lf["dist"]
+    if geom != "square":
+        p0 = fdph.Params(eta=eta0, leaf=32, lmin=0.0)
+        assert _worst_travel_time_error(el, p0) > 0.25 * eta0 * 16.0
+
+
+def test_eta2dist_needs_lmin():
+    el, _ = _setup("straight", 64)
+    with pytest.raises(ValueError):
+        fdph.block_tree(el, fdph.Params(eta=0.5, eta_scheme=1, lmin=0.0))

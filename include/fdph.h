@@ -161,9 +161,11 @@ int fdph_run(fdph_plan_t plan, int32_t steps, const double* D, double* T);
 
 /* Dynamic rupture (Sec. 6.2): the slip rate is not prescribed but follows from a friction law
  * at every element.  The unruptured element keeps zero slip rate; it ruptures when the shear
- * traction reaches its strength, then the traction equals the strength, with linear slip
- * weakening (the paper uses exponential weakening; linear is the reading of the configs):
- *     strength(u) = sigma_n * (mu_s - (mu_s - mu_d) * min(u / Dc, 1)),  u = accumulated slip.
+ * traction reaches its strength, then the traction equals the strength, with slip weakening of
+ * the accumulated slip u, linear (law 0) or the paper's exponential form (law 1):
+ *     law 0: strength(u) = sigma_n * (mu_s - (mu_s - mu_d) * min(u / Dc, 1))
+ *     law 1: strength(u) = sigma_n * (mu_d + (mu_s - mu_d) * exp(-u / Dc))
+ * (Sec. 6.2 writes law 1 with T_th = sigma_n mu_s and T_dy = sigma_n mu_d).
  * The instantaneous term of Eq. 4 is local (K_{ij,0} = 0 for j != i when cs dt <= dx/2,
  * K_{ii,0} = -mu/(2 cs) the radiation damping), so each step is: predict the traction with
  * D_n = 0, solve D_n >= 0 element by element (explicit strength at the slip of the previous
@@ -173,6 +175,7 @@ typedef struct fdph_friction {
     double sigma_n;       /* normal stress (compression positive) */
     double mu_s, mu_d;    /* static and dynamic friction coefficients */
     double Dc;            /* slip-weakening distance */
+    int32_t law;          /* 0: linear slip weakening, 1: exponential slip weakening */
 } fdph_friction;
 
 /* Attach a friction law to a plan (copies tau0; zero slip).  Errors: FDPH_E_ARG, FDPH_E_OOM,
@@ -190,6 +193,26 @@ int fdph_rupture_run(fdph_plan_t plan, int32_t steps, double* D, double* T);
 
 /* Copy the accumulated slip (device, n doubles, geometry order). */
 int fdph_rupture_slip(fdph_plan_t plan, double* slip);
+
+/* One step of Eq. 4 split in two for a caller's own local solve (any friction law or boundary
+ * condition, Sec. 6.2 / Sec. 2.1), the way the rupture step splits internally:
+ *   fdph_predict writes T_pred = sum_{m >= 1} K_m D_{n-m} (device, n doubles, geometry order),
+ *     the traction of the current step n with D_n = 0;
+ *   the caller computes D_n (with T_n = T_pred + K_0 D_n; K_0 is diagonal when cs dt <= half the
+ *     shortest element, its diagonal given by fdph_self);
+ *   fdph_commit(D_n) (device, n doubles) appends D_n to the history and advances to n + 1.
+ * fdph_predict advances the transient and exponential-tail states of step n, so each step takes
+ * exactly one predict and one commit; between the two every other stepping or state call
+ * returns FDPH_E_STATE (fdph_reset discards the pending step).  Both are asynchronous on the
+ * plan's stream.  Errors: FDPH_E_ARG (null plan or pointer), FDPH_E_STATE (n == M, a predict
+ * already pending, a commit with none pending), FDPH_E_CUDA. */
+int fdph_predict(fdph_plan_t plan, double* T_pred);
+int fdph_commit(fdph_plan_t plan, const double* D_n);
+
+/* Instantaneous self coefficients K_{ii,0} (Eq. 4 with m = 0; -mu/(2 cs) on a straight fault at
+ * cs dt = dx/2, the radiation damping) into diag (HOST, n doubles, geometry order).
+ * FDPH_E_STATE when cs dt exceeds half the shortest element (K_0 is then not diagonal). */
+int fdph_self(fdph_plan_t plan, double* diag);
 
 /* Like fdph_step but D_n and T_n are HOST buffers; the call copies D_n in, steps, copies T_n
  * out and returns when T_n is ready (synchronous). */

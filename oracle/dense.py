@@ -46,22 +46,30 @@ def march_rows_fft(K_rows, D):
     return out
 
 
-def rupture_march(K, tau0, sigma_n, mu_s, mu_d, Dc, dt, M):
-    """Dynamic rupture, Sec. 6.2, with linear slip weakening (the configs' reading; the paper's
-    law is exponential):  strength(u) = sigma_n (mu_s - (mu_s - mu_d) min(u / Dc, 1)).
-    Unruptured elements keep zero slip rate until the traction reaches the strength; slipping
-    elements carry traction = strength; no back slip (D >= 0); the strength uses the slip of
-    the previous step.  K[m, i, j] with m < M.  Returns D[n, i], T[n, i] (total traction)."""
+def rupture_march(K, tau0, sigma_n, mu_s, mu_d, Dc, dt, M, law="linear"):
+    """Dynamic rupture, Sec. 6.2.  Unruptured elements keep zero slip rate until the traction
+    reaches the strength; slipping elements carry traction = strength; no back slip (D >= 0);
+    the strength uses the slip u of the previous step:
+        law "linear":      strength(u) = sigma_n (mu_s - (mu_s - mu_d) min(u / Dc, 1))
+        law "exponential": strength(u) = (T_th - T_dy) exp(-u / Dc) + T_dy   (Sec. 6.2),
+                           T_th = sigma_n mu_s, T_dy = sigma_n mu_d.
+    K[m, i, j] with m < M.  Returns D[n, i], T[n, i] (total traction)."""
     N = K.shape[1]
     D = np.zeros((M, N))
     T = np.zeros((M, N))
     slip = np.zeros(N)
     k0 = np.diag(K[0]).copy()               # K_{i,i,0} = -mu / (2 cs)
+    t_th, t_dy = sigma_n * mu_s, sigma_n * mu_d
     for n in range(M):
         mm = min(n + 1, K.shape[0])
         pred = np.einsum("mij,mj->i", K[1:mm], D[n - 1::-1][:mm - 1]) if n > 0 else np.zeros(N)
         tau = tau0 + pred
-        strength = sigma_n * (mu_s - (mu_s - mu_d) * np.minimum(slip / Dc, 1.0))
+        if law == "exponential":
+            strength = (t_th - t_dy) * np.exp(-slip / Dc) + t_dy
+        elif law == "linear":
+            strength = sigma_n * (mu_s - (mu_s - mu_d) * np.minimum(slip / Dc, 1.0))
+        else:
+            raise ValueError("law is 'linear' or 'exponential'")
         v = np.where(tau > strength, (tau - strength) / (-k0), 0.0)
         D[n] = v
         T[n] = tau + k0 * v

@@ -739,6 +739,7 @@ struct FrictionDev {
     const double* k0;      // instantaneous self coefficient K_{ii,0} (< 0)
     double* slip;
     double sigma_n, mu_s, mu_d, Dc, dt;
+    int law;               // 0: linear slip weakening, 1: exponential (Sec. 6.2)
 };
 
 // D, T: this step's rows (graph replay: row n_dev[0] - n_dev[1] of a step-major array)
@@ -752,8 +753,13 @@ __global__ void friction_kernel(FrictionDev f, int N, double* D, double* T, cons
     }
     const double tau = f.tau0[e] + T[e];
     const double u = f.slip[e];
-    const double w = u < f.Dc ? u / f.Dc : 1.0;
-    const double strength = f.sigma_n * (f.mu_s - (f.mu_s - f.mu_d) * w);
+    double strength;
+    if (f.law == 1) {
+        strength = f.sigma_n * (f.mu_d + (f.mu_s - f.mu_d) * exp(-u / f.Dc));
+    } else {
+        const double w = u < f.Dc ? u / f.Dc : 1.0;
+        strength = f.sigma_n * (f.mu_s - (f.mu_s - f.mu_d) * w);
+    }
     const double eta = -f.k0[e];
     const double v = tau > strength ? (tau - strength) / eta : 0.0;
     D[e] = v;
@@ -919,6 +925,7 @@ struct fdph_plan_s {
     double* rho = nullptr;
     // rupture state
     bool rupture = false;
+    bool predicted = false;   // fdph_predict issued for step n, fdph_commit pending
     FrictionDev fr;
     double *ustate = nullptr, *vstate = nullptr, *trcoef = nullptr, *phi = nullptr;
     // state
@@ -1293,11 +1300,11 @@ static int step_impl(fdph_plan_t P, const double* D, double* T_) {
     return rc;
 }
 
-// One rupture step (Sec. 6.2): predict the traction with D_n = 0 (push of a zero row, transient,
-// near field, Eq. 39, gather), solve the friction law element by element, then commit D_n
-// (push, FIR, scatter).  `a` carries the step-index source (direct: a.n; graph: n_dev).
+// Prediction of step n (Sec. 6.2): the traction with D_n = 0 (push of a zero row, transient,
+// near field, Eq. 39, gather) into a.T_out.  Advances the transient and exponential-tail states,
+// so it runs once per step, followed by enqueue_commit.
 template <class T>
-static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaStream_t s) {
+static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
     a.D_in = nullptr;
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }          // D_n = 0
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
@@ -1310,11 +1317,41 @@ static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaSt
         if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
         gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
     }
-    friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, a.T_out, a.n_dev);
-    a.D_in = D;                                                                                // commit D_n
+}
+
+// Commit of step n: push D_n into the history (overwriting the zero row of the prediction), FIR,
+// scatter.
+template <class T>
+static void enqueue_commit(fdph_plan_t P, StepArgs<T> a, const double* D, cudaStream_t s) {
+    a.D_in = D;
     { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
     if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
+}
+
+// One rupture step (Sec. 6.2): predict, solve the friction law element by element, commit D_n.
+// `a` carries the step-index source (direct: a.n; graph: n_dev).
+template <class T>
+static void enqueue_rupture_step(fdph_plan_t P, StepArgs<T> a, double* D, cudaStream_t s) {
+    enqueue_predict<T>(P, a, s);
+    friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D, a.T_out, a.n_dev);
+    enqueue_commit<T>(P, a, D, s);
+}
+
+template <class T>
+static int launch_predict(fdph_plan_t P, double* T_pred) {
+    StepArgs<T> a = make_args<T>(P, nullptr, T_pred);
+    enqueue_predict<T>(P, a, P->stream);
+    FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
+}
+
+template <class T>
+static int launch_commit(fdph_plan_t P, const double* D_n) {
+    StepArgs<T> a = make_args<T>(P, D_n, nullptr);
+    enqueue_commit<T>(P, a, D_n, P->stream);
+    FDPH_CUDA(cudaGetLastError());
+    return FDPH_OK;
 }
 
 template <class T>
@@ -1995,8 +2032,17 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     return FDPH_OK;
 }
 
+// a step split by fdph_predict must be completed by fdph_commit before anything else steps or
+// copies the state
+static int pending_commit(fdph_plan_t P) {
+    if (!P->predicted) return FDPH_OK;
+    set_error("step predicted by fdph_predict awaits fdph_commit");
+    return FDPH_E_STATE;
+}
+
 int fdph_reset(fdph_plan_t P) {
     if (!P) return FDPH_E_ARG;
+    P->predicted = false;
     cudaSetDevice(P->device);
     double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->dhat, P->partial,
                       P->ustate, P->vstate};
@@ -2013,6 +2059,7 @@ int fdph_reset(fdph_plan_t P) {
 
 int fdph_step(fdph_plan_t P, const double* D_n, double* T_n) {
     if (!P || !D_n || !T_n) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (P->n >= P->M) {
         set_error("the plan has already taken M steps");
         return FDPH_E_STATE;
@@ -2022,6 +2069,7 @@ int fdph_step(fdph_plan_t P, const double* D_n, double* T_n) {
 
 int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
     if (!P || !D || !T || steps < 0) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (P->n + steps > P->M) {
         set_error("run would pass step M");
         return FDPH_E_STATE;
@@ -2037,6 +2085,7 @@ int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
 
 int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_host) {
     if (!P || !D_host || !T_host || steps < 0) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (P->n + steps > P->M) {
         set_error("run would pass step M");
         return FDPH_E_STATE;
@@ -2063,6 +2112,7 @@ int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_
 
 int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
     if (!P || !D_n_host || !T_n_host) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (!P->dD) {
         int rc;
         if ((rc = dalloc(P, &P->dD, P->N)) || (rc = dalloc(P, &P->dT, P->N))) return rc;
@@ -2105,6 +2155,7 @@ int fdph_selftest_wait_timeout(int32_t device, int64_t polls) {
 
 int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
     if (!P || steps < 1 || steps > 1024) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (P->prof) {
         set_error("fdph_autotune: profiling is on");
         return FDPH_E_STATE;
@@ -2183,6 +2234,7 @@ int fdph_get_stats(fdph_plan_t P, fdph_stats* s) {
 
 int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     if (!P || !len) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
@@ -2210,6 +2262,7 @@ int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
 
 int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
     if (!P || !buf) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     size_t need = 0;
     int rc = fdph_save_state(P, nullptr, &need);
     if (rc) return rc;
@@ -2239,20 +2292,18 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
     return FDPH_OK;
 }
 
-int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
-    if (!P || !f || !f->tau0 || !(f->sigma_n > 0.0) || !(f->Dc > 0.0) || f->mu_d > f->mu_s) {
-        set_error("fdph_rupture_init: friction with tau0, sigma_n > 0, Dc > 0, mu_d <= mu_s required");
-        return FDPH_E_ARG;
-    }
+// K_{ii,0} in geometry order: jump of the ramp response of each element at its own midpoint over
+// [0, dt] (Eq. 4 with m = 0).  FDPH_E_STATE when the instantaneous term is not local
+// (cs dt > half the shortest element: K_{ij,0} != 0 for neighbours).
+static int self_coefficients(fdph_plan_t P, std::vector<double>& k0) {
     const HostPlan& hp = P->hp;
     double minlen = 1e300;
     for (int p = 0; p < P->N; ++p) minlen = std::min(minlen, hp.slen[p]);
     if (hp.cs * P->dt > 0.5 * minlen * (1.0 + 1e-12)) {
-        set_error("fdph_rupture_init: cs dt exceeds half the shortest element; the instantaneous term is not local");
+        set_error("cs dt exceeds half the shortest element; the instantaneous term is not local");
         return FDPH_E_STATE;
     }
-    // K_{ii,0}: jump of the ramp response of each element at its own midpoint over [0, dt]
-    std::vector<double> k0(P->N);
+    k0.assign(P->N, 0.0);
     for (int p = 0; p < P->N; ++p) {
         Seg sg;
         sg.ax = hp.sax[p];
@@ -2263,6 +2314,19 @@ int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
         const Stress2 w = stress_jump(hp.px[p], hp.py[p], sg, 0.0, P->dt, hp.mu, hp.cs);
         k0[hp.perm[p]] = hp.pnx[p] * w.x + hp.pny[p] * w.y;
     }
+    return FDPH_OK;
+}
+
+int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
+    if (!P || !f || !f->tau0 || !(f->sigma_n > 0.0) || !(f->Dc > 0.0) || f->mu_d > f->mu_s ||
+        (f->law != 0 && f->law != 1)) {
+        set_error("fdph_rupture_init: friction with tau0, sigma_n > 0, Dc > 0, mu_d <= mu_s, law 0 or 1 required");
+        return FDPH_E_ARG;
+    }
+    if (P->predicted) return pending_commit(P);
+    std::vector<double> k0;
+    int rc0 = self_coefficients(P, k0);
+    if (rc0) return rc0;
     if (!P->rupture) {
         double *tau0 = nullptr, *kk = nullptr, *slip = nullptr;
         int rc;
@@ -2281,12 +2345,14 @@ int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
     P->fr.mu_d = f->mu_d;
     P->fr.Dc = f->Dc;
     P->fr.dt = P->dt;
+    P->fr.law = f->law;
     P->rupture = true;
     return FDPH_OK;
 }
 
 int fdph_rupture_step(fdph_plan_t P, double* D_n, double* T_n) {
     if (!P || !D_n || !T_n) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (!P->rupture) {
         set_error("fdph_rupture_init has not been called on this plan");
         return FDPH_E_STATE;
@@ -2302,6 +2368,7 @@ int fdph_rupture_step(fdph_plan_t P, double* D_n, double* T_n) {
 
 int fdph_rupture_run(fdph_plan_t P, int32_t steps, double* D, double* T) {
     if (!P || !D || !T || steps < 0) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
     if (P->n + steps > P->M) {
         set_error("run would pass step M");
         return FDPH_E_STATE;
@@ -2323,6 +2390,41 @@ int fdph_rupture_slip(fdph_plan_t P, double* slip) {
     if (!P || !slip) return FDPH_E_ARG;
     if (!P->rupture) return FDPH_E_STATE;
     FDPH_CUDA(cudaMemcpyAsync(slip, P->fr.slip, P->N * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+    return FDPH_OK;
+}
+
+int fdph_predict(fdph_plan_t P, double* T_pred) {
+    if (!P || !T_pred) return FDPH_E_ARG;
+    if (P->predicted) return pending_commit(P);
+    if (P->n >= P->M) {
+        set_error("the plan has already taken M steps");
+        return FDPH_E_STATE;
+    }
+    int rc = P->precision != FDPH_FP64 ? launch_predict<float>(P, T_pred) : launch_predict<double>(P, T_pred);
+    if (rc == FDPH_OK) P->predicted = true;
+    return rc;
+}
+
+int fdph_commit(fdph_plan_t P, const double* D_n) {
+    if (!P || !D_n) return FDPH_E_ARG;
+    if (!P->predicted) {
+        set_error("fdph_commit without a preceding fdph_predict of this step");
+        return FDPH_E_STATE;
+    }
+    int rc = P->precision != FDPH_FP64 ? launch_commit<float>(P, D_n) : launch_commit<double>(P, D_n);
+    if (rc == FDPH_OK) {
+        P->predicted = false;
+        P->n += 1;
+    }
+    return rc;
+}
+
+int fdph_self(fdph_plan_t P, double* diag) {
+    if (!P || !diag) return FDPH_E_ARG;
+    std::vector<double> k0;
+    int rc = self_coefficients(P, k0);
+    if (rc) return rc;
+    memcpy(diag, k0.data(), k0.size() * sizeof(double));
     return FDPH_OK;
 }
 

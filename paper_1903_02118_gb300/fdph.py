@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
 
 class Friction(ctypes.Structure):
     _fields_ = [("tau0", ctypes.c_void_p), ("sigma_n", ctypes.c_double), ("mu_s", ctypes.c_double),
-                ("mu_d", ctypes.c_double), ("Dc", ctypes.c_double)]
+                ("mu_d", ctypes.c_double), ("Dc", ctypes.c_double), ("law", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +65,8 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
-           "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune"]
+           "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
+           "fdph_predict", "fdph_commit", "fdph_self"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -105,6 +106,9 @@ def lib():
         L.fdph_rupture_step.argtypes = [c_p, c_p, c_p]
         L.fdph_rupture_run.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_rupture_slip.argtypes = [c_p, c_p]
+        L.fdph_predict.argtypes = [c_p, c_p]
+        L.fdph_commit.argtypes = [c_p, c_p]
+        L.fdph_self.argtypes = [c_p, c_p]
         L.fdph_autotune.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.fdph_autotune.restype = ctypes.c_int
         L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
@@ -117,7 +121,8 @@ def lib():
                      "fdph_current_step",
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
                      "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc",
-                     "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip"):
+                     "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip",
+                     "fdph_predict", "fdph_commit", "fdph_self"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -229,11 +234,26 @@ class Plan:
         _check(lib().fdph_get_stats(self.handle, ctypes.byref(s)))
         return s.as_dict()
 
-    def rupture_init(self, tau0, sigma_n, mu_s, mu_d, Dc):
-        """Attach linear slip-weakening friction (fdph_rupture_init); tau0 is a device buffer."""
+    def rupture_init(self, tau0, sigma_n, mu_s, mu_d, Dc, law=0):
+        """Attach slip-weakening friction (fdph_rupture_init), law 0 linear, 1 exponential;
+        tau0 is a device buffer."""
         self._tau0 = tau0
-        fr = Friction(_ptr(tau0).value, sigma_n, mu_s, mu_d, Dc)
+        fr = Friction(_ptr(tau0).value, sigma_n, mu_s, mu_d, Dc, int(law))
         _check(lib().fdph_rupture_init(self.handle, ctypes.byref(fr)))
+
+    def predict(self, T_pred):
+        """Traction of the current step with D_n = 0 into the device buffer T_pred (fdph_predict)."""
+        _check(lib().fdph_predict(self.handle, _ptr(T_pred)))
+
+    def commit(self, D_n):
+        """Append D_n (device buffer) and advance one step (fdph_commit)."""
+        _check(lib().fdph_commit(self.handle, _ptr(D_n)))
+
+    def self_coefficients(self):
+        """K_{ii,0} in geometry order (fdph_self), a numpy array."""
+        out = np.empty(self.n, dtype=np.float64)
+        _check(lib().fdph_self(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def rupture_step(self, D_n, T_n):
         _check(lib().fdph_rupture_step(self.handle, _ptr(D_n), _ptr(T_n)))

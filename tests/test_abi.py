@@ -50,6 +50,9 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_plan(ctypes.byref(gb), ctypes.byref(m), 0.5, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_NAN
     assert not h.value
     assert L.fdph_step(None, None, None) == fdph.E_ARG
+    assert L.fdph_predict(None, None) == fdph.E_ARG
+    assert L.fdph_commit(None, None) == fdph.E_ARG
+    assert L.fdph_self(None, None) == fdph.E_ARG
     assert L.fdph_strerror(fdph.E_CAUSALITY)
 
 

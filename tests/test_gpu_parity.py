@@ -176,10 +176,11 @@ def test_config2_full_size_sampled_receivers():
     assert _rel(T[:, rows], T0) < 1e-9
 
 
-@pytest.mark.parametrize("mode", ["plain", "fdph"])
-def test_rupture_matches_oracle(mode):
-    """Dynamic rupture (Sec. 6.2, linear slip weakening): slip rate and traction of every element
-    and step against the oracle's rupture march on the same operator."""
+@pytest.mark.parametrize("mode,law", [("plain", "linear"), ("fdph", "linear"), ("plain", "exponential"),
+                                      ("fdph", "exponential")])
+def test_rupture_matches_oracle(mode, law):
+    """Dynamic rupture (Sec. 6.2, linear or the paper's exponential slip weakening): slip rate and
+    traction of every element and step against the oracle's rupture march on the same operator."""
     _need_gpu()
     N, M, dt = 200, 240, 0.5
     xy = _geom("straight", N)
@@ -195,9 +196,9 @@ def test_rupture_matches_oracle(mode):
         oplan = ofd.build_plan(el, p)
         Kop = ofd.operator_rows(el, oplan, np.arange(N))
         plan = fdph.Plan(xy, dt, M, 1e-6, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
-    D0, T0 = dense.rupture_march(Kop, tau0, 1.0, 0.6, 0.3, 2.0, dt, M)
+    D0, T0 = dense.rupture_march(Kop, tau0, 1.0, 0.6, 0.3, 2.0, dt, M, law=law)
     t0 = torch.from_numpy(tau0).cuda()
-    plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0)
+    plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0, law=0 if law == "linear" else 1)
     Dd = torch.zeros((M, N), dtype=torch.float64, device="cuda")
     Td = torch.zeros_like(Dd)
     plan.rupture_run(M, Dd, Td)
@@ -329,3 +330,69 @@ def test_autotune_keeps_state_and_results():
     plan.run(M - 50, Dd[50:], Td[50:])
     plan.synchronize()
     assert _rel(Td.cpu().numpy(), T_ref) < 1e-13
+
+
+def test_predict_commit_split_equals_step_and_rupture():
+    """fdph_predict + local solve + fdph_commit: with the prescribed slip rate it reproduces
+    fdph_run (T_n = T_pred + K_{ii,0} D_n); with a friction law solved by the caller it reproduces
+    fdph_rupture_run; K_{ii,0} equals the oracle's instantaneous self term; misuse is refused."""
+    _need_gpu()
+    N, M, dt = 180, 120, 0.5
+    xy = _geom("straight", N)
+    el = kn.element_table(xy)
+    K0 = kn.discrete_kernel(el, dt, 1, 1.0, 1.0)[0]
+    plan = fdph.Plan(xy, dt, M, 1e-6, eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16)
+    k0 = plan.self_coefficients()
+    assert np.abs(k0 - np.diag(K0)).max() < 1e-13
+    D = inputs.gaussian_filtered_history(N, M, 11)
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    plan.run(M, Dd, Td)
+    plan.synchronize()
+    T_run = Td.cpu().numpy()
+    plan.reset()
+    k0d = torch.from_numpy(k0).cuda()
+    Tp = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    for n in range(M):
+        plan.predict(Tp[n])
+        if n == 3:
+            with pytest.raises(fdph.FdphError):
+                plan.predict(Tp[n])               # one predict per step
+            with pytest.raises(fdph.FdphError):
+                plan.step(Dd[n], Td[n])           # the pending step blocks other stepping
+        plan.commit(Dd[n])
+    with pytest.raises(fdph.FdphError):
+        plan.commit(Dd[0])                        # no predict pending
+    plan.synchronize()
+    T_split = (Tp + k0d[None, :] * Dd).cpu().numpy()
+    assert _rel(T_split, T_run) < 1e-13
+
+    # exponential slip weakening solved in the caller's code between predict and commit
+    rng = np.random.default_rng(inputs.seed_for(3, inputs.FRICTION))
+    tau0 = 0.45 * (1.0 + 0.05 * rng.standard_normal(N))
+    tau0[N // 2 - 8:N // 2 + 8] = 0.61
+    t0 = torch.from_numpy(tau0).cuda()
+    plan.reset()
+    plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0, law=1)
+    Dr = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    Tr = torch.zeros_like(Dr)
+    plan.rupture_run(M, Dr, Tr)
+    plan.synchronize()
+    plan.reset()
+    slip = torch.zeros(N, dtype=torch.float64, device="cuda")
+    Du = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    Tu = torch.zeros_like(Du)
+    for n in range(M):
+        plan.predict(Tu[n])
+        plan.synchronize()
+        tau = t0 + Tu[n]
+        strength = 0.3 * torch.exp(-slip / 2.0) + 0.3
+        v = torch.where(tau > strength, (tau - strength) / (-k0d), torch.zeros_like(tau))
+        Du[n] = v
+        Tu[n] = tau + k0d * v
+        slip += v * dt
+        torch.cuda.synchronize()
+        plan.commit(Du[n])
+    plan.synchronize()
+    assert (Dr > 0).sum().item() > 0.2 * Dr.numel()
+    assert _rel(Du.cpu().numpy(), Dr.cpu().numpy()) < 1e-10 and _rel(Tu.cpu().numpy(), Tr.cpu().numpy()) < 1e-10

@@ -1,5 +1,8 @@
 """Pins of the oracle's plain (dense) time march (CPU only)."""
+import math
+
 import numpy as np
+import pytest
 
 from oracle import dense
 from oracle import kernel as kn
@@ -62,25 +65,57 @@ def test_fft_rows_equal_march():
     assert np.abs(Tr - T[:, rows]).max() < 1e-12 * np.abs(T).max()
 
 
-def test_rupture_follows_the_plane_wave_recursion_inside_the_causal_cone():
+@pytest.mark.parametrize("law", ["linear", "exponential"])
+def test_rupture_follows_the_plane_wave_recursion_inside_the_causal_cone(law):
     # Uniform overstress on a long planar fault: before edge waves arrive every interior element
-    # is a 1-D plane-wave problem, T = tau0 - mu/(2 cs) v, so with linear weakening the slip rate
-    # obeys eta v_n = tau0 - strength(u_n), u_{n+1} = u_n + v_n dt exactly (Sec. 6.2 law).
+    # is a 1-D plane-wave problem, T = tau0 - mu/(2 cs) v, so the slip rate obeys
+    # eta v_n = tau0 - strength(u_n), u_{n+1} = u_n + v_n dt exactly (Sec. 6.2 law).  For the
+    # exponential law this explicit recursion is the Euler scheme of
+    # eta du/dt = a - b exp(-u / Dc) (a = tau0 - T_dy, b = T_th - T_dy), whose solution is
+    # exp(u / Dc) = b / a + (1 - b / a) exp(a t / (eta Dc)).
     N, M, dt = 160, 60, 0.5
     el = kn.element_table(inputs.straight_fault(N))
     K = kn.discrete_kernel(el, dt, M, 1.0, 1.0)
     tau0 = np.full(N, 0.62)
-    D, T = dense.rupture_march(K, tau0, 1.0, 0.6, 0.3, 4.0, dt, M)
+    Dc = 4.0
+    D, T = dense.rupture_march(K, tau0, 1.0, 0.6, 0.3, Dc, dt, M, law=law)
     u, eta = 0.0, 0.5
     i = N // 2
     for n in range(M):
         if (n + 1) * dt >= el["mx"][i] - 1.0:   # edge waves could have arrived
             break
-        s = 0.6 - 0.3 * min(u / 4.0, 1.0)
+        if law == "linear":
+            s = 0.6 - 0.3 * min(u / Dc, 1.0)
+        else:
+            s = 0.3 + 0.3 * math.exp(-u / Dc)
         v = max(0.62 - s, 0.0) / eta
         assert abs(D[n, i] - v) < 1e-12 and abs(T[n, i] - (0.62 - eta * v)) < 1e-12
         u += v * dt
     assert n > 40
+    if law == "exponential":
+        a, b, t = 0.32, 0.3, n * dt
+        u_ode = Dc * math.log(b / a + (1 - b / a) * math.exp(a * t / (eta * Dc)))
+        u_march = D[:n, i].sum() * dt
+        # Euler (lambda dt = a dt / (eta Dc) = 0.08) is 6 % behind the ODE here; the linear law
+        # with the same T_th, T_dy, Dc would be 28 % ahead
+        assert abs(u_march - u_ode) < 0.1 * u_ode
+
+
+def test_exponential_weakening_limits():
+    # Sec. 6.2: rupture starts when the traction reaches T_th; after slip >> Dc the traction
+    # of slipping elements settles at T_dy.
+    N, M, dt = 120, 160, 0.5
+    el = kn.element_table(inputs.straight_fault(N))
+    K = kn.discrete_kernel(el, dt, M, 1.0, 1.0)
+    tau0 = np.full(N, 0.5)
+    tau0[55:65] = 0.7
+    D, T = dense.rupture_march(K, tau0, 1.0, 0.6, 0.3, 0.5, dt, M, law="exponential")
+    assert np.all(D[0, :55] == 0.0) and np.all(D[0, 55:65] > 0.0)
+    assert np.all(T[D == 0.0] <= 0.6 + 1e-12)
+    slip = D.sum(0) * dt
+    deep = slip > 20 * 0.5
+    assert deep.sum() > 10
+    assert np.abs(T[-1, deep] - 0.3).max() < 1e-6
 
 
 def test_rupture_respects_locking_and_no_back_slip():

@@ -275,6 +275,7 @@ def main():
     ap.add_argument("--eta-scheme", type=int, default=None, choices=[0, 1],
                     help="admissibility: 0 constant eta (Eq. 8), 1 constant eta^2 dist (Eq. 25, needs --lmin)")
     ap.add_argument("--lmin", type=float, default=None, help="lmin of Eq. 9 / Eq. 25, in element lengths")
+    ap.add_argument("--leaf", type=int, default=None, help="largest cluster of an inadmissible leaf")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--quick", action="store_true",
                     help="plan + roll forward + warm-up + timed steps only (for profiler launch lists)")
@@ -299,6 +300,8 @@ def main():
         cfg["eta_scheme"] = args.eta_scheme
     if args.lmin is not None:
         cfg["lmin"] = args.lmin
+    if args.leaf is not None:
+        cfg["leaf"] = args.leaf
     if args.n:
         cfg["N"] = args.n
     if args.m:

@@ -64,6 +64,7 @@ typedef enum fdph_precision {
 } fdph_precision;
 
 typedef struct fdph_plan_s* fdph_plan_t;
+typedef struct fdph_batch_s* fdph_batch_t;   /* opaque set of plans stepped together */
 
 /* Fault geometry: n straight elements, host memory, xy[4*e + (0,1,2,3)] = (x0, y0, x1, y1)
  * of element e.  Collocation point = midpoint; normal = tangent rotated by +90 degrees
@@ -208,6 +209,31 @@ int fdph_rupture_slip(fdph_plan_t plan, double* slip);
  * already pending, a commit with none pending), FDPH_E_CUDA. */
 int fdph_predict(fdph_plan_t plan, double* T_pred);
 int fdph_commit(fdph_plan_t plan, const double* D_n);
+
+/* Batches (no counterpart in the paper; the serving pattern of independent scenarios): plans
+ * that share the device and the precision, stepped together.  Each step of a batch runs every
+ * plan's push, FIR / scatter (Eqs. 32, 42) and transient / Eq. 39 kernels on that plan's streams,
+ * then ONE persistent near-field launch (App. E) whose CTAs take the work items of all plans,
+ * dealt largest first over the SMs, then every plan's gather; the step is captured once per
+ * (kind, buffers) as a CUDA graph and replayed.  Each plan keeps its own state and step index,
+ * and its results are bit-identical to stepping it alone.
+ *
+ * fdph_batch_create: `plans` (count >= 1, distinct, host array, copied) must outlive the batch.
+ *   Errors: FDPH_E_ARG (null, duplicate, mixed device or precision), FDPH_E_STATE (a predict
+ *   pending), FDPH_E_CUDA.  fdph_autotune on a member plan invalidates the batch (later batch
+ *   calls return FDPH_E_STATE; create it again).
+ * fdph_batch_run: `steps` steps of every plan; D[p], T[p] (host arrays of device pointers):
+ *   plan p's rows, steps * n_p doubles, step-major, as fdph_run.  Asynchronous; every plan's
+ *   stream is ordered after the batch's work.  Errors as fdph_run for any plan.
+ * fdph_batch_rupture_run: the same for rupture steps (fdph_rupture_init on every plan) with the
+ *   outputs of fdph_rupture_run.
+ * fdph_batch_synchronize: wait for the batch and its plans; reports a near-field wait that gave
+ *   up (FDPH_E_TIMEOUT).  fdph_batch_destroy: release the batch (not its plans); NULL ignored. */
+int fdph_batch_create(const fdph_plan_t* plans, int32_t count, fdph_batch_t* out);
+int fdph_batch_run(fdph_batch_t batch, int32_t steps, const double* const* D, double* const* T);
+int fdph_batch_rupture_run(fdph_batch_t batch, int32_t steps, double* const* D, double* const* T);
+int fdph_batch_synchronize(fdph_batch_t batch);
+void fdph_batch_destroy(fdph_batch_t batch);
 
 /* Instantaneous self coefficients K_{ii,0} (Eq. 4 with m = 0; -mu/(2 cs) on a straight fault at
  * cs dt = dx/2, the radiation damping) into diag (HOST, n doubles, geometry order).

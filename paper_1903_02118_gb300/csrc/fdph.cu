@@ -81,8 +81,10 @@ struct NearDev {
 struct __align__(16) NearTask {
     long long off;       // element offset of the item's first slice (tensor, or aux for kind 1)
     int item, k0, k1, kind, nr, ns, sl, s0, W, vstate;
-    int pad[2];
+    int scen;            // plan of the item in a batch (0 otherwise)
+    int pad;
 };
+static_assert(sizeof(NearTask) == 64, "one work item is four 16-byte loads");
 
 static const int kMaxSoe = 16;
 
@@ -392,6 +394,38 @@ __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
     return tk.kind ? tk.k1 : min(tk.k1, n + 1) - tk.k0;
 }
 
+// What a near-field work item reads of its plan (the plan of the launch, or for a batch of
+// plans the item's own plan), with the plan's step index n.
+struct NearView {
+    const double* Dring;
+    const double* Cring;
+    double* vstate;
+    const double* rho;
+    const void* tensor;
+    const void* stat;
+    double* partial;
+    int* err;
+    int N, WD, WC, n;
+};
+
+template <class T>
+__device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
+    NearView v;
+    v.Dring = a.Dring;
+    v.Cring = a.Cring;
+    v.vstate = a.vstate;
+    v.rho = a.rho;
+    v.tensor = a.tensor;
+    v.stat = a.stat;
+    v.partial = a.partial;
+    v.err = a.err;
+    v.N = a.N;
+    v.WD = a.WD;
+    v.WC = a.WC;
+    v.n = step_index(a);
+    return v;
+}
+
 // The vectors of one work item (rows of 32 in the storage type) are
 // gathered by the consumer warps in two halves: near_issue loads this warp's rows (w, w + C, ...)
 // into registers, near_commit (one item later, so that the loads are in flight meanwhile) forms
@@ -401,10 +435,10 @@ __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers >= 17, "aux rows (1 + 16 tail terms) fit the row registers");
 
-template <class T>
-__device__ __forceinline__ void near_issue(const StepArgs<T>& a, const NearTask& tk, int n, int warp, int lane,
+__device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
                                            double (&r)[kRowsPerWarp], double& dW) {
-    const int nsl = near_slices<T>(tk, n);
+    const int n = a.n;
+    const int nsl = near_slices<double>(tk, n);
     const bool on = lane < tk.ns;
     const size_t col = (size_t)tk.s0 + lane;
     if (!tk.kind) {
@@ -433,10 +467,10 @@ __device__ __forceinline__ void near_issue(const StepArgs<T>& a, const NearTask&
     }
 }
 
-template <class R, class T>
-__device__ __forceinline__ void near_commit(const StepArgs<T>& a, const NearTask& tk, int n, int warp, int lane,
+template <class R>
+__device__ __forceinline__ void near_commit(const NearView& a, const NearTask& tk, int warp, int lane,
                                             const double (&r)[kRowsPerWarp], double dW, unsigned char* vb) {
-    const int nsl = near_slices<T>(tk, n);
+    const int nsl = near_slices<double>(tk, a.n);
 #pragma unroll
     for (int m = 0; m < kRowsPerWarp; ++m) {
         const int k = warp + m * kNearConsumers;
@@ -553,9 +587,10 @@ static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer
 // load the vectors of the next item into a second shared buffer while they consume the current
 // one; consumer warp w takes slices w, w + kNearConsumers, ... of each stage, lane i = receiver i,
 // reading its coefficients and the vector 16 bytes at a time.  At the end of an item the
-// consumers' sums are combined in FP64 into the item's partial-sum slot.
-template <class T, class H>
-__global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
+// consumers' sums are combined in FP64 into the item's partial-sum slot.  kBatch: the items of
+// several plans in one launch (fdph_batch_run); item tk belongs to plan scen[tk.scen].
+template <class T, class H, bool kBatch>
+__global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, const StepArgs<T>* scen) {
     using C = NearCfg<H>;
     using A = typename NearTypes<H>::Aux;
     using R = typename NearTypes<H>::Row;
@@ -564,7 +599,8 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
     __shared__ double red[2][kNearConsumers][32];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
-    const int n = step_index(a);
+    const NearView v0 = kBatch ? NearView{} : near_view(a);
+    auto view = [&](const NearTask& tk) -> NearView { return kBatch ? near_view(scen[tk.scen]) : v0; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
     unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
@@ -590,17 +626,18 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
             const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
             for (int ti = t0; ti < t1; ++ti) {
                 const NearTask tk = task(ti);
+                const NearView v = view(tk);
                 const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
-                const int nsl = near_slices<T>(tk, n);
+                const int nsl = near_slices<T>(tk, v.n);
                 const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
                 const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
-                const unsigned char* src = tk.kind ? (const unsigned char*)((const A*)a.stat + tk.off)
-                                                   : (const unsigned char*)((const H*)a.tensor + tk.off);
+                const unsigned char* src = tk.kind ? (const unsigned char*)((const A*)v.stat + tk.off)
+                                                   : (const unsigned char*)((const H*)v.tensor + tk.off);
                 for (int q = 0; q < nst; ++q, ++g) {
                     const int s = g % C::stages;
                     if (!mbar_wait_bounded(&empty[s], (unsigned)(((g / C::stages) & 1) ^ 1))) {
                         abort_flag = 1;
-                        atomicExch(a.err, 1);
+                        atomicExch(v.err, 1);
                     }
                     const int cnt = min(per, nsl - q * per);
                     const unsigned bytes = (unsigned)(cnt * tk.sl * esz);
@@ -615,23 +652,27 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
         // ---------------- consumers
         double rows[kRowsPerWarp], dW = 0.0;
         NearTask nxt;
+        NearView vn;
         if (t0 < t1) {
             nxt = task(t0);
-            near_issue(a, nxt, n, warp, lane, rows, dW);
-            near_commit<R>(a, nxt, n, warp, lane, rows, dW, vbuf);
+            vn = view(nxt);
+            near_issue(vn, nxt, warp, lane, rows, dW);
+            near_commit<R>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         consumer_barrier();
         int par = 0;
         for (int ti = t0; ti < t1; ++ti, par ^= 1) {
             const NearTask tk = nxt;
+            const NearView v = vn;
             // the next item's vector loads stay in flight while this item is consumed
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
-                near_issue(a, nxt, n, warp, lane, rows, dW);
+                vn = view(nxt);
+                near_issue(vn, nxt, warp, lane, rows, dW);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
-            const int nsl = near_slices<T>(tk, n);
+            const int nsl = near_slices<T>(tk, v.n);
             const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
             const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
             const int li = lane < tk.nr ? lane : 0;     // lanes past nr read a valid element, unused
@@ -642,7 +683,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 const int cnt = min(per, nsl - q * per);
                 if (!mbar_wait_bounded(&full[s], (unsigned)((g / C::stages) & 1))) {
                     abort_flag = 1;
-                    atomicExch(a.err, 1);
+                    atomicExch(v.err, 1);
                 }
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
                 for (int kk = warp; kk < cnt; kk += kNearConsumers) {
@@ -655,13 +696,13 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            if (ti + 1 < t1) near_commit<R>(a, nxt, n, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            if (ti + 1 < t1) near_commit<R>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             red[par][warp][lane] = lane < tk.nr ? (double)acc + accd : 0.0;
             consumer_barrier();   // also publishes the next item's vectors
             if (warp == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < kNearConsumers; ++w) sum += red[par][w][lane];
-                a.partial[(size_t)tk.item * 32 + lane] = sum;
+                v.partial[(size_t)tk.item * 32 + lane] = sum;
             }
         }
     }
@@ -955,6 +996,7 @@ struct fdph_plan_s {
     std::vector<int32_t> near_W;
     std::vector<char> near_tail;
     int chunk = 0;            // steps of exact kernel per near-field work item
+    int sched_version = 0;    // bumped whenever the near-field items are rebuilt
     size_t partial_cap = 0;   // capacity of `partial`, in doubles
     // branches of a step that run concurrently with the near field: [0] FIR + scatter,
     // [1] transient convolution + Eq. 39 evaluation (fork after push, join before gather)
@@ -1080,12 +1122,12 @@ static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (P->precision == FDPH_FP16) {
             cfg.dynamicSmemBytes = NearCfg<__half>::smem;
-            cudaLaunchKernelEx(&cfg, near_kernel<T, __half>, a);
+            cudaLaunchKernelEx(&cfg, near_kernel<T, __half, false>, a, (const StepArgs<T>*)nullptr);
             return;
         }
     }
     cfg.dynamicSmemBytes = NearCfg<T>::smem;
-    cudaLaunchKernelEx(&cfg, near_kernel<T, T>, a);
+    cudaLaunchKernelEx(&cfg, near_kernel<T, T, false>, a, (const StepArgs<T>*)nullptr);
 }
 
 template <class T>
@@ -1378,22 +1420,13 @@ static int rupture_graph(fdph_plan_t P, int steps, double* D, double* Tout) {
     return FDPH_OK;
 }
 
-// Persistent near-field grid: CTAs per SM from the occupancy of the kernel, work items dealt
-// largest first to the least-loaded CTA (steady-state bytes); uploads the task lists and the
-// receiver -> partial-slot map of the current items.
+// The plan's near-field work items as the persistent kernel reads them, with their steady-state
+// cost in bytes (+ a fixed per-item overhead).
 template <class T, class H>
-static int build_schedule(fdph_plan_t P) {
+static void near_tasks(fdph_plan_t P, int scen, std::vector<NearTask>& tasks, std::vector<double>& cost) {
     using A = typename NearTypes<H>::Aux;
-    HostPlan& hp = P->hp;
-    int rc;
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
-    int sms = 0, per_sm = 0;
-    FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
-    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H>, kNearThreads, NearCfg<H>::smem));
+    const HostPlan& hp = P->hp;
     const int ni = (int)hp.items.size();
-    const int ncta = std::max(1, std::min(ni, sms * std::max(per_sm, 1)));
-    std::vector<NearTask> tasks_all(ni);
-    std::vector<double> cost(ni);
     for (int q = 0; q < ni; ++q) {
         const NearItem& it = hp.items[q];
         const NearLeaf& L = hp.near[it.leaf];
@@ -1410,9 +1443,17 @@ static int build_schedule(fdph_plan_t P) {
         t.s0 = L.s0;
         t.W = L.W;
         t.vstate = (int)L.vstate;
-        tasks_all[q] = t;
-        cost[q] = (double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0;
+        t.scen = scen;
+        tasks.push_back(t);
+        cost.push_back((double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0);
     }
+}
+
+// Work items dealt largest first to the least-loaded of ncta CTAs; per-CTA task lists in CTA
+// order and their offsets.
+static void deal_tasks(const std::vector<NearTask>& all, const std::vector<double>& cost, int ncta,
+                       std::vector<NearTask>& tasks, std::vector<int>& cptr) {
+    const int ni = (int)all.size();
     std::vector<int> order(ni);
     for (int q = 0; q < ni; ++q) order[q] = q;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
@@ -1429,13 +1470,41 @@ static int build_schedule(fdph_plan_t P) {
         own[heap.back().second].push_back(q);
         std::push_heap(heap.begin(), heap.end(), cmp);
     }
-    std::vector<NearTask> tasks;
-    std::vector<int> cptr(1, 0);
+    tasks.clear();
+    cptr.assign(1, 0);
     for (int c = 0; c < ncta; ++c) {
-        for (int q : own[c]) tasks.push_back(tasks_all[q]);
+        for (int q : own[c]) tasks.push_back(all[q]);
         cptr.push_back((int)tasks.size());
     }
+}
+
+// CTAs of the persistent near-field grid: SMs x resident CTAs per SM of the kernel
+template <class T, class H, bool kBatch>
+static int near_grid(int device, int* ncta_max) {
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
+    int sms = 0, per_sm = 0;
+    FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H, kBatch>, kNearThreads, NearCfg<H>::smem));
+    *ncta_max = sms * std::max(per_sm, 1);
+    return FDPH_OK;
+}
+
+// Persistent near-field grid of one plan: work items dealt over the CTAs (steady-state bytes);
+// uploads the task lists and the receiver -> partial-slot map of the current items.
+template <class T, class H>
+static int build_schedule(fdph_plan_t P) {
+    HostPlan& hp = P->hp;
+    int rc, ncta_max = 1;
+    if ((rc = near_grid<T, H, false>(P->device, &ncta_max))) return rc;
+    std::vector<NearTask> all, tasks;
+    std::vector<double> cost;
+    std::vector<int> cptr;
+    near_tasks<T, H>(P, 0, all, cost);
+    const int ni = (int)all.size();
+    const int ncta = std::max(1, std::min(ni, ncta_max));
+    deal_tasks(all, cost, ncta, tasks, cptr);
     P->n_cta = ni ? ncta : 0;
+    P->sched_version += 1;
     if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
         (rc = upload(P, &P->np_ptr, hp.np_ptr)) || (rc = upload(P, &P->np_idx, hp.np_idx)))
         return rc;
@@ -1749,6 +1818,263 @@ static int set_chunk_any(fdph_plan_t P, int chunk) {
                                        : set_chunk<double, double>(P, chunk);
 }
 
+// a step split by fdph_predict must be completed by fdph_commit before anything else steps or
+// copies the state
+static int pending_commit(fdph_plan_t P) {
+    if (!P->predicted) return FDPH_OK;
+    set_error("step predicted by fdph_predict awaits fdph_commit");
+    return FDPH_E_STATE;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batches of plans: one near-field launch per step for all of them
+
+// A set of plans (same device, same precision) stepped together: per step, each plan's push,
+// FIR / scatter and transient / Eq. 39 kernels on that plan's streams, then ONE persistent
+// near-field launch over the work items of all plans (dealt together over the CTAs), then each
+// plan's gather.  Graphs of one batch step are captured per (kind, buffers) and replayed.
+struct fdph_batch_s {
+    int device = 0, precision = 0;
+    std::vector<fdph_plan_t> plans;
+    std::vector<int> version;            // each plan's near-field schedule at creation
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_near = nullptr, ev_end = nullptr;
+    std::vector<cudaEvent_t> ev_ready, ev_done;
+    NearTask* tasks = nullptr;
+    int* cta_ptr = nullptr;
+    int n_cta = 0;
+    int near_priority = 0;
+    struct Entry {
+        int kind;
+        std::vector<const void*> D, T;
+        void* scen;                      // device StepArgs of every plan for this entry
+        cudaGraphExec_t ex;
+    };
+    std::vector<Entry> graphs;
+};
+
+template <class T>
+static void launch_near_batch(fdph_batch_t B, const StepArgs<T>* scen, cudaStream_t s) {
+    StepArgs<T> ab;
+    memset(&ab, 0, sizeof(ab));
+    ab.tasks = B->tasks;
+    ab.cta_ptr = B->cta_ptr;
+    ab.n_cta = B->n_cta;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B->n_cta);
+    cfg.blockDim = dim3(kNearThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = B->near_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if constexpr (sizeof(T) == 4) {
+        if (B->precision == FDPH_FP16) {
+            cfg.dynamicSmemBytes = NearCfg<__half>::smem;
+            cudaLaunchKernelEx(&cfg, near_kernel<T, __half, true>, ab, scen);
+            return;
+        }
+    }
+    cfg.dynamicSmemBytes = NearCfg<T>::smem;
+    cudaLaunchKernelEx(&cfg, near_kernel<T, T, true>, ab, scen);
+}
+
+// One step of every plan of the batch (kind GRAPH_RUN or GRAPH_RUPTURE), for capture on the
+// batch stream.  av[p]: plan p's arguments (step index from its n_dev); D[p]: its rupture rows.
+template <class T>
+static void enqueue_batch_step(fdph_batch_t B, int kind, const std::vector<StepArgs<T>>& av,
+                               const std::vector<double*>& D, const StepArgs<T>* scen) {
+    cudaStream_t bs = B->stream;
+    const size_t np = B->plans.size();
+    cudaEventRecord(B->ev_start, bs);
+    for (size_t p = 0; p < np; ++p) {
+        fdph_plan_t P = B->plans[p];
+        StepArgs<T> a = av[p];
+        cudaStream_t s = P->stream;
+        cudaStreamWaitEvent(s, B->ev_start, 0);
+        if (kind == GRAPH_RUN) {
+            push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a);
+            cudaEventRecord(P->ev_fork, s);
+            cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
+            cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
+            if (a.n_fir) fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, P->side[0]>>>(a);
+            if (a.n_sct) scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, P->side[0]>>>(a);
+            if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, P->side[1]>>>(a);
+            if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, P->side[1]>>>(a);
+            cudaEventRecord(P->ev_join[0], P->side[0]);
+            cudaEventRecord(P->ev_join[1], P->side[1]);
+        } else {   // rupture prediction: zero row, transient, Eq. 39 evaluation
+            a.D_in = nullptr;
+            push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a);
+            if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a);
+            if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
+        }
+        cudaEventRecord(B->ev_ready[p], s);
+        cudaStreamWaitEvent(bs, B->ev_ready[p], 0);
+    }
+    if (B->n_cta) launch_near_batch<T>(B, scen, bs);
+    cudaEventRecord(B->ev_near, bs);
+    for (size_t p = 0; p < np; ++p) {
+        fdph_plan_t P = B->plans[p];
+        StepArgs<T> a = av[p];
+        cudaStream_t s = P->stream;
+        cudaStreamWaitEvent(s, B->ev_near, 0);
+        if (kind == GRAPH_RUN) {
+            cudaStreamWaitEvent(s, P->ev_join[0], 0);
+            cudaStreamWaitEvent(s, P->ev_join[1], 0);
+            gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+        } else {
+            a.D_in = nullptr;
+            gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+            friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D[p], a.T_out, a.n_dev);
+            enqueue_commit<T>(P, a, D[p], s);
+        }
+        advance_step_kernel<<<1, 1, 0, s>>>(P->n_dev);
+        cudaEventRecord(B->ev_done[p], s);
+        cudaStreamWaitEvent(bs, B->ev_done[p], 0);
+    }
+}
+
+// `steps` steps of every plan of the batch as replays of one captured batch-step graph
+template <class T>
+static int batch_run(fdph_batch_t B, int kind, int steps, const double* const* D, double* const* Tt) {
+    const size_t np = B->plans.size();
+    cudaStream_t bs = B->stream;
+    // ordered after the work already queued on every plan's stream; step indices on the device
+    for (size_t p = 0; p < np; ++p) {
+        fdph_plan_t P = B->plans[p];
+        if (!P->n_dev) {
+            int rc = dalloc(P, &P->n_dev, 2);
+            if (rc) return rc;
+        }
+        FDPH_CUDA(cudaEventRecord(B->ev_ready[p], P->stream));
+        FDPH_CUDA(cudaStreamWaitEvent(bs, B->ev_ready[p], 0));
+    }
+    for (size_t p = 0; p < np; ++p) set_step_kernel<<<1, 1, 0, bs>>>(B->plans[p]->n_dev, B->plans[p]->n);
+    cudaGraphExec_t ex = nullptr;
+    for (const auto& ge : B->graphs) {
+        if (ge.kind != kind) continue;
+        bool same = true;
+        for (size_t p = 0; p < np && same; ++p) same = ge.D[p] == (const void*)D[p] && ge.T[p] == (const void*)Tt[p];
+        if (same) {
+            ex = ge.ex;
+            break;
+        }
+    }
+    if (!ex) {
+        std::vector<StepArgs<T>> av(np);
+        std::vector<double*> Dr(np);
+        for (size_t p = 0; p < np; ++p) {
+            fdph_plan_t P = B->plans[p];
+            av[p] = make_args<T>(P, kind == GRAPH_RUPTURE ? nullptr : D[p], Tt[p]);
+            av[p].n_dev = P->n_dev;
+            av[p].io_stride = P->N;
+            av[p].io_ring = 0;
+            Dr[p] = (double*)D[p];
+        }
+        void* scen = nullptr;
+        FDPH_CUDA(cudaMalloc(&scen, np * sizeof(StepArgs<T>)));
+        cudaError_t e = cudaMemcpy(scen, av.data(), np * sizeof(StepArgs<T>), cudaMemcpyHostToDevice);
+        cudaGraph_t g = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_batch_step<T>(B, kind, av, Dr, (const StepArgs<T>*)scen);
+            e = cudaStreamEndCapture(bs, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaFree(scen);
+            set_error(std::string("batch graph: ") + cudaGetErrorString(e));
+            return FDPH_E_CUDA;
+        }
+        if (B->graphs.size() >= 4) {   // bounded cache: drop the oldest graph
+            cudaStreamSynchronize(bs);
+            cudaGraphExecDestroy(B->graphs.front().ex);
+            cudaFree(B->graphs.front().scen);
+            B->graphs.erase(B->graphs.begin());
+        }
+        fdph_batch_s::Entry en;
+        en.kind = kind;
+        en.D.assign(D, D + np);
+        en.T.assign(Tt, Tt + np);
+        en.scen = scen;
+        en.ex = ex;
+        B->graphs.push_back(en);
+    }
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, bs);
+    if (e == cudaSuccess) e = cudaEventRecord(B->ev_end, bs);
+    for (size_t p = 0; p < np && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(B->plans[p]->stream, B->ev_end, 0);
+    if (e != cudaSuccess) {
+        set_error(std::string("batch run: ") + cudaGetErrorString(e));
+        return FDPH_E_CUDA;
+    }
+    for (size_t p = 0; p < np; ++p) B->plans[p]->n += steps;
+    return FDPH_OK;
+}
+
+template <class T, class H>
+static int batch_schedule(fdph_batch_t B) {
+    int ncta_max = 1, rc;
+    if ((rc = near_grid<T, H, true>(B->device, &ncta_max))) return rc;
+    std::vector<NearTask> all, tasks;
+    std::vector<double> cost;
+    std::vector<int> cptr;
+    for (size_t p = 0; p < B->plans.size(); ++p) near_tasks<T, H>(B->plans[p], (int)p, all, cost);
+    const int ni = (int)all.size();
+    const int ncta = std::max(1, std::min(ni, ncta_max));
+    deal_tasks(all, cost, ncta, tasks, cptr);
+    B->n_cta = ni ? ncta : 0;
+    FDPH_CUDA(cudaMalloc(&B->tasks, std::max<size_t>(1, tasks.size()) * sizeof(NearTask)));
+    FDPH_CUDA(cudaMalloc(&B->cta_ptr, cptr.size() * sizeof(int)));
+    if (!tasks.empty())
+        FDPH_CUDA(cudaMemcpy(B->tasks, tasks.data(), tasks.size() * sizeof(NearTask), cudaMemcpyHostToDevice));
+    FDPH_CUDA(cudaMemcpy(B->cta_ptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return FDPH_OK;
+}
+
+static void batch_free(fdph_batch_t B) {
+    if (!B) return;
+    cudaSetDevice(B->device);
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    for (auto& ge : B->graphs) {
+        cudaGraphExecDestroy(ge.ex);
+        cudaFree(ge.scen);
+    }
+    if (B->tasks) cudaFree(B->tasks);
+    if (B->cta_ptr) cudaFree(B->cta_ptr);
+    for (cudaEvent_t e : B->ev_ready) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : B->ev_done) if (e) cudaEventDestroy(e);
+    if (B->ev_start) cudaEventDestroy(B->ev_start);
+    if (B->ev_near) cudaEventDestroy(B->ev_near);
+    if (B->ev_end) cudaEventDestroy(B->ev_end);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+// batch calls: every plan still has the schedule the batch was built on and no pending predict
+static int batch_check(fdph_batch_t B, int steps) {
+    for (size_t p = 0; p < B->plans.size(); ++p) {
+        fdph_plan_t P = B->plans[p];
+        if (P->predicted) return pending_commit(P);
+        if (P->sched_version != B->version[p]) {
+            set_error("a plan of the batch has rebuilt its near-field items (fdph_autotune): create the batch again");
+            return FDPH_E_STATE;
+        }
+        if (P->prof) {
+            set_error("batch run: profiling is on for a plan of the batch");
+            return FDPH_E_STATE;
+        }
+        if (P->n + steps > P->M) {
+            set_error("batch run would pass step M of a plan");
+            return FDPH_E_STATE;
+        }
+    }
+    return FDPH_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // C ABI
 
@@ -2030,14 +2356,6 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     P->st.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P;
     return FDPH_OK;
-}
-
-// a step split by fdph_predict must be completed by fdph_commit before anything else steps or
-// copies the state
-static int pending_commit(fdph_plan_t P) {
-    if (!P->predicted) return FDPH_OK;
-    set_error("step predicted by fdph_predict awaits fdph_commit");
-    return FDPH_E_STATE;
 }
 
 int fdph_reset(fdph_plan_t P) {
@@ -2450,6 +2768,97 @@ int fdph_kernel_times(fdph_plan_t P, double* ms, int64_t* launches) {
     }
     return FDPH_OK;
 }
+
+int fdph_batch_create(const fdph_plan_t* plans, int32_t count, fdph_batch_t* out) {
+    if (!plans || !out || count < 1 || count > 1024) return FDPH_E_ARG;
+    *out = nullptr;
+    for (int p = 0; p < count; ++p) {
+        if (!plans[p]) return FDPH_E_ARG;
+        for (int q = 0; q < p; ++q)
+            if (plans[q] == plans[p]) {
+                set_error("fdph_batch_create: a plan appears twice");
+                return FDPH_E_ARG;
+            }
+        if (plans[p]->device != plans[0]->device || plans[p]->precision != plans[0]->precision) {
+            set_error("fdph_batch_create: plans of one batch share the device and the precision");
+            return FDPH_E_ARG;
+        }
+        if (plans[p]->predicted) return pending_commit(plans[p]);
+    }
+    fdph_batch_t B = new fdph_batch_s;
+    B->device = plans[0]->device;
+    B->precision = plans[0]->precision;
+    B->plans.assign(plans, plans + count);
+    for (int p = 0; p < count; ++p) B->version.push_back(plans[p]->sched_version);
+    B->near_priority = plans[0]->near_priority;
+    if (cudaSetDevice(B->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_near, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_end, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("fdph_batch_create: stream / event creation failed");
+        batch_free(B);
+        return FDPH_E_CUDA;
+    }
+    B->ev_ready.assign(count, nullptr);
+    B->ev_done.assign(count, nullptr);
+    for (int p = 0; p < count; ++p)
+        if (cudaEventCreateWithFlags(&B->ev_ready[p], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev_done[p], cudaEventDisableTiming) != cudaSuccess) {
+            set_error("fdph_batch_create: event creation failed");
+            batch_free(B);
+            return FDPH_E_CUDA;
+        }
+    int rc = B->precision == FDPH_FP16   ? batch_schedule<float, __half>(B)
+             : B->precision == FDPH_FP32 ? batch_schedule<float, float>(B)
+                                         : batch_schedule<double, double>(B);
+    if (rc) {
+        batch_free(B);
+        return rc;
+    }
+    *out = B;
+    return FDPH_OK;
+}
+
+int fdph_batch_run(fdph_batch_t B, int32_t steps, const double* const* D, double* const* T) {
+    if (!B || !D || !T || steps < 0) return FDPH_E_ARG;
+    for (size_t p = 0; p < B->plans.size(); ++p)
+        if (!D[p] || !T[p]) return FDPH_E_ARG;
+    int rc = batch_check(B, steps);
+    if (rc || steps == 0) return rc;
+    cudaSetDevice(B->device);
+    return B->precision != FDPH_FP64 ? batch_run<float>(B, GRAPH_RUN, steps, D, T)
+                                     : batch_run<double>(B, GRAPH_RUN, steps, D, T);
+}
+
+int fdph_batch_rupture_run(fdph_batch_t B, int32_t steps, double* const* D, double* const* T) {
+    if (!B || !D || !T || steps < 0) return FDPH_E_ARG;
+    for (size_t p = 0; p < B->plans.size(); ++p) {
+        if (!D[p] || !T[p]) return FDPH_E_ARG;
+        if (!B->plans[p]->rupture) {
+            set_error("fdph_rupture_init has not been called on a plan of the batch");
+            return FDPH_E_STATE;
+        }
+    }
+    int rc = batch_check(B, steps);
+    if (rc || steps == 0) return rc;
+    cudaSetDevice(B->device);
+    return B->precision != FDPH_FP64 ? batch_run<float>(B, GRAPH_RUPTURE, steps, (const double* const*)D, T)
+                                     : batch_run<double>(B, GRAPH_RUPTURE, steps, (const double* const*)D, T);
+}
+
+int fdph_batch_synchronize(fdph_batch_t B) {
+    if (!B) return FDPH_E_ARG;
+    FDPH_CUDA(cudaStreamSynchronize(B->stream));
+    for (fdph_plan_t P : B->plans) {
+        FDPH_CUDA(cudaStreamSynchronize(P->stream));
+        int rc = check_device_error(P);
+        if (rc) return rc;
+    }
+    return FDPH_OK;
+}
+
+void fdph_batch_destroy(fdph_batch_t B) { batch_free(B); }
 
 void fdph_destroy(fdph_plan_t P) {
     if (!P) return;

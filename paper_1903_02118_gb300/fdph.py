@@ -66,7 +66,8 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
-           "fdph_predict", "fdph_commit", "fdph_self"]
+           "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run",
+           "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -109,6 +110,12 @@ def lib():
         L.fdph_predict.argtypes = [c_p, c_p]
         L.fdph_commit.argtypes = [c_p, c_p]
         L.fdph_self.argtypes = [c_p, c_p]
+        L.fdph_batch_create.argtypes = [ctypes.POINTER(c_p), ctypes.c_int32, ctypes.POINTER(c_p)]
+        L.fdph_batch_run.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(c_p), ctypes.POINTER(c_p)]
+        L.fdph_batch_rupture_run.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(c_p), ctypes.POINTER(c_p)]
+        L.fdph_batch_synchronize.argtypes = [c_p]
+        L.fdph_batch_destroy.argtypes = [c_p]
+        L.fdph_batch_destroy.restype = None
         L.fdph_autotune.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.fdph_autotune.restype = ctypes.c_int
         L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
@@ -122,7 +129,8 @@ def lib():
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
                      "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc",
                      "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip",
-                     "fdph_predict", "fdph_commit", "fdph_self"):
+                     "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run",
+                     "fdph_batch_rupture_run", "fdph_batch_synchronize"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -184,6 +192,7 @@ class Plan:
         self.handle = h
         self.n = int(xy.shape[0])
         self.M = int(M)
+        self.precision = int(p.precision)
 
     def step(self, D_n, T_n):
         _check(lib().fdph_step(self.handle, _ptr(D_n), _ptr(T_n)))
@@ -301,6 +310,45 @@ def plain_step_noalloc(K, n, W, D_hist, hist_len, step, T, stream=None):
     """fdph_plain_step_noalloc: one plain step from caller-held device buffers, no allocation."""
     s = ctypes.c_void_p(stream) if stream else None
     _check(lib().fdph_plain_step_noalloc(_ptr(K), int(n), int(W), _ptr(D_hist), int(hist_len), int(step), _ptr(T), s))
+
+
+class Batch:
+    """Plans stepped together with one near-field launch per step (fdph_batch_create); the
+    plans must outlive the batch."""
+
+    def __init__(self, plans):
+        L = lib()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(L.fdph_batch_create(arr, len(self.plans), ctypes.byref(h)))
+        self.handle = h
+
+    def _ptrs(self, bufs):
+        if len(bufs) != len(self.plans):
+            raise ValueError("one buffer per plan")
+        return (ctypes.c_void_p * len(bufs))(*[_ptr(b).value for b in bufs])
+
+    def run(self, steps, D, T):
+        """`steps` steps of every plan: D[p], T[p] device buffers of plan p (fdph_batch_run)."""
+        _check(lib().fdph_batch_run(self.handle, int(steps), self._ptrs(D), self._ptrs(T)))
+
+    def rupture_run(self, steps, D, T):
+        _check(lib().fdph_batch_rupture_run(self.handle, int(steps), self._ptrs(D), self._ptrs(T)))
+
+    def synchronize(self):
+        _check(lib().fdph_batch_synchronize(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().fdph_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tree_export(xy, dt, mu=1.0, cs=1.0, **params):

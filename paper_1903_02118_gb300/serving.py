@@ -71,13 +71,17 @@ class Server:
     the budget (the estimate is replaced by the plan's real footprint once it exists)."""
 
     def __init__(self, hbm_budget=64 << 30, max_live=16, chunk=64, device=0, time_scale=1.0, planners=1,
-                 precision=None):
+                 precision=None, batch=True):
         import torch
         self.torch = torch
         self.budget, self.max_live, self.chunk, self.device = hbm_budget, max_live, chunk, device
         self.time_scale = time_scale
         self.planners = planners
         self.precision = precision
+        # batch=True: live scenarios with a full chunk ahead step together, one near-field launch
+        # per step for all of them (fdph_batch_rupture_run); otherwise each on its own stream
+        self.batch = batch
+        self._batch, self._batch_key = None, None
         # each planner builds with its share of the host cores (the builds run at the same time)
         self.host_threads = max(1, (os.cpu_count() or 16) // max(1, planners))
         self.used = 0
@@ -121,6 +125,44 @@ class Server:
         s["plan"].close()
         self.used -= s["foot"]
 
+    def _drop_batch(self):
+        if self._batch is not None:
+            self._batch.close()
+        self._batch, self._batch_key = None, None
+
+    def _advance(self, live):
+        """One chunk for every live scenario; returns the element-steps done."""
+        done = 0
+        together = []
+        if self.batch:
+            groups = {}
+            for s in live:
+                if s["req"].M - s["n"] >= self.chunk:
+                    groups.setdefault(s["plan"].precision, []).append(s)
+            together = max(groups.values(), key=len) if groups else []
+            if len(together) < 2:
+                together = []
+        if together:
+            key = tuple(id(s) for s in together)
+            if key != self._batch_key:
+                self._drop_batch()
+                self._batch = fdph.Batch([s["plan"] for s in together])
+                self._batch_key = key
+            self._batch.rupture_run(self.chunk, [s["D"] for s in together], [s["T"] for s in together])
+            for s in together:
+                s["n"] += self.chunk
+                done += self.chunk * s["req"].N
+        ids = set(id(s) for s in together)
+        for s in live:
+            if id(s) in ids:
+                continue
+            req = s["req"]
+            k = min(self.chunk, req.M - s["n"])
+            s["plan"].rupture_run(k, s["D"], s["T"])
+            s["n"] += k
+            done += k * req.N
+        return done
+
     def serve(self, requests, realtime=True):
         """Run all requests; returns summary metrics.  With realtime=False arrivals are ignored
         (everything waits at t = 0), which gives the closed-batch throughput."""
@@ -153,14 +195,11 @@ class Server:
                 if not live:
                     time.sleep(0.001)
                     continue
-                # every live scenario advances by one chunk of steps, each on its own stream
-                for s in live:
-                    req = s["req"]
-                    k = min(self.chunk, req.M - s["n"])
-                    s["plan"].rupture_run(k, s["D"], s["T"])
-                    s["n"] += k
-                    steps_done += k * req.N
+                # every live scenario advances by one chunk of steps
+                steps_done += self._advance(live)
                 still = []
+                if any(s["n"] >= s["req"].M for s in live):
+                    self._drop_batch()
                 for s in live:
                     if s["n"] >= s["req"].M:
                         s["plan"].synchronize()
@@ -170,6 +209,7 @@ class Server:
                         still.append(s)
                 live = still
         finally:
+            self._drop_batch()
             pool.shutdown(wait=True)
         wall = time.perf_counter() - t0
         lat = np.array([r.t_done - (r.arrival / self.time_scale if realtime else 0.0) for r in requests])

@@ -202,7 +202,8 @@ def run_rupture(args, cfg):
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
-                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0))
+                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
+                     extra_steps=cfg.get("extra_steps", -1))
     plan_s = time.perf_counter() - t0
     st = plan.stats()
     plan.rupture_init(torch.from_numpy(tau0).cuda(), 1.0, 0.6, 0.3, 6.4)
@@ -256,8 +257,59 @@ def run_serving(args):
             "arrivals": "Poisson 8/s", "N_range": [256, 2048], "M": "N / CFL / 2, CFL in {0.25, 0.5}",
             "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, "planners": args.planners, **mix},
             "one_at_a_time_fp64": {"precision": "f64", "max_live": 1, **alone},
+            "stepping_only": batch_vs_streams(fdph, serving),
             "data": "synthetic"}
     print(json.dumps(line))
+
+
+def batch_vs_streams(fdph, serving, count=16, chunk=64, rounds=4):
+    """GPU stepping of `count` resident rupture scenarios (plans built beforehand, N log-uniform
+    in [256, 2048], curved, CFL 1/2, FP32): `rounds` chunks of `chunk` steps as one batch (one
+    near-field launch per step for all) against each scenario's own step graph on its own
+    stream.  Device-side time of the whole chunk round, host clock around synchronisations."""
+    import torch
+    reqs = serving.poisson_requests(count, rate=8.0, seed=9, n_min=256, n_max=2048, cfls=(0.5,))
+    M = chunk * (rounds + 1)
+    plans, bufs, taus = [], [], []
+    for r in reqs:
+        xy, tau0 = r.inputs()
+        p = fdph.Plan(xy, r.cfl, M, r.eps, eta=r.eta, eps_st=r.eps_st, leaf_size=r.leaf, precision=fdph.FP32,
+                      soe_terms=r.soe_terms)
+        t0 = torch.from_numpy(tau0).cuda()
+        D = torch.zeros((chunk, r.N), dtype=torch.float64, device="cuda")
+        plans.append(p)
+        taus.append(t0)
+        bufs.append((D, torch.zeros_like(D)))
+    torch.cuda.synchronize()
+    elements = sum(p.n for p in plans)
+
+    def run(batched):
+        for p, t0 in zip(plans, taus):
+            p.reset()
+            p.rupture_init(t0, 1.0, 0.6, 0.3, 6.4)
+        batch = fdph.Batch(plans) if batched else None
+        for k in range(rounds + 1):          # round 0: graph capture, untimed
+            if k == 1:
+                for p in plans:
+                    p.synchronize()
+                t = time.perf_counter()
+            if batched:
+                batch.rupture_run(chunk, [b[0] for b in bufs], [b[1] for b in bufs])
+            else:
+                for p, b in zip(plans, bufs):
+                    p.rupture_run(chunk, b[0], b[1])
+        for p in plans:
+            p.synchronize()
+        dt = time.perf_counter() - t
+        if batch:
+            batch.close()
+        return elements * chunk * rounds / dt
+
+    out = {"scenarios": count, "elements": elements, "chunk": chunk, "rounds": rounds,
+           "streams_element_steps_per_s": run(False), "batch_element_steps_per_s": run(True)}
+    for p in plans:
+        p.close()
+    return out
 
 
 def main():
@@ -276,6 +328,8 @@ def main():
                     help="admissibility: 0 constant eta (Eq. 8), 1 constant eta^2 dist (Eq. 25, needs --lmin)")
     ap.add_argument("--lmin", type=float, default=None, help="lmin of Eq. 9 / Eq. 25, in element lengths")
     ap.add_argument("--leaf", type=int, default=None, help="largest cluster of an inadmissible leaf")
+    ap.add_argument("--extra-steps", type=int, default=None,
+                    help="n_c: steps of Domain F beyond the source duration (default 10 dx / (c dt))")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--quick", action="store_true",
                     help="plan + roll forward + warm-up + timed steps only (for profiler launch lists)")
@@ -302,6 +356,8 @@ def main():
         cfg["lmin"] = args.lmin
     if args.leaf is not None:
         cfg["leaf"] = args.leaf
+    if args.extra_steps is not None:
+        cfg["extra_steps"] = args.extra_steps
     if args.n:
         cfg["N"] = args.n
     if args.m:
@@ -329,7 +385,8 @@ def main():
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
-                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0))
+                     eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
+                     extra_steps=cfg.get("extra_steps", -1))
     plan_s = time.perf_counter() - t0
     # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
     # profiler commands rely on)
@@ -436,6 +493,7 @@ def main():
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
                        "eta_scheme": cfg.get("eta_scheme", 0), "lmin": cfg.get("lmin", 0.0),
+                       "extra_steps": cfg.get("extra_steps", -1),
                        "first_timed_step": n0 + W, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

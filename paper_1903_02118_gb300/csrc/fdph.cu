@@ -59,7 +59,7 @@ static const int kChunk = 64;      // steps of exact kernel per near-field work 
 static const int kNearConsumers = 4;                       // consumer warps of the near-field kernel
 static const int kNearThreads = 32 * (kNearConsumers + 1);  // + one producer warp
 static const int kNearStageBytes = 16384;                  // one pipeline stage
-static const int kMaxPer = 8;                              // slices per stage at most
+static const int kMaxPer = kChunk;                         // slices per stage at most
 static const int kTaskCache = 48;                          // work items per CTA kept in shared memory
 static_assert(kNearStageBytes >= 32 * 32 * 8, "a stage holds at least one FP64 slice of a 32 x 32 leaf");
 static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls before giving up
@@ -675,7 +675,11 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
             const int nsl = near_slices<T>(tk, v.n);
             const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
             const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
-            const int li = lane < tk.nr ? lane : 0;     // lanes past nr read a valid element, unused
+            // leaves of at most 16 receivers: the warp splits into 32 / span lane groups of span
+            // lanes, each taking its own slices (lane = group * span + receiver)
+            const int span = tk.nr > 16 ? 32 : tk.nr > 8 ? 16 : tk.nr > 4 ? 8 : tk.nr > 2 ? 4 : tk.nr > 1 ? 2 : 1;
+            const int ngrp = 32 / span, grp = lane / span, ri = lane - grp * span;
+            const int li = ri < tk.nr ? ri : 0;         // lanes past nr read a valid element, unused
             R acc = (R)0;
             double accd = 0.0;
             for (int q = 0; q < nst; ++q, ++g) {
@@ -686,7 +690,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                     atomicExch(v.err, 1);
                 }
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
-                for (int kk = warp; kk < cnt; kk += kNearConsumers) {
+                for (int kk = warp * ngrp + grp; kk < cnt; kk += kNearConsumers * ngrp) {
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * 32 * sizeof(R));
                     if (tk.kind)   // static and tail slices: FP64 across slices
                         accd += (double)slice_dot((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
@@ -697,7 +701,9 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
             if (ti + 1 < t1) near_commit<R>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
-            red[par][warp][lane] = lane < tk.nr ? (double)acc + accd : 0.0;
+            double tot = (double)acc + accd;
+            for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            red[par][warp][lane] = lane < tk.nr ? tot : 0.0;
             consumer_barrier();   // also publishes the next item's vectors
             if (warp == 0) {
                 double sum = 0.0;

@@ -122,17 +122,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(cfg, rank):
+def make_workload(cfg, rank, nrhs=1):
+    """Geometry and slip-rate history (M, N); with nrhs > 1 the histories of all right-hand sides
+    (M, nrhs, N), right-hand side r seeded apart from the others."""
     from paper_1903_02118_gb300 import inputs
     k = 1 if cfg["geometry"] == "curved" else 0
     N, M = cfg["N"], cfg["M"]
-    if cfg["geometry"] == "curved":
-        xy = inputs.curved_fault(N, inputs.seed_for(k, inputs.GEOMETRY))
-        D = inputs.gaussian_pulse(N, M, DT, inputs.seed_for(k + 10 * rank, inputs.SLIP))
-    else:
-        xy = inputs.straight_fault(N)
-        D = inputs.gaussian_filtered_history(N, M, inputs.seed_for(k + 10 * rank, inputs.SLIP))
-    return xy, D
+    Ds = []
+    for r in range(nrhs):
+        seed = inputs.seed_for(k + 10 * rank + 100 * r, inputs.SLIP)
+        if cfg["geometry"] == "curved":
+            Ds.append(inputs.gaussian_pulse(N, M, DT, seed))
+        else:
+            Ds.append(inputs.gaussian_filtered_history(N, M, seed))
+    xy = inputs.curved_fault(N, inputs.seed_for(k, inputs.GEOMETRY)) if cfg["geometry"] == "curved" \
+        else inputs.straight_fault(N)
+    return xy, (Ds[0] if nrhs == 1 else np.ascontiguousarray(np.stack(Ds, 1)))
 
 
 def oracle_rows(xy, D, rows):
@@ -328,6 +333,7 @@ def main():
                     help="admissibility: 0 constant eta (Eq. 8), 1 constant eta^2 dist (Eq. 25, needs --lmin)")
     ap.add_argument("--lmin", type=float, default=None, help="lmin of Eq. 9 / Eq. 25, in element lengths")
     ap.add_argument("--leaf", type=int, default=None, help="largest cluster of an inadmissible leaf")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (slip-rate histories) per step")
     ap.add_argument("--extra-steps", type=int, default=None,
                     help="n_c: steps of Domain F beyond the source duration (default 10 dx / (c dt))")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -376,7 +382,9 @@ def main():
     from paper_1903_02118_gb300 import build, fdph
     build.build()
     N, M = cfg["N"], cfg["M"]
-    xy, D = make_workload(cfg, rank)
+    R = args.nrhs
+    xy, D = make_workload(cfg, rank, R)
+    D1 = D if R == 1 else D[:, 0]          # right-hand side 0 (accuracy check)
     # the plan runs on this (non-default) torch stream so that events recorded on it bracket
     # the library's kernels
     stream = torch.cuda.Stream()
@@ -386,7 +394,7 @@ def main():
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
                      eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
-                     extra_steps=cfg.get("extra_steps", -1))
+                     extra_steps=cfg.get("extra_steps", -1), nrhs=R)
     plan_s = time.perf_counter() - t0
     # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
     # profiler commands rely on)
@@ -438,7 +446,7 @@ def main():
         torch.cuda.synchronize()
     replicas.barrier(world)
     ms = replicas.max_over_ranks(s0.elapsed_time(s1), world)
-    value = world * N * K / (ms * 1e-3)
+    value = world * N * R * K / (ms * 1e-3)
 
     # per-kernel times (CUDA events inside the library, same stream) for the roofline
     roll_to(n0 + W)
@@ -464,27 +472,27 @@ def main():
     # step's D_n in and T_n out inside the timed region
     roll_to(n0 + W)
     hD = torch.from_numpy(np.ascontiguousarray(D[n0 + W:n0 + W + K])).pin_memory()
-    hT = torch.empty((K, N), dtype=torch.float64).pin_memory()
+    hT = torch.empty(tuple(hD.shape), dtype=torch.float64).pin_memory()
     replicas.barrier(world)
     te0 = time.perf_counter()
     plan.run_host(hD, hT)
     te = replicas.max_over_ranks(time.perf_counter() - te0, world)
     if not np.array_equal(hT.numpy(), T_full[n0 + W:n0 + W + K]):
         raise SystemExit("fdph_run_host result differs from fdph_run")
-    e2e = {"value": world * N * K / te, "unit": "element-steps/s", "h2d_bytes_per_step": N * 8,
-           "d2h_bytes_per_step": N * 8, "api": "fdph_run_host (per-step copies, pipelined)"}
+    e2e = {"value": world * N * R * K / te, "unit": "element-steps/s", "h2d_bytes_per_step": N * R * 8,
+           "d2h_bytes_per_step": N * R * 8, "api": "fdph_run_host (per-step copies, pipelined)"}
     # the same through the synchronous one-step call (a host round trip per step)
     roll_to(n0 + W)
     import ctypes
     L = fdph.lib()
-    h1 = torch.empty((N,), dtype=torch.float64).pin_memory()
+    h1 = torch.empty((R * N,), dtype=torch.float64).pin_memory()
     te0 = time.perf_counter()
     for s in range(K):
         rc = L.fdph_step_host(plan.handle, ctypes.c_void_p(hD[s].data_ptr()), ctypes.c_void_p(h1.data_ptr()))
         if rc:
             raise SystemExit("fdph_step_host failed: %d" % rc)
     te1 = replicas.max_over_ranks(time.perf_counter() - te0, world)
-    e2e["step_host_value"] = world * N * K / te1
+    e2e["step_host_value"] = world * N * R * K / te1
 
     line = {"metric": "element-steps/s", "value": value, "unit": "element-steps/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -493,7 +501,7 @@ def main():
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
                        "eta_scheme": cfg.get("eta_scheme", 0), "lmin": cfg.get("lmin", 0.0),
-                       "extra_steps": cfg.get("extra_steps", -1),
+                       "extra_steps": cfg.get("extra_steps", -1), "nrhs": R,
                        "first_timed_step": n0 + W, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -506,13 +514,14 @@ def main():
                      "max_window": st["max_window"], "arena_bytes": st["arena_bytes"]}}
     if rank == 0 and not args.no_cpu:
         rows = ((np.arange(32) + 0.5) * N / 32).astype(int)
-        T_or = np.concatenate([oracle_rows(xy, D, rows[c:c + 4])[1] for c in range(0, rows.size, 4)], axis=1)
-        line["rel_err_vs_plain_fp64"] = float(np.linalg.norm(T_full[:, rows] - T_or) / np.linalg.norm(T_or))
+        T_or = np.concatenate([oracle_rows(xy, D1, rows[c:c + 4])[1] for c in range(0, rows.size, 4)], axis=1)
+        T1 = T_full if R == 1 else T_full[:, 0]
+        line["rel_err_vs_plain_fp64"] = float(np.linalg.norm(T1[:, rows] - T_or) / np.linalg.norm(T_or))
         line["rel_err_note"] = ("relative L2 over all %d steps at %d evenly spaced receivers vs the CPU FP64 "
                                 "plain march (Eq. 4)" % (M, rows.size))
-        Kr, _ = oracle_rows(xy, D, rows[:2])
+        Kr, _ = oracle_rows(xy, D1, rows[:2])
         cpu_steps = min(M, 640)
-        rate, secs = oracle_step_rate(Kr, D, cpu_steps, M)
+        rate, secs = oracle_step_rate(Kr, D1, cpu_steps, M)
         line["cpu_baseline"] = {"value": rate, "unit": "element-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": "plain FP64 ST-BIEM step (Eq. 4, stored kernel rows) for %d receivers "
                                           "x %d steps at n ~ M; %.1f s" % (Kr.shape[1], cpu_steps, secs)}

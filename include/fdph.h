@@ -112,6 +112,13 @@ typedef struct fdph_params {
                              sqrt(eta lmin dist) (eta = eta_0, lmin > 0 required), which bounds the
                              travel-time error of the plane-wave approximation by eta lmin / (4 c)
                              (Eq. 26) at a cost that grows like N^(3/2) */
+    int32_t nrhs;         /* right-hand sides: independent slip-rate histories stepped together on
+                             the one operator (1..16; 0 => 1).  D_n and T_n of fdph_step,
+                             fdph_run, fdph_step_host and fdph_run_host are then nrhs rows of n
+                             (RHS-major: row r, element i at r * n + i) per step, and the state is
+                             kept per RHS; the near-field coefficients are streamed once per step
+                             and re-read from L2 for the other RHS.  Rupture, fdph_predict /
+                             fdph_commit and batches take nrhs = 1 (FDPH_E_ARG otherwise) */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */

@@ -82,11 +82,12 @@ struct __align__(16) NearTask {
     long long off;       // element offset of the item's first slice (tensor, or aux for kind 1)
     int item, k0, k1, kind, nr, ns, sl, s0, W, vstate;
     int scen;            // plan of the item in a batch (0 otherwise)
-    int pad;
+    int rhs;             // right-hand side of the item
 };
 static_assert(sizeof(NearTask) == 64, "one work item is four 16-byte loads");
 
 static const int kMaxSoe = 16;
+static const int kMaxRhs = 16;   // right-hand sides of one plan at most
 
 template <class T>
 struct StepArgs {
@@ -151,6 +152,10 @@ struct StepArgs {
     double* vstate;           // inadmissible leaves: [soe][ns] per leaf
     const double* tail;       // inadmissible leaves: [soe][ns][nr] coefficients per leaf (FP64: the
                               // fitted coefficients partly cancel, so they are not rounded to FP32)
+    // right-hand sides: every time-stepping state array above is [nrhs][...] with these strides
+    // (elements); the caller's rows D_n, T_n are [nrhs][N] (io_stride = nrhs N per step)
+    int nrhs;
+    long long rs_D, rs_C, rs_ring, rs_zring, rs_dhat, rs_fval, rs_ustate, rs_vstate, rs_partial;
 };
 
 // ring slot of step a (a may be negative; |a| < 2^31)
@@ -172,6 +177,29 @@ __device__ __forceinline__ long long io_offset(const StepArgs<T>& a, int n) {
     return (long long)(a.io_ring > 0 ? k % a.io_ring : k) * a.io_stride;
 }
 
+// the arguments of right-hand side r (grid y of the per-step kernels)
+template <class T>
+__device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
+    StepArgs<T> a = a0;
+    if (r) {
+        const long long rN = (long long)r * a0.N;
+        if (a0.D_in) a.D_in = a0.D_in + rN;
+        if (a0.T_out) a.T_out = a0.T_out + rN;
+        a.Dring = a0.Dring + r * a0.rs_D;
+        a.Cring = a0.Cring + r * a0.rs_C;
+        a.C = a0.C + rN;
+        a.Ccomp = a0.Ccomp + rN;
+        a.ring = a0.ring + r * a0.rs_ring;
+        a.zring = a0.zring + r * a0.rs_zring;
+        a.dhat = a0.dhat + r * a0.rs_dhat;
+        a.fval = a0.fval + r * a0.rs_fval;
+        if (a0.ustate) a.ustate = a0.ustate + r * a0.rs_ustate;
+        if (a0.vstate) a.vstate = a0.vstate + r * a0.rs_vstate;
+        a.partial = a0.partial + r * a0.rs_partial;
+    }
+    return a;
+}
+
 __global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
 
 __global__ void set_step_kernel(int* n_dev, int v) {
@@ -180,7 +208,8 @@ __global__ void set_step_kernel(int* n_dev, int v) {
 }
 
 template <class T>
-__global__ void push_kernel(StepArgs<T> a) {
+__global__ void push_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.N) return;
@@ -200,7 +229,8 @@ __global__ void push_kernel(StepArgs<T> a) {
 }
 
 template <class T>
-__global__ void fir_kernel(StepArgs<T> a) {
+__global__ void fir_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= a.n_fir) return;
@@ -241,7 +271,8 @@ __device__ __forceinline__ double source_value(const StepArgs<T>& a, const SbDev
 // cover the rank index l, so a run writes its ring slot row [slot][0, rank) in one coalesced pass.
 // One writer per (slot, l): the runs of a block have distinct delays.
 template <class T>
-__global__ void scatter_kernel(StepArgs<T> a) {
+__global__ void scatter_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -285,7 +316,8 @@ __global__ void scatter_kernel(StepArgs<T> a) {
 
 // one warp per (transient block, rank index)
 template <class T>
-__global__ void trconv_kernel(StepArgs<T> a) {
+__global__ void trconv_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -349,6 +381,12 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
     return p;
 }
 
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ __forceinline__ bool mbar_wait_limit(unsigned long long* bar, unsigned phase, long long limit) {
     const unsigned a = smem_u32(bar);
     for (long long it = 0; it < limit; ++it) {
@@ -405,7 +443,8 @@ struct NearView {
     const void* stat;
     double* partial;
     int* err;
-    int N, WD, WC, n;
+    int N, WD, WC, n, nrhs;
+    long long rs_D, rs_C, rs_vstate, rs_partial;
 };
 
 template <class T>
@@ -423,6 +462,22 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     v.WD = a.WD;
     v.WC = a.WC;
     v.n = step_index(a);
+    v.nrhs = a.nrhs;
+    v.rs_D = a.rs_D;
+    v.rs_C = a.rs_C;
+    v.rs_vstate = a.rs_vstate;
+    v.rs_partial = a.rs_partial;
+    return v;
+}
+
+// the view of right-hand side r
+__device__ __forceinline__ NearView near_rhs(NearView v, int r) {
+    if (r) {
+        v.Dring += r * v.rs_D;
+        v.Cring += r * v.rs_C;
+        if (v.vstate) v.vstate += r * v.rs_vstate;
+        v.partial += r * v.rs_partial;
+    }
     return v;
 }
 
@@ -600,7 +655,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
-    auto view = [&](const NearTask& tk) -> NearView { return kBatch ? near_view(scen[tk.scen]) : v0; };
+    auto view = [&](const NearTask& tk) -> NearView { return near_rhs(kBatch ? near_view(scen[tk.scen]) : v0, tk.rhs); };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
     unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
@@ -623,7 +678,9 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
     if (warp == kNearConsumers) {
         // ---------------- producer (one thread)
         if (lane == 0) {
-            const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
+            // coefficients are read once per step: evict-first, except for the passes of the right-hand
+            // sides before the last, whose re-reads follow at once on this CTA (evict-last)
+            const unsigned long long first = l2_evict_first_policy(), last = l2_evict_last_policy();
             for (int ti = t0; ti < t1; ++ti) {
                 const NearTask tk = task(ti);
                 const NearView v = view(tk);
@@ -644,7 +701,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                     fence_proxy_async();
                     mbar_expect_tx(&full[s], bytes);
                     bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
-                                  policy);
+                                  tk.rhs + 1 < v.nrhs ? last : first);
                 }
             }
         }
@@ -727,7 +784,8 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
 // f_{., i} . Tbar'[n - dm_i] goes to the receiver's CSR slot.  A block kept exact with F = I
 // reads one ring entry per receiver (2^lg = 1).
 template <class T>
-__global__ void far_eval_kernel(StepArgs<T> a) {
+__global__ void far_eval_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -768,7 +826,8 @@ __global__ void far_eval_kernel(StepArgs<T> a) {
 
 // one warp per receiver: sum of its far entries and near-field partials, fixed order
 template <class T>
-__global__ void gather_kernel(StepArgs<T> a) {
+__global__ void gather_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int n = step_index(a);
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -946,6 +1005,7 @@ struct fdph_plan_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int N = 0, M = 0, n = 0, WD = 1, WC = 1;
+    int nrhs = 1;             // right-hand sides (slip-rate histories) stepped together
     double dt = 0;
     HostPlan hp;
     fdph_stats st;
@@ -1098,6 +1158,16 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.trcoef = P->trcoef;
     a.phi = P->hp.interp ? P->phi : nullptr;
     a.vstate = P->vstate;
+    a.nrhs = P->nrhs;
+    a.rs_D = (long long)P->WD * P->N;
+    a.rs_C = (long long)P->WC * P->N;
+    a.rs_ring = std::max<long long>(P->hp.ring_len, 1);
+    a.rs_zring = std::max<long long>(P->hp.zring_len, 1);
+    a.rs_dhat = std::max<long long>(P->hp.dhat_len, 1);
+    a.rs_fval = std::max<long long>((long long)P->hp.e_pos.size(), 1);
+    a.rs_ustate = std::max<long long>(P->hp.ustate_len, 1);
+    a.rs_vstate = std::max<long long>(P->hp.vstate_len, 1);
+    a.rs_partial = std::max<long long>((long long)P->partial_cap, 1);
     return a;
 }
 
@@ -1138,7 +1208,7 @@ static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
 
 template <class T>
 static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
-    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
+    { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }
     if (!P->prof && P->side[0]) {
         // Within a step, FIR + scatter (writes ring slots n + delay >= n + 1), the transient
         // convolution + Eq. 39 (read slots <= n - min dm, completed by earlier steps; causality
@@ -1146,30 +1216,30 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         cudaEventRecord(P->ev_fork, s);
         cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
         cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
-        if (a.n_fir) fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, P->side[0]>>>(a);
-        if (a.n_sct) scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, P->side[0]>>>(a);
-        if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, P->side[1]>>>(a);
-        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, P->side[1]>>>(a);
+        if (a.n_fir) fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+        if (a.n_sct) scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+        if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
         if (a.n_cta) launch_near<T>(P, a, s);
         cudaEventRecord(P->ev_join[0], P->side[0]);
         cudaEventRecord(P->ev_join[1], P->side[1]);
         cudaStreamWaitEvent(s, P->ev_join[0], 0);
         cudaStreamWaitEvent(s, P->ev_join[1], 0);
-        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
         return;
     }
     // serial order (per-kernel timing)
-    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
-    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
-    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
+    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a); }
+    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
         launch_near<T>(P, a, s);
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
-        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
 
@@ -1205,7 +1275,7 @@ static int step_graph(fdph_plan_t P, int kind, const double* D, double* Tout, in
         }
     StepArgs<T> a = make_args<T>(P, kind == GRAPH_RUPTURE ? nullptr : D, Tout);
     a.n_dev = P->n_dev;
-    a.io_stride = P->N;
+    a.io_stride = (long long)P->N * P->nrhs;
     a.io_ring = io_ring;
     cudaGraph_t g = nullptr;
     FDPH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1257,7 +1327,7 @@ static int run_graph(fdph_plan_t P, int steps, const double* D, double* Tout) {
 template <class T>
 static int run_host(fdph_plan_t P, int steps, const double* D_host, double* T_host) {
     const int S = fdph_plan_s::kIoSlots;
-    const size_t row = (size_t)P->N;
+    const size_t row = (size_t)P->N * P->nrhs;
     if (!P->io_D) {
         int rc;
         if ((rc = dalloc(P, &P->io_D, S * row)) || (rc = dalloc(P, &P->io_T, S * row))) return rc;
@@ -1354,16 +1424,16 @@ static int step_impl(fdph_plan_t P, const double* D, double* T_) {
 template <class T>
 static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
     a.D_in = nullptr;
-    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }          // D_n = 0
-    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a); }
+    { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }          // D_n = 0
+    if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
         launch_near<T>(P, a, s);
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
-        gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
 
@@ -1372,9 +1442,9 @@ static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
 template <class T>
 static void enqueue_commit(fdph_plan_t P, StepArgs<T> a, const double* D, cudaStream_t s) {
     a.D_in = D;
-    { ProfScope ps(P, 0); push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a); }
-    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, s>>>(a); }
-    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, s>>>(a); }
+    { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
+    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a); }
 }
 
 // One rupture step (Sec. 6.2): predict, solve the friction law element by element, commit D_n.
@@ -1451,13 +1521,16 @@ static void near_tasks(fdph_plan_t P, int scen, std::vector<NearTask>& tasks, st
         t.vstate = (int)L.vstate;
         t.scen = scen;
         tasks.push_back(t);
-        cost.push_back((double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0);
+        // the right-hand sides of an item run back to back on one CTA (deal_tasks), their
+        // re-reads of the coefficients hitting L2
+        cost.push_back(((double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0) *
+                       std::max(P->nrhs, 1));
     }
 }
 
 // Work items dealt largest first to the least-loaded of ncta CTAs; per-CTA task lists in CTA
 // order and their offsets.
-static void deal_tasks(const std::vector<NearTask>& all, const std::vector<double>& cost, int ncta,
+static void deal_tasks(const std::vector<NearTask>& all, const std::vector<double>& cost, int ncta, int nrhs,
                        std::vector<NearTask>& tasks, std::vector<int>& cptr) {
     const int ni = (int)all.size();
     std::vector<int> order(ni);
@@ -1479,7 +1552,12 @@ static void deal_tasks(const std::vector<NearTask>& all, const std::vector<doubl
     tasks.clear();
     cptr.assign(1, 0);
     for (int c = 0; c < ncta; ++c) {
-        for (int q : own[c]) tasks.push_back(all[q]);
+        for (int q : own[c])
+            for (int r = 0; r < nrhs; ++r) {
+                NearTask t = all[q];
+                t.rhs = r;
+                tasks.push_back(t);
+            }
         cptr.push_back((int)tasks.size());
     }
 }
@@ -1508,7 +1586,7 @@ static int build_schedule(fdph_plan_t P) {
     near_tasks<T, H>(P, 0, all, cost);
     const int ni = (int)all.size();
     const int ncta = std::max(1, std::min(ni, ncta_max));
-    deal_tasks(all, cost, ncta, tasks, cptr);
+    deal_tasks(all, cost, ncta, P->nrhs, tasks, cptr);
     P->n_cta = ni ? ncta : 0;
     P->sched_version += 1;
     if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
@@ -1806,9 +1884,9 @@ static int set_chunk(fdph_plan_t P, int chunk) {
     }
     const size_t need = hp.items.size() * 32;
     if (need > P->partial_cap) {
-        int rc = dalloc(P, &P->partial, need);
+        int rc = dalloc(P, &P->partial, need * P->nrhs);
         if (rc) return rc;
-        FDPH_CUDA(cudaMemsetAsync(P->partial, 0, need * sizeof(double), P->stream));
+        FDPH_CUDA(cudaMemsetAsync(P->partial, 0, need * P->nrhs * sizeof(double), P->stream));
         P->partial_cap = need;
     }
     int rc = build_schedule<T, H>(P);
@@ -1900,21 +1978,21 @@ static void enqueue_batch_step(fdph_batch_t B, int kind, const std::vector<StepA
         cudaStream_t s = P->stream;
         cudaStreamWaitEvent(s, B->ev_start, 0);
         if (kind == GRAPH_RUN) {
-            push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a);
+            push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a);
             cudaEventRecord(P->ev_fork, s);
             cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
             cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
-            if (a.n_fir) fir_kernel<T><<<blocks(a.n_fir, 128), 128, 0, P->side[0]>>>(a);
-            if (a.n_sct) scatter_kernel<T><<<blocks((long long)a.n_sct * 32, 128), 128, 0, P->side[0]>>>(a);
-            if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, P->side[1]>>>(a);
-            if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, P->side[1]>>>(a);
+            if (a.n_fir) fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+            if (a.n_sct) scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+            if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
+            if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
             cudaEventRecord(P->ev_join[0], P->side[0]);
             cudaEventRecord(P->ev_join[1], P->side[1]);
         } else {   // rupture prediction: zero row, transient, Eq. 39 evaluation
             a.D_in = nullptr;
-            push_kernel<T><<<blocks(a.N, 256), 256, 0, s>>>(a);
-            if (a.n_tr) trconv_kernel<T><<<blocks((long long)a.n_tr * 32, 128), 128, 0, s>>>(a);
-            if (a.n_evt) far_eval_kernel<T><<<blocks((long long)a.n_evt * 32, 128), 128, 0, s>>>(a);
+            push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a);
+            if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a);
+            if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
         }
         cudaEventRecord(B->ev_ready[p], s);
         cudaStreamWaitEvent(bs, B->ev_ready[p], 0);
@@ -1929,10 +2007,10 @@ static void enqueue_batch_step(fdph_batch_t B, int kind, const std::vector<StepA
         if (kind == GRAPH_RUN) {
             cudaStreamWaitEvent(s, P->ev_join[0], 0);
             cudaStreamWaitEvent(s, P->ev_join[1], 0);
-            gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+            gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
         } else {
             a.D_in = nullptr;
-            gather_kernel<T><<<blocks((long long)a.N * 32, 128), 128, 0, s>>>(a);
+            gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
             friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D[p], a.T_out, a.n_dev);
             enqueue_commit<T>(P, a, D[p], s);
         }
@@ -2031,7 +2109,7 @@ static int batch_schedule(fdph_batch_t B) {
     for (size_t p = 0; p < B->plans.size(); ++p) near_tasks<T, H>(B->plans[p], (int)p, all, cost);
     const int ni = (int)all.size();
     const int ncta = std::max(1, std::min(ni, ncta_max));
-    deal_tasks(all, cost, ncta, tasks, cptr);
+    deal_tasks(all, cost, ncta, 1, tasks, cptr);
     B->n_cta = ni ? ncta : 0;
     FDPH_CUDA(cudaMalloc(&B->tasks, std::max<size_t>(1, tasks.size()) * sizeof(NearTask)));
     FDPH_CUDA(cudaMalloc(&B->cta_ptr, cptr.size() * sizeof(int)));
@@ -2097,6 +2175,7 @@ void fdph_default_params(fdph_params* p) {
     p->precision = FDPH_FP64;
     p->device = 0;
     p->cuda_stream = nullptr;
+    p->nrhs = 1;
 }
 
 const char* fdph_strerror(int s) {
@@ -2122,10 +2201,11 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
     }
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
               (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
+              p->nrhs < 0 || p->nrhs > kMaxRhs ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
         set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
-                  "lmin > 0), precision FP64, FP32 or FP16, "
+                  "lmin > 0), nrhs in [0, 16], precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -2227,6 +2307,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if (!P) return FDPH_E_OOM;
     P->device = p.device;
     P->precision = p.precision;
+    P->nrhs = std::max(p.nrhs, 1);
     P->N = geometry->n;
     P->M = M;
     P->dt = dt;
@@ -2345,9 +2426,10 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     P->WD = std::max(std::max(hp.max_W + (hp.soe > 0 ? 1 : 0), hp.max_taps), 1);
     P->WC = hp.max_W + 1;
     size_t sb = 0;
-    auto st = [&](double** p, size_t cnt) {
-        sb += std::max<size_t>(cnt, 1) * 8;
-        return dalloc(P, p, cnt);
+    auto st = [&](double** p, size_t cnt) {   // one copy per right-hand side
+        const size_t c = std::max<size_t>(cnt, 1) * P->nrhs;
+        sb += c * 8;
+        return dalloc(P, p, c);
     };
     if ((rc = st(&P->Dring, (size_t)P->WD * P->N)) || (rc = st(&P->Cring, (size_t)P->WC * P->N)) ||
         (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
@@ -2356,7 +2438,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
         return fail(rc);
     P->state_bytes = sb;
-    P->partial_cap = hp.items.size() * 32;
+    P->partial_cap = std::max<size_t>(hp.items.size() * 32, 1);
     if ((rc = fdph_reset(P))) return fail(rc);
     fill_stats(P);
     P->st.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2372,9 +2454,10 @@ int fdph_reset(fdph_plan_t P) {
                       P->ustate, P->vstate};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.dhat_len,
-                    P->hp.items.size() * 32, (size_t)P->hp.ustate_len, (size_t)P->hp.vstate_len};
-    for (int q = 0; q < 10; ++q)
-        if (bufs[q] && cnt[q]) FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, cnt[q] * sizeof(double), P->stream));
+                    P->partial_cap, (size_t)P->hp.ustate_len, (size_t)P->hp.vstate_len};
+    for (int q = 0; q < 10; ++q)   // every right-hand side: [nrhs][max(count, 1)]
+        if (bufs[q])
+            FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, std::max<size_t>(cnt[q], 1) * P->nrhs * sizeof(double), P->stream));
     if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->n = 0;
@@ -2401,7 +2484,8 @@ int fdph_run(fdph_plan_t P, int32_t steps, const double* D, double* T) {
     if (steps >= 8 && !P->prof)   // launch-bound steps: replay a captured graph of one step
         return P->precision != FDPH_FP64 ? run_graph<float>(P, steps, D, T) : run_graph<double>(P, steps, D, T);
     for (int s = 0; s < steps; ++s) {
-        int rc = step_impl(P, D + (size_t)s * P->N, T + (size_t)s * P->N);
+        const size_t row = (size_t)P->N * P->nrhs;
+        int rc = step_impl(P, D + s * row, T + s * row);
         if (rc) return rc;
     }
     return FDPH_OK;
@@ -2417,12 +2501,13 @@ int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_
     if (steps == 0) return FDPH_OK;
     int rc;
     if (P->prof) {   // per-kernel timing: plain launches, one staging row
-        if (!P->dD && ((rc = dalloc(P, &P->dD, P->N)) || (rc = dalloc(P, &P->dT, P->N)))) return rc;
+        const size_t row = (size_t)P->N * P->nrhs;
+        if (!P->dD && ((rc = dalloc(P, &P->dD, row)) || (rc = dalloc(P, &P->dT, row)))) return rc;
         for (int k = 0; k < steps; ++k) {
-            FDPH_CUDA(cudaMemcpyAsync(P->dD, D_host + (size_t)k * P->N, P->N * sizeof(double),
+            FDPH_CUDA(cudaMemcpyAsync(P->dD, D_host + k * row, row * sizeof(double),
                                       cudaMemcpyHostToDevice, P->stream));
             if ((rc = step_impl(P, P->dD, P->dT))) return rc;
-            FDPH_CUDA(cudaMemcpyAsync(T_host + (size_t)k * P->N, P->dT, P->N * sizeof(double),
+            FDPH_CUDA(cudaMemcpyAsync(T_host + k * row, P->dT, row * sizeof(double),
                                       cudaMemcpyDeviceToHost, P->stream));
         }
         FDPH_CUDA(cudaStreamSynchronize(P->stream));
@@ -2437,14 +2522,15 @@ int fdph_run_host(fdph_plan_t P, int32_t steps, const double* D_host, double* T_
 int fdph_step_host(fdph_plan_t P, const double* D_n_host, double* T_n_host) {
     if (!P || !D_n_host || !T_n_host) return FDPH_E_ARG;
     if (P->predicted) return pending_commit(P);
+    const size_t row = (size_t)P->N * P->nrhs;
     if (!P->dD) {
         int rc;
-        if ((rc = dalloc(P, &P->dD, P->N)) || (rc = dalloc(P, &P->dT, P->N))) return rc;
+        if ((rc = dalloc(P, &P->dD, row)) || (rc = dalloc(P, &P->dT, row))) return rc;
     }
-    FDPH_CUDA(cudaMemcpyAsync(P->dD, D_n_host, P->N * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    FDPH_CUDA(cudaMemcpyAsync(P->dD, D_n_host, row * sizeof(double), cudaMemcpyHostToDevice, P->stream));
     int rc = fdph_step(P, P->dD, P->dT);
     if (rc) return rc;
-    FDPH_CUDA(cudaMemcpyAsync(T_n_host, P->dT, P->N * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    FDPH_CUDA(cudaMemcpyAsync(T_n_host, P->dT, row * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     return check_device_error(P);
 }
@@ -2563,6 +2649,7 @@ int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
                     (size_t)P->hp.vstate_len};
+    for (size_t& c : cnt) c = c ? c * P->nrhs : 0;   // [nrhs][count] (a zero count stays empty)
     size_t need = sizeof(int32_t) * 2;
     for (int q = 0; q < 8; ++q) need += cnt[q] * sizeof(double);
     if (!buf) {
@@ -2606,6 +2693,7 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
                     (size_t)P->hp.vstate_len};
+    for (size_t& c : cnt) c = c ? c * P->nrhs : 0;   // [nrhs][count] (a zero count stays empty)
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     for (int q = 0; q < 8; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice, P->stream));
@@ -2648,6 +2736,10 @@ int fdph_rupture_init(fdph_plan_t P, const fdph_friction* f) {
         return FDPH_E_ARG;
     }
     if (P->predicted) return pending_commit(P);
+    if (P->nrhs != 1) {
+        set_error("fdph_rupture_init: dynamic rupture takes plans of one right-hand side (nrhs = 1)");
+        return FDPH_E_ARG;
+    }
     std::vector<double> k0;
     int rc0 = self_coefficients(P, k0);
     if (rc0) return rc0;
@@ -2719,6 +2811,10 @@ int fdph_rupture_slip(fdph_plan_t P, double* slip) {
 
 int fdph_predict(fdph_plan_t P, double* T_pred) {
     if (!P || !T_pred) return FDPH_E_ARG;
+    if (P->nrhs != 1) {
+        set_error("this call takes plans of one right-hand side (nrhs = 1)");
+        return FDPH_E_ARG;
+    }
     if (P->predicted) return pending_commit(P);
     if (P->n >= P->M) {
         set_error("the plan has already taken M steps");
@@ -2731,6 +2827,10 @@ int fdph_predict(fdph_plan_t P, double* T_pred) {
 
 int fdph_commit(fdph_plan_t P, const double* D_n) {
     if (!P || !D_n) return FDPH_E_ARG;
+    if (P->nrhs != 1) {
+        set_error("this call takes plans of one right-hand side (nrhs = 1)");
+        return FDPH_E_ARG;
+    }
     if (!P->predicted) {
         set_error("fdph_commit without a preceding fdph_predict of this step");
         return FDPH_E_STATE;
@@ -2790,6 +2890,10 @@ int fdph_batch_create(const fdph_plan_t* plans, int32_t count, fdph_batch_t* out
             return FDPH_E_ARG;
         }
         if (plans[p]->predicted) return pending_commit(plans[p]);
+        if (plans[p]->nrhs != 1) {
+            set_error("fdph_batch_create: batches take plans of one right-hand side (nrhs = 1)");
+            return FDPH_E_ARG;
+        }
     }
     fdph_batch_t B = new fdph_batch_s;
     B->device = plans[0]->device;

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
                 ("leaf_size", ctypes.c_int32), ("extra_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32)]
 
 
 class Friction(ctypes.Structure):
@@ -160,11 +160,12 @@ def default_params():
 
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
-                device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None):
+                device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None,
+                nrhs=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
-                 ("host_threads", host_threads), ("eta_scheme", eta_scheme),
+                 ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)
@@ -193,6 +194,7 @@ class Plan:
         self.n = int(xy.shape[0])
         self.M = int(M)
         self.precision = int(p.precision)
+        self.nrhs = max(int(p.nrhs), 1)
 
     def step(self, D_n, T_n):
         _check(lib().fdph_step(self.handle, _ptr(D_n), _ptr(T_n)))
@@ -203,7 +205,7 @@ class Plan:
     def step_host(self, D_n, T_n=None):
         D_n = np.ascontiguousarray(D_n, dtype=np.float64)
         if T_n is None:
-            T_n = np.empty(self.n)
+            T_n = np.empty(self.n * self.nrhs)
         _check(lib().fdph_step_host(self.handle, ctypes.c_void_p(D_n.ctypes.data), ctypes.c_void_p(T_n.ctypes.data)))
         return T_n
 

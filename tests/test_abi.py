@@ -44,6 +44,8 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), -1.0, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_ARG
     p = fdph.make_params(leaf_size=64)
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
+    p = fdph.make_params(nrhs=17)
+    assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
     bad = xy.copy()
     bad[3, 2] = np.nan
     gb = fdph.Geometry(8, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -53,6 +55,14 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_predict(None, None) == fdph.E_ARG
     assert L.fdph_commit(None, None) == fdph.E_ARG
     assert L.fdph_self(None, None) == fdph.E_ARG
+    out = ctypes.c_void_p()
+    assert L.fdph_batch_create(None, 0, ctypes.byref(out)) == fdph.E_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.fdph_batch_create(arr, 1, ctypes.byref(out)) == fdph.E_ARG and not out.value
+    assert L.fdph_batch_run(None, 1, None, None) == fdph.E_ARG
+    assert L.fdph_batch_rupture_run(None, 1, None, None) == fdph.E_ARG
+    assert L.fdph_batch_synchronize(None) == fdph.E_ARG
+    L.fdph_batch_destroy(None)
     assert L.fdph_strerror(fdph.E_CAUSALITY)
 
 

@@ -396,3 +396,43 @@ def test_predict_commit_split_equals_step_and_rupture():
     plan.synchronize()
     assert (Dr > 0).sum().item() > 0.2 * Dr.numel()
     assert _rel(Du.cpu().numpy(), Dr.cpu().numpy()) < 1e-10 and _rel(Tu.cpu().numpy(), Tr.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [fdph.FP64, fdph.FP32, fdph.FP16])
+def test_multiple_right_hand_sides_equal_single_rhs_plans(prec):
+    """nrhs = 3 slip-rate histories on one operator: every RHS equals the single-RHS plan on that
+    history bit for bit, through graph replay, plain steps, host buffers and a saved state."""
+    _need_gpu()
+    N, M, R = 170, 100, 3
+    xy = _geom("curved", N)
+    kw = dict(eta=0.5, eps_st=1e-4, leaf_size=16, soe_terms=16, precision=prec)
+    Ds = [inputs.gaussian_filtered_history(N, M, 30 + r) for r in range(R)]
+    single = fdph.Plan(xy, 0.5, M, 1e-5, **kw)
+    ref = []
+    for D in Ds:
+        single.reset()
+        ref.append(_run(single, D))
+    ref = np.stack(ref, 1)                                  # (M, R, N)
+    plan = fdph.Plan(xy, 0.5, M, 1e-5, nrhs=R, **kw)
+    Dm = np.ascontiguousarray(np.stack(Ds, 1))
+    Dd = torch.from_numpy(Dm).cuda()
+    Td = torch.empty_like(Dd)
+    torch.cuda.synchronize()
+    plan.run(M, Dd, Td)                                     # graph replay
+    plan.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), ref)
+    plan.reset()
+    Td.zero_()
+    torch.cuda.synchronize()
+    for n in range(6):                                      # plain launches
+        plan.step(Dd[n], Td[n])
+    plan.synchronize()
+    buf = plan.save_state()
+    plan.run(M - 6, Dd[6:], Td[6:])
+    plan.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), ref)
+    plan.load_state(buf)                                    # continue again from step 6
+    T2 = plan.run_host(Dm[6:])
+    assert np.array_equal(T2, ref[6:])
+    with pytest.raises(fdph.FdphError):
+        plan.predict(Td[0])                                 # single-RHS calls refuse nrhs > 1

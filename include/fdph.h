@@ -218,12 +218,12 @@ int fdph_predict(fdph_plan_t plan, double* T_pred);
 int fdph_commit(fdph_plan_t plan, const double* D_n);
 
 /* Batches (no counterpart in the paper; the serving pattern of independent scenarios): plans
- * that share the device and the precision, stepped together.  Each step of a batch runs every
- * plan's push, FIR / scatter (Eqs. 32, 42) and transient / Eq. 39 kernels on that plan's streams,
- * then ONE persistent near-field launch (App. E) whose CTAs take the work items of all plans,
- * dealt largest first over the SMs, then every plan's gather; the step is captured once per
- * (kind, buffers) as a CUDA graph and replayed.  Each plan keeps its own state and step index,
- * and its results are bit-identical to stepping it alone.
+ * that share the device and the precision, stepped together.  Every kernel of a batch step is
+ * ONE launch over the work of all plans: push, FIR and scatter (Eqs. 32, 42), transient and
+ * Eq. 39 over the concatenated elements and warp tasks, and the persistent near-field kernel
+ * (App. E) over the work items of all plans, dealt largest first over the SMs; the step is
+ * captured once per (kind, buffers) as a CUDA graph and replayed.  Each plan keeps its own state
+ * and step index, and its results are bit-identical to stepping it alone.
  *
  * fdph_batch_create: `plans` (count >= 1, distinct, host array, copied) must outlive the batch.
  *   Errors: FDPH_E_ARG (null, duplicate, mixed device or precision), FDPH_E_STATE (a predict

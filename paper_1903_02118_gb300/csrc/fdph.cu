@@ -207,13 +207,13 @@ __global__ void set_step_kernel(int* n_dev, int v) {
     n_dev[1] = v;   // step of the call's first row of D / T
 }
 
+// Every per-step kernel is a body over one work index of one plan (element, task or warp task),
+// launched either for one plan (grid y = right-hand side) or for a batch of plans (one launch
+// over the work of all plans; the plan of a work index from the prefix sums of their counts).
 template <class T>
-__global__ void push_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+__device__ __forceinline__ void push_body(const StepArgs<T>& a, int p, bool zero) {
     const int n = step_index(a);
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.N) return;
-    if (!a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
+    if (zero || !a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
         a.Dring[(size_t)wrap(n, a.WD) * a.N + p] = 0.0;
         return;
     }
@@ -229,11 +229,15 @@ __global__ void push_kernel(StepArgs<T> a0) {
 }
 
 template <class T>
-__global__ void fir_kernel(StepArgs<T> a0) {
+__global__ void push_kernel(StepArgs<T> a0) {
     const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < a.N) push_body(a, p, false);
+}
+
+template <class T>
+__device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
     const int n = step_index(a);
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= a.n_fir) return;
     const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
     const int ns = sb.ns;
@@ -258,6 +262,13 @@ __global__ void fir_kernel(StepArgs<T> a0) {
     a.dhat[sb.dhat + jl] = s0 + s1;
 }
 
+template <class T>
+__global__ void fir_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < a.n_fir) fir_body(a, q);
+}
+
 // source quantity u_j of Eq. 42 for block kind: Dhat (Domain F), dt * cumulative slip (Domain S,
 // App. B.1), slip rate (transient)
 template <class T>
@@ -271,12 +282,8 @@ __device__ __forceinline__ double source_value(const StepArgs<T>& a, const SbDev
 // cover the rank index l, so a run writes its ring slot row [slot][0, rank) in one coalesced pass.
 // One writer per (slot, l): the runs of a block have distinct delays.
 template <class T>
-__global__ void scatter_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+__device__ __forceinline__ void scatter_body(const StepArgs<T>& a, int w, int lane) {
     const int n = step_index(a);
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= a.n_sct) return;
     const int4 tk = a.sc_tasks[w];
     const SbDev& sb = a.sbs[tk.x];
     const int lg = tk.w, G = 1 << lg;
@@ -314,14 +321,17 @@ __global__ void scatter_kernel(StepArgs<T> a0) {
     }
 }
 
+template <class T>
+__global__ void scatter_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w < a.n_sct) scatter_body(a, w, threadIdx.x & 31);
+}
+
 // one warp per (transient block, rank index)
 template <class T>
-__global__ void trconv_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+__device__ __forceinline__ void trconv_body(const StepArgs<T>& a, int q, int lane) {
     const int n = step_index(a);
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (q >= a.n_tr) return;
     const SbDev sb = a.sbs[a.tr_sb[q]];
     const int l = a.tr_l[q];
     const int t0 = n - sb.mindm;
@@ -338,6 +348,13 @@ __global__ void trconv_kernel(StepArgs<T> a0) {
     }
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
     if (lane == 0) a.zring[sb.zring + (long long)wrap(t0, sb.LZ) * sb.rank + l] = z;
+}
+
+template <class T>
+__global__ void trconv_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q < a.n_tr) trconv_body(a, q, threadIdx.x & 31);
 }
 
 // ---- bulk-async copy + mbarrier helpers (PTX)
@@ -784,12 +801,8 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
 // f_{., i} . Tbar'[n - dm_i] goes to the receiver's CSR slot.  A block kept exact with F = I
 // reads one ring entry per receiver (2^lg = 1).
 template <class T>
-__global__ void far_eval_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+__device__ __forceinline__ void far_eval_body(const StepArgs<T>& a, int w, int lane) {
     const int n = step_index(a);
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= a.n_evt) return;   // warp-uniform
     const int4 tk = a.ev_tasks[w];
     const SbDev& sb = a.sbs[tk.x];
     const int lg = tk.w, G = 1 << lg;
@@ -824,19 +837,29 @@ __global__ void far_eval_kernel(StepArgs<T> a0) {
     if (valid && lj == 0) a.fval[a.e_pos[sb.e0 + il]] = s;
 }
 
+template <class T>
+__global__ void far_eval_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w < a.n_evt) far_eval_body(a, w, threadIdx.x & 31);   // warp-uniform
+}
+
 // one warp per receiver: sum of its far entries and near-field partials, fixed order
 template <class T>
-__global__ void gather_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+__device__ __forceinline__ void gather_body(const StepArgs<T>& a, int p, int lane) {
     const int n = step_index(a);
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= a.N) return;
     double s = 0.0;
     for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
     for (int e = a.np_ptr[p] + lane; e < a.np_ptr[p + 1]; e += 32) s += a.partial[a.np_idx[e]];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) a.T_out[io_offset(a, n) + a.perm[p]] = s;
+}
+
+template <class T>
+__global__ void gather_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p < a.N) gather_body(a, p, threadIdx.x & 31);
 }
 
 // Local friction solve (geometry order): T_pred holds the traction change with D_n = 0.
@@ -849,9 +872,8 @@ struct FrictionDev {
 };
 
 // D, T: this step's rows (graph replay: row n_dev[0] - n_dev[1] of a step-major array)
-__global__ void friction_kernel(FrictionDev f, int N, double* D, double* T, const int* n_dev) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= N) return;
+__device__ __forceinline__ void friction_body(const FrictionDev& f, int N, int e, double* D, double* T,
+                                              const int* n_dev) {
     if (n_dev) {
         const long long off = (long long)(n_dev[0] - n_dev[1]) * N;
         D += off;
@@ -871,6 +893,87 @@ __global__ void friction_kernel(FrictionDev f, int N, double* D, double* T, cons
     D[e] = v;
     T[e] = tau + f.k0[e] * v;
     f.slip[e] = u + v * f.dt;
+}
+
+__global__ void friction_kernel(FrictionDev f, int N, double* D, double* T, const int* n_dev) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N) friction_body(f, N, e, D, T, n_dev);
+}
+
+// ---- the per-step kernels over a batch of plans: one launch covers the work of every plan;
+// pre[0..np] are the prefix sums of the plans' work counts (elements, FIR tasks, ...)
+
+// plan of global work index t: the largest p with pre[p] <= t
+__device__ __forceinline__ int plan_of(const int* pre, int np, int t) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class T>
+__global__ void push_batch(const StepArgs<T>* scen, const int* pre, int np, int zero) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[np]) return;
+    const int p = plan_of(pre, np, t);
+    push_body(scen[p], t - pre[p], zero != 0);
+}
+
+template <class T>
+__global__ void fir_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[np]) return;
+    const int p = plan_of(pre, np, t);
+    fir_body(scen[p], t - pre[p]);
+}
+
+template <class T>
+__global__ void scatter_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= pre[np]) return;   // warp-uniform
+    const int p = plan_of(pre, np, w);
+    scatter_body(scen[p], w - pre[p], threadIdx.x & 31);
+}
+
+template <class T>
+__global__ void trconv_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= pre[np]) return;
+    const int p = plan_of(pre, np, w);
+    trconv_body(scen[p], w - pre[p], threadIdx.x & 31);
+}
+
+template <class T>
+__global__ void far_eval_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= pre[np]) return;
+    const int p = plan_of(pre, np, w);
+    far_eval_body(scen[p], w - pre[p], threadIdx.x & 31);
+}
+
+template <class T>
+__global__ void gather_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= pre[np]) return;
+    const int p = plan_of(pre, np, w);
+    gather_body(scen[p], w - pre[p], threadIdx.x & 31);
+}
+
+template <class T>
+__global__ void friction_batch(const FrictionDev* fr, const StepArgs<T>* scen, const int* pre, int np) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[np]) return;
+    const int p = plan_of(pre, np, t);
+    const StepArgs<T>& a = scen[p];
+    friction_body(fr[p], a.N, t - pre[p], const_cast<double*>(a.D_in), a.T_out, a.n_dev);
+}
+
+template <class T>
+__global__ void advance_batch(const StepArgs<T>* scen, int np) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) *const_cast<int*>(scen[p].n_dev) += 1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1913,21 +2016,29 @@ static int pending_commit(fdph_plan_t P) {
 // ------------------------------------------------------------------------------------------
 // Batches of plans: one near-field launch per step for all of them
 
-// A set of plans (same device, same precision) stepped together: per step, each plan's push,
-// FIR / scatter and transient / Eq. 39 kernels on that plan's streams, then ONE persistent
-// near-field launch over the work items of all plans (dealt together over the CTAs), then each
-// plan's gather.  Graphs of one batch step are captured per (kind, buffers) and replayed.
+// work kinds of a batch's prefix sums
+enum { BW_ELEM = 0, BW_FIR = 1, BW_SCT = 2, BW_TR = 3, BW_EVT = 4, BW_KINDS = 5 };
+
+// A set of plans (same device, same precision) stepped together: each kernel of a step is ONE
+// launch over the work of all plans (the persistent near-field kernel over the work items of
+// all plans, dealt together over the CTAs; the others over the concatenated elements and warp
+// tasks).  Graphs of one batch step are captured per (kind, buffers) and replayed.
 struct fdph_batch_s {
     int device = 0, precision = 0;
     std::vector<fdph_plan_t> plans;
     std::vector<int> version;            // each plan's near-field schedule at creation
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_near = nullptr, ev_end = nullptr;
-    std::vector<cudaEvent_t> ev_ready, ev_done;
+    cudaStream_t side[2] = {nullptr, nullptr};   // FIR + scatter | transient + Eq. 39
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr}, ev_end = nullptr;
+    std::vector<cudaEvent_t> ev_ready;           // per plan: its queued work before a batch call
     NearTask* tasks = nullptr;
     int* cta_ptr = nullptr;
     int n_cta = 0;
     int near_priority = 0;
+    int* pre = nullptr;                          // device prefix sums [BW_KINDS][np + 1]
+    int tot[5] = {0, 0, 0, 0, 0};                // their totals
+    FrictionDev* fr_dev = nullptr;               // friction of every plan (rupture batches)
+    std::vector<FrictionDev> fr_host;
     struct Entry {
         int kind;
         std::vector<const void*> D, T;
@@ -1965,59 +2076,50 @@ static void launch_near_batch(fdph_batch_t B, const StepArgs<T>* scen, cudaStrea
 }
 
 // One step of every plan of the batch (kind GRAPH_RUN or GRAPH_RUPTURE), for capture on the
-// batch stream.  av[p]: plan p's arguments (step index from its n_dev); D[p]: its rupture rows.
+// batch stream; scen: every plan's arguments on the device (step index from its n_dev; D_in the
+// plan's D rows, the rupture outputs for GRAPH_RUPTURE).
 template <class T>
-static void enqueue_batch_step(fdph_batch_t B, int kind, const std::vector<StepArgs<T>>& av,
-                               const std::vector<double*>& D, const StepArgs<T>* scen) {
+static void enqueue_batch_step(fdph_batch_t B, int kind, const StepArgs<T>* scen) {
     cudaStream_t bs = B->stream;
-    const size_t np = B->plans.size();
-    cudaEventRecord(B->ev_start, bs);
-    for (size_t p = 0; p < np; ++p) {
-        fdph_plan_t P = B->plans[p];
-        StepArgs<T> a = av[p];
-        cudaStream_t s = P->stream;
-        cudaStreamWaitEvent(s, B->ev_start, 0);
-        if (kind == GRAPH_RUN) {
-            push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a);
-            cudaEventRecord(P->ev_fork, s);
-            cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
-            cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
-            if (a.n_fir) fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
-            if (a.n_sct) scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
-            if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
-            if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
-            cudaEventRecord(P->ev_join[0], P->side[0]);
-            cudaEventRecord(P->ev_join[1], P->side[1]);
-        } else {   // rupture prediction: zero row, transient, Eq. 39 evaluation
-            a.D_in = nullptr;
-            push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a);
-            if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a);
-            if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        }
-        cudaEventRecord(B->ev_ready[p], s);
-        cudaStreamWaitEvent(bs, B->ev_ready[p], 0);
+    const int np = (int)B->plans.size();
+    auto pre = [&](int k) { return (const int*)B->pre + k * (np + 1); };
+    const int* tot = B->tot;
+    auto fir = [&](cudaStream_t s) {
+        if (tot[BW_FIR]) fir_batch<T><<<blocks(tot[BW_FIR], 128), 128, 0, s>>>(scen, pre(BW_FIR), np);
+        if (tot[BW_SCT])
+            scatter_batch<T><<<blocks((long long)tot[BW_SCT] * 32, 128), 128, 0, s>>>(scen, pre(BW_SCT), np);
+    };
+    auto far = [&](cudaStream_t s) {
+        if (tot[BW_TR]) trconv_batch<T><<<blocks((long long)tot[BW_TR] * 32, 128), 128, 0, s>>>(scen, pre(BW_TR), np);
+        if (tot[BW_EVT])
+            far_eval_batch<T><<<blocks((long long)tot[BW_EVT] * 32, 128), 128, 0, s>>>(scen, pre(BW_EVT), np);
+    };
+    auto gather = [&]() {
+        gather_batch<T><<<blocks((long long)tot[BW_ELEM] * 32, 128), 128, 0, bs>>>(scen, pre(BW_ELEM), np);
+    };
+    if (kind == GRAPH_RUN) {
+        push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 0);
+        cudaEventRecord(B->ev_fork, bs);
+        cudaStreamWaitEvent(B->side[0], B->ev_fork, 0);
+        cudaStreamWaitEvent(B->side[1], B->ev_fork, 0);
+        fir(B->side[0]);
+        far(B->side[1]);
+        if (B->n_cta) launch_near_batch<T>(B, scen, bs);
+        cudaEventRecord(B->ev_join[0], B->side[0]);
+        cudaEventRecord(B->ev_join[1], B->side[1]);
+        cudaStreamWaitEvent(bs, B->ev_join[0], 0);
+        cudaStreamWaitEvent(bs, B->ev_join[1], 0);
+        gather();
+    } else {   // rupture: predict with D_n = 0, friction, commit D_n
+        push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 1);
+        far(bs);
+        if (B->n_cta) launch_near_batch<T>(B, scen, bs);
+        gather();
+        friction_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(B->fr_dev, scen, pre(BW_ELEM), np);
+        push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 0);
+        fir(bs);
     }
-    if (B->n_cta) launch_near_batch<T>(B, scen, bs);
-    cudaEventRecord(B->ev_near, bs);
-    for (size_t p = 0; p < np; ++p) {
-        fdph_plan_t P = B->plans[p];
-        StepArgs<T> a = av[p];
-        cudaStream_t s = P->stream;
-        cudaStreamWaitEvent(s, B->ev_near, 0);
-        if (kind == GRAPH_RUN) {
-            cudaStreamWaitEvent(s, P->ev_join[0], 0);
-            cudaStreamWaitEvent(s, P->ev_join[1], 0);
-            gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        } else {
-            a.D_in = nullptr;
-            gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
-            friction_kernel<<<blocks(a.N, 256), 256, 0, s>>>(P->fr, a.N, D[p], a.T_out, a.n_dev);
-            enqueue_commit<T>(P, a, D[p], s);
-        }
-        advance_step_kernel<<<1, 1, 0, s>>>(P->n_dev);
-        cudaEventRecord(B->ev_done[p], s);
-        cudaStreamWaitEvent(bs, B->ev_done[p], 0);
-    }
+    advance_batch<T><<<blocks(np, 128), 128, 0, bs>>>(scen, np);
 }
 
 // `steps` steps of every plan of the batch as replays of one captured batch-step graph
@@ -2036,6 +2138,10 @@ static int batch_run(fdph_batch_t B, int kind, int steps, const double* const* D
         FDPH_CUDA(cudaStreamWaitEvent(bs, B->ev_ready[p], 0));
     }
     for (size_t p = 0; p < np; ++p) set_step_kernel<<<1, 1, 0, bs>>>(B->plans[p]->n_dev, B->plans[p]->n);
+    if (kind == GRAPH_RUPTURE) {   // the friction of every plan as it is now (pageable copy: staged at once)
+        for (size_t p = 0; p < np; ++p) B->fr_host[p] = B->plans[p]->fr;
+        FDPH_CUDA(cudaMemcpyAsync(B->fr_dev, B->fr_host.data(), np * sizeof(FrictionDev), cudaMemcpyHostToDevice, bs));
+    }
     cudaGraphExec_t ex = nullptr;
     for (const auto& ge : B->graphs) {
         if (ge.kind != kind) continue;
@@ -2048,14 +2154,12 @@ static int batch_run(fdph_batch_t B, int kind, int steps, const double* const* D
     }
     if (!ex) {
         std::vector<StepArgs<T>> av(np);
-        std::vector<double*> Dr(np);
         for (size_t p = 0; p < np; ++p) {
             fdph_plan_t P = B->plans[p];
-            av[p] = make_args<T>(P, kind == GRAPH_RUPTURE ? nullptr : D[p], Tt[p]);
+            av[p] = make_args<T>(P, D[p], Tt[p]);
             av[p].n_dev = P->n_dev;
             av[p].io_stride = P->N;
             av[p].io_ring = 0;
-            Dr[p] = (double*)D[p];
         }
         void* scen = nullptr;
         FDPH_CUDA(cudaMalloc(&scen, np * sizeof(StepArgs<T>)));
@@ -2063,7 +2167,7 @@ static int batch_run(fdph_batch_t B, int kind, int steps, const double* const* D
         cudaGraph_t g = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            enqueue_batch_step<T>(B, kind, av, Dr, (const StepArgs<T>*)scen);
+            enqueue_batch_step<T>(B, kind, (const StepArgs<T>*)scen);
             e = cudaStreamEndCapture(bs, &g);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
@@ -2116,6 +2220,32 @@ static int batch_schedule(fdph_batch_t B) {
     if (!tasks.empty())
         FDPH_CUDA(cudaMemcpy(B->tasks, tasks.data(), tasks.size() * sizeof(NearTask), cudaMemcpyHostToDevice));
     FDPH_CUDA(cudaMemcpy(B->cta_ptr, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // prefix sums of the plans' work counts, per kind
+    const int np = (int)B->plans.size();
+    std::vector<int> pre((size_t)BW_KINDS * (np + 1), 0);
+    for (int k = 0; k < BW_KINDS; ++k) {
+        long long acc = 0;
+        for (int p = 0; p < np; ++p) {
+            const fdph_plan_t P = B->plans[p];
+            const long long c = k == BW_ELEM ? P->N
+                                : k == BW_FIR ? (long long)P->hp.fir_sb.size()
+                                : k == BW_SCT ? P->n_sct
+                                : k == BW_TR ? (long long)P->hp.tr_sb.size()
+                                             : P->n_evt;
+            pre[(size_t)k * (np + 1) + p] = (int)acc;
+            acc += c;
+        }
+        if (acc > INT32_MAX / 32) {
+            set_error("fdph_batch_create: the plans' work exceeds the batch index range");
+            return FDPH_E_ARG;
+        }
+        pre[(size_t)k * (np + 1) + np] = (int)acc;
+        B->tot[k] = (int)acc;
+    }
+    FDPH_CUDA(cudaMalloc(&B->pre, pre.size() * sizeof(int)));
+    FDPH_CUDA(cudaMemcpy(B->pre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+    FDPH_CUDA(cudaMalloc(&B->fr_dev, np * sizeof(FrictionDev)));
+    B->fr_host.assign(np, FrictionDev{});
     return FDPH_OK;
 }
 
@@ -2129,10 +2259,14 @@ static void batch_free(fdph_batch_t B) {
     }
     if (B->tasks) cudaFree(B->tasks);
     if (B->cta_ptr) cudaFree(B->cta_ptr);
+    if (B->pre) cudaFree(B->pre);
+    if (B->fr_dev) cudaFree(B->fr_dev);
     for (cudaEvent_t e : B->ev_ready) if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : B->ev_done) if (e) cudaEventDestroy(e);
-    if (B->ev_start) cudaEventDestroy(B->ev_start);
-    if (B->ev_near) cudaEventDestroy(B->ev_near);
+    for (int k = 0; k < 2; ++k) {
+        if (B->ev_join[k]) cudaEventDestroy(B->ev_join[k]);
+        if (B->side[k]) cudaStreamDestroy(B->side[k]);
+    }
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     if (B->ev_end) cudaEventDestroy(B->ev_end);
     if (B->stream) cudaStreamDestroy(B->stream);
     delete B;
@@ -2586,8 +2720,9 @@ int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
     std::vector<char> saved(len);
     if ((rc = fdph_save_state(P, saved.data(), &len))) return rc;
     double *Dz = nullptr, *Tz = nullptr;
-    if ((rc = dalloc(P, &Dz, (size_t)(steps + 2) * P->N)) || (rc = dalloc(P, &Tz, (size_t)(steps + 2) * P->N))) return rc;
-    FDPH_CUDA(cudaMemsetAsync(Dz, 0, (size_t)(steps + 2) * P->N * sizeof(double), P->stream));
+    const size_t rows = (size_t)(steps + 2) * P->N * P->nrhs;   // steps of nrhs rows of N
+    if ((rc = dalloc(P, &Dz, rows)) || (rc = dalloc(P, &Tz, rows))) return rc;
+    FDPH_CUDA(cudaMemsetAsync(Dz, 0, rows * sizeof(double), P->stream));
     // trials at a steady-state step index (every window full); the values stepped are irrelevant
     const int n0 = std::max(0, std::min(P->hp.max_W, M - steps - 2));
     cudaEvent_t e0, e1;
@@ -2903,18 +3038,19 @@ int fdph_batch_create(const fdph_plan_t* plans, int32_t count, fdph_batch_t* out
     B->near_priority = plans[0]->near_priority;
     if (cudaSetDevice(B->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&B->ev_near, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->side[0], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->side[1], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&B->ev_end, cudaEventDisableTiming) != cudaSuccess) {
         set_error("fdph_batch_create: stream / event creation failed");
         batch_free(B);
         return FDPH_E_CUDA;
     }
     B->ev_ready.assign(count, nullptr);
-    B->ev_done.assign(count, nullptr);
     for (int p = 0; p < count; ++p)
-        if (cudaEventCreateWithFlags(&B->ev_ready[p], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&B->ev_done[p], cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&B->ev_ready[p], cudaEventDisableTiming) != cudaSuccess) {
             set_error("fdph_batch_create: event creation failed");
             batch_free(B);
             return FDPH_E_CUDA;

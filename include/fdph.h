@@ -113,12 +113,13 @@ typedef struct fdph_params {
                              travel-time error of the plane-wave approximation by eta lmin / (4 c)
                              (Eq. 26) at a cost that grows like N^(3/2) */
     int32_t nrhs;         /* right-hand sides: independent slip-rate histories stepped together on
-                             the one operator (1..16; 0 => 1).  D_n and T_n of fdph_step,
+                             the one operator (1, 2, 4 or 8; 0 => 1).  D_n and T_n of fdph_step,
                              fdph_run, fdph_step_host and fdph_run_host are then nrhs rows of n
                              (RHS-major: row r, element i at r * n + i) per step, and the state is
-                             kept per RHS; the near-field coefficients are streamed once per step
-                             and re-read from L2 for the other RHS.  Rupture, fdph_predict /
-                             fdph_commit and batches take nrhs = 1 (FDPH_E_ARG otherwise) */
+                             kept per RHS; each near-field coefficient is read once per step and
+                             multiplied with the slip rates of all RHS (near-field work items
+                             are nrhs times shorter).  Rupture, fdph_predict / fdph_commit and
+                             batches take nrhs = 1 (FDPH_E_ARG otherwise) */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */

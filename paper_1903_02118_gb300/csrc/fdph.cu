@@ -82,12 +82,12 @@ struct __align__(16) NearTask {
     long long off;       // element offset of the item's first slice (tensor, or aux for kind 1)
     int item, k0, k1, kind, nr, ns, sl, s0, W, vstate;
     int scen;            // plan of the item in a batch (0 otherwise)
-    int rhs;             // right-hand side of the item
+    int pad;
 };
 static_assert(sizeof(NearTask) == 64, "one work item is four 16-byte loads");
 
 static const int kMaxSoe = 16;
-static const int kMaxRhs = 16;   // right-hand sides of one plan at most
+static const int kMaxRhs = 8;    // right-hand sides of one plan at most (1, 2, 4 or 8)
 
 template <class T>
 struct StepArgs {
@@ -398,11 +398,7 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
     return p;
 }
 
-__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
-    unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
+
 
 __device__ __forceinline__ bool mbar_wait_limit(unsigned long long* bar, unsigned phase, long long limit) {
     const unsigned a = smem_u32(bar);
@@ -446,7 +442,7 @@ __device__ __forceinline__ void consumer_barrier() {
 
 template <class T>
 __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
-    return tk.kind ? tk.k1 : min(tk.k1, n + 1) - tk.k0;
+    return tk.kind ? tk.k1 - tk.k0 : min(tk.k1, n + 1) - tk.k0;
 }
 
 // What a near-field work item reads of its plan (the plan of the launch, or for a batch of
@@ -487,28 +483,19 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     return v;
 }
 
-// the view of right-hand side r
-__device__ __forceinline__ NearView near_rhs(NearView v, int r) {
-    if (r) {
-        v.Dring += r * v.rs_D;
-        v.Cring += r * v.rs_C;
-        if (v.vstate) v.vstate += r * v.rs_vstate;
-        v.partial += r * v.rs_partial;
-    }
-    return v;
-}
-
-// The vectors of one work item (rows of 32 in the storage type) are
-// gathered by the consumer warps in two halves: near_issue loads this warp's rows (w, w + C, ...)
-// into registers, near_commit (one item later, so that the loads are in flight meanwhile) forms
-// the values and stores them to shared memory.  Window row k: D_{n - k0 - k, j}.  Aux row 0:
-// C_j(n - W) (the static tile carries dt); aux row q + 1: the tail state
-// V_qj(n) = rho_q V_qj(n - 1) + D_{j, n-W}, updated here by its only reader.
+// The vectors of one work item (rows of 32 in the row type; with NR right-hand sides row
+// k * NR + r holds slice k of right-hand side r) are gathered by the consumer warps in two
+// halves: near_issue loads this warp's rows (w, w + C, ...) into registers, near_commit (one
+// item later, so that the loads are in flight meanwhile) forms the values and stores them to
+// shared memory.  Window row k: D_{n - k0 - k, j}.  Aux row a = k0 + k: a = 0, C_j(n - W) (the
+// static tile carries dt); a = q + 1, the tail state V_qj(n) = rho_q V_qj(n - 1) + D_{j, n-W},
+// updated here by its only reader.
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
-static_assert(kRowsPerWarp * kNearConsumers >= 17, "aux rows (1 + 16 tail terms) fit the row registers");
+static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
+template <int NR>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
-                                           double (&r)[kRowsPerWarp], double& dW) {
+                                           double (&r)[kRowsPerWarp], double (&dW)[NR]) {
     const int n = a.n;
     const int nsl = near_slices<double>(tk, n);
     const bool on = lane < tk.ns;
@@ -517,45 +504,52 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
         const int b0 = wrap(n - tk.k0, a.WD);
 #pragma unroll
         for (int m = 0; m < kRowsPerWarp; ++m) {
-            const int k = warp + m * kNearConsumers;
+            const int v = warp + m * kNearConsumers;
+            const int k = v / NR, q = v % NR;
             int slot = b0 - k;                     // k < W < WD: one wrap at most
             slot += slot < 0 ? a.WD : 0;
-            r[m] = (on && k < nsl) ? a.Dring[(size_t)slot * a.N + col] : 0.0;
+            r[m] = (on && k < nsl) ? a.Dring[q * a.rs_D + (size_t)slot * a.N + col] : 0.0;
         }
-        dW = 0.0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) dW[q] = 0.0;
     } else {
         const int t = n - tk.W;
-        dW = (on && t >= 0) ? a.Dring[(size_t)wrap(t, a.WD) * a.N + col] : 0.0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+            dW[q] = (on && t >= 0 && tk.k1 > 1) ? a.Dring[q * a.rs_D + (size_t)wrap(t, a.WD) * a.N + col] : 0.0;
 #pragma unroll
         for (int m = 0; m < kRowsPerWarp; ++m) {
-            const int k = warp + m * kNearConsumers;
-            double v = 0.0;
+            const int v = warp + m * kNearConsumers;
+            const int k = v / NR, q = v % NR, ai = tk.k0 + k;
+            double x = 0.0;
             if (on && k < nsl) {
-                if (k == 0) v = t >= 0 ? a.Cring[(size_t)wrap(t, a.WC) * a.N + col] : 0.0;
-                else v = a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane];
+                if (ai == 0) x = t >= 0 ? a.Cring[q * a.rs_C + (size_t)wrap(t, a.WC) * a.N + col] : 0.0;
+                else x = a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane];
             }
-            r[m] = v;
+            r[m] = x;
         }
     }
 }
 
-template <class R>
+template <class R, int NR>
 __device__ __forceinline__ void near_commit(const NearView& a, const NearTask& tk, int warp, int lane,
-                                            const double (&r)[kRowsPerWarp], double dW, unsigned char* vb) {
+                                            const double (&r)[kRowsPerWarp], const double (&dW)[NR],
+                                            unsigned char* vb) {
     const int nsl = near_slices<double>(tk, a.n);
 #pragma unroll
     for (int m = 0; m < kRowsPerWarp; ++m) {
-        const int k = warp + m * kNearConsumers;
+        const int v = warp + m * kNearConsumers;
+        const int k = v / NR, q = v % NR, ai = tk.k0 + k;
         if (k < nsl) {
-            double v = r[m];
-            if (tk.kind && k > 0) {
-                v = 0.0;
+            double x = r[m];
+            if (tk.kind && ai > 0) {
+                x = 0.0;
                 if (lane < tk.ns) {
-                    v = a.rho[k - 1] * r[m] + dW;
-                    a.vstate[tk.vstate + (size_t)(k - 1) * tk.ns + lane] = v;
+                    x = a.rho[ai - 1] * r[m] + dW[q];
+                    a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane] = x;
                 }
             }
-            ((R*)vb)[k * 32 + lane] = (R)v;
+            ((R*)vb)[v * 32 + lane] = (R)x;
         }
     }
 }
@@ -566,10 +560,12 @@ __device__ __forceinline__ void near_commit(const NearView& a, const NearTask& t
 template <class H> struct NearTypes { using Aux = H; using Row = H; };
 template <> struct NearTypes<__half> { using Aux = float; using Row = float; };
 
-template <class H>
+template <class H, int NR = 1>
 struct NearCfg {
     using R = typename NearTypes<H>::Row;
-    static constexpr int stages = sizeof(R) == 4 ? 5 : 4;          // shared-memory pipeline depth
+    // shared-memory pipeline depth (fewer stages with several right-hand sides: their partial
+    // sums take static shared memory)
+    static constexpr int stages = sizeof(R) == 4 && NR < 4 ? 5 : 4;
     static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(R);  // one item's vectors
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
 };
@@ -652,6 +648,86 @@ __device__ __forceinline__ float slice_dot(const __half* buf, const float* vrow,
 }
 static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer");
 
+// The same slice products for NR right-hand sides (vector rows vrows, vrows + 32, ...): each
+// coefficient load serves the NR vectors; per right-hand side the operations and their order are
+// those of slice_dot, so every right-hand side gets the single-RHS result bit for bit.
+template <int NR>
+__device__ __forceinline__ void slice_dot_nr(const float* buf, const float* vrows, int ns, int nr, int li,
+                                             float (&out)[NR]) {
+    const float4* tile = (const float4*)buf + li;
+    float s0[NR], s1[NR], s2[NR], s3[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) s0[q] = s1[q] = s2[q] = s3[q] = 0.f;
+    const int nb = (ns + 3) >> 2;
+    const int stride = nb == 8 && nr == 32 ? 32 : nr;
+    for (int jb = 0; jb < nb; ++jb) {
+        const float4 x = tile[jb * stride];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const float4 y = ((const float4*)(vrows + q * 32))[jb];
+            s0[q] = fmaf(x.x, y.x, s0[q]);
+            s1[q] = fmaf(x.y, y.y, s1[q]);
+            s2[q] = fmaf(x.z, y.z, s2[q]);
+            s3[q] = fmaf(x.w, y.w, s3[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) out[q] = (s0[q] + s1[q]) + (s2[q] + s3[q]);
+}
+
+template <int NR>
+__device__ __forceinline__ void slice_dot_nr(const double* buf, const double* vrows, int ns, int nr, int li,
+                                             double (&out)[NR]) {
+    const double2* tile = (const double2*)buf + li;
+    double s0[NR], s1[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) s0[q] = s1[q] = 0.0;
+    const int nb = (ns + 1) >> 1;
+    for (int jb = 0; jb < nb; ++jb) {
+        const double2 x = tile[jb * nr];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const double2 y = ((const double2*)(vrows + q * 32))[jb];
+            s0[q] = fma(x.x, y.x, s0[q]);
+            s1[q] = fma(x.y, y.y, s1[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) out[q] = s0[q] + s1[q];
+}
+
+template <int NR>
+__device__ __forceinline__ void slice_dot_nr(const __half* buf, const float* vrows, int ns, int nr, int li,
+                                             float (&out)[NR]) {
+    const uint4* tile = (const uint4*)buf + li;
+    float s0[NR], s1[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) s0[q] = s1[q] = 0.f;
+    const int nb = (ns + 7) >> 3;
+    if (nb == 4 && nr == 32) {
+        for (int jb = 0; jb < 4; jb += 2) {
+            const uint4 x0 = tile[jb * 32], x1 = tile[(jb + 1) * 32];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const float4* d = (const float4*)(vrows + q * 32);
+                s0[q] = half8_dot(x0, d[2 * jb], d[2 * jb + 1], s0[q]);
+                s1[q] = half8_dot(x1, d[2 * jb + 2], d[2 * jb + 3], s1[q]);
+            }
+        }
+    } else {
+        for (int jb = 0; jb < nb; ++jb) {
+            const uint4 x = tile[jb * nr];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const float4* d = (const float4*)(vrows + q * 32);
+                s0[q] = half8_dot(x, d[2 * jb], d[2 * jb + 1], s0[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) out[q] = s0[q] + s1[q];
+}
+
 // Near field (App. E), persistent and warp-specialised.  Each CTA owns a list of work items
 // (window slices [k0, k1) of a leaf, or the leaf's aux slices: static tile and exponential
 // tail).  One producer thread streams the items' slices through a ring of shared-memory stages
@@ -660,19 +736,21 @@ static_assert(17 <= kChunk, "aux vectors (1 + 16 tail terms) fit a vector buffer
 // one; consumer warp w takes slices w, w + kNearConsumers, ... of each stage, lane i = receiver i,
 // reading its coefficients and the vector 16 bytes at a time.  At the end of an item the
 // consumers' sums are combined in FP64 into the item's partial-sum slot.  kBatch: the items of
-// several plans in one launch (fdph_batch_run); item tk belongs to plan scen[tk.scen].
-template <class T, class H, bool kBatch>
+// several plans in one launch (fdph_batch_run); item tk belongs to plan scen[tk.scen].  NR: the
+// plan's right-hand sides, consumed together (each coefficient read once per step, the vectors
+// of all right-hand sides in the item's vector buffer).
+template <class T, class H, bool kBatch, int NR>
 __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, const StepArgs<T>* scen) {
-    using C = NearCfg<H>;
+    using C = NearCfg<H, NR>;
     using A = typename NearTypes<H>::Aux;
     using R = typename NearTypes<H>::Row;
     extern __shared__ __align__(128) unsigned char near_smem[];
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
-    __shared__ double red[2][kNearConsumers][32];
+    __shared__ double red[2][kNearConsumers][NR][32];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
-    auto view = [&](const NearTask& tk) -> NearView { return near_rhs(kBatch ? near_view(scen[tk.scen]) : v0, tk.rhs); };
+    auto view = [&](const NearTask& tk) -> NearView { return kBatch ? near_view(scen[tk.scen]) : v0; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
     unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
@@ -695,9 +773,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
     if (warp == kNearConsumers) {
         // ---------------- producer (one thread)
         if (lane == 0) {
-            // coefficients are read once per step: evict-first, except for the passes of the right-hand
-            // sides before the last, whose re-reads follow at once on this CTA (evict-last)
-            const unsigned long long first = l2_evict_first_policy(), last = l2_evict_last_policy();
+            const unsigned long long policy = l2_evict_first_policy();   // coefficients are read once
             for (int ti = t0; ti < t1; ++ti) {
                 const NearTask tk = task(ti);
                 const NearView v = view(tk);
@@ -718,20 +794,20 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                     fence_proxy_async();
                     mbar_expect_tx(&full[s], bytes);
                     bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
-                                  tk.rhs + 1 < v.nrhs ? last : first);
+                                  policy);
                 }
             }
         }
     } else {
         // ---------------- consumers
-        double rows[kRowsPerWarp], dW = 0.0;
+        double rows[kRowsPerWarp], dW[NR];
         NearTask nxt;
         NearView vn;
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue(vn, nxt, warp, lane, rows, dW);
-            near_commit<R>(vn, nxt, warp, lane, rows, dW, vbuf);
+            near_issue<NR>(vn, nxt, warp, lane, rows, dW);
+            near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         consumer_barrier();
         int par = 0;
@@ -742,7 +818,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue(vn, nxt, warp, lane, rows, dW);
+                near_issue<NR>(vn, nxt, warp, lane, rows, dW);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -754,8 +830,13 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
             const int span = tk.nr > 16 ? 32 : tk.nr > 8 ? 16 : tk.nr > 4 ? 8 : tk.nr > 2 ? 4 : tk.nr > 1 ? 2 : 1;
             const int ngrp = 32 / span, grp = lane / span, ri = lane - grp * span;
             const int li = ri < tk.nr ? ri : 0;         // lanes past nr read a valid element, unused
-            R acc = (R)0;
-            double accd = 0.0;
+            R acc[NR];
+            double accd[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                acc[r] = (R)0;
+                accd[r] = 0.0;
+            }
             for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % C::stages;
                 const int cnt = min(per, nsl - q * per);
@@ -765,24 +846,43 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                 }
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
                 for (int kk = warp * ngrp + grp; kk < cnt; kk += kNearConsumers * ngrp) {
-                    const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * 32 * sizeof(R));
-                    if (tk.kind)   // static and tail slices: FP64 across slices
-                        accd += (double)slice_dot((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
-                    else
-                        acc += slice_dot((const H*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
+                    const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
+                    if constexpr (NR == 1) {
+                        if (tk.kind)   // static and tail slices: FP64 across slices
+                            accd[0] += (double)slice_dot((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
+                        else
+                            acc[0] += slice_dot((const H*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
+                    } else {
+                        R t[NR];
+                        if (tk.kind) {
+                            slice_dot_nr<NR>((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li, t);
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) accd[r] += (double)t[r];
+                        } else {
+                            slice_dot_nr<NR>((const H*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li, t);
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) acc[r] += t[r];
+                        }
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            if (ti + 1 < t1) near_commit<R>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
-            double tot = (double)acc + accd;
-            for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-            red[par][warp][lane] = lane < tk.nr ? tot : 0.0;
+            if (ti + 1 < t1) near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                double tot = (double)acc[r] + accd[r];
+                for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                red[par][warp][r][lane] = lane < tk.nr ? tot : 0.0;
+            }
             consumer_barrier();   // also publishes the next item's vectors
             if (warp == 0) {
-                double sum = 0.0;
-                for (int w = 0; w < kNearConsumers; ++w) sum += red[par][w][lane];
-                v.partial[(size_t)tk.item * 32 + lane] = sum;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    double sum = 0.0;
+                    for (int w = 0; w < kNearConsumers; ++w) sum += red[par][w][r][lane];
+                    v.partial[r * v.rs_partial + (size_t)tk.item * 32 + lane] = sum;
+                }
             }
         }
     }
@@ -1284,6 +1384,23 @@ struct ProfScope {
     ~ProfScope();
 };
 
+template <class T, class H, int NR>
+static void launch_near_nr(cudaLaunchConfig_t& cfg, const StepArgs<T>& a) {
+    cfg.dynamicSmemBytes = NearCfg<H, NR>::smem;
+    cudaLaunchKernelEx(&cfg, near_kernel<T, H, false, NR>, a, (const StepArgs<T>*)nullptr);
+}
+
+// the instantiation for the plan's right-hand sides (1, 2, 4 or 8)
+template <class T, class H>
+static void launch_near_h(cudaLaunchConfig_t& cfg, const StepArgs<T>& a, int nrhs) {
+    switch (nrhs) {
+        case 2: launch_near_nr<T, H, 2>(cfg, a); break;
+        case 4: launch_near_nr<T, H, 4>(cfg, a); break;
+        case 8: launch_near_nr<T, H, 8>(cfg, a); break;
+        default: launch_near_nr<T, H, 1>(cfg, a);
+    }
+}
+
 // The near-field kernel is persistent with a static schedule (one CTA pair per SM), so it is
 // launched at the greatest stream priority: when it shares the GPU with the far-field branches of
 // the same step its CTAs are placed first and none starts late.
@@ -1300,13 +1417,11 @@ static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     cfg.numAttrs = 1;
     if constexpr (sizeof(T) == 4) {
         if (P->precision == FDPH_FP16) {
-            cfg.dynamicSmemBytes = NearCfg<__half>::smem;
-            cudaLaunchKernelEx(&cfg, near_kernel<T, __half, false>, a, (const StepArgs<T>*)nullptr);
+            launch_near_h<T, __half>(cfg, a, P->nrhs);
             return;
         }
     }
-    cfg.dynamicSmemBytes = NearCfg<T>::smem;
-    cudaLaunchKernelEx(&cfg, near_kernel<T, T, false>, a, (const StepArgs<T>*)nullptr);
+    launch_near_h<T, T>(cfg, a, P->nrhs);
 }
 
 template <class T>
@@ -1611,7 +1726,7 @@ static void near_tasks(fdph_plan_t P, int scen, std::vector<NearTask>& tasks, st
         const NearLeaf& L = hp.near[it.leaf];
         NearTask t;
         memset(&t, 0, sizeof(t));
-        t.off = it.kind ? (long long)L.stat : (long long)L.tensor + (long long)it.k0 * L.sl;
+        t.off = it.kind ? (long long)L.stat + (long long)it.k0 * L.sla : (long long)L.tensor + (long long)it.k0 * L.sl;
         t.item = q;
         t.k0 = it.k0;
         t.k1 = it.k1;
@@ -1624,16 +1739,13 @@ static void near_tasks(fdph_plan_t P, int scen, std::vector<NearTask>& tasks, st
         t.vstate = (int)L.vstate;
         t.scen = scen;
         tasks.push_back(t);
-        // the right-hand sides of an item run back to back on one CTA (deal_tasks), their
-        // re-reads of the coefficients hitting L2
-        cost.push_back(((double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0) *
-                       std::max(P->nrhs, 1));
+        cost.push_back((double)(it.k1 - it.k0) * t.sl * (double)(it.kind ? sizeof(A) : sizeof(H)) + 4096.0);
     }
 }
 
 // Work items dealt largest first to the least-loaded of ncta CTAs; per-CTA task lists in CTA
 // order and their offsets.
-static void deal_tasks(const std::vector<NearTask>& all, const std::vector<double>& cost, int ncta, int nrhs,
+static void deal_tasks(const std::vector<NearTask>& all, const std::vector<double>& cost, int ncta,
                        std::vector<NearTask>& tasks, std::vector<int>& cptr) {
     const int ni = (int)all.size();
     std::vector<int> order(ni);
@@ -1655,23 +1767,20 @@ static void deal_tasks(const std::vector<NearTask>& all, const std::vector<doubl
     tasks.clear();
     cptr.assign(1, 0);
     for (int c = 0; c < ncta; ++c) {
-        for (int q : own[c])
-            for (int r = 0; r < nrhs; ++r) {
-                NearTask t = all[q];
-                t.rhs = r;
-                tasks.push_back(t);
-            }
+        for (int q : own[c]) tasks.push_back(all[q]);
         cptr.push_back((int)tasks.size());
     }
 }
 
 // CTAs of the persistent near-field grid: SMs x resident CTAs per SM of the kernel
-template <class T, class H, bool kBatch>
+template <class T, class H, bool kBatch, int NR>
 static int near_grid(int device, int* ncta_max) {
-    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, NearCfg<H>::smem));
+    FDPH_CUDA(cudaFuncSetAttribute(near_kernel<T, H, kBatch, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   NearCfg<H, NR>::smem));
     int sms = 0, per_sm = 0;
     FDPH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H, kBatch>, kNearThreads, NearCfg<H>::smem));
+    FDPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, near_kernel<T, H, kBatch, NR>, kNearThreads,
+                                                            NearCfg<H, NR>::smem));
     *ncta_max = sms * std::max(per_sm, 1);
     return FDPH_OK;
 }
@@ -1682,14 +1791,18 @@ template <class T, class H>
 static int build_schedule(fdph_plan_t P) {
     HostPlan& hp = P->hp;
     int rc, ncta_max = 1;
-    if ((rc = near_grid<T, H, false>(P->device, &ncta_max))) return rc;
+    rc = P->nrhs == 8   ? near_grid<T, H, false, 8>(P->device, &ncta_max)
+         : P->nrhs == 4 ? near_grid<T, H, false, 4>(P->device, &ncta_max)
+         : P->nrhs == 2 ? near_grid<T, H, false, 2>(P->device, &ncta_max)
+                        : near_grid<T, H, false, 1>(P->device, &ncta_max);
+    if (rc) return rc;
     std::vector<NearTask> all, tasks;
     std::vector<double> cost;
     std::vector<int> cptr;
     near_tasks<T, H>(P, 0, all, cost);
     const int ni = (int)all.size();
     const int ncta = std::max(1, std::min(ni, ncta_max));
-    deal_tasks(all, cost, ncta, P->nrhs, tasks, cptr);
+    deal_tasks(all, cost, ncta, tasks, cptr);
     P->n_cta = ni ? ncta : 0;
     P->sched_version += 1;
     if ((rc = upload(P, &P->tasks, tasks)) || (rc = upload(P, &P->cta_ptr, cptr)) ||
@@ -1787,9 +1900,10 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
     // resident CTAs (152 SMs x 3), so small problems (the plain config) fill the device too
     long long slices = 0;
     for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
-    int chunk = kChunk;
-    while (chunk > 8 && slices / chunk < 4LL * 152 * 3) chunk /= 2;
-    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
+    // (with nrhs right-hand sides an item's vectors, nrhs per slice, fill the same buffer)
+    int chunk = kChunk / P->nrhs;
+    while (chunk > std::max(1, 8 / P->nrhs) && slices / chunk < 4LL * 152 * 3) chunk /= 2;
+    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A), kChunk / P->nrhs);
     P->near_W = W;
     P->near_tail = has_tail;
     P->chunk = chunk;
@@ -1979,7 +2093,8 @@ static int set_chunk(fdph_plan_t P, int chunk) {
     for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);
     P->graphs.clear();
     const int64_t tens0 = hp.near_tensor_len, aux0 = hp.near_aux_len, vst0 = hp.vstate_len;
-    finish_near_layout(hp, P->near_W, P->near_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A));
+    finish_near_layout(hp, P->near_W, P->near_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A),
+                       kChunk / P->nrhs);
     if (hp.near_tensor_len != tens0 || hp.near_aux_len != aux0 || hp.vstate_len != vst0) {
         // the stored coefficients and states must keep their places (only the items change)
         set_error("set_chunk: near-field layout changed; the plan is unusable");
@@ -2067,12 +2182,12 @@ static void launch_near_batch(fdph_batch_t B, const StepArgs<T>* scen, cudaStrea
     if constexpr (sizeof(T) == 4) {
         if (B->precision == FDPH_FP16) {
             cfg.dynamicSmemBytes = NearCfg<__half>::smem;
-            cudaLaunchKernelEx(&cfg, near_kernel<T, __half, true>, ab, scen);
+            cudaLaunchKernelEx(&cfg, near_kernel<T, __half, true, 1>, ab, scen);
             return;
         }
     }
     cfg.dynamicSmemBytes = NearCfg<T>::smem;
-    cudaLaunchKernelEx(&cfg, near_kernel<T, T, true>, ab, scen);
+    cudaLaunchKernelEx(&cfg, near_kernel<T, T, true, 1>, ab, scen);
 }
 
 // One step of every plan of the batch (kind GRAPH_RUN or GRAPH_RUPTURE), for capture on the
@@ -2206,14 +2321,14 @@ static int batch_run(fdph_batch_t B, int kind, int steps, const double* const* D
 template <class T, class H>
 static int batch_schedule(fdph_batch_t B) {
     int ncta_max = 1, rc;
-    if ((rc = near_grid<T, H, true>(B->device, &ncta_max))) return rc;
+    if ((rc = near_grid<T, H, true, 1>(B->device, &ncta_max))) return rc;
     std::vector<NearTask> all, tasks;
     std::vector<double> cost;
     std::vector<int> cptr;
     for (size_t p = 0; p < B->plans.size(); ++p) near_tasks<T, H>(B->plans[p], (int)p, all, cost);
     const int ni = (int)all.size();
     const int ncta = std::max(1, std::min(ni, ncta_max));
-    deal_tasks(all, cost, ncta, 1, tasks, cptr);
+    deal_tasks(all, cost, ncta, tasks, cptr);
     B->n_cta = ni ? ncta : 0;
     FDPH_CUDA(cudaMalloc(&B->tasks, std::max<size_t>(1, tasks.size()) * sizeof(NearTask)));
     FDPH_CUDA(cudaMalloc(&B->cta_ptr, cptr.size() * sizeof(int)));
@@ -2335,11 +2450,11 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
     }
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
               (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
-              p->nrhs < 0 || p->nrhs > kMaxRhs ||
+              (p->nrhs != 0 && p->nrhs != 1 && p->nrhs != 2 && p->nrhs != 4 && p->nrhs != kMaxRhs) ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
         set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
-                  "lmin > 0), nrhs in [0, 16], precision FP64, FP32 or FP16, "
+                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -2728,7 +2843,7 @@ int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
     cudaEvent_t e0, e1;
     FDPH_CUDA(cudaEventCreate(&e0));
     FDPH_CUDA(cudaEventCreate(&e1));
-    const int cands[3] = {kChunk, kChunk / 2, kChunk / 4};
+    const int cands[3] = {kChunk / P->nrhs, kChunk / 2 / P->nrhs, kChunk / 4 / P->nrhs};
     int best = P->chunk;
     float best_ms = 1e30f;
     for (int c : cands) {

@@ -378,7 +378,7 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
 }
 
 void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
-                        int vec, int vec_aux) {
+                        int vec, int vec_aux, int aux_chunk) {
     const int nl = (int)hp.near_r0.size();
     hp.near.resize(nl);
     hp.items.clear();
@@ -411,19 +411,20 @@ void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::
             hp.vstate_len += (int64_t)hp.soe * L.ns;
         }
         hp.max_W = std::max(hp.max_W, L.W);
-        // one work item per chunk of window steps, and one for the aux slices (static term from
-        // step W on, exponential tail)
-        const int nchunk = (L.W + chunk - 1) / chunk;
-        for (int c = 0; c <= nchunk; ++c) {
+        // one work item per chunk of window steps, and per aux_chunk of the aux slices (static
+        // term from step W on, exponential tail)
+        auto add = [&](int kind, int k0, int k1) {
             NearItem it;
             it.leaf = l;
-            it.kind = c == nchunk ? 1 : 0;
-            it.k0 = it.kind ? 0 : c * chunk;
-            it.k1 = it.kind ? L.naux : std::min(L.W, (c + 1) * chunk);
+            it.kind = kind;
+            it.k0 = k0;
+            it.k1 = k1;
             const int id = (int)hp.items.size();
             hp.items.push_back(it);
             for (int il = 0; il < L.nr; ++il) slots[L.r0 + il].push_back(id * 32 + il);
-        }
+        };
+        for (int k0 = 0; k0 < L.W; k0 += chunk) add(0, k0, std::min(L.W, k0 + chunk));
+        for (int k0 = 0; k0 < L.naux; k0 += aux_chunk) add(1, k0, std::min(L.naux, k0 + aux_chunk));
     }
     hp.np_ptr.assign(hp.n + 1, 0);
     hp.np_idx.clear();

@@ -48,6 +48,8 @@ struct NearLeaf {
 };
 
 // A near-field work item: window slices [k0, k1) of a leaf (kind 0), or its aux slices (kind 1).
+// a work item: window slices [k0, k1) of a leaf (kind 0), or its aux slices [k0, k1) (kind 1:
+// slice 0 the static tile, slice 1 + q the exponential-tail coefficients of term q)
 struct NearItem {
     int32_t leaf, k0, k1, kind;
 };
@@ -97,8 +99,9 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
 void build_host_tree(const Elements& el, const PlanInputs& in, HostPlan& hp);
 int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
-// vec, vec_aux: sources per 16 bytes of the window and aux storage types (8 FP16, 4 FP32, 2 FP64).
+// vec, vec_aux: sources per 16 bytes of the window and aux storage types (8 FP16, 4 FP32, 2 FP64);
+// chunk, aux_chunk: window and aux slices per work item at most.
 void finish_near_layout(HostPlan& hp, const std::vector<int32_t>& W, const std::vector<char>& has_tail, int chunk,
-                        int vec, int vec_aux);
+                        int vec, int vec_aux, int aux_chunk);
 
 }  // namespace fdph

@@ -44,7 +44,7 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), -1.0, 10, 1e-4, None, ctypes.byref(h)) == fdph.E_ARG
     p = fdph.make_params(leaf_size=64)
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
-    p = fdph.make_params(nrhs=17)
+    p = fdph.make_params(nrhs=3)
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
     bad = xy.copy()
     bad[3, 2] = np.nan

@@ -3,16 +3,18 @@
 Requests (fault geometry, size N, CFL, friction heterogeneity) arrive over time.  A request is
 admitted as soon as its device footprint (plan operator + time-stepping state + outputs) fits
 the HBM budget and a slot is free; admitted scenarios stay resident and all of them advance
-together, each iteration moving every live scenario forward by `chunk` time steps on its own
-CUDA stream, so that the kernels of different scenarios overlap on the device.  A finished
-scenario releases its memory at once and the next waiting request takes its place.  Per
-request the loop records queueing, plan and run times and the time to solution (arrival to
-last step on the device).
+together, each iteration moving every live scenario forward by `chunk` time steps: the
+scenarios with a full chunk ahead as one batch (fdph_batch_rupture_run: every kernel of a step
+is one launch over all of them), the others (a last, shorter chunk) with their own step graphs
+on their own CUDA streams.  A finished scenario releases its memory at once and the next
+waiting request takes its place.  Per request the loop records queueing, plan and run times and
+the time to solution (arrival to last step on the device).
 
-All arithmetic runs in libfdph (fdph_plan, fdph_rupture_init, fdph_rupture_run: one cached step
-graph replayed per chunk); this module only schedules, and builds plans on background threads
-so that planning overlaps the stepping of the live scenarios.  Plans are independent, so a scenario's result is bit-identical alone and in
-the mix (tests/test_gpu_serving.py).
+All arithmetic runs in libfdph (fdph_plan, fdph_rupture_init, fdph_batch_rupture_run,
+fdph_rupture_run: captured step graphs replayed per chunk); this module only schedules, and
+builds plans on background threads so that planning overlaps the stepping of the live
+scenarios.  Plans are independent, so a scenario's result is bit-identical alone and in the mix
+(tests/test_gpu_serving.py).
 """
 import os
 import time

@@ -102,6 +102,7 @@ struct StepArgs {
     double* T_out;            // caller's T_n (geometry order)
     const int* perm;          // internal -> geometry
     double* Dring;            // [WD][N]
+    float* Dring32;           // [WD][N] FP32 copy of Dring (plans whose near-field rows are FP32)
     double* Cring;            // [WC][N]
     double* C;                // [N] cumulative slip (rounded sum)
     double* Ccomp;            // [N] Kahan compensation
@@ -186,6 +187,7 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         if (a0.D_in) a.D_in = a0.D_in + rN;
         if (a0.T_out) a.T_out = a0.T_out + rN;
         a.Dring = a0.Dring + r * a0.rs_D;
+        if (a0.Dring32) a.Dring32 = a0.Dring32 + r * a0.rs_D;
         a.Cring = a0.Cring + r * a0.rs_C;
         a.C = a0.C + rN;
         a.Ccomp = a0.Ccomp + rN;
@@ -202,6 +204,12 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
 
 __global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
 
+// FP32 copy of a restored slip-rate ring
+__global__ void ring_to_float_kernel(const double* x, float* y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+
 __global__ void set_step_kernel(int* n_dev, int v) {
     n_dev[0] = v;   // step index
     n_dev[1] = v;   // step of the call's first row of D / T
@@ -213,12 +221,15 @@ __global__ void set_step_kernel(int* n_dev, int v) {
 template <class T>
 __device__ __forceinline__ void push_body(const StepArgs<T>& a, int p, bool zero) {
     const int n = step_index(a);
+    const size_t slot = (size_t)wrap(n, a.WD) * a.N + p;
     if (zero || !a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
-        a.Dring[(size_t)wrap(n, a.WD) * a.N + p] = 0.0;
+        a.Dring[slot] = 0.0;
+        if (a.Dring32) a.Dring32[slot] = 0.f;
         return;
     }
     const double d = a.D_in[io_offset(a, n) + a.perm[p]];
-    a.Dring[(size_t)wrap(n, a.WD) * a.N + p] = d;
+    a.Dring[slot] = d;
+    if (a.Dring32) a.Dring32[slot] = (float)d;
     // compensated running sum of the slip (units of dt)
     const double y = d - a.Ccomp[p];
     const double c0 = a.C[p];
@@ -436,6 +447,20 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// asynchronous 4- / 8-byte copy global -> shared (cp.async); src_bytes = 0 zero-fills the destination
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// this thread's cp.async copies have landed (a barrier then publishes them to the block)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void consumer_barrier() {
     asm volatile("bar.sync 1, %0;" ::"n"(kNearConsumers * 32) : "memory");
 }
@@ -449,6 +474,7 @@ __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
 // plans the item's own plan), with the plan's step index n.
 struct NearView {
     const double* Dring;
+    const float* Dring32;
     const double* Cring;
     double* vstate;
     const double* rho;
@@ -464,6 +490,7 @@ template <class T>
 __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     NearView v;
     v.Dring = a.Dring;
+    v.Dring32 = a.Dring32;
     v.Cring = a.Cring;
     v.vstate = a.vstate;
     v.rho = a.rho;
@@ -484,34 +511,40 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
 }
 
 // The vectors of one work item (rows of 32 in the row type; with NR right-hand sides row
-// k * NR + r holds slice k of right-hand side r) are gathered by the consumer warps in two
-// halves: near_issue loads this warp's rows (w, w + C, ...) into registers, near_commit (one
-// item later, so that the loads are in flight meanwhile) forms the values and stores them to
-// shared memory.  Window row k: D_{n - k0 - k, j}.  Aux row a = k0 + k: a = 0, C_j(n - W) (the
+// k * NR + r holds slice k of right-hand side r) are gathered by the consumer warps, this warp
+// taking rows w, w + C, ...: window rows D_{n - k0 - k, j} are copied from the slip-rate ring in
+// the row type straight to shared memory (cp.async, issued one item ahead, awaited before the
+// item's closing barrier); aux rows go through registers in two halves, near_issue loading
+// them and near_commit (one item later, so that the loads are in flight meanwhile) forming the
+// values and storing them.  Aux row a = k0 + k: a = 0, C_j(n - W) (the
 // static tile carries dt); a = q + 1, the tail state V_qj(n) = rho_q V_qj(n - 1) + D_{j, n-W},
 // updated here by its only reader.
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
-template <int NR>
+template <class R, int NR>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
-                                           double (&r)[kRowsPerWarp], double (&dW)[NR]) {
+                                           double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb) {
     const int n = a.n;
     const int nsl = near_slices<double>(tk, n);
     const bool on = lane < tk.ns;
-    const size_t col = (size_t)tk.s0 + lane;
+    const size_t col = (size_t)tk.s0 + (on ? lane : 0);   // lanes past ns zero-fill from a valid address
     if (!tk.kind) {
         const int b0 = wrap(n - tk.k0, a.WD);
 #pragma unroll
         for (int m = 0; m < kRowsPerWarp; ++m) {
             const int v = warp + m * kNearConsumers;
             const int k = v / NR, q = v % NR;
-            int slot = b0 - k;                     // k < W < WD: one wrap at most
-            slot += slot < 0 ? a.WD : 0;
-            r[m] = (on && k < nsl) ? a.Dring[q * a.rs_D + (size_t)slot * a.N + col] : 0.0;
+            if (k < nsl) {
+                int slot = b0 - k;                     // k < W < WD: one wrap at most
+                slot += slot < 0 ? a.WD : 0;
+                const size_t off = q * a.rs_D + (size_t)slot * a.N + col;
+                if constexpr (sizeof(R) == 4)
+                    cp_async_4((R*)vb + v * 32 + lane, a.Dring32 + off, on ? 4 : 0);
+                else
+                    cp_async_8((R*)vb + v * 32 + lane, a.Dring + off, on ? 8 : 0);
+            }
         }
-#pragma unroll
-        for (int q = 0; q < NR; ++q) dW[q] = 0.0;
     } else {
         const int t = n - tk.W;
 #pragma unroll
@@ -535,6 +568,7 @@ template <class R, int NR>
 __device__ __forceinline__ void near_commit(const NearView& a, const NearTask& tk, int warp, int lane,
                                             const double (&r)[kRowsPerWarp], const double (&dW)[NR],
                                             unsigned char* vb) {
+    if (!tk.kind) return;   // window rows: asynchronous copies, awaited by cp_async_wait_all
     const int nsl = near_slices<double>(tk, a.n);
 #pragma unroll
     for (int m = 0; m < kRowsPerWarp; ++m) {
@@ -806,9 +840,10 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<NR>(vn, nxt, warp, lane, rows, dW);
+            near_issue<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
             near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
+        cp_async_wait_all();
         consumer_barrier();
         int par = 0;
         for (int ti = t0; ti < t1; ++ti, par ^= 1) {
@@ -818,7 +853,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<NR>(vn, nxt, warp, lane, rows, dW);
+                near_issue<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -875,6 +910,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
                 for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
                 red[par][warp][r][lane] = lane < tk.nr ? tot : 0.0;
             }
+            cp_async_wait_all();
             consumer_barrier();   // also publishes the next item's vectors
             if (warp == 0) {
 #pragma unroll
@@ -1240,6 +1276,7 @@ struct fdph_plan_s {
     double *ustate = nullptr, *vstate = nullptr, *trcoef = nullptr, *phi = nullptr;
     // state
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
+    float* Dring32 = nullptr;   // FP32 copy of Dring (FP32 / FP16 plans)
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
     size_t state_bytes = 0;
     // host staging for fdph_step_host
@@ -1316,6 +1353,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.T_out = T_;
     a.perm = P->perm;
     a.Dring = P->Dring;
+    a.Dring32 = P->Dring32;
     a.Cring = P->Cring;
     a.C = P->C;
     a.Ccomp = P->Ccomp;
@@ -2686,6 +2724,11 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_pos.size())) ||
         (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
         return fail(rc);
+    if (P->precision != FDPH_FP64) {   // FP32 copy of the slip-rate ring for the near-field rows
+        const size_t c = (size_t)P->WD * P->N * P->nrhs;
+        if ((rc = dalloc(P, &P->Dring32, c))) return fail(rc);
+        sb += c * 4;
+    }
     P->state_bytes = sb;
     P->partial_cap = std::max<size_t>(hp.items.size() * 32, 1);
     if ((rc = fdph_reset(P))) return fail(rc);
@@ -2707,6 +2750,8 @@ int fdph_reset(fdph_plan_t P) {
     for (int q = 0; q < 10; ++q)   // every right-hand side: [nrhs][max(count, 1)]
         if (bufs[q])
             FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, std::max<size_t>(cnt[q], 1) * P->nrhs * sizeof(double), P->stream));
+    if (P->Dring32)
+        FDPH_CUDA(cudaMemsetAsync(P->Dring32, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(float), P->stream));
     if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->n = 0;
@@ -2948,6 +2993,11 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
     for (int q = 0; q < 8; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice, P->stream));
         o += cnt[q] * sizeof(double);
+    }
+    if (P->Dring32) {
+        const long long c = (long long)P->WD * P->N * P->nrhs;
+        ring_to_float_kernel<<<blocks(c, 256), 256, 0, P->stream>>>(P->Dring, P->Dring32, c);
+        FDPH_CUDA(cudaGetLastError());
     }
     FDPH_CUDA(cudaStreamSynchronize(P->stream));   // the caller may reuse the buffer on return
     P->n = hdr[0];

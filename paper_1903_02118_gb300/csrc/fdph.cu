@@ -522,7 +522,7 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
-template <class R, int NR>
+template <class R, int NR, int VR>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
                                            double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb) {
     const int n = a.n;
@@ -532,7 +532,7 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
     if (!tk.kind) {
         const int b0 = wrap(n - tk.k0, a.WD);
 #pragma unroll
-        for (int m = 0; m < kRowsPerWarp; ++m) {
+        for (int m = 0; m < VR / kNearConsumers; ++m) {
             const int v = warp + m * kNearConsumers;
             const int k = v / NR, q = v % NR;
             if (k < nsl) {
@@ -597,12 +597,20 @@ template <> struct NearTypes<__half> { using Aux = float; using Row = float; };
 template <class H, int NR = 1>
 struct NearCfg {
     using R = typename NearTypes<H>::Row;
-    // shared-memory pipeline depth (fewer stages with several right-hand sides: their partial
-    // sums take static shared memory)
-    static constexpr int stages = sizeof(R) == 4 && NR < 4 ? 5 : 4;
-    static constexpr int vec_bytes = kChunk * 32 * (int)sizeof(R);  // one item's vectors
+    // vector rows of one item: 64, or 128 for several right-hand sides in FP32 rows (their window
+    // rows go by cp.async, without registers), so that items stay 128 / NR slices long
+    static constexpr int vec_rows = NR >= 2 && sizeof(R) == 4 ? 2 * kChunk : kChunk;
+    // shared-memory pipeline depth, within two CTAs per SM next to the vector buffers and the
+    // partial sums of the right-hand sides
+    static constexpr int stages = NR >= 8 ? 3 : NR >= 2 ? 4 : sizeof(R) == 4 ? 5 : 4;
+    static constexpr int vec_bytes = vec_rows * 32 * (int)sizeof(R);  // one item's vectors
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
 };
+
+// the longest work item (window slices) of a plan: the item's vector rows over its right-hand sides
+static inline int near_max_chunk(int nrhs, int precision) {
+    return (nrhs >= 2 && precision != FDPH_FP64 ? 2 * kChunk : kChunk) / nrhs;
+}
 
 // slice . vector for one receiver lane: 16-byte loads of the source-interleaved slice (plan.h)
 // and of the vector row; products and the sum in the row type
@@ -840,7 +848,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
+            near_issue<R, NR, C::vec_rows>(vn, nxt, warp, lane, rows, dW, vbuf);
             near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         cp_async_wait_all();
@@ -853,7 +861,7 @@ __global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, co
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+                near_issue<R, NR, C::vec_rows>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -1939,7 +1947,7 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
     long long slices = 0;
     for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
     // (with nrhs right-hand sides an item's vectors, nrhs per slice, fill the same buffer)
-    int chunk = kChunk / P->nrhs;
+    int chunk = near_max_chunk(P->nrhs, P->precision);
     while (chunk > std::max(1, 8 / P->nrhs) && slices / chunk < 4LL * 152 * 3) chunk /= 2;
     finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A), kChunk / P->nrhs);
     P->near_W = W;
@@ -2888,7 +2896,8 @@ int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
     cudaEvent_t e0, e1;
     FDPH_CUDA(cudaEventCreate(&e0));
     FDPH_CUDA(cudaEventCreate(&e1));
-    const int cands[3] = {kChunk / P->nrhs, kChunk / 2 / P->nrhs, kChunk / 4 / P->nrhs};
+    const int cmax = near_max_chunk(P->nrhs, P->precision);
+    const int cands[3] = {cmax, cmax / 2, cmax / 4};
     int best = P->chunk;
     float best_ms = 1e30f;
     for (int c : cands) {

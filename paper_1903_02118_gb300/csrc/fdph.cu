@@ -1,7 +1,8 @@
 // fdph.cu -- device side of the FDP=H time step and the C ABI (include/fdph.h).
 //
-// One time step n (Eq. 4 evaluated through the plan's operator) runs these kernels in order
-// on the plan's stream:
+// One time step n (Eq. 4 evaluated through the plan's operator) runs these kernels (captured
+// as one CUDA graph: FIR + scatter and transient + Eq. 39 on two side streams, concurrently with
+// the near field, all joined before gather; grid y = right-hand side):
 //   push     D_n -> slip-rate ring (internal order); cumulative slip C_j(n) = sum_{s<=n} D_j,s
 //            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring
 //   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}
@@ -17,6 +18,8 @@
 //            partials, written in the caller's element order
 // Causality (min(dm + delay) >= 1, checked at plan time) guarantees that the ring slots read
 // at step n were completed by steps < n and that the slots written at step n are not read.
+// A rupture step (Sec. 6.2) predicts with D_n = 0, solves the friction law per element and
+// then commits D_n; a batch of plans runs each of these kernels as one launch over all plans.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>

@@ -784,8 +784,11 @@ __device__ __forceinline__ void slice_dot_nr(const __half* buf, const float* vro
 // several plans in one launch (fdph_batch_run); item tk belongs to plan scen[tk.scen].  NR: the
 // plan's right-hand sides, consumed together (each coefficient read once per step, the vectors
 // of all right-hand sides in the item's vector buffer).
+// (one right-hand side: registers bounded as for three CTAs per SM, ~128 per thread, although
+// shared memory admits two: the far-field kernels of the step then find room beside it and
+// finish alongside it instead of after it)
 template <class T, class H, bool kBatch, int NR>
-__global__ void __launch_bounds__(kNearThreads, 2) near_kernel(StepArgs<T> a, const StepArgs<T>* scen) {
+__global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(StepArgs<T> a, const StepArgs<T>* scen) {
     using C = NearCfg<H, NR>;
     using A = typename NearTypes<H>::Aux;
     using R = typename NearTypes<H>::Row;

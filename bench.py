@@ -334,6 +334,8 @@ def main():
     ap.add_argument("--lmin", type=float, default=None, help="lmin of Eq. 9 / Eq. 25, in element lengths")
     ap.add_argument("--leaf", type=int, default=None, help="largest cluster of an inadmissible leaf")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides (slip-rate histories) per step")
+    ap.add_argument("--far-mode", type=int, default=0, choices=[0, 1],
+                    help="Eq. 42: 0 scatter into delay rings, 1 delayed-history gather (Sec. 5.3)")
     ap.add_argument("--extra-steps", type=int, default=None,
                     help="n_c: steps of Domain F beyond the source duration (default 10 dx / (c dt))")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
@@ -396,7 +398,7 @@ def main():
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
                      eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
-                     extra_steps=cfg.get("extra_steps", -1), nrhs=R)
+                     extra_steps=cfg.get("extra_steps", -1), nrhs=R, far_mode=args.far_mode)
     plan_s = time.perf_counter() - t0
     # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
     # profiler commands rely on)
@@ -503,7 +505,7 @@ def main():
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
                        "eta_scheme": cfg.get("eta_scheme", 0), "lmin": cfg.get("lmin", 0.0),
-                       "extra_steps": cfg.get("extra_steps", -1), "nrhs": R,
+                       "extra_steps": cfg.get("extra_steps", -1), "nrhs": R, "far_mode": args.far_mode,
                        "first_timed_step": n0 + W, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -120,6 +120,13 @@ typedef struct fdph_params {
                              multiplied with the slip rates of all RHS (near-field work items
                              are nrhs times shorter).  Rupture, fdph_predict / fdph_commit and
                              batches take nrhs = 1 (FDPH_E_ARG otherwise) */
+    int32_t far_mode;     /* Eq. 42 of the admissible blocks: 0 (default) scatter -- each step adds
+                             g_{l,j} u_j into the delay-ring slots n + delay_j; 1 the delayed-history
+                             gather of Sec. 5.3 -- each step records u_j(n) in a history of the last
+                             maxdelay - mindelay + 1 steps per block and computes the one slot it
+                             completes, Tbar'_l[n + mindelay] = sum_j g_{l,j} u_j(n + mindelay -
+                             delay_j).  Same arithmetic (up to summation order) with more memory
+                             (the histories); batches take far_mode 0 */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */
@@ -287,8 +294,8 @@ int fdph_synchronize(fdph_plan_t plan);
 /* Copy the plan's statistics. */
 int fdph_get_stats(fdph_plan_t plan, fdph_stats* stats);
 
-/* Save / restore the time-stepping state (rings, accumulators, step index) to / from a host
- * buffer.  fdph_save_state with buf == NULL sets *len to the size needed.  Restoring into a
+/* Save / restore the time-stepping state (rings, accumulators, histories, step index; with a
+ * friction law attached, the accumulated slip too) to / from a host buffer.  fdph_save_state with buf == NULL sets *len to the size needed.  Restoring into a
  * plan built from the same inputs reproduces the continuation bit for bit. */
 int fdph_save_state(fdph_plan_t plan, void* buf, size_t* len);
 int fdph_load_state(fdph_plan_t plan, const void* buf, size_t len);

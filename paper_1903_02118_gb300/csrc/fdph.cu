@@ -71,8 +71,10 @@ static const long long kWaitLimit = 1LL << 22;   // bounded mbarrier polls befor
 // device-side views
 
 struct SbDev {
-    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, ident, e0, pad;
+    int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, ident, e0, LH;
     long long f, g, h, ring, zring, dhat, delay, dm, ustate, trc, phi;
+    long long uhist;    // delayed-history form: [LH][ns] source values u_j of the last LH steps
+    int mindelay, pad;
 };
 
 struct NearDev {
@@ -160,6 +162,12 @@ struct StepArgs {
     // (elements); the caller's rows D_n, T_n are [nrhs][N] (io_stride = nrhs N per step)
     int nrhs;
     long long rs_D, rs_C, rs_ring, rs_zring, rs_dhat, rs_fval, rs_ustate, rs_vstate, rs_partial;
+    // delayed-history form of Eq. 42 (far_mode 1)
+    double* uhist;            // [blocks][LH][ns] source values
+    long long rs_uhist;
+    const int2* rec_tasks;    // (block, source) recorded per step
+    const int2* gat_tasks;    // (block, rank index) gathered per step
+    int n_rec, n_gat;
 };
 
 // ring slot of step a (a may be negative; |a| < 2^31)
@@ -201,6 +209,7 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         if (a0.ustate) a.ustate = a0.ustate + r * a0.rs_ustate;
         if (a0.vstate) a.vstate = a0.vstate + r * a0.rs_vstate;
         a.partial = a0.partial + r * a0.rs_partial;
+        if (a0.uhist) a.uhist = a0.uhist + r * a0.rs_uhist;
     }
     return a;
 }
@@ -340,6 +349,56 @@ __global__ void scatter_kernel(StepArgs<T> a0) {
     const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w < a.n_sct) scatter_body(a, w, threadIdx.x & 31);
+}
+
+// Delayed-history form of Eq. 42 (the gather variant of Sec. 5.3): instead of adding g_{l,j} u_j
+// to the future slots n + delay_j, every step records u_j(n) in the block's history of the last
+// LH = maxdelay - mindelay + 1 steps and computes the one slot that the step completes,
+//     Tbar'_l[n + mindelay] = sum_j g_{l,j} u_j(n + mindelay - delay_j),
+// by causality (min(dm + delay) >= 1) a slot no evaluation of step n reads yet.
+template <class T>
+__device__ __forceinline__ void record_body(const StepArgs<T>& a, int q) {
+    const int n = step_index(a);
+    const int2 t = a.rec_tasks[q];
+    const SbDev& sb = a.sbs[t.x];
+    const int dslot = sb.kind == SB_TR ? wrap(n, a.WD) : 0;
+    a.uhist[sb.uhist + (long long)wrap(n, sb.LH) * sb.ns + t.y] = source_value(a, sb, t.y, dslot);
+}
+
+template <class T>
+__global__ void record_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < a.n_rec) record_body(a, q);
+}
+
+// one warp per (block, rank index l), lanes over the sources
+template <class T>
+__device__ __forceinline__ void hgather_body(const StepArgs<T>& a, int w, int lane) {
+    const int n = step_index(a);
+    const int2 t = a.gat_tasks[w];
+    const SbDev& sb = a.sbs[t.x];
+    const int l = t.y;
+    const int s = n + sb.mindelay;
+    const int* dl = a.ints + sb.delay;
+    const double* u = a.uhist + sb.uhist;
+    double acc = 0.0;
+    if (sb.ident == 2) {   // G is the identity: rank index l is source l
+        if (lane == 0) acc = u[(long long)wrap(s - dl[l], sb.LH) * sb.ns + l];
+    } else {
+        const T* g = a.fac + sb.g;
+        for (int j = lane; j < sb.ns; j += 32)
+            acc += (double)g[(long long)j * sb.rank + l] * u[(long long)wrap(s - dl[j], sb.LH) * sb.ns + j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
+    if (lane == 0) a.ring[sb.ring + (long long)wrap(s, sb.L) * sb.rank + l] = acc;
+}
+
+template <class T>
+__global__ void hgather_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w < a.n_gat) hgather_body(a, w, threadIdx.x & 31);   // warp-uniform
 }
 
 // one warp per (transient block, rank index)
@@ -1259,6 +1318,11 @@ struct fdph_plan_s {
     bool own_stream = false;
     int N = 0, M = 0, n = 0, WD = 1, WC = 1;
     int nrhs = 1;             // right-hand sides (slip-rate histories) stepped together
+    int far_mode = 0;         // 0: Eq. 42 as scatter into delay rings; 1: delayed-history gather
+    long long uhist_len = 0;  // far_mode 1: source-value histories (doubles per right-hand side)
+    int2 *rec_tasks = nullptr, *gat_tasks = nullptr;
+    int n_rec = 0, n_gat = 0;
+    double* uhist = nullptr;
     double dt = 0;
     HostPlan hp;
     fdph_stats st;
@@ -1423,6 +1487,12 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.rs_ustate = std::max<long long>(P->hp.ustate_len, 1);
     a.rs_vstate = std::max<long long>(P->hp.vstate_len, 1);
     a.rs_partial = std::max<long long>((long long)P->partial_cap, 1);
+    a.uhist = P->uhist;
+    a.rs_uhist = std::max<long long>(P->uhist_len, 1);
+    a.rec_tasks = P->rec_tasks;
+    a.gat_tasks = P->gat_tasks;
+    a.n_rec = P->n_rec;
+    a.n_gat = P->n_gat;
     return a;
 }
 
@@ -1435,6 +1505,18 @@ struct ProfScope {
     ProfScope(fdph_plan_t P_, int id_);
     ~ProfScope();
 };
+
+// Eq. 42 of a step: scatter into the delay rings, or (far_mode 1) record the source values and
+// gather the completed slot from the histories
+template <class T>
+static void eq42(const StepArgs<T>& a, cudaStream_t s) {
+    if (a.n_rec) {
+        record_kernel<T><<<dim3(blocks(a.n_rec, 128), a.nrhs), 128, 0, s>>>(a);
+        if (a.n_gat) hgather_kernel<T><<<dim3(blocks((long long)a.n_gat * 32, 128), a.nrhs), 128, 0, s>>>(a);
+    } else if (a.n_sct) {
+        scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a);
+    }
+}
 
 template <class T, class H, int NR>
 static void launch_near_nr(cudaLaunchConfig_t& cfg, const StepArgs<T>& a) {
@@ -1487,7 +1569,7 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
         cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
         if (a.n_fir) fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
-        if (a.n_sct) scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+        eq42<T>(a, P->side[0]);
         if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
         if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
         if (a.n_cta) launch_near<T>(P, a, s);
@@ -1500,7 +1582,7 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     }
     // serial order (per-kernel timing)
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
-    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a); }
+    { ProfScope ps(P, 2); eq42<T>(a, s); }
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
@@ -1714,7 +1796,7 @@ static void enqueue_commit(fdph_plan_t P, StepArgs<T> a, const double* D, cudaSt
     a.D_in = D;
     { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }
     if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
-    if (a.n_sct) { ProfScope ps(P, 2); scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a); }
+    { ProfScope ps(P, 2); eq42<T>(a, s); }
 }
 
 // One rupture step (Sec. 6.2): predict, solve the friction law element by element, commit D_n.
@@ -2503,10 +2585,11 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
               (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
               (p->nrhs != 0 && p->nrhs != 1 && p->nrhs != 2 && p->nrhs != 4 && p->nrhs != kMaxRhs) ||
+              (p->far_mode != 0 && p->far_mode != 1) ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
         set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
-                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), precision FP64, FP32 or FP16, "
+                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), far_mode 0 or 1, precision FP64, FP32 or FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -2609,6 +2692,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     P->device = p.device;
     P->precision = p.precision;
     P->nrhs = std::max(p.nrhs, 1);
+    P->far_mode = p.far_mode;
     P->N = geometry->n;
     P->M = M;
     P->dt = dt;
@@ -2671,11 +2755,25 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     std::vector<SbDev> sd(hp.sbs.size());
     for (size_t q = 0; q < sd.size(); ++q) {
         const SubBlock& b = hp.sbs[q];
+        const int LH = b.maxdelay - b.mindelay + 1;
         sd[q] = {b.kind, b.rank, b.r0, b.nr, b.s0, b.ns, b.L, b.LZ, b.taps, b.maxdelay, b.mindm, b.run0,
-                 b.soe, b.ident, b.e0, 0, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
+                 b.soe, b.ident, b.e0, LH, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
                  (long long)b.dhat, (long long)b.delay, (long long)b.dm, (long long)b.ustate, (long long)b.trc,
-                 (long long)b.phi};
+                 (long long)b.phi, 0, b.mindelay, 0};
     }
+    // delayed-history form of Eq. 42 (far_mode 1): per block a history [LH][ns] of the source
+    // values, recorded every step, and one gather task per (block, rank index)
+    std::vector<int2> rec, gat;
+    if (P->far_mode == 1)
+        for (size_t q = 0; q < sd.size(); ++q) {
+            sd[q].uhist = P->uhist_len;
+            P->uhist_len += (long long)sd[q].LH * sd[q].ns;
+            for (int j = 0; j < sd[q].ns; ++j) rec.push_back(make_int2((int)q, j));
+            for (int l = 0; l < sd[q].rank; ++l) gat.push_back(make_int2((int)q, l));
+        }
+    P->n_rec = (int)rec.size();
+    P->n_gat = (int)gat.size();
+    if ((rc = upload(P, &P->rec_tasks, rec)) || (rc = upload(P, &P->gat_tasks, gat))) return fail(rc);
     // warp tasks: 2^lg lanes per run (scatter) / per receiver (Eq. 39), 2^lg the rank rounded up
     // to a power of two (at most 32); identity factors need one lane
     std::vector<int4> sct, evt;
@@ -2736,7 +2834,8 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = st(&P->C, P->N)) || (rc = st(&P->Ccomp, P->N)) || (rc = st(&P->ring, hp.ring_len)) ||
         (rc = st(&P->zring, hp.zring_len)) || (rc = st(&P->dhat, hp.dhat_len)) ||
         (rc = st(&P->partial, hp.items.size() * 32)) || (rc = st(&P->fval, hp.e_pos.size())) ||
-        (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)))
+        (rc = st(&P->ustate, hp.ustate_len)) || (rc = st(&P->vstate, hp.vstate_len)) ||
+        (rc = st(&P->uhist, (size_t)P->uhist_len)))
         return fail(rc);
     if (P->precision != FDPH_FP64) {   // FP32 copy of the slip-rate ring for the near-field rows
         const size_t c = (size_t)P->WD * P->N * P->nrhs;
@@ -2757,11 +2856,11 @@ int fdph_reset(fdph_plan_t P) {
     P->predicted = false;
     cudaSetDevice(P->device);
     double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->dhat, P->partial,
-                      P->ustate, P->vstate};
+                      P->ustate, P->vstate, P->uhist};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.dhat_len,
-                    P->partial_cap, (size_t)P->hp.ustate_len, (size_t)P->hp.vstate_len};
-    for (int q = 0; q < 10; ++q)   // every right-hand side: [nrhs][max(count, 1)]
+                    P->partial_cap, (size_t)P->hp.ustate_len, (size_t)P->hp.vstate_len, (size_t)P->uhist_len};
+    for (int q = 0; q < 11; ++q)   // every right-hand side: [nrhs][max(count, 1)]
         if (bufs[q])
             FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, std::max<size_t>(cnt[q], 1) * P->nrhs * sizeof(double), P->stream));
     if (P->Dring32)
@@ -2955,13 +3054,15 @@ int fdph_get_stats(fdph_plan_t P, fdph_stats* s) {
 int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     if (!P || !len) return FDPH_E_ARG;
     if (P->predicted) return pending_commit(P);
-    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate};
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate, P->uhist,
+                      P->rupture ? P->fr.slip : nullptr};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
-                    (size_t)P->hp.vstate_len};
+                    (size_t)P->hp.vstate_len, (size_t)P->uhist_len, 0};
     for (size_t& c : cnt) c = c ? c * P->nrhs : 0;   // [nrhs][count] (a zero count stays empty)
+    if (P->rupture) cnt[9] = (size_t)P->N;             // the friction law's accumulated slip
     size_t need = sizeof(int32_t) * 2;
-    for (int q = 0; q < 8; ++q) need += cnt[q] * sizeof(double);
+    for (int q = 0; q < 10; ++q) need += cnt[q] * sizeof(double);
     if (!buf) {
         *len = need;
         return FDPH_OK;
@@ -2972,7 +3073,7 @@ int fdph_save_state(fdph_plan_t P, void* buf, size_t* len) {
     int32_t hdr[2] = {P->n, P->N};
     memcpy(o, hdr, sizeof(hdr));
     o += sizeof(hdr);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 10; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(o, bufs[q], cnt[q] * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
         o += cnt[q] * sizeof(double);
     }
@@ -2999,13 +3100,15 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
         return FDPH_E_ARG;
     }
     o += sizeof(hdr);
-    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate};
+    double* bufs[] = {P->Dring, P->Cring, P->C, P->Ccomp, P->ring, P->zring, P->ustate, P->vstate, P->uhist,
+                      P->rupture ? P->fr.slip : nullptr};
     size_t cnt[] = {(size_t)P->WD * P->N, (size_t)P->WC * P->N, (size_t)P->N, (size_t)P->N,
                     (size_t)P->hp.ring_len, (size_t)P->hp.zring_len, (size_t)P->hp.ustate_len,
-                    (size_t)P->hp.vstate_len};
+                    (size_t)P->hp.vstate_len, (size_t)P->uhist_len, 0};
     for (size_t& c : cnt) c = c ? c * P->nrhs : 0;   // [nrhs][count] (a zero count stays empty)
+    if (P->rupture) cnt[9] = (size_t)P->N;             // the friction law's accumulated slip
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 10; ++q) {
         if (cnt[q]) FDPH_CUDA(cudaMemcpyAsync(bufs[q], o, cnt[q] * sizeof(double), cudaMemcpyHostToDevice, P->stream));
         o += cnt[q] * sizeof(double);
     }
@@ -3205,8 +3308,8 @@ int fdph_batch_create(const fdph_plan_t* plans, int32_t count, fdph_batch_t* out
             return FDPH_E_ARG;
         }
         if (plans[p]->predicted) return pending_commit(plans[p]);
-        if (plans[p]->nrhs != 1) {
-            set_error("fdph_batch_create: batches take plans of one right-hand side (nrhs = 1)");
+        if (plans[p]->nrhs != 1 || plans[p]->far_mode != 0) {
+            set_error("fdph_batch_create: batches take plans of one right-hand side (nrhs = 1) and far_mode 0");
             return FDPH_E_ARG;
         }
     }

@@ -37,7 +37,8 @@ class Params(ctypes.Structure):
                 ("leaf_size", ctypes.c_int32), ("extra_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("far_mode", ctypes.c_int32)]
 
 
 class Friction(ctypes.Structure):
@@ -161,11 +162,11 @@ def default_params():
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
                 device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None,
-                nrhs=None):
+                nrhs=None, far_mode=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
-                 ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs),
+                 ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs), ("far_mode", far_mode),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)

@@ -46,6 +46,8 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
     p = fdph.make_params(nrhs=3)
     assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
+    p = fdph.make_params(far_mode=2)
+    assert L.fdph_plan(ctypes.byref(g), ctypes.byref(m), 0.5, 10, 1e-4, ctypes.byref(p), ctypes.byref(h)) == fdph.E_ARG
     bad = xy.copy()
     bad[3, 2] = np.nan
     gb = fdph.Geometry(8, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))

@@ -452,3 +452,64 @@ def test_multiple_right_hand_sides_equal_single_rhs_plans(prec, R):
     assert c <= (64 if prec == fdph.FP64 else 128) // R
     with pytest.raises(fdph.FdphError):
         plan.predict(Td[0])                                 # single-RHS calls refuse nrhs > 1
+
+
+@pytest.mark.parametrize("geom,N,M,soe,prec", [("curved", 256, 320, 0, fdph.FP64), ("kinked", 200, 900, 16, fdph.FP64),
+                                               ("curved", 180, 300, 16, fdph.FP32)])
+def test_delayed_history_gather_equals_scatter(geom, N, M, soe, prec):
+    """Eq. 42 in the delayed-history gather form of Sec. 5.3 (far_mode 1) gives the scatter form's
+    traction (summation order aside) and, in FP64, the oracle's compressed operator; also with
+    rupture steps and after a state save / restore."""
+    _need_gpu()
+    eps, leaf = 1e-5, 16
+    eps_st = 1e-4 if soe else 1e-6
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    kw = dict(eta=0.5, eps_st=eps_st, leaf_size=leaf, soe_terms=soe, precision=prec)
+    T = [_run(fdph.Plan(xy, 0.5, M, eps, far_mode=f, **kw), D) for f in (0, 1)]
+    assert _rel(T[1], T[0]) < (1e-13 if prec == fdph.FP64 else 1e-6)
+    if prec == fdph.FP64 and soe == 0:
+        T0, _ = _oracle_fdph(xy, M, eps, leaf, D)
+        assert _rel(T[1], T0) < TOL64
+    # a restored state continues bit for bit (the histories are part of the state)
+    plan = fdph.Plan(xy, 0.5, M, eps, far_mode=1, **kw)
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    torch.cuda.synchronize()
+    plan.run(M // 2, Dd, Td)
+    plan.synchronize()
+    buf = plan.save_state()
+    plan.run(M - M // 2, Dd[M // 2:], Td[M // 2:])
+    plan.synchronize()
+    T_cont = Td.cpu().numpy()
+    plan.load_state(buf)
+    plan.run(M - M // 2, Dd[M // 2:], Td[M // 2:])
+    plan.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), T_cont)
+    # rupture steps (predict, friction, commit) through the history form
+    rng = np.random.default_rng(inputs.seed_for(7, inputs.FRICTION))
+    tau0 = 0.45 * (1.0 + 0.05 * rng.standard_normal(N))
+    tau0[N // 2 - 8:N // 2 + 8] = 0.61
+    t0 = torch.from_numpy(tau0).cuda()
+    out = []
+    for f in (0, 1):
+        plan = fdph.Plan(xy, 0.5, M, eps, far_mode=f, **kw)
+        plan.rupture_init(t0, 1.0, 0.6, 0.3, 2.0)
+        Dr = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+        Tr = torch.zeros_like(Dr)
+        torch.cuda.synchronize()
+        plan.rupture_run(M // 2, Dr, Tr)
+        plan.synchronize()
+        buf = plan.save_state()                # includes the friction law's accumulated slip
+        plan.rupture_run(M - M // 2, Dr[M // 2:], Tr[M // 2:])
+        plan.synchronize()
+        out.append((Dr.cpu().numpy(), Tr.cpu().numpy()))
+        plan.load_state(buf)                   # the continuation repeats bit for bit
+        Tr.zero_()
+        torch.cuda.synchronize()
+        plan.rupture_run(M - M // 2, Dr[M // 2:], Tr[M // 2:])
+        plan.synchronize()
+        assert np.array_equal(Tr[M // 2:].cpu().numpy(), out[-1][1][M // 2:])
+    assert (out[0][0] > 0).mean() > 0.1
+    tol = 1e-10 if prec == fdph.FP64 else 1e-5
+    assert _rel(out[1][0], out[0][0]) < tol and _rel(out[1][1], out[0][1]) < tol

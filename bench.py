@@ -293,7 +293,7 @@ def batch_vs_streams(fdph, serving, count=16, chunk=64, rounds=4):
             p.reset()
             p.rupture_init(t0, 1.0, 0.6, 0.3, 6.4)
         batch = fdph.Batch(plans) if batched else None
-        for k in range(rounds + 1):          # round 0: graph capture, untimed
+        for k in range(rounds + 1):          # chunk 0: graph capture, untimed
             if k == 1:
                 for p in plans:
                     p.synchronize()
@@ -543,7 +543,7 @@ def main():
 def accuracy_variant(fdph, torch, xy, D, Dd, Td, cfg, prec, device, stream, K, W, rows, T_or, world):
     """The same workload under the constant eta^2 dist admissibility (Eq. 25; eta0 = 1/4,
     lmin = 8, leaf 8) with a Domain-F extra width of 2 steps: the most accurate setting measured
-    at a cost within a few times the configs' plan.  Throughput over K steady-state steps and
+    at a cost within a few times the default workload's plan.  Throughput over K steady-state steps and
     the error against the same plain-march receivers."""
     N, M = cfg["N"], cfg["M"]
     var = dict(eta=0.25, eta_scheme=1, lmin=8.0, leaf=8, extra_steps=2)

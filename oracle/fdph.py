@@ -37,7 +37,7 @@ LRA (Sec. 2.3 criterion |K - K_LRA|_F < eps |K|_F): truncated SVD with the
 minimal rank meeting the criterion; the block is kept exact when
 rank * (N_r + N_s) >= N_r * N_s (the "original rank" fallback of Sec. 6.2).
 
-Readings where the paper is silent or garbled (listed in the design doc):
+Readings where the paper is silent or garbled:
 * eps_t = 1; leaf size bounds the inadmissible clusters; l_min = 0 by default.
 * Khat^F_ij is integrated over the ART-shifted discrete window of the pair.
 * Near a nodal direction the waveform of one stress component is ill

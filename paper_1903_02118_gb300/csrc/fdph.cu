@@ -2031,7 +2031,7 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
         FDPH_CUDA(cudaMemcpyAsync(d_ms, ms.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, P->stream));
     }
     // work-item length: the longest chunk (kChunk) that still yields about four waves of
-    // resident CTAs (152 SMs x 3), so small problems (the plain config) fill the device too
+    // resident CTAs (152 SMs x 3), so small problems (the plain N = 256 march) fill the device too
     long long slices = 0;
     for (int l = 0; l < nl; ++l) slices += std::max(W[l], 1);
     // (with nrhs right-hand sides an item's vectors, nrhs per slice, fill the same buffer)

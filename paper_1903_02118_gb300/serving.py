@@ -38,8 +38,8 @@ class Request:
         self.last_D = self.last_T = None
 
     def inputs(self):
-        """Fault trace and prestress (config-3 friction: 0.45 + 5 % Gaussian heterogeneity, an
-        overstressed nucleation patch of 64 elements at 0.61; mu_s 0.6, mu_d 0.3, Dc = 6.4)."""
+        """Fault trace and prestress for linear slip weakening (0.45 + 5 % Gaussian heterogeneity,
+        an overstressed nucleation patch of 64 elements at 0.61; mu_s 0.6, mu_d 0.3, Dc = 6.4)."""
         if self.geometry == "curved":
             xy = inputs.curved_fault(self.N, inputs.seed_for(self.seed, inputs.GEOMETRY))
         else:

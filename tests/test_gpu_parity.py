@@ -48,7 +48,8 @@ def _geom(name, N):
 
 @pytest.mark.parametrize("geom,N,M", [("straight", 256, 256), ("kinked", 203, 150)])
 def test_plain_st_biem_fp64(geom, N, M):
-    """Config 1 (N = 256, M = 256, CFL 1/2, Gaussian-filtered slip rate) and a ragged kinked case."""
+    """The plain straight-fault workload (N = 256, M = 256, CFL 1/2, Gaussian-filtered slip rate)
+    and a ragged kinked case."""
     _need_gpu()
     xy = _geom(geom, N)
     D = inputs.gaussian_filtered_history(N, M, inputs.seed_for(0, inputs.SLIP))
@@ -158,7 +159,7 @@ def test_step_run_host_reset_and_state_are_consistent():
 
 
 def test_config2_full_size_sampled_receivers():
-    """Config 2 at full size (curved N = 4096, M = 4096, eps = 1e-4, leaf 32, eta = 1/2), in the
+    """The curved-fault workload at full size (N = 4096, M = 4096, eps = 1e-4, leaf 32, eta = 1/2), in the
     launch configuration the benchmark times, against the oracle's compressed operator on sampled
     receivers (all steps)."""
     _need_gpu()

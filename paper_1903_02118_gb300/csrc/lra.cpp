@@ -3,13 +3,15 @@
 // The criterion of the paper is |K_a - K_a,LRA|_F < eps |K_a|_F.  The best approximation of a
 // given rank is the truncated SVD, so the rank chosen here is the smallest r whose discarded
 // singular values satisfy the criterion.  The SVD is computed in two exact stages:
-//   1. Householder QR with column pivoting, stopped once the trailing block is below
+//   1. Householder QR with column pivoting (column norms downdated, recomputed on cancellation),
+//      stopped once the trailing block is below
 //      1e-11 |A|_F (A P = Q R + E): E changes the factors by at most 1e-11 relative, far
 //      below any criterion eps used with the method, and it is counted in the discarded part
 //      of the rank decision.  Rounding noise of the kernel values makes the numerical rank
 //      at 1e-15 nearly full (512 x 512 blocks: ~490-514); at 1e-11 the mean k of the curved
 //      N = 4096 plan is 16 (30 at 1e-12), and the Jacobi stage below costs O(n k^2) a sweep;
-//   2. one-sided (Hestenes) Jacobi SVD of the k x n row space R P^T.
+//   2. SVD of the k x n row space B = R P^T: Householder QR of B^T, then one-sided (Hestenes)
+//      Jacobi on the k x k triangular factor.
 // Factors are balanced: F = U_r sqrt(S_r), G = V_r sqrt(S_r).  When the chosen rank would
 // store at least as many numbers as the block (rank (m + n) >= m n) the block is kept exact
 // (the fallback of Sec. 6.2): F = I, G = A^T (or F = A, G = I).
@@ -24,6 +26,20 @@
 namespace fdph {
 
 namespace {
+
+// x . y over n entries with four partial sums (independent chains the compiler can pipeline)
+inline double dot4(const double* x, const double* y, int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 3 < n; i += 4) {
+        s0 += x[i] * y[i];
+        s1 += x[i + 1] * y[i + 1];
+        s2 += x[i + 2] * y[i + 2];
+        s3 += x[i + 3] * y[i + 3];
+    }
+    for (; i < n; ++i) s0 += x[i] * y[i];
+    return (s0 + s1) + (s2 + s3);
+}
 
 // One-sided Jacobi on the columns of X (rows x cols, column-major), accumulating V.
 // On return columns of X are mutually orthogonal: X_in = X_out V^T.
@@ -104,28 +120,38 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
         for (int j = 0; j < n; ++j) W[(size_t)j * m + i] = A[(size_t)i * n + j];
     std::vector<int> piv(n);
     std::iota(piv.begin(), piv.end(), 0);
-    std::vector<double> cn(n), tau;
+    std::vector<double> tau;
     std::vector<std::vector<double>> hv;  // Householder vectors (length m - k)
     const int kmax = std::min(m, n);
     int k = 0;
     const double stop2 = 1e-22 * norm2;
+    // squared norms of the columns' trailing parts, downdated after each reflection (cn) and
+    // recomputed from the column when the downdate has cancelled most of the value they had at
+    // their last recomputation (cn0), as in the usual pivoted QR
+    auto trailing = [&](int j, int from) {
+        const double* col = &W[(size_t)j * m] + from;
+        return dot4(col, col, m - from);
+    };
+    std::vector<double> cn(n), cn0(n);
+    for (int j = 0; j < n; ++j) cn[j] = cn0[j] = trailing(j, 0);
     for (; k < kmax; ++k) {
         double trail = 0.0;
-        int best = k;
-        for (int j = k; j < n; ++j) {
-            const double* col = &W[(size_t)j * m];
-            double s = 0.0;
-            for (int i = k; i < m; ++i) s += col[i] * col[i];
-            cn[j] = s;
-            trail += s;
-            if (s > cn[best]) best = j;
+        for (int j = k; j < n; ++j) trail += cn[j];
+        if (trail <= 4.0 * stop2) {   // near the stop: decide on exact norms
+            trail = 0.0;
+            for (int j = k; j < n; ++j) trail += (cn[j] = cn0[j] = trailing(j, k));
         }
         if (trail <= stop2) break;
+        int best = k;
+        for (int j = k + 1; j < n; ++j)
+            if (cn[j] > cn[best]) best = j;
         if (best != k) {
             std::swap_ranges(&W[(size_t)k * m], &W[(size_t)k * m] + m, &W[(size_t)best * m]);
             std::swap(piv[k], piv[best]);
             std::swap(cn[k], cn[best]);
+            std::swap(cn0[k], cn0[best]);
         }
+        cn[k] = trailing(k, k);   // the pivot column's norm exactly (it defines the reflector)
         double* col = &W[(size_t)k * m];
         const double alpha = sqrt(cn[k]);
         const double beta = col[k] >= 0 ? -alpha : alpha;
@@ -136,11 +162,14 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
         if (vn2 > 0.0) {
             for (int j = k + 1; j < n; ++j) {
                 double* cj = &W[(size_t)j * m];
-                double d = 0.0;
-                for (int i = 0; i < m - k; ++i) d += v[i] * cj[k + i];
-                const double f = 2.0 * d / vn2;
+                const double f = 2.0 * dot4(v.data(), cj + k, m - k) / vn2;
                 for (int i = 0; i < m - k; ++i) cj[k + i] -= f * v[i];
             }
+        }
+        for (int j = k + 1; j < n; ++j) {   // row k of R leaves the trailing part
+            const double r = W[(size_t)j * m + k];
+            cn[j] -= r * r;
+            if (!(cn[j] > 1e-8 * cn0[j])) cn[j] = cn0[j] = trailing(j, k + 1);
         }
         col[k] = beta;
         for (int i = k + 1; i < m; ++i) col[i] = 0.0;
@@ -154,18 +183,47 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
         for (int i = kr; i < m; ++i) resid2 += col[i] * col[i];
     }
     if (kr == 0) return;
-    // ---- stage 2: SVD of B = R P^T (kr x n) via Jacobi on B^T (n x kr, column-major)
+    // ---- stage 2: SVD of B = R P^T (kr x n): Householder QR B^T = Q2 R2 (n x kr), then Jacobi on
+    // the kr x kr factor R2 (R2 V = U2 S), so that B^T V = Q2 U2 S and the Jacobi sweeps cost
+    // O(kr^3) instead of O(n kr^2)
     std::vector<double> BT((size_t)n * kr, 0.0);
     for (int j = 0; j < n; ++j) {
         const double* col = &W[(size_t)j * m];
         for (int i = 0; i < std::min(kr, j + 1); ++i) BT[(size_t)i * n + piv[j]] = col[i];
     }
+    std::vector<std::vector<double>> hv2;  // reflectors of the QR of B^T (length n - c)
+    std::vector<double> tau2;
+    for (int c = 0; c < kr; ++c) {
+        double* col = &BT[(size_t)c * n];
+        double a2 = 0.0;
+        for (int i = c; i < n; ++i) a2 += col[i] * col[i];
+        const double alpha = sqrt(a2);
+        const double beta = col[c] >= 0 ? -alpha : alpha;
+        std::vector<double> v(col + c, col + n);
+        v[0] -= beta;
+        double vn2 = 0.0;
+        for (double x : v) vn2 += x * x;
+        if (vn2 > 0.0) {
+            for (int c2 = c + 1; c2 < kr; ++c2) {
+                double* cj = &BT[(size_t)c2 * n];
+                const double f = 2.0 * dot4(v.data(), cj + c, n - c) / vn2;
+                for (int i = 0; i < n - c; ++i) cj[c + i] -= f * v[i];
+            }
+            col[c] = beta;
+            for (int i = c + 1; i < n; ++i) col[i] = 0.0;
+        }
+        hv2.push_back(v);
+        tau2.push_back(vn2);
+    }
+    std::vector<double> R2((size_t)kr * kr, 0.0);   // column-major, upper triangular
+    for (int c = 0; c < kr; ++c)
+        for (int i = 0; i <= c; ++i) R2[(size_t)c * kr + i] = BT[(size_t)c * n + i];
     std::vector<double> V;
-    hestenes(BT, n, kr, V);
+    hestenes(R2, kr, kr, V);
     std::vector<double> sv(kr);
     for (int c = 0; c < kr; ++c) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i) s += BT[(size_t)c * n + i] * BT[(size_t)c * n + i];
+        for (int i = 0; i < kr; ++i) s += R2[(size_t)c * kr + i] * R2[(size_t)c * kr + i];
         sv[c] = sqrt(s);
     }
     std::vector<int> ord(kr);
@@ -204,7 +262,18 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
             for (int i = 0; i < m - h; ++i) y[h + i] -= f * v[i];
         }
         for (int i = 0; i < m; ++i) out.F[(size_t)i * r + l] = y[i] * rs;
-        for (int j = 0; j < n; ++j) out.G[(size_t)j * r + l] = BT[(size_t)c * n + j] / s * rs;
+        // column c of B^T V = Q2 (R2 V)_c, applying the reflectors of Q2 in reverse
+        std::vector<double> z(n, 0.0);
+        for (int i = 0; i < kr; ++i) z[i] = R2[(size_t)c * kr + i];
+        for (int h = kr - 1; h >= 0; --h) {
+            if (!(tau2[h] > 0.0)) continue;
+            const std::vector<double>& v = hv2[h];
+            double d = 0.0;
+            for (int i = 0; i < n - h; ++i) d += v[i] * z[h + i];
+            const double f = 2.0 * d / tau2[h];
+            for (int i = 0; i < n - h; ++i) z[h + i] -= f * v[i];
+        }
+        for (int j = 0; j < n; ++j) out.G[(size_t)j * r + l] = z[j] / s * rs;
     }
 }
 

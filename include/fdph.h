@@ -323,6 +323,16 @@ int fdph_kernel_times(fdph_plan_t plan, double* ms, int64_t* launches);
 int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* material, double dt,
                      const fdph_params* params, int32_t* buf, int64_t cap, int64_t* len);
 
+/* Host-only inspection of the plan's low-rank approximation of one block (Sec. 2.3, Eq. 13),
+ * no device needed: A (m x n, row-major) ~ F G^T with the smallest rank meeting
+ * |A - F G^T|_F < eps |A|_F (the truncated SVD), or the block kept exact when that rank would
+ * store at least m n numbers (Sec. 6.2 fallback: F = I, G = A^T when m <= n, else F = A, G = I).
+ * F (m x rank) and G (n x rank) are written row-major into buffers of m * min(m, n) and
+ * n * min(m, n) doubles; *rank and *exact (0 / 1) receive the result.  eps <= 0 keeps the block
+ * exact.  Errors: FDPH_E_ARG (null pointer, m or n < 1), FDPH_E_NAN (non-finite entry). */
+int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
+                  int32_t* exact);
+
 /* Allocation-free plain step.  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory (code running inside another runtime's memory pool or
  * allocator budget, or where a cudaMalloc would synchronise the device at a bad moment).

@@ -2627,6 +2627,23 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     return in;
 }
 
+int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
+                  int32_t* exact) {
+    if (!A || !F || !G || !rank || !exact || m < 1 || n < 1) return FDPH_E_ARG;
+    for (long long q = 0; q < (long long)m * n; ++q)
+        if (!std::isfinite(A[q])) {
+            set_error("fdph_low_rank: non-finite entry");
+            return FDPH_E_NAN;
+        }
+    LowRank lr;
+    low_rank(A, m, n, eps, lr);
+    *rank = lr.rank;
+    *exact = lr.exact ? 1 : 0;
+    std::copy(lr.F.begin(), lr.F.end(), F);
+    std::copy(lr.G.begin(), lr.G.end(), G);
+    return FDPH_OK;
+}
+
 int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* material, double dt,
                      const fdph_params* params, int32_t* buf, int64_t cap, int64_t* len) {
     int rc = check_inputs(geometry, material, dt, params);

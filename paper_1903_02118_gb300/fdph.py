@@ -68,7 +68,7 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
            "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run",
-           "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy"]
+           "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy", "fdph_low_rank"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -117,6 +117,9 @@ def lib():
         L.fdph_batch_synchronize.argtypes = [c_p]
         L.fdph_batch_destroy.argtypes = [c_p]
         L.fdph_batch_destroy.restype = None
+        L.fdph_low_rank.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, c_p, c_p,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.fdph_low_rank.restype = ctypes.c_int
         L.fdph_autotune.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.fdph_autotune.restype = ctypes.c_int
         L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
@@ -352,6 +355,21 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def low_rank(A, eps):
+    """The plan's low-rank approximation of one block (fdph_low_rank): returns (F, G, exact)
+    with A ~ F G^T."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    k = min(m, n)
+    F = np.zeros(m * k)
+    G = np.zeros(n * k)
+    r, ex = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().fdph_low_rank(ctypes.c_void_p(A.ctypes.data), m, n, float(eps), ctypes.c_void_p(F.ctypes.data),
+                               ctypes.c_void_p(G.ctypes.data), ctypes.byref(r), ctypes.byref(ex)))
+    r = r.value
+    return F[:m * r].reshape(m, r), G[:n * r].reshape(n, r), bool(ex.value)
 
 
 def tree_export(xy, dt, mu=1.0, cs=1.0, **params):

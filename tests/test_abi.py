@@ -127,3 +127,42 @@ def test_eta2dist_needs_lmin(L):
     xy = np.ascontiguousarray(inputs.straight_fault(64))
     with pytest.raises(fdph.FdphError):
         fdph.tree_export(xy, 0.5, eta=0.5, eta_scheme=1, lmin=0.0)
+
+
+def _svd_truncation(A, eps):
+    """The definition the plan's LRA follows (Sec. 2.3): the truncated SVD of minimal rank with
+    |A - A_r|_F < eps |A|_F."""
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    tail = np.sqrt(np.append(np.cumsum((s * s)[::-1])[::-1], 0.0))
+    r = int(np.argmax(tail < eps * np.linalg.norm(A)))
+    return r, (U[:, :r] * s[:r]) @ Vt[:r]
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+@pytest.mark.parametrize("r0,nr,s0,ns", [(0, 48, 200, 64), (300, 100, 40, 30), (10, 20, 560, 120)])
+def test_low_rank_is_the_truncated_svd(L, eps, r0, nr, s0, ns):
+    """The host LRA of the plan (QR with column pivoting + Jacobi SVD) gives the minimal rank of
+    the truncated SVD and its product to 1e-11 of the block, on static-kernel blocks of the
+    curved fault (the oracle's closed form), with the exact fallback of Sec. 6.2."""
+    el = kn.element_table(inputs.curved_fault(700, inputs.seed_for(1, 0)))
+    A = kn.static_kernel(el, 1.0, receivers=np.arange(r0, r0 + nr), sources=np.arange(s0, s0 + ns))
+    F, G, exact = fdph.low_rank(A, eps)
+    r, Ar = _svd_truncation(A, eps)
+    if r * (nr + ns) >= nr * ns:
+        assert exact and np.array_equal(F @ G.T, A)
+        return
+    assert not exact and F.shape[1] == r
+    assert np.linalg.norm(F @ G.T - Ar) < 1e-11 * np.linalg.norm(A)
+    assert np.linalg.norm(F @ G.T - A) < eps * np.linalg.norm(A)
+
+
+def test_low_rank_fallback_zero_and_nan(L):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((12, 9))                  # full rank: kept exact
+    F, G, exact = fdph.low_rank(A, 1e-4)
+    assert exact and np.array_equal(F @ G.T, A)
+    F, G, exact = fdph.low_rank(np.zeros((5, 7)), 1e-4)
+    assert F.shape == (5, 0) and G.shape == (7, 0) and not exact
+    A[2, 3] = np.nan
+    with pytest.raises(fdph.FdphError):
+        fdph.low_rank(A, 1e-4)

@@ -127,6 +127,16 @@ typedef struct fdph_params {
                              completes, Tbar'_l[n + mindelay] = sum_j g_{l,j} u_j(n + mindelay -
                              delay_j).  Same arithmetic (up to summation order) with more memory
                              (the histories); batches take far_mode 0 */
+    int32_t amp_window;   /* time window of the Domain-F amplitude Khat^F_ij (Eq. 12 / Eq. 28):
+                             0 (default) the pair's discrete window as the operator places it,
+                             steps [dm_i + mbar_j, dm_i + mbar_j + Dm_j), so that amplitude, waveform
+                             and the following static part add up to the exact kernel's impulse;
+                             1 Eq. 28 as written, the pair's own continuous Domain F
+                             (t^-_ij, t^+_ij) = mbar_j dt + (r_ij - r_{i* j}) / c + (0, Dm_j dt),
+                             the window of the representative receiver i* (App. C.3) moved by the
+                             pair's travel-time difference: smooth in i and j, hence low rank on
+                             curved faults, at the price of an O(dt Kstat) mismatch at the start
+                             of Domain S */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */
@@ -145,9 +155,15 @@ typedef struct fdph_stats {
     int64_t arena_bytes;       /* device bytes of the plan (operator data) */
     int64_t state_bytes;       /* device bytes of the time-stepping state (rings, accumulators) */
     double bytes_per_step;     /* algorithmic HBM bytes of one full step at steady state */
-    double near_bytes_per_step;/* of which the near-field kernel tensor */
+    double near_bytes_per_step;/* of which the near-field kernel: coefficients, slip-rate window rows, tail states */
     double flops_per_step;     /* multiply-adds x 2 of one full step */
     double plan_seconds;       /* wall time of fdph_plan */
+    int32_t n_exact;           /* low-rank operators kept exact (Sec. 6.2 fallback) */
+    int32_t pad_;
+    double mean_rank_f;        /* Domain-F amplitude ranks, weighted by the blocks' entries (the
+                                  paper's "mean rank", Sec. 6.4.1); exact blocks count at full rank */
+    double mean_rank_s;        /* the same for the Domain-S static blocks */
+    double mean_rank_tr;       /* the same for the 2-D Domain-S transient blocks */
 } fdph_stats;
 
 /* Fill *p with the defaults above. Never fails. */

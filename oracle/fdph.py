@@ -39,7 +39,11 @@ rank * (N_r + N_s) >= N_r * N_s (the "original rank" fallback of Sec. 6.2).
 
 Readings where the paper is silent or garbled:
 * eps_t = 1; leaf size bounds the inadmissible clusters; l_min = 0 by default.
-* Khat^F_ij is integrated over the ART-shifted discrete window of the pair.
+* Khat^F_ij is integrated over the ART-shifted discrete window of the pair (amp_window 0), so
+  that amplitude, waveform and the static part that follows add up to the kernel's impulse;
+  amp_window 1 takes Eq. 28 as written, the pair's own continuous Domain F
+  (t-_ij, t+_ij) = mbar_j dt + (r_ij - r_{i* j}) / c + (0, Dm_j dt): the App. C.3 window of i*
+  moved by the pair's travel-time difference (smooth in i, j; the placed window is not).
 * Near a nodal direction the waveform of one stress component is ill
   conditioned (its amplitude at i* is nearly zero).  A component whose
   amplitude at i* is below 0.2 of the stress-vector impulse |Khat^F_{i* j}|
@@ -73,13 +77,18 @@ NODAL_TAU = 0.2   # nodal-direction threshold of the waveform choice (reading, s
 
 class Params:
     def __init__(self, eta=0.5, leaf=32, eps=1e-4, eps_st=1e-6, extra_steps=-1, lmin=0.0,
-                 mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False, eta_scheme=0):
+                 mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False, eta_scheme=0,
+                 amp_window=0, transient=True):
         self.eta, self.leaf, self.eps, self.eps_st = eta, leaf, eps, eps_st
         self.extra_steps, self.lmin, self.mu, self.cs, self.dt, self.M = extra_steps, lmin, mu, cs, dt, M
         self.soe_terms = soe_terms
         self.eps_tr = eps_st if eps_tr is None else eps_tr
         self.art_interp = art_interp
         self.eta_scheme = eta_scheme   # 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25), needs lmin > 0
+        # Domain-F amplitude window: 0 the pair's placed discrete window [a, a + Dm); 1 the pair's
+        # own continuous Domain F of Eq. 28 (see the header)
+        self.amp_window = amp_window
+        self.transient = transient     # False drops the 2-D Domain-S transient (App. A.3 study)
 
 
 def soe_min_len(W):
@@ -228,7 +237,16 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
     NX = el["nx"][I][:, None]
     NY = el["ny"][I][:, None]
     # --- Domain F amplitudes (per stress component) and waveforms at i*
-    sxz, syz = kn.stress_jump(PX, PY, srcJ, a * dt, kS * dt, mu, cs)
+    if p.amp_window == 1:
+        # Eq. 28 as written: the integral over the pair's own Domain F (t-_ij, t+_ij), which is
+        # the Domain F of the representative receiver i* (App. C.3: [mbar_j dt, (mbar_j + Dm_j) dt])
+        # moved by the pair's travel-time difference (r_ij - r_{i* j}) / c
+        r_ij = _dist(PX, PY, el["mx"][J][None, :], el["my"][J][None, :])
+        t_lo = mbar[None, :] * dt + (r_ij - r_isj[None, :]) / cs
+        t_hi = t_lo + Dm[None, :] * dt
+        sxz, syz = kn.stress_jump(PX, PY, srcJ, np.maximum(t_lo, 0.0), t_hi, mu, cs)   # R = 0 before t = 0
+    else:
+        sxz, syz = kn.stress_jump(PX, PY, srcJ, a * dt, kS * dt, mu, cs)
     A = {"x": NX * sxz, "y": NY * syz}
     s1 = _src(el, J)
     hxz, hyz = kn.stress_jump(istar[0], istar[1], s1, mbar * dt, (mbar + Dm) * dt, mu, cs)
@@ -285,6 +303,8 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
                 B = np.exp(-lam[None, :] * np.arange(p.M - Dtr, dtype=np.float64)[:, None])
                 coef, *_ = np.linalg.lstsq(B, fib[Dtr:] / fib[0], rcond=None)
                 tail_fit = B @ coef
+        if not p.transient:
+            Br, rT, exT, h, Dtr, tail_fit = np.zeros_like(Br), 0, False, np.zeros(0), 0, np.zeros(0)
         TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit)
     out.update(a=a, kS=kS, F=F, S=dict(op=Sr, rank=rS, exact=exS), TR=TR)
     return out

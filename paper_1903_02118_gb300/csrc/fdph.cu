@@ -2166,19 +2166,27 @@ static void fill_stats(fdph_plan_t P) {
     s.n_subblocks = (int)hp.sbs.size();
     s.max_rank = hp.max_rank;
     s.mean_rank = hp.mean_rank;
+    s.n_exact = hp.n_exact[0] + hp.n_exact[1] + hp.n_exact[2];
+    s.mean_rank_f = hp.ent_w[SB_F] > 0 ? hp.rank_w[SB_F] / hp.ent_w[SB_F] : 0.0;
+    s.mean_rank_s = hp.ent_w[SB_S] > 0 ? hp.rank_w[SB_S] / hp.ent_w[SB_S] : 0.0;
+    s.mean_rank_tr = hp.ent_w[SB_TR] > 0 ? hp.rank_w[SB_TR] / hp.ent_w[SB_TR] : 0.0;
     s.extra_steps = hp.tree.nc;
     s.max_window = hp.max_W;
     s.near_entries = hp.near_tensor_len;
     s.far_entries = hp.far_entries;
     // algorithmic bytes of one steady-state step
     double near_b = 0, far_b = 0, flops = 0;
+    // slip-rate window rows are read from the FP32 copy of the ring unless the plan is FP64;
+    // every right-hand side reads its own rows and keeps its own tail states
+    const double prow = P->precision != FDPH_FP64 ? 4.0 : 8.0;
+    const double R = P->nrhs;
     for (const NearLeaf& L : hp.near) {
         near_b += (double)L.W * L.ns * L.nr * pw + (double)L.ns * L.nr * ps;   // tensor + static tile
-        near_b += (double)(L.W + 1) * L.ns * 8.0;                              // slip history read
-        flops += 2.0 * ((double)L.W + 1) * L.ns * L.nr;
+        near_b += R * ((double)L.W * L.ns * prow + L.ns * 8.0);                // window rows + C row
+        flops += 2.0 * R * ((double)L.W + 1) * L.ns * L.nr;
         if (L.tail >= 0) {                                                     // tail coefficients + states
-            near_b += (double)hp.soe * L.ns * L.nr * ps + (double)hp.soe * L.ns * 16.0;
-            flops += 2.0 * hp.soe * L.ns * (L.nr + 1.0);
+            near_b += (double)hp.soe * L.ns * L.nr * ps + R * hp.soe * L.ns * 16.0;
+            flops += 2.0 * R * hp.soe * L.ns * (L.nr + 1.0);
         }
     }
     for (const SubBlock& sb : hp.sbs) {
@@ -2585,11 +2593,12 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
     if (p && (p->leaf_size < 1 || p->leaf_size > 32 || p->eta < 0.0 || p->eps_st < 0.0 || p->host_threads < 0 ||
               (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
               (p->nrhs != 0 && p->nrhs != 1 && p->nrhs != 2 && p->nrhs != 4 && p->nrhs != kMaxRhs) ||
-              (p->far_mode != 0 && p->far_mode != 1) ||
+              (p->far_mode != 0 && p->far_mode != 1) || (p->amp_window != 0 && p->amp_window != 1) ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
         set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
-                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), far_mode 0 or 1, precision FP64, FP32 or FP16, "
+                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), far_mode 0 or 1, amp_window 0 or 1, precision FP64, FP32 or "
+                  "FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
     }
@@ -2624,6 +2633,7 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.interp = p.art_interp ? 1 : 0;
     in.threads = p.host_threads > 0 ? p.host_threads : omp_get_max_threads();
     in.eta_scheme = p.eta_scheme;
+    in.amp_window = p.amp_window;
     return in;
 }
 

@@ -51,6 +51,7 @@ struct PlanInputs {
     int interp;        // 1: receiver delays interpolated between steps (extension)
     int threads;       // host threads of the build (OpenMP), > 0
     int eta_scheme;    // 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25)
+    int amp_window;    // Domain-F amplitude window: 0 the placed discrete window, 1 the pair's own (Eq. 28)
 };
 
 // Decay factors rho_q = exp(-lambda_q) of the exponential tail basis, lambda_q spaced

@@ -79,8 +79,9 @@ extern "C" int fdph_plain_step_noalloc(const double* K, int32_t n, int32_t W, co
         fdph::set_error("fdph_plain_step_noalloc: hist_len must cover min(step + 1, W) steps");
         return FDPH_E_ARG;
     }
-    const long long tiles = (n + kTile - 1) / kTile;
-    const long long nchunks = (kmax + kSteps - 1) / kSteps;
+    // sizes in 64-bit arithmetic: n + kTile - 1 would overflow int32 for n near INT32_MAX
+    const long long tiles = ((long long)n + kTile - 1) / kTile;
+    const long long nchunks = ((long long)kmax + kSteps - 1) / kSteps;
     if (tiles * nchunks * kTile > FDPH_NOALLOC_MAX_PARTIALS) {
         fdph::set_error("fdph_plain_step_noalloc: ceil(n/32) * ceil(min(step+1, W)/64) * 32 = " +
                         std::to_string(tiles * nchunks * kTile) + " exceeds FDPH_NOALLOC_MAX_PARTIALS = " +
@@ -110,7 +111,7 @@ extern "C" int fdph_plain_step_noalloc(const double* K, int32_t n, int32_t W, co
     cudaStream_t s = (cudaStream_t)stream;
     noalloc_partial_kernel<<<(unsigned)(tiles * nchunks), kThreads, 0, s>>>(K, n, kmax, D_hist, hist_len, step,
                                                                              (int)nchunks, partial);
-    noalloc_reduce_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, n, (int)nchunks, T);
+    noalloc_reduce_kernel<<<(unsigned)(((long long)n + 127) / 128), 128, 0, s>>>(partial, n, (int)nchunks, T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         fdph::set_error(std::string("fdph_plain_step_noalloc launch: ") + cudaGetErrorString(e));

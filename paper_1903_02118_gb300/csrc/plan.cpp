@@ -4,8 +4,10 @@
 //   a_ij = dm_i + mbar_j          start of the pair's discrete Domain F (Eq. 31)
 //   kS_ij = a_ij + Dm_j           start of Domain S
 //   Domain F, per global stress component c (App. C.2, stress first, traction afterwards):
-//     amplitude  Khat^c_ij = R^c_ij(kS dt) - R^c_ij(a dt)       (Eq. 28), low-rank after the
-//                projection n^c_i                                (Eq. 13)
+//     amplitude  Khat^c_ij = R^c_ij(kS dt) - R^c_ij(a dt) over the placed window, or (amp_window 1)
+//                R^c_ij(t+_ij) - R^c_ij(t-_ij) over the pair's own Domain F (Eq. 28),
+//                t-_ij = mbar_j dt + (r_ij - r_i*j) / c, t+_ij = t-_ij + Dm_j dt; low-rank after
+//                the projection n^c_i                            (Eq. 13)
 //     waveform   h^c_{j,m} = K^c_{i* j, mbar_j + m} / Khat^c_{i* j}  (Eq. 29), or, when
 //                component c is nearly nodal at i*, the waveform of the stress vector
 //                projected on its impulse direction
@@ -78,7 +80,16 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
             const Seg s = seg_of(el, ej);
             const long a = (long)o.art.dm[il] + o.art.mbar[jl];
             const long kS = a + o.art.Dm[jl];
-            const Stress2 amp = stress_jump(px, py, s, (double)a * dt, (double)kS * dt, mu, c);
+            double t_lo = (double)a * dt, t_hi = (double)kS * dt;
+            if (in.amp_window == 1) {
+                // Eq. 28: the pair's own Domain F, the window of i* moved by r_ij - r_{i* j}
+                const double dxi = px - el.mx[ej], dyi = py - el.my[ej];
+                const double dxs = ist[0] - el.mx[ej], dys = ist[1] - el.my[ej];
+                t_lo = (double)o.art.mbar[jl] * dt + (sqrt(dxi * dxi + dyi * dyi) - sqrt(dxs * dxs + dys * dys)) / c;
+                t_hi = t_lo + (double)o.art.Dm[jl] * dt;
+                t_lo = t_lo > 0.0 ? t_lo : 0.0;   // the ramp response is zero before t = 0
+            }
+            const Stress2 amp = stress_jump(px, py, s, t_lo, t_hi, mu, c);
             const Stress2 st = stress_static(px, py, s, mu);
             const Stress2 tl = stress_tail(px, py, s, (double)kS * dt, (double)(kS + 1) * dt, mu, c);
             const size_t q = (size_t)il * ns + jl;
@@ -347,6 +358,9 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             hp.max_taps = std::max(hp.max_taps, kind == SB_F ? taps : 0);
             rank_sum += sb.rank;
             rank_cnt += 1;
+            hp.rank_w[kind] += (double)sb.rank * o.nr * o.ns;   // entry-weighted, as the paper's mean rank
+            hp.ent_w[kind] += (double)o.nr * o.ns;
+            hp.n_exact[kind] += lr.exact ? 1 : 0;
             hp.far_entries += (int64_t)lr.F.size() + lr.G.size() + (h ? h->size() : 0);
         };
         add(SB_F, o.F[0], dF, dF_off, &o.h[0], o.HM, 0, nullptr);

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32),
-                ("far_mode", ctypes.c_int32)]
+                ("far_mode", ctypes.c_int32), ("amp_window", ctypes.c_int32)]
 
 
 class Friction(ctypes.Structure):
@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("far_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("state_bytes", ctypes.c_int64), ("bytes_per_step", ctypes.c_double),
                 ("near_bytes_per_step", ctypes.c_double), ("flops_per_step", ctypes.c_double),
-                ("plan_seconds", ctypes.c_double)]
+                ("plan_seconds", ctypes.c_double), ("n_exact", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("mean_rank_f", ctypes.c_double), ("mean_rank_s", ctypes.c_double), ("mean_rank_tr", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -165,11 +166,12 @@ def default_params():
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
                 device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None,
-                nrhs=None, far_mode=None):
+                nrhs=None, far_mode=None, amp_window=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
                  ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs), ("far_mode", far_mode),
+                 ("amp_window", amp_window),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)
@@ -313,9 +315,27 @@ class Plan:
 
 
 def plain_step_noalloc(K, n, W, D_hist, hist_len, step, T, stream=None):
-    """fdph_plain_step_noalloc: one plain step from caller-held device buffers, no allocation."""
+    """fdph_plain_step_noalloc: one plain step from caller-held device buffers, no allocation.
+
+    K (W n n), D_hist (hist_len n) and T (n) must be contiguous float64 CUDA tensors on one
+    device and hold at least those many elements: the library reads and writes them through raw
+    pointers, so a short buffer would be read out of bounds on the GPU.  stream: a cudaStream_t
+    handle (int); None means torch's current stream on T's device."""
+    import torch
+    n, W, hist_len, step = int(n), int(W), int(hist_len), int(step)
+    need = {"K": (K, W * n * n), "D_hist": (D_hist, hist_len * n), "T": (T, n)}
+    for name, (t, count) in need.items():
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise FdphError(E_ARG, "plain_step_noalloc: %s must be a contiguous float64 CUDA tensor" % name)
+        if t.device != T.device:
+            raise FdphError(E_ARG, "plain_step_noalloc: %s is not on T's device" % name)
+        if n > 0 and W > 0 and hist_len > 0 and t.numel() < count:
+            raise FdphError(E_ARG, "plain_step_noalloc: %s holds %d elements, %d needed" % (name, t.numel(), count))
+    if stream is None:
+        stream = torch.cuda.current_stream(T.device).cuda_stream
     s = ctypes.c_void_p(stream) if stream else None
-    _check(lib().fdph_plain_step_noalloc(_ptr(K), int(n), int(W), _ptr(D_hist), int(hist_len), int(step), _ptr(T), s))
+    with torch.cuda.device(T.device):
+        _check(lib().fdph_plain_step_noalloc(_ptr(K), n, W, _ptr(D_hist), hist_len, step, _ptr(T), s))
 
 
 class Batch:

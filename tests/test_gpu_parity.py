@@ -63,38 +63,45 @@ def test_plain_st_biem_fp64(geom, N, M):
     assert st["n_admissible"] == 0 and st["max_window"] == M
 
 
-def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6, soe_terms=0, eta=0.5, art_interp=False, eta_scheme=0, lmin=0.0):
+def _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-6, soe_terms=0, eta=0.5, art_interp=False, eta_scheme=0, lmin=0.0,
+                 amp_window=0):
     el = kn.element_table(xy)
     p = ofd.Params(eta=eta, leaf=leaf, eps=eps, eps_st=eps_st, M=M, soe_terms=soe_terms, art_interp=art_interp,
-                   eta_scheme=eta_scheme, lmin=lmin)
+                   eta_scheme=eta_scheme, lmin=lmin, amp_window=amp_window)
     plan = ofd.build_plan(el, p)
     Kc = ofd.operator_rows(el, plan, np.arange(xy.shape[0]))
     return dense.march(Kc, D), plan
 
 
-@pytest.mark.parametrize("geom,N,leaf", [("straight", 256, 16), ("curved", 256, 16), ("kinked", 233, 13)])
-def test_fdph_fp64_equals_compressed_operator(geom, N, leaf):
+@pytest.mark.parametrize("geom,N,leaf,amp", [("straight", 256, 16, 0), ("curved", 256, 16, 0), ("kinked", 233, 13, 0),
+                                             ("curved", 256, 16, 1), ("kinked", 233, 13, 1)])
+def test_fdph_fp64_equals_compressed_operator(geom, N, leaf, amp):
+    """amp = 1: the Domain-F amplitude over the pair's own window of Eq. 28 (amp_window 1)."""
     _need_gpu()
     M, eps = 320, 1e-5
     xy = _geom(geom, N)
     D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
-    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D)
-    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-6, leaf_size=leaf)
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, amp_window=amp)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-6, leaf_size=leaf, amp_window=amp)
     T = _run(plan, D)
     st = plan.stats()
     assert st["n_admissible"] == len(oplan["adm"]) and st["n_near"] == len(oplan["near"])
     assert _rel(T, T0) < TOL64
 
 
-@pytest.mark.parametrize("geom,N,leaf,eta,interp", [("curved", 160, 16, 0.5, False), ("straight", 150, 12, 0.25, False),
-                                                    ("curved", 170, 16, 0.5, True)])
-def test_fdph_exponential_tails_fp64_equals_compressed_operator(geom, N, leaf, eta, interp):
+@pytest.mark.parametrize("geom,N,leaf,eta,interp,amp", [("curved", 160, 16, 0.5, False, 0),
+                                                        ("straight", 150, 12, 0.25, False, 0),
+                                                        ("curved", 170, 16, 0.5, True, 0),
+                                                        ("curved", 160, 16, 0.5, False, 1)])
+def test_fdph_exponential_tails_fp64_equals_compressed_operator(geom, N, leaf, eta, interp, amp):
     _need_gpu()
     M, eps = 900, 1e-5      # long enough that the exponential tails are used (fit range >= 512)
     xy = _geom(geom, N)
     D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
-    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-4, soe_terms=16, eta=eta, art_interp=interp)
-    plan = fdph.Plan(xy, 0.5, M, eps, eta=eta, eps_st=1e-4, leaf_size=leaf, soe_terms=16, art_interp=interp)
+    T0, oplan = _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-4, soe_terms=16, eta=eta, art_interp=interp,
+                             amp_window=amp)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=eta, eps_st=1e-4, leaf_size=leaf, soe_terms=16, art_interp=interp,
+                     amp_window=amp)
     T = _run(plan, D)
     assert plan.stats()["max_window"] == max(d["W"] for d in oplan["near"]) < M
     assert _rel(T, T0) < TOL64

@@ -196,9 +196,20 @@ class OraclePool:
     def __init__(self, workers=None):
         import multiprocessing as mp
         self.workers = workers or host_cores()
-        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ[v] = "1"                        # inherited by the spawned workers
-        self.pool = mp.get_context("spawn").Pool(self.workers)
+        # one thread per worker: the variables are set only while the workers are spawned (they
+        # inherit them); this process's own OpenMP runtime (the plan build) keeps every core
+        names = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {v: os.environ.get(v) for v in names}
+        for v in names:
+            os.environ[v] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
 
     def rows(self, cfg, rows, per=2):
         """Plain-march traction T[n, r] of the sampled receivers, `per` receivers per task."""

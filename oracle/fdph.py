@@ -43,7 +43,8 @@ Readings where the paper is silent or garbled:
   that amplitude, waveform and the static part that follows add up to the kernel's impulse;
   amp_window 1 takes Eq. 28 as written, the pair's own continuous Domain F
   (t-_ij, t+_ij) = mbar_j dt + (r_ij - r_{i* j}) / c + (0, Dm_j dt): the App. C.3 window of i*
-  moved by the pair's travel-time difference (smooth in i, j; the placed window is not).
+  moved by the pair's travel-time difference (smooth in i, j; the placed window is not), and the
+  transient below then takes its temporal pivot at the end of that window, t+_ij, instead of kS dt.
 * Near a nodal direction the waveform of one stress component is ill
   conditioned (its amplitude at i* is nearly zero).  A component whose
   amplitude at i* is below 0.2 of the stress-vector impulse |Khat^F_{i* j}|
@@ -245,8 +246,10 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
         t_lo = mbar[None, :] * dt + (r_ij - r_isj[None, :]) / cs
         t_hi = t_lo + Dm[None, :] * dt
         sxz, syz = kn.stress_jump(PX, PY, srcJ, np.maximum(t_lo, 0.0), t_hi, mu, cs)   # R = 0 before t = 0
+        tS = t_hi                        # the pair's own Domain-S start: temporal pivot of the transient
     else:
         sxz, syz = kn.stress_jump(PX, PY, srcJ, a * dt, kS * dt, mu, cs)
+        tS = kS * dt
     A = {"x": NX * sxz, "y": NY * syz}
     s1 = _src(el, J)
     hxz, hyz = kn.stress_jump(istar[0], istar[1], s1, mbar * dt, (mbar + Dm) * dt, mu, cs)
@@ -269,13 +272,13 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
     F = {}
     for c in ("x", "y"):
         Ar, r, ex = lra(A[c], p.eps)
-        F[c] = dict(op=Ar, rank=r, exact=ex, h=h[c])
+        F[c] = dict(op=Ar, rank=r, exact=ex, h=h[c], raw=A[c])
     # --- Domain S static
     Ks = kn.static_kernel(el, mu, I, J)
     Sr, rS, exS = lra(Ks, p.eps)
     # --- Domain S transient (per stress component)
     thr = p.eps_tr * mu / (2.0 * cs)
-    txz, tyz = kn.stress_tail(PX, PY, srcJ, kS * dt, (kS + 1) * dt, mu, cs)
+    txz, tyz = kn.stress_tail(PX, PY, srcJ, tS, tS + dt, mu, cs)
     TR = {}
     for c, tc, Nc in (("x", txz, NX), ("y", tyz, NY)):
         flat = int(np.argmax(np.abs(tc)))
@@ -283,10 +286,10 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
         if tc[pi, pj] == 0.0:
             TR[c] = dict(op=np.zeros_like(tc), rank=0, exact=False, h=np.zeros(0), Dm=0, pivot=(pi, pj))
             continue
-        k0 = int(kS[pi, pj])
+        t0 = float(tS[pi, pj])
         m = np.arange(p.M, dtype=np.float64)
         f1, f2 = kn.stress_tail(el["mx"][I[pi]], el["my"][I[pi]], _src(el, J[pj]),
-                                (k0 + m) * dt, (k0 + m + 1.0) * dt, mu, cs)
+                                t0 + m * dt, t0 + (m + 1.0) * dt, mu, cs)
         fib = f1 if c == "x" else f2
         big = np.nonzero(np.abs(fib) >= thr)[0]
         Dtr = 0 if big.size == 0 else int(big.max()) + 1
@@ -305,8 +308,8 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
                 tail_fit = B @ coef
         if not p.transient:
             Br, rT, exT, h, Dtr, tail_fit = np.zeros_like(Br), 0, False, np.zeros(0), 0, np.zeros(0)
-        TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit)
-    out.update(a=a, kS=kS, F=F, S=dict(op=Sr, rank=rS, exact=exS), TR=TR)
+        TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit, raw=Nc * tc)
+    out.update(a=a, kS=kS, F=F, S=dict(op=Sr, rank=rS, exact=exS, raw=Ks), TR=TR)
     return out
 
 

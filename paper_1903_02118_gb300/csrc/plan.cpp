@@ -13,8 +13,9 @@
 //                projected on its impulse direction
 //   Domain S: static traction kernel per unit slip, low-rank, applied as dt * slip from kS on
 //             (App. B.1; the App. C.3 integers make its second term vanish)
-//   transient (App. B.3, App. H): K - Khat^S dt ~ Khat^tr h^tr with the temporal pivot at kS
-//             and the spatial pivot at the largest |entry| of the leaf; Dm_tr from eps_st
+//   transient (App. B.3, App. H): K - Khat^S dt ~ Khat^tr h^tr with the temporal pivot at the start
+//             of the pair's Domain S (kS dt, or t+_ij with amp_window 1) and the spatial pivot at
+//             the largest |entry| of the leaf; Dm_tr from eps_st
 // Inadmissible leaves only get their geometry here; their exact-kernel windows are computed on
 // the device (fdph.cu) because they need O(pairs * M) kernel evaluations.
 #include <math.h>
@@ -72,6 +73,7 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
     const double ist[2] = {0.5 * (tn.box.lo[0] + tn.box.hi[0]), 0.5 * (tn.box.lo[1] + tn.box.hi[1])};
     std::vector<double> Ax((size_t)nr * ns), Ay((size_t)nr * ns), Ks((size_t)nr * ns);
     std::vector<double> tx((size_t)nr * ns), ty((size_t)nr * ns);
+    std::vector<double> tS((size_t)nr * ns);   // start time of the pair's Domain S (transient pivot)
     for (int il = 0; il < nr; ++il) {
         const int ei = tr.perm[o.r0 + il];
         const double px = el.mx[ei], py = el.my[ei], nx = el.nx[ei], ny = el.ny[ei];
@@ -91,8 +93,9 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
             }
             const Stress2 amp = stress_jump(px, py, s, t_lo, t_hi, mu, c);
             const Stress2 st = stress_static(px, py, s, mu);
-            const Stress2 tl = stress_tail(px, py, s, (double)kS * dt, (double)(kS + 1) * dt, mu, c);
+            const Stress2 tl = stress_tail(px, py, s, t_hi, t_hi + dt, mu, c);
             const size_t q = (size_t)il * ns + jl;
+            tS[q] = t_hi;
             Ax[q] = nx * amp.x;
             Ay[q] = ny * amp.y;
             Ks[q] = nx * st.x + ny * st.y;
@@ -144,12 +147,12 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
         const int pi = (int)(best / ns), pj = (int)(best % ns);
         const int ei = tr.perm[o.r0 + pi], ej = tr.perm[o.s0 + pj];
         const Seg s = seg_of(el, ej);
-        const long k0 = (long)o.art.dm[pi] + o.art.mbar[pj] + o.art.Dm[pj];
+        const double t0 = tS[best];   // kS dt, or the pivot pair's own Domain-S start (amp_window 1)
         std::vector<double> fib(in.M);
         int last = -1;
         for (int m = 0; m < in.M; ++m) {
-            const Stress2 v = stress_tail(el.mx[ei], el.my[ei], s, (double)(k0 + m) * dt,
-                                          (double)(k0 + m + 1) * dt, mu, c);
+            const Stress2 v = stress_tail(el.mx[ei], el.my[ei], s, t0 + (double)m * dt, t0 + (double)(m + 1) * dt,
+                                          mu, c);
             fib[m] = cc == 0 ? v.x : v.y;
             if (fabs(fib[m]) >= thr) last = m;
         }

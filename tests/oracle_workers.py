@@ -40,10 +40,20 @@ def _operator_task(job):
 
 def operator_march_rows(desc, params, rows, per=1, workers=None):
     """(T, B): the compressed operator's march T[n, r] and the march of |K|, |D| at the receivers."""
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"
     chunks = [list(map(int, rows[c:c + per])) for c in range(0, len(rows), per)]
     n = workers or min(len(chunks), os.cpu_count() or 1)
-    with mp.get_context("spawn").Pool(n) as pool:
+    names = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {v: os.environ.get(v) for v in names}
+    for v in names:
+        os.environ[v] = "1"          # inherited by the workers spawned now, not kept by this process
+    try:
+        pool = mp.get_context("spawn").Pool(n)
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    with pool:
         out = pool.map(_operator_task, [(desc, params, c) for c in chunks])
     return np.concatenate([o[0] for o in out], axis=1), np.concatenate([o[1] for o in out], axis=1)

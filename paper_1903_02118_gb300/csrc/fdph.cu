@@ -2727,6 +2727,13 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         fdph_destroy(P);
         return code;
     };
+    // host trees and the discretised causality of every admissible leaf first: a plan that
+    // violates it is refused before any device resource is taken
+    PlanInputs in = make_inputs(material, dt, M, eps, p);
+    Elements el = make_elements(geometry->n, geometry->xy);
+    HostPlan& hp = P->hp;
+    build_host_tree(el, in, hp);
+    if (check_causality(el, in, hp.tree)) return fail(FDPH_E_CAUSALITY);
     if (cudaSetDevice(p.device) != cudaSuccess) {
         set_error("cudaSetDevice failed");
         return fail(FDPH_E_CUDA);
@@ -2754,16 +2761,12 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         int least = 0, greatest = 0;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) P->near_priority = greatest;
     }
-    PlanInputs in = make_inputs(material, dt, M, eps, p);
-    Elements el = make_elements(geometry->n, geometry->xy);
-    HostPlan& hp = P->hp;
     const bool verbose = getenv("FDPH_VERBOSE") != nullptr;
     auto stamp = [&](const char* what) {
         if (verbose)
             fprintf(stderr, "[fdph_plan] %-28s %8.3f s\n", what,
                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     };
-    build_host_tree(el, in, hp);
     stamp("cluster and block trees");
     // near field on the device (exact windows, tail projections) while the host factorises the
     // admissible blocks

@@ -209,6 +209,16 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     return build_host_far(el, in, hp);
 }
 
+int check_causality(const Elements& el, const PlanInputs& in, const Tree& tr) {
+    for (const Leaf& lf : tr.leaves)
+        if (lf.kind == 1 && art_integers(el, tr, lf, in).causal < 1) {
+            set_error("discretised causality min(dm_i + mbar_j) >= 1 violated by an admissible leaf "
+                      "(Sec. 5.2, App. D): increase l_min / eta or reduce dt");
+            return -3;
+        }
+    return 0;
+}
+
 void build_host_tree(const Elements& el, const PlanInputs& in, HostPlan& hp) {
     hp.n = el.n;
     hp.M = in.M;

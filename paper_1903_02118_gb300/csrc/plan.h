@@ -99,6 +99,8 @@ int build_host_plan(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // admissible blocks (ART integers, low-rank factors, waveforms, transients).  The near-field
 // build needs only the first stage, so the device can work on it during the second.
 void build_host_tree(const Elements& el, const PlanInputs& in, HostPlan& hp);
+// Discretised causality of every admissible leaf of the tree (Sec. 5.2): -3 if one violates it.
+int check_causality(const Elements& el, const PlanInputs& in, const Tree& tr);
 int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp);
 // Second stage once the near-field windows W are known (fills offsets, items, CSR).
 // vec, vec_aux: sources per 16 bytes of the window and aux storage types (8 FP16, 4 FP32, 2 FP64);

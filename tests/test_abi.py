@@ -68,6 +68,29 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.fdph_strerror(fdph.E_CAUSALITY)
 
 
+def test_plan_refuses_a_causality_violation_before_any_device_work():
+    """Sec. 5.2 / App. D: a time step so coarse that an admissible leaf's nearest pair has
+    dm_i + mbar_j < 1 (cs dt = 4 dx, eta = 1/2, clusters down to one element) must be refused with
+    FDPH_E_CAUSALITY and no plan; the check runs on the host before the device is touched, so it
+    answers the same with or without a GPU.  A step half as long passes.  The oracle agrees."""
+    L = fdph.lib()
+    xy = inputs.straight_fault(64)
+    g, keep = fdph._geometry(xy)
+    mat = fdph.Material(1.0, 1.0)
+    p = fdph.make_params(eta=0.5, leaf_size=1)
+    h = ctypes.c_void_p()
+    rc = L.fdph_plan(ctypes.byref(g), ctypes.byref(mat), 4.0, 64, 1e-4, ctypes.byref(p), ctypes.byref(h))
+    assert rc == fdph.E_CAUSALITY and not h.value
+    assert b"causality" in L.fdph_last_error()
+    with pytest.raises(fdph.FdphError) as e:
+        fdph.tree_export(xy, 4.0, eta=0.5, leaf_size=1)
+    assert e.value.status == fdph.E_CAUSALITY
+    fdph.tree_export(xy, 2.0, eta=0.5, leaf_size=1)        # causal
+    el = kn.element_table(xy)
+    with pytest.raises(ValueError, match="causality"):
+        ofd.build_plan(el, ofd.Params(eta=0.5, leaf=1, dt=4.0, M=64))
+
+
 def _compare_tree(xy, eta, leaf, eta_scheme=0, lmin=0.0):
     tr = fdph.tree_export(xy, 0.5, eta=eta, leaf_size=leaf, eta_scheme=eta_scheme, lmin=lmin)
     perm = tr["perm"]

@@ -24,19 +24,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CONFIGS = {
+    # amp_window 1: the Domain-F amplitude over each pair's own window (Eq. 28), the reading that
+    # keeps the paper's O(1) ranks on a curved fault (and halves this workload's error)
     "fdph": dict(name="FDP=H single scenario, 2-D antiplane curved fault", N=4096, M=4096, eps=1e-4, eta=0.5,
-                 leaf=32, eps_st=1e-6, geometry="curved"),
+                 leaf=32, eps_st=1e-6, geometry="curved", amp_window=1),
     "plain": dict(name="Plain dense ST-BIEM, 2-D antiplane straight fault", N=256, M=256, eps=0.0, eta=0.0,
                   leaf=32, eps_st=0.0, geometry="straight"),
     # the curved workload's pulse on a straight fault of the same size (the plane-wave travel times
-    # of Sec. 4.2.2 are exact on a line), with eta = 1/8: the setting that meets the metric's accuracy
-    "planar": dict(name="FDP=H single scenario, 2-D antiplane planar fault", N=4096, M=4096, eps=1e-4, eta=0.125,
-                   leaf=32, eps_st=1e-6, geometry="planar"),
+    # of Sec. 4.2.2 are exact on a line, and the error falls with eta): eta = 1/16 with the
+    # near-field window in FP16 is the setting measured to meet the metric's accuracy
+    "planar": dict(name="FDP=H single scenario, 2-D antiplane planar fault", N=4096, M=4096, eps=1e-4, eta=0.0625,
+                   leaf=32, eps_st=1e-6, geometry="planar", amp_window=1, precision="fp16"),
     # dynamic rupture on a planar fault (linear slip weakening); N is 4096 instead of 16384 because
     # the host plan of the 16384-element fault (exact QR + Jacobi factorisation of every block)
     # takes tens of minutes
     "rupture": dict(name="FDP=H dynamic rupture, 2-D antiplane planar fault, linear slip weakening", N=4096,
-                    M=8192, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="straight"),
+                    M=8192, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="straight", amp_window=1),
 }
 DT = 0.5
 DTYPE = {0: "f64", 1: "f32-storage/f64-accumulate", 2: "f16-near-window/f32-storage/f64-accumulate"}
@@ -275,7 +278,7 @@ def run_rupture(args, cfg):
     plan = fdph.Plan(xy, DT, M, cfg["eps"], eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"],
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
                      eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
-                     extra_steps=cfg.get("extra_steps", -1))
+                     extra_steps=cfg.get("extra_steps", -1), amp_window=cfg.get("amp_window", 0))
     plan_s = time.perf_counter() - t0
     st = plan.stats()
     plan.rupture_init(torch.from_numpy(tau0).cuda(), 1.0, 0.6, 0.3, 6.4)
@@ -683,9 +686,11 @@ def run_fdph(args, cfg):
             # (Sec. 4.2.2) and the error falls with eta: the setting that meets the metric's accuracy
             pl = dict(CONFIGS["planar"], soe=cfg.get("soe", 16), eps_st=cfg["eps_st"])
             T_pl = pool.rows(pl, rows)
+            pl_prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[pl["precision"]]
             line["at_metric_accuracy"] = guarded(lambda: dict(
-                workload=pl["name"], setting={k: pl[k] for k in ("N", "M", "eps", "eta", "leaf", "eps_st", "soe")},
-                **sub_run(fdph, torch, pl, prec, local, stream, K, W, rows, T_pl, hbm_peak)))
+                workload=pl["name"], dtype=DTYPE[pl_prec],
+                setting={k: pl[k] for k in ("N", "M", "eps", "eta", "leaf", "eps_st", "soe", "amp_window", "precision")},
+                **sub_run(fdph, torch, pl, pl_prec, local, stream, K, W, rows, T_pl, hbm_peak)))
         pool.close()
     if rank == 0:
         print(json.dumps(line))

@@ -30,6 +30,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -144,6 +145,7 @@ struct StepArgs {
     int n_cta;
     int n_items;
     const void* tensor;       // near-field window slices (window storage type)
+    float kinv;               // inverse of the window coefficients' storage scale (FP16: 2^-e, else 1)
     const void* stat;         // aux slices: static tiles, exponential-tail coefficients (aux storage type)
     double* partial;          // [n_items][32]
     const int* np_ptr;
@@ -544,6 +546,7 @@ struct NearView {
     const void* stat;
     double* partial;
     int* err;
+    float kinv;
     int N, WD, WC, n, nrhs;
     long long rs_D, rs_C, rs_vstate, rs_partial;
 };
@@ -557,6 +560,7 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     v.vstate = a.vstate;
     v.rho = a.rho;
     v.tensor = a.tensor;
+    v.kinv = a.kinv;
     v.stat = a.stat;
     v.partial = a.partial;
     v.err = a.err;
@@ -832,6 +836,138 @@ __device__ __forceinline__ void slice_dot_nr(const __half* buf, const float* vro
     for (int q = 0; q < NR; ++q) out[q] = s0[q] + s1[q];
 }
 
+// ---- several right-hand sides on the tensor cores (FP16 window, NR >= 2)
+//
+// One slice is a 32 x 32 (receivers x sources) FP16 tile times the slip rates of the NR right-hand
+// sides, a dense (32 x 32) x (32 x NR) contraction: warp-level mma.sync m16n8k16 (FP16 inputs, FP32
+// accumulation), two 16-receiver tiles x two 16-source steps.  The A fragments come straight from
+// the stage with ldmatrix (the source-interleaved slice layout of plan.h puts 8 sources of one
+// receiver in 16 contiguous bytes, the rows of an 8 x 8 ldmatrix tile).  The slip rates are FP32:
+// each (slice, RHS) row of 32 sources is scaled by a power of two that brings its largest entry
+// into [2^13, 2^14) and split into two FP16 parts, hi = fp16(x s) and lo = fp16(x s - hi), so that
+// the tensor-core products carry the slip rates to about 2^-22 relative (2^-39 of the row's largest
+// entry in absolute terms) and the only rounding of the FP16 path remains that of the stored
+// coefficients.  hi and lo are two B columns (NR <= 4: one 8-column pass holds both, columns v and
+// v + NR) or two passes into the same accumulator (NR = 8); each slice's products are scaled back
+// by 2^-s per column and added to the item's FP32 sums.
+constexpr int kBtStride = 40;   // halves per B row: 80-byte rows, ldmatrix rows on distinct bank groups
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2(unsigned (&r)[2], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_16816(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
+
+// One window slice (sl: its stage copy; rows: its NR FP32 slip-rate rows, lane = source) into the
+// warp's accumulators acc[m-tile][fragment] (rows g, g + 8 of each 16-receiver tile, columns 2t,
+// 2t + 1 with g = lane / 4, t = lane % 4).  bt: the warp's B tile, 2 NR rows of kBtStride halves.
+template <int NR>
+__device__ __forceinline__ void tc_slice(const __half* sl, const float* rows, int nr, int ns, __half* bt, int lane,
+                                         float (&acc)[2][4]) {
+    static_assert(NR == 2 || NR == 4 || NR == 8, "tensor-core slices take 2, 4 or 8 right-hand sides");
+    float inv[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        const float x = rows[q * 32 + lane];
+        float m = fabsf(x);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // m = f 2^e with f in [0.5, 1) (e from the exponent field; a zero or subnormal row takes the
+        // largest shift); scale by 2^sh, sh = 14 - e, clamped to stay a normal float
+        const int e = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xffu) - 126 : -126;
+        const int sh = min(max(14 - e, -100), 100);
+        inv[q] = pow2f(-sh);
+        const float y = x * pow2f(sh);
+        const __half hi = __float2half_rn(y);
+        bt[q * kBtStride + lane] = hi;
+        bt[(NR + q) * kBtStride + lane] = __float2half_rn(y - __half2float(hi));
+    }
+    __syncwarp();
+    const int ng = (ns + 7) >> 3;          // 8-source groups of the slice (zero-padded)
+    const int nks = (ng + 1) >> 1;         // 16-source steps
+    const int nmt = nr > 16 ? 2 : 1;       // 16-receiver tiles
+    constexpr int npass = (2 * NR + 7) / 8;
+    float c[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) c[mt][f] = 0.f;
+    const int mq = lane >> 3, mr = lane & 7;   // ldmatrix: lane gives row mr of matrix mq
+    for (int kk = 0; kk < nks; ++kk) {
+        unsigned b[npass][2];
+#pragma unroll
+        for (int p = 0; p < npass; ++p) {
+            // rows past 2 NR repeat the last one (their columns are not used)
+            const int v = min(8 * p + mr, 2 * NR - 1);
+            ldsm_x2(b[p], bt + v * kBtStride + 16 * kk + 8 * (mq & 1));
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            if (mt < nmt) {
+                // receivers past nr and source groups past ng read valid rows of this slice (their
+                // products land in unused rows, or meet zero slip rates)
+                const int i = min(16 * mt + 8 * (mq & 1) + mr, nr - 1);
+                const int gg = min(2 * kk + (mq >> 1), ng - 1);
+                unsigned a[4];
+                ldsm_x4(a, sl + ((size_t)gg * nr + i) * 8);
+#pragma unroll
+                for (int p = 0; p < npass; ++p) mma_16816(c[mt], a, b[p]);
+            }
+        }
+    }
+    __syncwarp();   // bt is rewritten by the next slice
+    // column v holds right-hand side v % NR; the scale is picked without a dynamic register index
+    const int t = lane & 3;
+    float s0 = inv[0], s1 = inv[1 % NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        s0 = (2 * t) % NR == q ? inv[q] : s0;
+        s1 = (2 * t + 1) % NR == q ? inv[q] : s1;
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        acc[mt][0] = fmaf(c[mt][0], s0, acc[mt][0]);
+        acc[mt][1] = fmaf(c[mt][1], s1, acc[mt][1]);
+        acc[mt][2] = fmaf(c[mt][2], s0, acc[mt][2]);
+        acc[mt][3] = fmaf(c[mt][3], s1, acc[mt][3]);
+    }
+}
+
+// The item's sums of one warp into red[q][receiver] (FP64): the hi and lo columns of a right-hand
+// side are added first (NR <= 4), then scaled by the window's storage scale kinv.
+template <int NR>
+__device__ __forceinline__ void tc_item_to_red(float (&acc)[2][4], int lane, int nr, float kinv, double (*red)[32]) {
+    if constexpr (NR < 8) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[mt][f] += __shfl_xor_sync(0xffffffffu, acc[mt][f], NR / 2);
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int v = 2 * t + (f & 1), r = 16 * mt + g + 8 * (f >> 1);
+            if (v < NR) red[v][r] = r < nr ? (double)(acc[mt][f] * kinv) : 0.0;
+        }
+}
+
 // Near field (App. E), persistent and warp-specialised.  Each CTA owns a list of work items
 // (window slices [k0, k1) of a leaf, or the leaf's aux slices: static tile and exponential
 // tail).  One producer thread streams the items' slices through a ring of shared-memory stages
@@ -851,9 +987,12 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
     using C = NearCfg<H, NR>;
     using A = typename NearTypes<H>::Aux;
     using R = typename NearTypes<H>::Row;
+    // FP16 windows with several right-hand sides: window slices on the tensor cores (tc_slice)
+    constexpr bool kTC = std::is_same<H, __half>::value && NR >= 2 && !kBatch;
     extern __shared__ __align__(128) unsigned char near_smem[];
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][NR][32];
+    __shared__ __align__(16) __half btile[kTC ? kNearConsumers : 1][kTC ? 2 * NR * kBtStride : 8];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
@@ -934,8 +1073,10 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
             const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
             // leaves of at most 16 receivers: the warp splits into 32 / span lane groups of span
-            // lanes, each taking its own slices (lane = group * span + receiver)
-            const int span = tk.nr > 16 ? 32 : tk.nr > 8 ? 16 : tk.nr > 4 ? 8 : tk.nr > 2 ? 4 : tk.nr > 1 ? 2 : 1;
+            // lanes, each taking its own slices (lane = group * span + receiver); tensor-core
+            // slices take the whole warp
+            const bool tc = kTC && !tk.kind;
+            const int span = tc || tk.nr > 16 ? 32 : tk.nr > 8 ? 16 : tk.nr > 4 ? 8 : tk.nr > 2 ? 4 : tk.nr > 1 ? 2 : 1;
             const int ngrp = 32 / span, grp = lane / span, ri = lane - grp * span;
             const int li = ri < tk.nr ? ri : 0;         // lanes past nr read a valid element, unused
             R acc[NR];
@@ -945,6 +1086,11 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                 acc[r] = (R)0;
                 accd[r] = 0.0;
             }
+            float tacc[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) tacc[mt][f] = 0.f;
             for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % C::stages;
                 const int cnt = min(per, nsl - q * per);
@@ -955,6 +1101,13 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                 const unsigned char* buf = near_smem + s * kNearStageBytes;
                 for (int kk = warp * ngrp + grp; kk < cnt; kk += kNearConsumers * ngrp) {
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
+                    if constexpr (kTC) {
+                        if (tc) {
+                            tc_slice<NR>((const __half*)buf + (size_t)kk * tk.sl, (const float*)vrow, tk.nr, tk.ns,
+                                         btile[warp], lane, tacc);
+                            continue;
+                        }
+                    }
                     if constexpr (NR == 1) {
                         if (tk.kind)   // static and tail slices: FP64 across slices
                             accd[0] += (double)slice_dot((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li);
@@ -966,7 +1119,7 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                             slice_dot_nr<NR>((const A*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li, t);
 #pragma unroll
                             for (int r = 0; r < NR; ++r) accd[r] += (double)t[r];
-                        } else {
+                        } else if constexpr (!kTC) {   // (with kTC window slices took tc_slice)
                             slice_dot_nr<NR>((const H*)buf + (size_t)kk * tk.sl, vrow, tk.ns, tk.nr, li, t);
 #pragma unroll
                             for (int r = 0; r < NR; ++r) acc[r] += t[r];
@@ -977,11 +1130,17 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
             if (ti + 1 < t1) near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            if (tc) {
+                if constexpr (kTC) tc_item_to_red<NR>(tacc, lane, tk.nr, v.kinv, red[par][warp]);
+            } else {
+                // window sums carry the storage scale of the window (FP16), aux sums none
+                const double ks = tk.kind ? 1.0 : (double)v.kinv;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                double tot = (double)acc[r] + accd[r];
-                for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                red[par][warp][r][lane] = lane < tk.nr ? tot : 0.0;
+                for (int r = 0; r < NR; ++r) {
+                    double tot = (double)acc[r] * ks + accd[r];
+                    for (int o = span; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                    red[par][warp][r][lane] = lane < tk.nr ? tot : 0.0;
+                }
             }
             cp_async_wait_all();
             consumer_barrier();   // also publishes the next item's vectors
@@ -1236,7 +1395,7 @@ __global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const in
 // coefficients [k][j][i] for k < W: exact kernel below m_S(i, j), static * dt above
 template <class H, class A>
 __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double dt, double mu, double c,
-                                 H* tensor, A* stat) {
+                                 double kscale, H* tensor, A* stat) {
     const long long total = (long long)L.W * L.ns * L.nr;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
@@ -1256,7 +1415,7 @@ __global__ void near_fill_kernel(GeoDev g, NearDev L, const int* ms_leaf, double
             v = (g.nx[pi] * w.x + g.ny[pi] * w.y) * dt;
         }
         constexpr int vh = 16 / (int)sizeof(H), va = 16 / (int)sizeof(A);   // source-interleaved slices (plan.h)
-        tensor[L.tensor + (long long)k * L.sl + ((jl / vh) * L.nr + il) * vh + jl % vh] = (H)v;
+        tensor[L.tensor + (long long)k * L.sl + ((jl / vh) * L.nr + il) * vh + jl % vh] = (H)(v * kscale);
         if (k == 0) {
             const Stress2 w = stress_static(g.px[pi], g.py[pi], s, mu);
             stat[L.stat + ((jl / va) * L.nr + il) * va + jl % va] = (A)((g.nx[pi] * w.x + g.ny[pi] * w.y) * dt);
@@ -1380,6 +1539,7 @@ struct fdph_plan_s {
     std::vector<int32_t> near_W;
     std::vector<char> near_tail;
     int chunk = 0;            // steps of exact kernel per near-field work item
+    double kscale = 1.0;      // FP16 window coefficients are stored as K * kscale (a power of two)
     int sched_version = 0;    // bumped whenever the near-field items are rebuilt
     size_t partial_cap = 0;   // capacity of `partial`, in doubles
     // branches of a step that run concurrently with the near field: [0] FIR + scatter,
@@ -1466,6 +1626,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.n_cta = P->n_cta;
     a.n_items = (int)P->hp.items.size();
     a.tensor = P->tensor;
+    a.kinv = (float)(1.0 / P->kscale);
     a.stat = P->stat;
     a.partial = P->partial;
     a.np_ptr = P->np_ptr;
@@ -2048,6 +2209,12 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
                  (long long)L.vstate};
     }
     if ((rc = upload(P, &P->near, nd))) return rc;
+    // FP16 windows: coefficients are stored times 2^e, e = 13 - ceil(log2(mu / (2 cs))), so that
+    // the radiation-damping self term mu / (2 cs), the largest coefficient, sits near 2^13: far
+    // from the FP16 overflow (65504) whatever the units, and small coefficients keep the normal
+    // FP16 range; the products are scaled back by 2^-e
+    P->kscale = std::is_same<H, __half>::value ? std::ldexp(1.0, 13 - (int)std::ceil(std::log2(in.mu / (2.0 * in.cs))))
+                                                : 1.0;
     H* tens = nullptr;
     A* aux = nullptr;
     if ((rc = dalloc(P, &tens, hp.near_tensor_len)) || (rc = dalloc(P, &aux, hp.near_aux_len))) return rc;
@@ -2068,10 +2235,10 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
             L1.W = 1;
             L1.tensor = 0;
             near_fill_kernel<H, A><<<blocks((long long)L.ns * L.nr, 128), 128, 0, P->stream>>>(g, L1, d_ms + pair0[l], in.dt,
-                                                                            in.mu, in.cs, tmp, aux);
+                                                                            in.mu, in.cs, P->kscale, tmp, aux);
         } else {
             near_fill_kernel<H, A><<<std::min<long long>(blocks(tot, 256), 4096), 256, 0, P->stream>>>(
-                g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, tens, aux);
+                g, L, d_ms + pair0[l], in.dt, in.mu, in.cs, P->kscale, tens, aux);
         }
         FDPH_CUDA(cudaGetLastError());
     }

@@ -109,6 +109,8 @@ struct StepArgs {
     const int* perm;          // internal -> geometry
     double* Dring;            // [WD][N]
     float* Dring32;           // [WD][N] FP32 copy of Dring (plans whose near-field rows are FP32)
+    __half2* Dring16;         // [WD][N] scaled FP16 (hi, lo) pairs of Dring (FP16 plans, nrhs >= 2)
+    float* Dscale;            // [WD] inverse power-of-two scale of each Dring16 row
     double* Cring;            // [WC][N]
     double* C;                // [N] cumulative slip (rounded sum)
     double* Ccomp;            // [N] Kahan compensation
@@ -201,6 +203,8 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         if (a0.T_out) a.T_out = a0.T_out + rN;
         a.Dring = a0.Dring + r * a0.rs_D;
         if (a0.Dring32) a.Dring32 = a0.Dring32 + r * a0.rs_D;
+        if (a0.Dring16) a.Dring16 = a0.Dring16 + r * a0.rs_D;
+        if (a0.Dscale) a.Dscale = a0.Dscale + (long long)r * a0.WD;
         a.Cring = a0.Cring + r * a0.rs_C;
         a.C = a0.C + rN;
         a.Ccomp = a0.Ccomp + rN;
@@ -222,6 +226,45 @@ __global__ void advance_step_kernel(int* n_dev) { *n_dev += 1; }
 __global__ void ring_to_float_kernel(const double* x, float* y, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (float)x[i];
+}
+
+// Slip-rate rows for the tensor-core near field (FP16 window, nrhs >= 2): ring row (slot, RHS) as
+// (hi, lo) FP16 pairs of x 2^sh, sh = 14 - e for the row's largest |x| = f 2^e, f in [0.5, 1)
+// (e from the exponent field; a zero or subnormal row takes the largest shift), hi = fp16(x 2^sh),
+// lo = fp16(x 2^sh - hi), and Dscale = 2^-sh.  One CTA per row: the row of step n (all_slots 0,
+// after push), or every slot (all_slots 1, after a state restore).  grid (slots or 1, nrhs).
+constexpr int kRowThreads = 256;
+
+__device__ __forceinline__ int row_shift(float m) {
+    const int e = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xffu) - 126 : -126;
+    return min(max(14 - e, -100), 100);
+}
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
+
+template <class T>
+__global__ void __launch_bounds__(kRowThreads) tc_rows_kernel(StepArgs<T> a0, int all_slots) {
+    __shared__ float wmax[kRowThreads / 32];
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int slot = all_slots ? blockIdx.x : wrap(step_index(a), a.WD);
+    const double* row = a.Dring + (size_t)slot * a.N;
+    float m = 0.f;
+    for (int p = threadIdx.x; p < a.N; p += kRowThreads) m = fmaxf(m, fabsf((float)row[p]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < kRowThreads / 32; ++w) m = fmaxf(m, wmax[w]);
+    const int sh = row_shift(m);
+    const float s = pow2f(sh);
+    __half2* out = a.Dring16 + (size_t)slot * a.N;
+    for (int p = threadIdx.x; p < a.N; p += kRowThreads) {
+        const float y = (float)row[p] * s;
+        const __half hi = __float2half_rn(y);
+        out[p] = __halves2half2(hi, __float2half_rn(y - __half2float(hi)));
+    }
+    if (threadIdx.x == 0) a.Dscale[slot] = pow2f(-sh);
 }
 
 __global__ void set_step_kernel(int* n_dev, int v) {
@@ -539,6 +582,8 @@ __device__ __forceinline__ int near_slices(const NearTask& tk, int n) {
 struct NearView {
     const double* Dring;
     const float* Dring32;
+    const __half2* Dring16;
+    const float* Dscale;
     const double* Cring;
     double* vstate;
     const double* rho;
@@ -556,6 +601,8 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     NearView v;
     v.Dring = a.Dring;
     v.Dring32 = a.Dring32;
+    v.Dring16 = a.Dring16;
+    v.Dscale = a.Dscale;
     v.Cring = a.Cring;
     v.vstate = a.vstate;
     v.rho = a.rho;
@@ -588,7 +635,11 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
-template <class R, int NR, int VR>
+// tensor-core window rows in the vector buffer: (hi, lo) pairs, rows of kTcRow words (160 bytes:
+// the 64-bit fragment loads of one half-warp land on distinct banks), then one scale per row
+constexpr int kTcRow = 40;
+
+template <class R, int NR, int VR, bool TC>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
                                            double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb) {
     const int n = a.n;
@@ -605,10 +656,14 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
                 int slot = b0 - k;                     // k < W < WD: one wrap at most
                 slot += slot < 0 ? a.WD : 0;
                 const size_t off = q * a.rs_D + (size_t)slot * a.N + col;
-                if constexpr (sizeof(R) == 4)
+                if constexpr (TC) {
+                    cp_async_4((unsigned*)vb + v * kTcRow + lane, a.Dring16 + off, on ? 4 : 0);
+                    if (lane == 0) cp_async_4((float*)vb + VR * kTcRow + v, a.Dscale + (size_t)q * a.WD + slot, 4);
+                } else if constexpr (sizeof(R) == 4) {
                     cp_async_4((R*)vb + v * 32 + lane, a.Dring32 + off, on ? 4 : 0);
-                else
+                } else {
                     cp_async_8((R*)vb + v * 32 + lane, a.Dring + off, on ? 8 : 0);
+                }
             }
         }
     } else {
@@ -669,7 +724,9 @@ struct NearCfg {
     // shared-memory pipeline depth, within two CTAs per SM next to the vector buffers and the
     // partial sums of the right-hand sides
     static constexpr int stages = NR >= 8 ? 3 : NR >= 2 ? 4 : sizeof(R) == 4 ? 5 : 4;
-    static constexpr int vec_bytes = vec_rows * 32 * (int)sizeof(R);  // one item's vectors
+    // tensor-core window rows (FP16 window, several right-hand sides) take more room per row
+    static constexpr bool tc = std::is_same<H, __half>::value && NR >= 2;
+    static constexpr int vec_bytes = tc ? vec_rows * (kTcRow * 4 + 4) : vec_rows * 32 * (int)sizeof(R);
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
 };
 
@@ -842,24 +899,18 @@ __device__ __forceinline__ void slice_dot_nr(const __half* buf, const float* vro
 // sides, a dense (32 x 32) x (32 x NR) contraction: warp-level mma.sync m16n8k16 (FP16 inputs, FP32
 // accumulation), two 16-receiver tiles x two 16-source steps.  The A fragments come straight from
 // the stage with ldmatrix (the source-interleaved slice layout of plan.h puts 8 sources of one
-// receiver in 16 contiguous bytes, the rows of an 8 x 8 ldmatrix tile).  The slip rates are FP32:
-// each (slice, RHS) row of 32 sources is scaled by a power of two that brings its largest entry
-// into [2^13, 2^14) and split into two FP16 parts, hi = fp16(x s) and lo = fp16(x s - hi), so that
-// the tensor-core products carry the slip rates to about 2^-22 relative (2^-39 of the row's largest
-// entry in absolute terms) and the only rounding of the FP16 path remains that of the stored
-// coefficients.  hi and lo are two B columns (NR <= 4: one 8-column pass holds both, columns v and
-// v + NR) or two passes into the same accumulator (NR = 8); each slice's products are scaled back
-// by 2^-s per column and added to the item's FP32 sums.
-constexpr int kBtStride = 40;   // halves per B row: 80-byte rows, ldmatrix rows on distinct bank groups
-
+// receiver in 16 contiguous bytes, the rows of an 8 x 8 ldmatrix tile).  The slip rates come from
+// the ring's FP16 (hi, lo) copy (tc_rows_kernel: each ring row scaled by a power of two that puts
+// its largest entry in [2^13, 2^14), hi + lo carrying it to ~2^-22 relative, 2^-39 of the row's
+// largest entry absolute), so that the only rounding of the FP16 path remains that of the stored
+// coefficients.  hi and lo are separate B columns: one 8-column pass holds both for NR <= 4
+// (columns q and q + NR), NR = 8 takes a hi pass and a lo pass into the same accumulator; the B
+// fragments are packed from the (hi, lo) pairs with byte permutes.  Each slice's products are
+// scaled back per column by its row's 2^-sh and added to the item's FP32 sums.
 __device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void ldsm_x2(unsigned (&r)[2], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_u32(p)));
 }
 
 __device__ __forceinline__ void mma_16816(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
@@ -870,38 +921,28 @@ __device__ __forceinline__ void mma_16816(float (&c)[4], const unsigned (&a)[4],
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// 2^k as a float, k in [-126, 127]
-__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
-
-// One window slice (sl: its stage copy; rows: its NR FP32 slip-rate rows, lane = source) into the
-// warp's accumulators acc[m-tile][fragment] (rows g, g + 8 of each 16-receiver tile, columns 2t,
-// 2t + 1 with g = lane / 4, t = lane % 4).  bt: the warp's B tile, 2 NR rows of kBtStride halves.
+// One window slice (sl: its stage copy; rows: its NR (hi, lo) rows of kTcRow words, lane =
+// source; sc: their NR scales) into the warp's accumulators acc[m-tile][fragment] (rows g, g + 8 of
+// each 16-receiver tile, columns 2t, 2t + 1, with g = lane / 4, t = lane % 4).
 template <int NR>
-__device__ __forceinline__ void tc_slice(const __half* sl, const float* rows, int nr, int ns, __half* bt, int lane,
-                                         float (&acc)[2][4]) {
+__device__ __forceinline__ void tc_slice(const __half* sl, const unsigned* rows, const float* sc, int nr, int ns,
+                                         int lane, float (&acc)[2][4]) {
     static_assert(NR == 2 || NR == 4 || NR == 8, "tensor-core slices take 2, 4 or 8 right-hand sides");
-    float inv[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-        const float x = rows[q * 32 + lane];
-        float m = fabsf(x);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        // m = f 2^e with f in [0.5, 1) (e from the exponent field; a zero or subnormal row takes the
-        // largest shift); scale by 2^sh, sh = 14 - e, clamped to stay a normal float
-        const int e = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xffu) - 126 : -126;
-        const int sh = min(max(14 - e, -100), 100);
-        inv[q] = pow2f(-sh);
-        const float y = x * pow2f(sh);
-        const __half hi = __float2half_rn(y);
-        bt[q * kBtStride + lane] = hi;
-        bt[(NR + q) * kBtStride + lane] = __float2half_rn(y - __half2float(hi));
-    }
-    __syncwarp();
     const int ng = (ns + 7) >> 3;          // 8-source groups of the slice (zero-padded)
     const int nks = (ng + 1) >> 1;         // 16-source steps
     const int nmt = nr > 16 ? 2 : 1;       // 16-receiver tiles
     constexpr int npass = (2 * NR + 7) / 8;
+    const int g = lane >> 2, t = lane & 3;
+    // B column g of pass p: virtual row 8 p + g = right-hand side (8p + g) % NR, part
+    // ((8p + g) / NR) & 1 (0 hi, 1 lo; NR = 2 repeats its four columns, unused)
+    const unsigned* brow[npass];
+    unsigned bsel[npass];
+#pragma unroll
+    for (int p = 0; p < npass; ++p) {
+        const int vr = 8 * p + g;
+        brow[p] = rows + (vr % NR) * kTcRow + 2 * t;
+        bsel[p] = ((vr / NR) & 1) ? 0x7632u : 0x5410u;   // high or low halves of two (hi, lo) pairs
+    }
     float c[2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -912,9 +953,11 @@ __device__ __forceinline__ void tc_slice(const __half* sl, const float* rows, in
         unsigned b[npass][2];
 #pragma unroll
         for (int p = 0; p < npass; ++p) {
-            // rows past 2 NR repeat the last one (their columns are not used)
-            const int v = min(8 * p + mr, 2 * NR - 1);
-            ldsm_x2(b[p], bt + v * kBtStride + 16 * kk + 8 * (mq & 1));
+            // sources 16 kk + 2t, + 1 (b[0]) and 16 kk + 8 + 2t, + 1 (b[1]); past ns they are zero
+            const uint2 w0 = *reinterpret_cast<const uint2*>(brow[p] + 16 * kk);
+            const uint2 w1 = *reinterpret_cast<const uint2*>(brow[p] + 16 * kk + 8);
+            b[p][0] = __byte_perm(w0.x, w0.y, bsel[p]);
+            b[p][1] = __byte_perm(w1.x, w1.y, bsel[p]);
         }
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
@@ -930,15 +973,8 @@ __device__ __forceinline__ void tc_slice(const __half* sl, const float* rows, in
             }
         }
     }
-    __syncwarp();   // bt is rewritten by the next slice
-    // column v holds right-hand side v % NR; the scale is picked without a dynamic register index
-    const int t = lane & 3;
-    float s0 = inv[0], s1 = inv[1 % NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-        s0 = (2 * t) % NR == q ? inv[q] : s0;
-        s1 = (2 * t + 1) % NR == q ? inv[q] : s1;
-    }
+    // column v holds right-hand side v % NR
+    const float s0 = sc[(2 * t) % NR], s1 = sc[(2 * t + 1) % NR];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
         acc[mt][0] = fmaf(c[mt][0], s0, acc[mt][0]);
@@ -992,7 +1028,6 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
     extern __shared__ __align__(128) unsigned char near_smem[];
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][NR][32];
-    __shared__ __align__(16) __half btile[kTC ? kNearConsumers : 1][kTC ? 2 * NR * kBtStride : 8];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
@@ -1052,7 +1087,7 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<R, NR, C::vec_rows>(vn, nxt, warp, lane, rows, dW, vbuf);
+            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf);
             near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         cp_async_wait_all();
@@ -1065,7 +1100,7 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<R, NR, C::vec_rows>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -1103,8 +1138,10 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
                     if constexpr (kTC) {
                         if (tc) {
-                            tc_slice<NR>((const __half*)buf + (size_t)kk * tk.sl, (const float*)vrow, tk.nr, tk.ns,
-                                         btile[warp], lane, tacc);
+                            const int ks = q * per + kk;   // slice of the item
+                            tc_slice<NR>((const __half*)buf + (size_t)kk * tk.sl,
+                                         (const unsigned*)vrows + (size_t)ks * NR * kTcRow,
+                                         (const float*)vrows + C::vec_rows * kTcRow + ks * NR, tk.nr, tk.ns, lane, tacc);
                             continue;
                         }
                     }
@@ -1514,6 +1551,8 @@ struct fdph_plan_s {
     // state
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
     float* Dring32 = nullptr;   // FP32 copy of Dring (FP32 / FP16 plans)
+    __half2* Dring16 = nullptr; // scaled FP16 (hi, lo) copy of Dring (tensor-core near field)
+    float* Dscale = nullptr;    // its per-row inverse scales
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
     size_t state_bytes = 0;
     // host staging for fdph_step_host
@@ -1592,6 +1631,8 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.perm = P->perm;
     a.Dring = P->Dring;
     a.Dring32 = P->Dring32;
+    a.Dring16 = P->Dring16;
+    a.Dscale = P->Dscale;
     a.Cring = P->Cring;
     a.C = P->C;
     a.Ccomp = P->Ccomp;
@@ -1721,7 +1762,11 @@ static void launch_near(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
 
 template <class T>
 static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
-    { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }
+    {
+        ProfScope ps(P, 0);
+        push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a);
+        if (a.Dring16) tc_rows_kernel<T><<<dim3(1, a.nrhs), kRowThreads, 0, s>>>(a, 0);
+    }
     if (!P->prof && P->side[0]) {
         // Within a step, FIR + scatter (writes ring slots n + delay >= n + 1), the transient
         // convolution + Eq. 39 (read slots <= n - min dm, completed by earlier steps; causality
@@ -3039,6 +3084,11 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         if ((rc = dalloc(P, &P->Dring32, c))) return fail(rc);
         sb += c * 4;
     }
+    if (P->precision == FDPH_FP16 && P->nrhs >= 2) {   // (hi, lo) FP16 rows of the tensor-core near field
+        const size_t c = (size_t)P->WD * P->N * P->nrhs;
+        if ((rc = dalloc(P, &P->Dring16, c)) || (rc = dalloc(P, &P->Dscale, (size_t)P->WD * P->nrhs))) return fail(rc);
+        sb += c * 4 + (size_t)P->WD * P->nrhs * 4;
+    }
     P->state_bytes = sb;
     P->partial_cap = std::max<size_t>(hp.items.size() * 32, 1);
     if ((rc = fdph_reset(P))) return fail(rc);
@@ -3062,6 +3112,10 @@ int fdph_reset(fdph_plan_t P) {
             FDPH_CUDA(cudaMemsetAsync(bufs[q], 0, std::max<size_t>(cnt[q], 1) * P->nrhs * sizeof(double), P->stream));
     if (P->Dring32)
         FDPH_CUDA(cudaMemsetAsync(P->Dring32, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(float), P->stream));
+    if (P->Dring16) {
+        FDPH_CUDA(cudaMemsetAsync(P->Dring16, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(__half2), P->stream));
+        FDPH_CUDA(cudaMemsetAsync(P->Dscale, 0, (size_t)P->WD * P->nrhs * sizeof(float), P->stream));
+    }
     if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->n = 0;
@@ -3312,6 +3366,13 @@ int fdph_load_state(fdph_plan_t P, const void* buf, size_t len) {
     if (P->Dring32) {
         const long long c = (long long)P->WD * P->N * P->nrhs;
         ring_to_float_kernel<<<blocks(c, 256), 256, 0, P->stream>>>(P->Dring, P->Dring32, c);
+        FDPH_CUDA(cudaGetLastError());
+    }
+    if (P->Dring16) {   // every slot of the (hi, lo) FP16 rows from the restored ring
+        if (P->precision == FDPH_FP16) {
+            const StepArgs<float> a = make_args<float>(P, nullptr, nullptr);
+            tc_rows_kernel<float><<<dim3(P->WD, P->nrhs), kRowThreads, 0, P->stream>>>(a, 1);
+        }
         FDPH_CUDA(cudaGetLastError());
     }
     FDPH_CUDA(cudaStreamSynchronize(P->stream));   // the caller may reuse the buffer on return

@@ -9,7 +9,10 @@
 //      below any criterion eps used with the method, and it is counted in the discarded part
 //      of the rank decision.  Rounding noise of the kernel values makes the numerical rank
 //      at 1e-15 nearly full (512 x 512 blocks: ~490-514); at 1e-11 the mean k of the curved
-//      N = 4096 plan is 16 (30 at 1e-12), and the Jacobi stage below costs O(n k^2) a sweep;
+//      N = 4096 plan is 16 (30 at 1e-12), and the Jacobi stage below costs O(n k^2) a sweep.
+//      Blocks whose rounding noise itself sits above 1e-11 (the transient's spatial slices of
+//      large blocks: 980 of 1024 singular values above 1e-11 on a planar fault) stop after 64
+//      steps once the trailing block is below 1e-3 eps |A|_F;
 //   2. SVD of the k x n row space B = R P^T: Householder QR of B^T, then one-sided (Hestenes)
 //      Jacobi on the k x k triangular factor.
 // Factors are balanced: F = U_r sqrt(S_r), G = V_r sqrt(S_r).  When the chosen rank would
@@ -125,6 +128,14 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
     const int kmax = std::min(m, n);
     int k = 0;
     const double stop2 = 1e-22 * norm2;
+    // A block still above the 1e-11 floor after kNoiseSteps steps is dominated by the rounding of
+    // its entries (the Domain-S transient's spatial slice is a difference of nearly equal kernel
+    // values, accurate to ~1e-11 relative: its numerical rank at 1e-11 is nearly full, and the QR
+    // would run to m n min(m, n) work); from there the QR also stops at (1e-3 eps)^2 |A|^2, which
+    // changes the rank decision by at most that share of the criterion (the remainder is counted
+    // as discarded) and the factors by at most 1e-3 eps |A|
+    const int kNoiseSteps = 64;
+    const double stop2_eps = 1e-6 * eps * eps * norm2;
     // squared norms of the columns' trailing parts, downdated after each reflection (cn) and
     // recomputed from the column when the downdate has cancelled most of the value they had at
     // their last recomputation (cn0), as in the usual pivoted QR
@@ -141,7 +152,7 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
             trail = 0.0;
             for (int j = k; j < n; ++j) trail += (cn[j] = cn0[j] = trailing(j, k));
         }
-        if (trail <= stop2) break;
+        if (trail <= stop2 || (k >= kNoiseSteps && trail <= stop2_eps)) break;
         int best = k;
         for (int j = k + 1; j < n; ++j)
             if (cn[j] > cn[best]) best = j;

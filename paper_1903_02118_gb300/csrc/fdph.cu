@@ -4,7 +4,9 @@
 // as one CUDA graph: FIR + scatter and transient + Eq. 39 on two side streams, concurrently with
 // the near field, all joined before gather; grid y = right-hand side):
 //   push     D_n -> slip-rate ring (internal order); cumulative slip C_j(n) = sum_{s<=n} D_j,s
-//            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring
+//            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring; with the tensor-core
+//            near field (FP16 window, several right-hand sides) also the ring row's scaled FP16
+//            (hi, lo) copy (tc_rows)
 //   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}
 //   scatter  formula 2 (Eq. 42): Tbar'_l[n + delay_j] += g_{l,j} u_j for every run of sources
 //            (rings are stored [slot][rank] so that one receiver's ranks share a sector)
@@ -14,8 +16,9 @@
 //   trconv   transient (App. B.3): Z_l(n - min dm) = sum_{m < Dm_tr} h^tr_m Y_l(n - min dm - m)
 //   near     inadmissible leaves (App. E): sum_{k < W} K_{ij,k} D_{j,n-k} + Kstat_ij dt C_j(n-W),
 //            per (leaf, chunk of k) work item into a partial-sum slot
-//   gather   formula 3 (Eq. 39): T_i = sum_{blocks} sum_l f_{l,i} Tbar'_l[n - dm_i] + near
-//            partials, written in the caller's element order
+//   far_eval + far_sum  formula 3 (Eq. 39): Tfar_i = sum_{blocks} sum_l f_{l,i} Tbar'_l[n - dm_i]
+//            (far-field branch)
+//   gather   T_i = Tfar_i + the receiver's near partials, written in the caller's element order
 // Causality (min(dm + delay) >= 1, checked at plan time) guarantees that the ring slots read
 // at step n were completed by steps < n and that the slots written at step n are not read.
 // A rupture step (Sec. 6.2) predicts with D_n = 0, solves the friction law per element and
@@ -128,6 +131,7 @@ struct StepArgs {
     int n_evt;
     const int* e_pos;         // CSR slot of each (block, receiver) entry, block-major
     double* fval;             // [entries] far-field value of each (block, receiver) entry, CSR order
+    double* tfar;             // [N] far-field traction of each receiver (sum of its entries)
     const int* fir_sb;
     const int* fir_j;
     int n_fir;
@@ -212,6 +216,7 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         a.zring = a0.zring + r * a0.rs_zring;
         a.dhat = a0.dhat + r * a0.rs_dhat;
         a.fval = a0.fval + r * a0.rs_fval;
+        a.tfar = a0.tfar + rN;
         if (a0.ustate) a.ustate = a0.ustate + r * a0.rs_ustate;
         if (a0.vstate) a.vstate = a0.vstate + r * a0.rs_vstate;
         a.partial = a0.partial + r * a0.rs_partial;
@@ -921,66 +926,73 @@ __device__ __forceinline__ void mma_16816(float (&c)[4], const unsigned (&a)[4],
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// One window slice (sl: its stage copy; rows: its NR (hi, lo) rows of kTcRow words, lane =
-// source; sc: their NR scales) into the warp's accumulators acc[m-tile][fragment] (rows g, g + 8 of
-// each 16-receiver tile, columns 2t, 2t + 1, with g = lane / 4, t = lane % 4).
-template <int NR>
-__device__ __forceinline__ void tc_slice(const __half* sl, const unsigned* rows, const float* sc, int nr, int ns,
-                                         int lane, float (&acc)[2][4]) {
+// S window slices at once (sl[s]: stage copy; rows[s]: their NR (hi, lo) rows of kTcRow words,
+// lane = source; sc[s]: their NR scales) into the warp's accumulators acc[m-tile][fragment] (rows g,
+// g + 8 of each 16-receiver tile, columns 2t, 2t + 1, with g = lane / 4, t = lane % 4).  All
+// fragments are loaded first and the MMAs of the S slices and two receiver tiles interleave, so
+// that 2 S independent accumulator chains are in flight.
+template <int NR, int S>
+__device__ __forceinline__ void tc_slices(const __half* const (&sl)[S], const unsigned* const (&rows)[S],
+                                          const float* const (&sc)[S], int nr, int ns, int lane, float (&acc)[2][4]) {
     static_assert(NR == 2 || NR == 4 || NR == 8, "tensor-core slices take 2, 4 or 8 right-hand sides");
     const int ng = (ns + 7) >> 3;          // 8-source groups of the slice (zero-padded)
     const int nks = (ng + 1) >> 1;         // 16-source steps
     const int nmt = nr > 16 ? 2 : 1;       // 16-receiver tiles
     constexpr int npass = (2 * NR + 7) / 8;
     const int g = lane >> 2, t = lane & 3;
-    // B column g of pass p: virtual row 8 p + g = right-hand side (8p + g) % NR, part
-    // ((8p + g) / NR) & 1 (0 hi, 1 lo; NR = 2 repeats its four columns, unused)
-    const unsigned* brow[npass];
-    unsigned bsel[npass];
-#pragma unroll
-    for (int p = 0; p < npass; ++p) {
-        const int vr = 8 * p + g;
-        brow[p] = rows + (vr % NR) * kTcRow + 2 * t;
-        bsel[p] = ((vr / NR) & 1) ? 0x7632u : 0x5410u;   // high or low halves of two (hi, lo) pairs
-    }
-    float c[2][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) c[mt][f] = 0.f;
     const int mq = lane >> 3, mr = lane & 7;   // ldmatrix: lane gives row mr of matrix mq
+    float c[S][2][4];
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) c[q][mt][f] = 0.f;
     for (int kk = 0; kk < nks; ++kk) {
-        unsigned b[npass][2];
+        // B column g of pass p: virtual row 8 p + g = right-hand side (8p + g) % NR, part
+        // ((8p + g) / NR) & 1 (0 hi, 1 lo; NR = 2 repeats its four columns, unused); sources
+        // 16 kk + 2t, + 1 (b[0]) and 16 kk + 8 + 2t, + 1 (b[1]), zero past ns
+        unsigned b[S][npass][2], a[S][2][4];
 #pragma unroll
-        for (int p = 0; p < npass; ++p) {
-            // sources 16 kk + 2t, + 1 (b[0]) and 16 kk + 8 + 2t, + 1 (b[1]); past ns they are zero
-            const uint2 w0 = *reinterpret_cast<const uint2*>(brow[p] + 16 * kk);
-            const uint2 w1 = *reinterpret_cast<const uint2*>(brow[p] + 16 * kk + 8);
-            b[p][0] = __byte_perm(w0.x, w0.y, bsel[p]);
-            b[p][1] = __byte_perm(w1.x, w1.y, bsel[p]);
-        }
+        for (int q = 0; q < S; ++q) {
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            if (mt < nmt) {
-                // receivers past nr and source groups past ng read valid rows of this slice (their
+            for (int p = 0; p < npass; ++p) {
+                const int vr = 8 * p + g;
+                const unsigned* br = rows[q] + (vr % NR) * kTcRow + 2 * t + 16 * kk;
+                const unsigned sel = ((vr / NR) & 1) ? 0x7632u : 0x5410u;   // high or low halves of two pairs
+                const uint2 w0 = *reinterpret_cast<const uint2*>(br);
+                const uint2 w1 = *reinterpret_cast<const uint2*>(br + 8);
+                b[q][p][0] = __byte_perm(w0.x, w0.y, sel);
+                b[q][p][1] = __byte_perm(w1.x, w1.y, sel);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                // receivers past nr and source groups past ng read valid rows of the slice (their
                 // products land in unused rows, or meet zero slip rates)
                 const int i = min(16 * mt + 8 * (mq & 1) + mr, nr - 1);
                 const int gg = min(2 * kk + (mq >> 1), ng - 1);
-                unsigned a[4];
-                ldsm_x4(a, sl + ((size_t)gg * nr + i) * 8);
-#pragma unroll
-                for (int p = 0; p < npass; ++p) mma_16816(c[mt], a, b[p]);
+                if (mt < nmt) ldsm_x4(a[q][mt], sl[q] + ((size_t)gg * nr + i) * 8);
             }
         }
+#pragma unroll
+        for (int p = 0; p < npass; ++p)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    if (mt < nmt) mma_16816(c[q][mt], a[q][mt], b[q][p]);
     }
     // column v holds right-hand side v % NR
-    const float s0 = sc[(2 * t) % NR], s1 = sc[(2 * t + 1) % NR];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        acc[mt][0] = fmaf(c[mt][0], s0, acc[mt][0]);
-        acc[mt][1] = fmaf(c[mt][1], s1, acc[mt][1]);
-        acc[mt][2] = fmaf(c[mt][2], s0, acc[mt][2]);
-        acc[mt][3] = fmaf(c[mt][3], s1, acc[mt][3]);
+    for (int q = 0; q < S; ++q) {
+        const float s0 = sc[q][(2 * t) % NR], s1 = sc[q][(2 * t + 1) % NR];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            acc[mt][0] = fmaf(c[q][mt][0], s0, acc[mt][0]);
+            acc[mt][1] = fmaf(c[q][mt][1], s1, acc[mt][1]);
+            acc[mt][2] = fmaf(c[q][mt][2], s0, acc[mt][2]);
+            acc[mt][3] = fmaf(c[q][mt][3], s1, acc[mt][3]);
+        }
     }
 }
 
@@ -1138,10 +1150,24 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
                     if constexpr (kTC) {
                         if (tc) {
+                            // this warp's slices kk and kk + kNearConsumers of the stage together
                             const int ks = q * per + kk;   // slice of the item
-                            tc_slice<NR>((const __half*)buf + (size_t)kk * tk.sl,
-                                         (const unsigned*)vrows + (size_t)ks * NR * kTcRow,
-                                         (const float*)vrows + C::vec_rows * kTcRow + ks * NR, tk.nr, tk.ns, lane, tacc);
+                            const unsigned* rw = (const unsigned*)vrows;
+                            const float* scl = (const float*)vrows + C::vec_rows * kTcRow;
+                            if (kk + kNearConsumers < cnt) {
+                                const int ks2 = ks + kNearConsumers;
+                                const __half* const sl2[2] = {(const __half*)buf + (size_t)kk * tk.sl,
+                                                              (const __half*)buf + (size_t)(kk + kNearConsumers) * tk.sl};
+                                const unsigned* const rw2[2] = {rw + (size_t)ks * NR * kTcRow, rw + (size_t)ks2 * NR * kTcRow};
+                                const float* const sc2[2] = {scl + ks * NR, scl + ks2 * NR};
+                                tc_slices<NR, 2>(sl2, rw2, sc2, tk.nr, tk.ns, lane, tacc);
+                                kk += kNearConsumers;
+                            } else {
+                                const __half* const sl1[1] = {(const __half*)buf + (size_t)kk * tk.sl};
+                                const unsigned* const rw1[1] = {rw + (size_t)ks * NR * kTcRow};
+                                const float* const sc1[1] = {scl + ks * NR};
+                                tc_slices<NR, 1>(sl1, rw1, sc1, tk.nr, tk.ns, lane, tacc);
+                            }
                             continue;
                         }
                     }
@@ -1249,22 +1275,38 @@ __global__ void far_eval_kernel(StepArgs<T> a0) {
     if (w < a.n_evt) far_eval_body(a, w, threadIdx.x & 31);   // warp-uniform
 }
 
-// one warp per receiver: sum of its far entries and near-field partials, fixed order
+// Eq. 39 summed per receiver: one warp per receiver adds its far entries (fixed order) into
+// tfar; this runs on the far-field branch, beside the near field
 template <class T>
-__device__ __forceinline__ void gather_body(const StepArgs<T>& a, int p, int lane) {
-    const int n = step_index(a);
+__device__ __forceinline__ void far_sum_body(const StepArgs<T>& a, int p, int lane) {
     double s = 0.0;
     for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
-    for (int e = a.np_ptr[p] + lane; e < a.np_ptr[p + 1]; e += 32) s += a.partial[a.np_idx[e]];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) a.T_out[io_offset(a, n) + a.perm[p]] = s;
+    if (lane == 0) a.tfar[p] = s;
+}
+
+template <class T>
+__global__ void far_sum_kernel(StepArgs<T> a0) {
+    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p < a.N) far_sum_body(a, p, threadIdx.x & 31);   // warp-uniform
+}
+
+// the step's output: far-field traction + the receiver's near-field partial sums (a few per
+// receiver, fixed order), one thread per receiver, written in the caller's element order
+template <class T>
+__device__ __forceinline__ void gather_body(const StepArgs<T>& a, int p) {
+    const int n = step_index(a);
+    double s = a.tfar[p];
+    for (int e = a.np_ptr[p]; e < a.np_ptr[p + 1]; ++e) s += a.partial[a.np_idx[e]];
+    a.T_out[io_offset(a, n) + a.perm[p]] = s;
 }
 
 template <class T>
 __global__ void gather_kernel(StepArgs<T> a0) {
     const StepArgs<T> a = rhs_args(a0, blockIdx.y);
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (p < a.N) gather_body(a, p, threadIdx.x & 31);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < a.N) gather_body(a, p);
 }
 
 // Local friction solve (geometry order): T_pred holds the traction change with D_n = 0.
@@ -1359,11 +1401,19 @@ __global__ void far_eval_batch(const StepArgs<T>* scen, const int* pre, int np) 
 }
 
 template <class T>
-__global__ void gather_batch(const StepArgs<T>* scen, const int* pre, int np) {
+__global__ void far_sum_batch(const StepArgs<T>* scen, const int* pre, int np) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= pre[np]) return;
     const int p = plan_of(pre, np, w);
-    gather_body(scen[p], w - pre[p], threadIdx.x & 31);
+    far_sum_body(scen[p], w - pre[p], threadIdx.x & 31);
+}
+
+template <class T>
+__global__ void gather_batch(const StepArgs<T>* scen, const int* pre, int np) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pre[np]) return;
+    const int p = plan_of(pre, np, t);
+    gather_body(scen[p], t - pre[p]);
 }
 
 template <class T>
@@ -1552,6 +1602,7 @@ struct fdph_plan_s {
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
     float* Dring32 = nullptr;   // FP32 copy of Dring (FP32 / FP16 plans)
     __half2* Dring16 = nullptr; // scaled FP16 (hi, lo) copy of Dring (tensor-core near field)
+    double* tfar = nullptr;     // [nrhs][N] far-field traction of the step (scratch)
     float* Dscale = nullptr;    // its per-row inverse scales
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
     size_t state_bytes = 0;
@@ -1633,6 +1684,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.Dring32 = P->Dring32;
     a.Dring16 = P->Dring16;
     a.Dscale = P->Dscale;
+    a.tfar = P->tfar;
     a.Cring = P->Cring;
     a.C = P->C;
     a.Ccomp = P->Ccomp;
@@ -1778,12 +1830,13 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         eq42<T>(a, P->side[0]);
         if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
         if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
+        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
         if (a.n_cta) launch_near<T>(P, a, s);
         cudaEventRecord(P->ev_join[0], P->side[0]);
         cudaEventRecord(P->ev_join[1], P->side[1]);
         cudaStreamWaitEvent(s, P->ev_join[0], 0);
         cudaStreamWaitEvent(s, P->ev_join[1], 0);
-        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
         return;
     }
     // serial order (per-kernel timing)
@@ -1797,7 +1850,8 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     {
         ProfScope ps(P, 5);
         if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
 
@@ -1991,7 +2045,8 @@ static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
     {
         ProfScope ps(P, 5);
         if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        gather_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
 
@@ -2562,9 +2617,10 @@ static void enqueue_batch_step(fdph_batch_t B, int kind, const StepArgs<T>* scen
         if (tot[BW_TR]) trconv_batch<T><<<blocks((long long)tot[BW_TR] * 32, 128), 128, 0, s>>>(scen, pre(BW_TR), np);
         if (tot[BW_EVT])
             far_eval_batch<T><<<blocks((long long)tot[BW_EVT] * 32, 128), 128, 0, s>>>(scen, pre(BW_EVT), np);
+        far_sum_batch<T><<<blocks((long long)tot[BW_ELEM] * 32, 128), 128, 0, s>>>(scen, pre(BW_ELEM), np);
     };
     auto gather = [&]() {
-        gather_batch<T><<<blocks((long long)tot[BW_ELEM] * 32, 128), 128, 0, bs>>>(scen, pre(BW_ELEM), np);
+        gather_batch<T><<<blocks(tot[BW_ELEM], 128), 128, 0, bs>>>(scen, pre(BW_ELEM), np);
     };
     if (kind == GRAPH_RUN) {
         push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 0);
@@ -3084,6 +3140,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         if ((rc = dalloc(P, &P->Dring32, c))) return fail(rc);
         sb += c * 4;
     }
+    if ((rc = dalloc(P, &P->tfar, (size_t)P->N * P->nrhs))) return fail(rc);   // far-field traction (scratch)
     if (P->precision == FDPH_FP16 && P->nrhs >= 2) {   // (hi, lo) FP16 rows of the tensor-core near field
         const size_t c = (size_t)P->WD * P->N * P->nrhs;
         if ((rc = dalloc(P, &P->Dring16, c)) || (rc = dalloc(P, &P->Dscale, (size_t)P->WD * P->nrhs))) return fail(rc);

@@ -554,7 +554,7 @@ def run_fdph(args, cfg):
         plan.run(n0 + W, Dd, Td)
         ms = time_steps(plan, stream, Dd, Td, n0 + W, K)
         print(json.dumps({"quick": True, "ms_per_step": ms / K, "steps_before_timed": n0 + W,
-                          "timed_steps": K, "n_near": st["n_near"], "N": N, "M": M,
+                          "timed_steps": K, "n_near": st["n_near"], "N": N, "M": M, "near_entries": st["near_entries"],
                           "near_bytes_per_step": st["near_bytes_per_step"], "bytes_per_step": st["bytes_per_step"]}))
         plan.close()
         return

@@ -47,7 +47,11 @@ typedef enum fdph_status {
     FDPH_E_CUDA = -4,      /* a CUDA runtime call failed */
     FDPH_E_TIMEOUT = -5,   /* a bounded device wait gave up */
     FDPH_E_NAN = -6,       /* non-finite value found where the call checks for one */
-    FDPH_E_STATE = -7      /* call not valid in the plan's current state (e.g. past M steps) */
+    FDPH_E_STATE = -7,     /* call not valid in the plan's current state (e.g. past M steps) */
+    FDPH_E_CHECK = -8      /* bounded-index debug build (libfdph_check.so, compiled with -DFDPH_CHECK)
+                              only: a ring, state, partial-sum or near-slice index of a step kernel
+                              fell outside its array (the access was skipped and the step's results
+                              are invalid), or a write ran past the end of a plan allocation */
 } fdph_status;
 
 typedef enum fdph_precision {

@@ -62,6 +62,23 @@ using namespace fdph;
         }                                                                                    \
     } while (0)
 
+// Bounded-index debug build (-DFDPH_CHECK, libfdph_check.so): every ring, state, partial-sum and
+// near-slice access of the step kernels is checked against the extent of its array; a failing
+// check records kErrIndex in the plan's error word and skips the access (no trap: the kernel
+// carries on and finishes), and the next synchronising call returns FDPH_E_CHECK.  In the normal
+// build FDPH_IDX is the constant true and costs nothing.
+static const int kErrTimeout = 1;   // error word: a bounded wait gave up
+static const int kErrIndex = 2;     // error word: an index check failed (FDPH_CHECK builds)
+__device__ __forceinline__ bool fdph_idx_check(bool ok, int* err) {
+    if (!ok && err) atomicExch(err, kErrIndex);
+    return ok;
+}
+#ifdef FDPH_CHECK
+#define FDPH_IDX(cond, err) fdph_idx_check((cond), (err))
+#else
+#define FDPH_IDX(cond, err) true
+#endif
+
 static const int kChunk = 64;      // steps of exact kernel per near-field work item
 static const int kNearConsumers = 4;                       // consumer warps of the near-field kernel
 static const int kNearThreads = 32 * (kNearConsumers + 1);  // + one producer warp
@@ -153,6 +170,7 @@ struct StepArgs {
     const void* tensor;       // near-field window slices (window storage type)
     float kinv;               // inverse of the window coefficients' storage scale (FP16: 2^-e, else 1)
     const void* stat;         // aux slices: static tiles, exponential-tail coefficients (aux storage type)
+    long long len_tensor, len_aux;   // elements of tensor and stat (index checks of FDPH_CHECK builds)
     double* partial;          // [n_items][32]
     const int* np_ptr;
     const int* np_idx;
@@ -284,6 +302,7 @@ template <class T>
 __device__ __forceinline__ void push_body(const StepArgs<T>& a, int p, bool zero) {
     const int n = step_index(a);
     const size_t slot = (size_t)wrap(n, a.WD) * a.N + p;
+    if (!FDPH_IDX(p < a.N && (long long)slot < a.rs_D, a.err)) return;
     if (zero || !a.D_in) {   // rupture predictor: the unknown slip rate of this step is held at zero
         a.Dring[slot] = 0.0;
         if (a.Dring32) a.Dring32[slot] = 0.f;
@@ -318,6 +337,7 @@ __device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
     const double* D = a.Dring + sb.s0 + jl;
     const int taps = min(sb.taps, n + 1);   // taps <= WD, so one wrap-around at most
     const int slot = wrap(n, a.WD);
+    if (!FDPH_IDX(taps <= a.WD && sb.s0 + jl < a.N && (long long)sb.dhat + jl < a.rs_dhat, a.err)) return;
     double s0 = 0.0, s1 = 0.0;
     int m = 0;
     for (; m + 1 < taps; m += 2) {
@@ -367,6 +387,9 @@ __device__ __forceinline__ void scatter_body(const StepArgs<T>& a, int w, int la
     const int rank = sb.rank;
     double* r = a.ring + sb.ring + (long long)wrap(n + delay, sb.L) * rank;
     const int dslot = sb.kind == SB_TR ? wrap(n, a.WD) : 0;
+    if (!FDPH_IDX(sb.ring + (long long)(wrap(n + delay, sb.L) + 1) * rank <= a.rs_ring &&
+                  (sb.ident != 2 || sb.ns <= rank), a.err))
+        return;
     if (sb.ident == 2) {
         // G is the identity: column j of a slot receives source j only, once
         for (int u = lj; u < len; u += G) {
@@ -459,6 +482,10 @@ __device__ __forceinline__ void trconv_body(const StepArgs<T>& a, int q, int lan
     const int l = a.tr_l[q];
     const int t0 = n - sb.mindm;
     const double* Y = a.ring + sb.ring + l;
+    if (!FDPH_IDX(sb.ring + (long long)sb.L * sb.rank <= a.rs_ring && l < sb.rank &&
+                  sb.zring + (long long)sb.LZ * sb.rank <= a.rs_zring &&
+                  (!sb.soe || sb.ustate + (long long)sb.rank * sb.soe <= a.rs_ustate), a.err))
+        return;
     double z = 0.0;
     for (int m = lane; m < sb.taps; m += 32)
         z += (double)a.fac[sb.h + m] * Y[(long long)wrap(t0 - m, sb.L) * sb.rank];
@@ -599,6 +626,7 @@ struct NearView {
     float kinv;
     int N, WD, WC, n, nrhs;
     long long rs_D, rs_C, rs_vstate, rs_partial;
+    long long len_tensor, len_aux;
 };
 
 template <class T>
@@ -625,6 +653,8 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     v.rs_C = a.rs_C;
     v.rs_vstate = a.rs_vstate;
     v.rs_partial = a.rs_partial;
+    v.len_tensor = a.len_tensor;
+    v.len_aux = a.len_aux;
     return v;
 }
 
@@ -657,9 +687,9 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
         for (int m = 0; m < VR / kNearConsumers; ++m) {
             const int v = warp + m * kNearConsumers;
             const int k = v / NR, q = v % NR;
-            if (k < nsl) {
-                int slot = b0 - k;                     // k < W < WD: one wrap at most
-                slot += slot < 0 ? a.WD : 0;
+            int slot = b0 - k;                         // k < W < WD: one wrap at most
+            slot += slot < 0 ? a.WD : 0;
+            if (k < nsl && FDPH_IDX(slot >= 0 && slot < a.WD && col < (size_t)a.N, a.err)) {
                 const size_t off = q * a.rs_D + (size_t)slot * a.N + col;
                 if constexpr (TC) {
                     cp_async_4((unsigned*)vb + v * kTcRow + lane, a.Dring16 + off, on ? 4 : 0);
@@ -683,7 +713,8 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
             double x = 0.0;
             if (on && k < nsl) {
                 if (ai == 0) x = t >= 0 ? a.Cring[q * a.rs_C + (size_t)wrap(t, a.WC) * a.N + col] : 0.0;
-                else x = a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane];
+                else if (FDPH_IDX(tk.vstate + (long long)(ai - 1) * tk.ns + lane < a.rs_vstate, a.err))
+                    x = a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane];
             }
             r[m] = x;
         }
@@ -706,7 +737,8 @@ __device__ __forceinline__ void near_commit(const NearView& a, const NearTask& t
                 x = 0.0;
                 if (lane < tk.ns) {
                     x = a.rho[ai - 1] * r[m] + dW[q];
-                    a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane] = x;
+                    if (FDPH_IDX(tk.vstate + (long long)(ai - 1) * tk.ns + lane < a.rs_vstate, a.err))
+                        a.vstate[q * a.rs_vstate + tk.vstate + (size_t)(ai - 1) * tk.ns + lane] = x;
                 }
             }
             ((R*)vb)[v * 32 + lane] = (R)x;
@@ -1084,10 +1116,15 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     }
                     const int cnt = min(per, nsl - q * per);
                     const unsigned bytes = (unsigned)(cnt * tk.sl * esz);
+                    // (index check: the stage's slices lie inside the stored coefficients; a failed
+                    // check completes the stage without data)
+                    const bool ok = FDPH_IDX(tk.off + (long long)(q * per + cnt) * tk.sl <= (tk.kind ? v.len_aux : v.len_tensor),
+                                             v.err);
                     fence_proxy_async();
-                    mbar_expect_tx(&full[s], bytes);
-                    bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
-                                  policy);
+                    mbar_expect_tx(&full[s], ok ? bytes : 0u);
+                    if (ok)
+                        bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
+                                      policy);
                 }
             }
         }
@@ -1207,7 +1244,7 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             }
             cp_async_wait_all();
             consumer_barrier();   // also publishes the next item's vectors
-            if (warp == 0) {
+            if (warp == 0 && FDPH_IDX((long long)tk.item * 32 + 32 <= v.rs_partial, v.err)) {
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     double sum = 0.0;
@@ -1239,8 +1276,15 @@ __device__ __forceinline__ void far_eval_body(const StepArgs<T>& a, int w, int l
     const int lg = tk.w, G = 1 << lg;
     const int gi = lane >> lg, lj = lane & (G - 1);
     const int il = tk.y + gi;
-    const bool valid = gi < tk.z;
+    bool valid = gi < tk.z;
     double s = 0.0;
+    if (valid) {   // (a failed index check leaves this receiver's lanes out; the shuffles take all lanes)
+        const bool tr = sb.kind == SB_TR;
+        valid = FDPH_IDX((tr ? sb.zring : sb.ring) + (long long)(tr ? sb.LZ : sb.L) * sb.rank <=
+                                 (tr ? a.rs_zring : a.rs_ring) &&
+                             (sb.ident != 1 || il < sb.rank) && a.e_pos[sb.e0 + il] < a.rs_fval,
+                         a.err);
+    }
     if (valid) {
         const bool tr = sb.kind == SB_TR;
         const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
@@ -1280,7 +1324,8 @@ __global__ void far_eval_kernel(StepArgs<T> a0) {
 template <class T>
 __device__ __forceinline__ void far_sum_body(const StepArgs<T>& a, int p, int lane) {
     double s = 0.0;
-    for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32) s += a.fval[e];
+    for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32)
+        if (FDPH_IDX(e < a.rs_fval, a.err)) s += a.fval[e];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) a.tfar[p] = s;
 }
@@ -1298,7 +1343,8 @@ template <class T>
 __device__ __forceinline__ void gather_body(const StepArgs<T>& a, int p) {
     const int n = step_index(a);
     double s = a.tfar[p];
-    for (int e = a.np_ptr[p]; e < a.np_ptr[p + 1]; ++e) s += a.partial[a.np_idx[e]];
+    for (int e = a.np_ptr[p]; e < a.np_ptr[p + 1]; ++e)
+        if (FDPH_IDX(a.np_idx[e] < a.rs_partial, a.err)) s += a.partial[a.np_idx[e]];
     a.T_out[io_offset(a, n) + a.perm[p]] = s;
 }
 
@@ -1603,6 +1649,7 @@ struct fdph_plan_s {
     float* Dring32 = nullptr;   // FP32 copy of Dring (FP32 / FP16 plans)
     __half2* Dring16 = nullptr; // scaled FP16 (hi, lo) copy of Dring (tensor-core near field)
     double* tfar = nullptr;     // [nrhs][N] far-field traction of the step (scratch)
+    std::vector<std::pair<unsigned char*, size_t>> canaries;   // FDPH_CHECK builds: allocation ends
     float* Dscale = nullptr;    // its per-row inverse scales
     double *ring = nullptr, *zring = nullptr, *dhat = nullptr, *partial = nullptr;
     size_t state_bytes = 0;
@@ -1643,17 +1690,47 @@ struct fdph_plan_s {
     cudaEvent_t ev_in[kIoSlots] = {}, ev_out[kIoSlots] = {}, ev_free[kIoSlots] = {};
 };
 
+// FDPH_CHECK builds: every device allocation of a plan ends in kCanaryBytes of a known pattern,
+// compared with the pattern whenever the plan synchronises (check_canaries)
+static const size_t kCanaryBytes = 256;
+static const unsigned char kCanary = 0xA5;
+
 template <class T>
 static int dalloc(fdph_plan_t P, T** out, size_t count) {
     void* p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
+#ifdef FDPH_CHECK
+    const size_t extra = kCanaryBytes;
+#else
+    const size_t extra = 0;
+#endif
+    cudaError_t e = cudaMalloc(&p, bytes + extra);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         return FDPH_E_OOM;
     }
     P->allocs.push_back(p);
+    if (extra) {
+        P->canaries.push_back({(unsigned char*)p + bytes, extra});
+        if (cudaMemsetAsync((unsigned char*)p + bytes, kCanary, extra, P->stream) != cudaSuccess) return FDPH_E_CUDA;
+    }
     *out = (T*)p;
+    return FDPH_OK;
+}
+
+// FDPH_CHECK builds: FDPH_E_CHECK if a write ran past the end of a device allocation
+static int check_canaries(fdph_plan_t P) {
+    std::vector<unsigned char> h;
+    for (const auto& c : P->canaries) {
+        h.assign(c.second, 0);
+        FDPH_CUDA(cudaMemcpyAsync(h.data(), c.first, c.second, cudaMemcpyDeviceToHost, P->stream));
+        FDPH_CUDA(cudaStreamSynchronize(P->stream));
+        for (unsigned char b : h)
+            if (b != kCanary) {
+                set_error("a device write ran past the end of a plan allocation (canary overwritten)");
+                return FDPH_E_CHECK;
+            }
+    }
     return FDPH_OK;
 }
 
@@ -1721,6 +1798,8 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.tensor = P->tensor;
     a.kinv = (float)(1.0 / P->kscale);
     a.stat = P->stat;
+    a.len_tensor = P->hp.near_tensor_len;
+    a.len_aux = P->hp.near_aux_len;
     a.partial = P->partial;
     a.np_ptr = P->np_ptr;
     a.np_idx = P->np_idx;
@@ -2017,11 +2096,19 @@ static int check_device_error(fdph_plan_t P) {
     FDPH_CUDA(cudaMemcpyAsync(&e, P->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     if (e) {
-        set_error("a bounded mbarrier wait in the near-field kernel gave up; results of the step are invalid");
         cudaMemsetAsync(P->err, 0, sizeof(int), P->stream);
+        if (e == kErrIndex) {
+            set_error("a device index check failed (bounded-index debug build); results of the step are invalid");
+            return FDPH_E_CHECK;
+        }
+        set_error("a bounded mbarrier wait in the near-field kernel gave up; results of the step are invalid");
         return FDPH_E_TIMEOUT;
     }
+#ifdef FDPH_CHECK
+    return check_canaries(P);
+#else
     return FDPH_OK;
+#endif
 }
 
 static int step_impl(fdph_plan_t P, const double* D, double* T_) {
@@ -2847,6 +2934,7 @@ const char* fdph_strerror(int s) {
         case FDPH_E_TIMEOUT: return "device wait timed out";
         case FDPH_E_NAN: return "non-finite value";
         case FDPH_E_STATE: return "invalid plan state";
+        case FDPH_E_CHECK: return "device index check failed (bounded-index debug build)";
         default: return "unknown status";
     }
 }

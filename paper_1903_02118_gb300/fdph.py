@@ -12,9 +12,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfdph.so")
+# FDPH_LIB=check selects the bounded-index debug build (build.build(check=True))
+LIB_PATH = os.path.join(_HERE, "libfdph_check.so" if os.environ.get("FDPH_LIB") == "check" else "libfdph.so")
 
-OK, E_ARG, E_OOM, E_CAUSALITY, E_CUDA, E_TIMEOUT, E_NAN, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, E_ARG, E_OOM, E_CAUSALITY, E_CUDA, E_TIMEOUT, E_NAN, E_STATE, E_CHECK = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FP64, FP32, FP16 = 0, 1, 2
 
 

@@ -23,6 +23,8 @@
 // at step n were completed by steps < n and that the slots written at step n are not read.
 // A rupture step (Sec. 6.2) predicts with D_n = 0, solves the friction law per element and
 // then commits D_n; a batch of plans runs each of these kernels as one launch over all plans.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -129,8 +131,12 @@ struct StepArgs {
     const int* perm;          // internal -> geometry
     double* Dring;            // [WD][N]
     float* Dring32;           // [WD][N] FP32 copy of Dring (plans whose near-field rows are FP32)
-    __half2* Dring16;         // [WD][N] scaled FP16 (hi, lo) pairs of Dring (FP16 plans, nrhs >= 2)
-    float* Dscale;            // [WD] inverse power-of-two scale of each Dring16 row
+    __half2* Dring16;         // [2 WD][nrhs][NP] scaled FP16 (hi, lo) pairs of Dring (FP16 plans, nrhs >= 2):
+                              // slot s is stored at s and s + WD (a window of <= WD slots never wraps),
+                              // all right-hand sides of a slot side by side, rows padded to NP (multiple of 4)
+    float* Dscale;            // [WD] inverse power-of-two scale of each Dring16 row (per right-hand side)
+    const void* tmap16;       // TMA tensor map of Dring16 (device memory): box 36 sources x nrhs x item slots
+    int NP;
     double* Cring;            // [WC][N]
     double* C;                // [N] cumulative slip (rounded sum)
     double* Ccomp;            // [N] Kahan compensation
@@ -225,7 +231,6 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         if (a0.T_out) a.T_out = a0.T_out + rN;
         a.Dring = a0.Dring + r * a0.rs_D;
         if (a0.Dring32) a.Dring32 = a0.Dring32 + r * a0.rs_D;
-        if (a0.Dring16) a.Dring16 = a0.Dring16 + r * a0.rs_D;
         if (a0.Dscale) a.Dscale = a0.Dscale + (long long)r * a0.WD;
         a.Cring = a0.Cring + r * a0.rs_C;
         a.C = a0.C + rN;
@@ -256,6 +261,7 @@ __global__ void ring_to_float_kernel(const double* x, float* y, long long n) {
 // (e from the exponent field; a zero or subnormal row takes the largest shift), hi = fp16(x 2^sh),
 // lo = fp16(x 2^sh - hi), and Dscale = 2^-sh.  One CTA per row: the row of step n (all_slots 0,
 // after push), or every slot (all_slots 1, after a state restore).  grid (slots or 1, nrhs).
+// The near kernel fetches a work item's rows of all right-hand sides with one TMA tensor copy.
 constexpr int kRowThreads = 256;
 
 __device__ __forceinline__ int row_shift(float m) {
@@ -281,11 +287,15 @@ __global__ void __launch_bounds__(kRowThreads) tc_rows_kernel(StepArgs<T> a0, in
     for (int w = 0; w < kRowThreads / 32; ++w) m = fmaxf(m, wmax[w]);
     const int sh = row_shift(m);
     const float s = pow2f(sh);
-    __half2* out = a.Dring16 + (size_t)slot * a.N;
+    // slot s of right-hand side q at rows (s, q) and (s + WD, q) of the mirrored [2 WD][nrhs][NP] layout
+    __half2* out0 = a.Dring16 + ((size_t)slot * a.nrhs + blockIdx.y) * a.NP;
+    __half2* out1 = out0 + (size_t)a.WD * a.nrhs * a.NP;
     for (int p = threadIdx.x; p < a.N; p += kRowThreads) {
         const float y = (float)row[p] * s;
         const __half hi = __float2half_rn(y);
-        out[p] = __halves2half2(hi, __float2half_rn(y - __half2float(hi)));
+        const __half2 v = __halves2half2(hi, __float2half_rn(y - __half2float(hi)));
+        out0[p] = v;
+        out1[p] = v;
     }
     if (threadIdx.x == 0) a.Dscale[slot] = pow2f(-sh);
 }
@@ -542,6 +552,16 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsign
         : "memory");
 }
 
+// 3-D TMA tile load of the box at (x, y, z) of the tensor map (global memory) into shared memory,
+// completing `bytes` of the mbarrier's transaction count
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
     unsigned long long p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -616,6 +636,7 @@ struct NearView {
     const float* Dring32;
     const __half2* Dring16;
     const float* Dscale;
+    const void* tmap16;
     const double* Cring;
     double* vstate;
     const double* rho;
@@ -636,6 +657,7 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
     v.Dring32 = a.Dring32;
     v.Dring16 = a.Dring16;
     v.Dscale = a.Dscale;
+    v.tmap16 = a.tmap16;
     v.Cring = a.Cring;
     v.vstate = a.vstate;
     v.rho = a.rho;
@@ -670,17 +692,33 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
-// tensor-core window rows in the vector buffer: (hi, lo) pairs, rows of kTcRow words (160 bytes:
-// the 64-bit fragment loads of one half-warp land on distinct banks), then one scale per row
-constexpr int kTcRow = 40;
+// tensor-core window rows in the vector buffer, as the TMA box lands: [slot][right-hand side][kTcBox]
+// (hi, lo) words, slots from the item's oldest
+constexpr int kTcBox = 36;
 
 template <class R, int NR, int VR, bool TC>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
-                                           double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb) {
+                                           double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb,
+                                           unsigned long long* vbar) {
     const int n = a.n;
     const int nsl = near_slices<double>(tk, n);
     const bool on = lane < tk.ns;
     const size_t col = (size_t)tk.s0 + (on ? lane : 0);   // lanes past ns zero-fill from a valid address
+    if constexpr (TC) {
+        if (!tk.kind) {
+            // the window rows of every right-hand side with one TMA tensor copy: a box of 36 sources
+            // from s0 rounded down to a multiple of 4 (the 16-byte rule of the innermost coordinate;
+            // the consumers index from the remainder) x nrhs x VR / NR slots from the item's oldest
+            // (the mirrored ring keeps them contiguous; past the ring the box reads zeros)
+            if (warp == 0 && lane == 0 && nsl > 0) {
+                const int z0 = wrap(n - tk.k0 - (nsl - 1), a.WD);
+                fence_proxy_async();
+                mbar_expect_tx(vbar, (unsigned)(VR * kTcBox * 4));
+                tma_load_3d(vb, a.tmap16, tk.s0 & ~3, 0, z0, vbar);
+            }
+            return;
+        }
+    }
     if (!tk.kind) {
         const int b0 = wrap(n - tk.k0, a.WD);
 #pragma unroll
@@ -691,10 +729,7 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
             slot += slot < 0 ? a.WD : 0;
             if (k < nsl && FDPH_IDX(slot >= 0 && slot < a.WD && col < (size_t)a.N, a.err)) {
                 const size_t off = q * a.rs_D + (size_t)slot * a.N + col;
-                if constexpr (TC) {
-                    cp_async_4((unsigned*)vb + v * kTcRow + lane, a.Dring16 + off, on ? 4 : 0);
-                    if (lane == 0) cp_async_4((float*)vb + VR * kTcRow + v, a.Dscale + (size_t)q * a.WD + slot, 4);
-                } else if constexpr (sizeof(R) == 4) {
+                if constexpr (sizeof(R) == 4) {
                     cp_async_4((R*)vb + v * 32 + lane, a.Dring32 + off, on ? 4 : 0);
                 } else {
                     cp_async_8((R*)vb + v * 32 + lane, a.Dring + off, on ? 8 : 0);
@@ -761,10 +796,11 @@ struct NearCfg {
     // shared-memory pipeline depth, within two CTAs per SM next to the vector buffers and the
     // partial sums of the right-hand sides
     static constexpr int stages = NR >= 8 ? 3 : NR >= 2 ? 4 : sizeof(R) == 4 ? 5 : 4;
-    // tensor-core window rows (FP16 window, several right-hand sides) take more room per row
+    // tensor-core window rows (FP16 window, several right-hand sides): TMA boxes of kTcBox words a
+    // row (a multiple of 128 bytes for vec_rows = 128), and 128 bytes of room to align them
     static constexpr bool tc = std::is_same<H, __half>::value && NR >= 2;
-    static constexpr int vec_bytes = tc ? vec_rows * (kTcRow * 4 + 4) : vec_rows * 32 * (int)sizeof(R);
-    static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes;
+    static constexpr int vec_bytes = tc ? vec_rows * kTcBox * 4 : vec_rows * 32 * (int)sizeof(R);
+    static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes + (tc ? 128 : 0);
 };
 
 // the longest work item (window slices) of a plan: the item's vector rows over its right-hand sides
@@ -958,14 +994,16 @@ __device__ __forceinline__ void mma_16816(float (&c)[4], const unsigned (&a)[4],
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// S window slices at once (sl[s]: stage copy; rows[s]: their NR (hi, lo) rows of kTcRow words,
-// lane = source; sc[s]: their NR scales) into the warp's accumulators acc[m-tile][fragment] (rows g,
+// S window slices at once (sl[s]: stage copy; rows[s]: their NR (hi, lo) rows of kTcBox words from
+// the source s0; sc[s]: their scales, right-hand side q at sc[s][q sstride]) into the warp's
+// accumulators acc[m-tile][fragment] (rows g,
 // g + 8 of each 16-receiver tile, columns 2t, 2t + 1, with g = lane / 4, t = lane % 4).  All
 // fragments are loaded first and the MMAs of the S slices and two receiver tiles interleave, so
 // that 2 S independent accumulator chains are in flight.
 template <int NR, int S>
 __device__ __forceinline__ void tc_slices(const __half* const (&sl)[S], const unsigned* const (&rows)[S],
-                                          const float* const (&sc)[S], int nr, int ns, int lane, float (&acc)[2][4]) {
+                                          const float* const (&sc)[S], int sstride, int nr, int ns, int lane,
+                                          float (&acc)[2][4]) {
     static_assert(NR == 2 || NR == 4 || NR == 8, "tensor-core slices take 2, 4 or 8 right-hand sides");
     const int ng = (ns + 7) >> 3;          // 8-source groups of the slice (zero-padded)
     const int nks = (ng + 1) >> 1;         // 16-source steps
@@ -990,20 +1028,24 @@ __device__ __forceinline__ void tc_slices(const __half* const (&sl)[S], const un
 #pragma unroll
             for (int p = 0; p < npass; ++p) {
                 const int vr = 8 * p + g;
-                const unsigned* br = rows[q] + (vr % NR) * kTcRow + 2 * t + 16 * kk;
+                // (32-bit loads: the row starts at the remainder of s0, not 8-byte aligned in general)
+                const unsigned* br = rows[q] + (vr % NR) * kTcBox + 2 * t + 16 * kk;
                 const unsigned sel = ((vr / NR) & 1) ? 0x7632u : 0x5410u;   // high or low halves of two pairs
-                const uint2 w0 = *reinterpret_cast<const uint2*>(br);
-                const uint2 w1 = *reinterpret_cast<const uint2*>(br + 8);
-                b[q][p][0] = __byte_perm(w0.x, w0.y, sel);
-                b[q][p][1] = __byte_perm(w1.x, w1.y, sel);
+                b[q][p][0] = __byte_perm(br[0], br[1], sel);
+                b[q][p][1] = __byte_perm(br[8], br[9], sel);
             }
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                // receivers past nr and source groups past ng read valid rows of the slice (their
-                // products land in unused rows, or meet zero slip rates)
+                // receivers past nr read valid rows of the slice (their products land in unused
+                // rows); a source group past ng (the upper half of the last 16-source step) is
+                // zeroed, since the TMA box carries the next elements' slip rates there (sources
+                // past ns inside the last group meet the slice's zero padding)
                 const int i = min(16 * mt + 8 * (mq & 1) + mr, nr - 1);
                 const int gg = min(2 * kk + (mq >> 1), ng - 1);
-                if (mt < nmt) ldsm_x4(a[q][mt], sl[q] + ((size_t)gg * nr + i) * 8);
+                if (mt < nmt) {
+                    ldsm_x4(a[q][mt], sl[q] + ((size_t)gg * nr + i) * 8);
+                    if (2 * kk + 1 >= ng) a[q][mt][2] = a[q][mt][3] = 0u;
+                }
             }
         }
 #pragma unroll
@@ -1017,7 +1059,7 @@ __device__ __forceinline__ void tc_slices(const __half* const (&sl)[S], const un
     // column v holds right-hand side v % NR
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-        const float s0 = sc[q][(2 * t) % NR], s1 = sc[q][(2 * t + 1) % NR];
+        const float s0 = __ldg(sc[q] + ((2 * t) % NR) * sstride), s1 = __ldg(sc[q] + ((2 * t + 1) % NR) * sstride);
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             acc[mt][0] = fmaf(c[q][mt][0], s0, acc[mt][0]);
@@ -1073,12 +1115,15 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][NR][32];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
+    __shared__ __align__(8) unsigned long long vbar[2];      // TMA rows of the two vector buffers (kTC)
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
     auto view = [&](const NearTask& tk) -> NearView { return kBatch ? near_view(scen[tk.scen]) : v0; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
     unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
+    if constexpr (C::tc)   // TMA boxes land on 128-byte boundaries (the configuration reserves the room)
+        vbuf = (unsigned char*)(((unsigned long long)vbuf + 127) & ~127ull);
     {
         const int nt = min(t1 - t0, kTaskCache) * (int)(sizeof(NearTask) / sizeof(int4));
         for (int e = threadIdx.x; e < nt; e += blockDim.x)
@@ -1090,6 +1135,8 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kNearConsumers);
         }
+        mbar_init(&vbar[0], 1);
+        mbar_init(&vbar[1], 1);
         abort_flag = 0;
         mbar_fence_init();
     }
@@ -1136,12 +1183,13 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf);
+            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf, &vbar[0]);
             near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         cp_async_wait_all();
         consumer_barrier();
         int par = 0;
+        unsigned vph = 0;   // phase bits of vbar[0], vbar[1] (a wait per TMA box of window rows)
         for (int ti = t0; ti < t1; ++ti, par ^= 1) {
             const NearTask tk = nxt;
             const NearView v = vn;
@@ -1149,7 +1197,8 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes,
+                                                    &vbar[par ^ 1]);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -1175,6 +1224,13 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int f = 0; f < 4; ++f) tacc[mt][f] = 0.f;
+            if (tc && nsl > 0) {   // this item's window rows (TMA box issued one item ahead)
+                if (!mbar_wait_bounded(&vbar[par], (vph >> par) & 1u)) {
+                    abort_flag = 1;
+                    atomicExch(v.err, kErrTimeout);
+                }
+                vph ^= 1u << par;
+            }
             for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % C::stages;
                 const int cnt = min(per, nsl - q * per);
@@ -1187,23 +1243,25 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
                     if constexpr (kTC) {
                         if (tc) {
-                            // this warp's slices kk and kk + kNearConsumers of the stage together
-                            const int ks = q * per + kk;   // slice of the item
-                            const unsigned* rw = (const unsigned*)vrows;
-                            const float* scl = (const float*)vrows + C::vec_rows * kTcRow;
+                            // this warp's slices kk and kk + kNearConsumers of the stage together;
+                            // slice ks of the item: box slot nsl - 1 - ks, ring slot of step n - k0 - ks
+                            const int ks = q * per + kk;
+                            const unsigned* rw = (const unsigned*)vrows + (tk.s0 & 3);
+                            auto rows_of = [&](int k) { return rw + (size_t)(nsl - 1 - k) * NR * kTcBox; };
+                            auto scale_of = [&](int k) { return v.Dscale + wrap(v.n - tk.k0 - k, v.WD); };
                             if (kk + kNearConsumers < cnt) {
                                 const int ks2 = ks + kNearConsumers;
                                 const __half* const sl2[2] = {(const __half*)buf + (size_t)kk * tk.sl,
                                                               (const __half*)buf + (size_t)(kk + kNearConsumers) * tk.sl};
-                                const unsigned* const rw2[2] = {rw + (size_t)ks * NR * kTcRow, rw + (size_t)ks2 * NR * kTcRow};
-                                const float* const sc2[2] = {scl + ks * NR, scl + ks2 * NR};
-                                tc_slices<NR, 2>(sl2, rw2, sc2, tk.nr, tk.ns, lane, tacc);
+                                const unsigned* const rw2[2] = {rows_of(ks), rows_of(ks2)};
+                                const float* const sc2[2] = {scale_of(ks), scale_of(ks2)};
+                                tc_slices<NR, 2>(sl2, rw2, sc2, v.WD, tk.nr, tk.ns, lane, tacc);
                                 kk += kNearConsumers;
                             } else {
                                 const __half* const sl1[1] = {(const __half*)buf + (size_t)kk * tk.sl};
-                                const unsigned* const rw1[1] = {rw + (size_t)ks * NR * kTcRow};
-                                const float* const sc1[1] = {scl + ks * NR};
-                                tc_slices<NR, 1>(sl1, rw1, sc1, tk.nr, tk.ns, lane, tacc);
+                                const unsigned* const rw1[1] = {rows_of(ks)};
+                                const float* const sc1[1] = {scale_of(ks)};
+                                tc_slices<NR, 1>(sl1, rw1, sc1, v.WD, tk.nr, tk.ns, lane, tacc);
                             }
                             continue;
                         }
@@ -1261,6 +1319,11 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             (void)mbar_wait_bounded(&full[s], 0u);
             (void)mbar_wait_bounded(&full[s], 1u);
         }
+        if constexpr (kTC)
+            for (int b = 0; b < 2; ++b) {
+                (void)mbar_wait_bounded(&vbar[b], 0u);
+                (void)mbar_wait_bounded(&vbar[b], 1u);
+            }
     }
 }
 
@@ -1278,13 +1341,11 @@ __device__ __forceinline__ void far_eval_body(const StepArgs<T>& a, int w, int l
     const int il = tk.y + gi;
     bool valid = gi < tk.z;
     double s = 0.0;
-    if (valid) {   // (a failed index check leaves this receiver's lanes out; the shuffles take all lanes)
-        const bool tr = sb.kind == SB_TR;
-        valid = FDPH_IDX((tr ? sb.zring : sb.ring) + (long long)(tr ? sb.LZ : sb.L) * sb.rank <=
-                                 (tr ? a.rs_zring : a.rs_ring) &&
+    if (valid)   // (a failed index check leaves this receiver's lanes out; the shuffles take all lanes)
+        valid = FDPH_IDX((sb.kind == SB_TR ? sb.zring + (long long)sb.LZ * sb.rank <= a.rs_zring
+                                           : sb.ring + (long long)sb.L * sb.rank <= a.rs_ring) &&
                              (sb.ident != 1 || il < sb.rank) && a.e_pos[sb.e0 + il] < a.rs_fval,
                          a.err);
-    }
     if (valid) {
         const bool tr = sb.kind == SB_TR;
         const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
@@ -1648,6 +1709,8 @@ struct fdph_plan_s {
     double *Dring = nullptr, *Cring = nullptr, *C = nullptr, *Ccomp = nullptr;
     float* Dring32 = nullptr;   // FP32 copy of Dring (FP32 / FP16 plans)
     __half2* Dring16 = nullptr; // scaled FP16 (hi, lo) copy of Dring (tensor-core near field)
+    void* tmap16 = nullptr;     // its TMA tensor map (device memory)
+    int NP = 0;                 // Dring16 row length (N rounded up to a multiple of 4)
     double* tfar = nullptr;     // [nrhs][N] far-field traction of the step (scratch)
     std::vector<std::pair<unsigned char*, size_t>> canaries;   // FDPH_CHECK builds: allocation ends
     float* Dscale = nullptr;    // its per-row inverse scales
@@ -1690,10 +1753,12 @@ struct fdph_plan_s {
     cudaEvent_t ev_in[kIoSlots] = {}, ev_out[kIoSlots] = {}, ev_free[kIoSlots] = {};
 };
 
+#ifdef FDPH_CHECK
 // FDPH_CHECK builds: every device allocation of a plan ends in kCanaryBytes of a known pattern,
 // compared with the pattern whenever the plan synchronises (check_canaries)
 static const size_t kCanaryBytes = 256;
 static const unsigned char kCanary = 0xA5;
+#endif
 
 template <class T>
 static int dalloc(fdph_plan_t P, T** out, size_t count) {
@@ -1710,14 +1775,15 @@ static int dalloc(fdph_plan_t P, T** out, size_t count) {
         return FDPH_E_OOM;
     }
     P->allocs.push_back(p);
-    if (extra) {
-        P->canaries.push_back({(unsigned char*)p + bytes, extra});
-        if (cudaMemsetAsync((unsigned char*)p + bytes, kCanary, extra, P->stream) != cudaSuccess) return FDPH_E_CUDA;
-    }
+#ifdef FDPH_CHECK
+    P->canaries.push_back({(unsigned char*)p + bytes, extra});
+    if (cudaMemsetAsync((unsigned char*)p + bytes, kCanary, extra, P->stream) != cudaSuccess) return FDPH_E_CUDA;
+#endif
     *out = (T*)p;
     return FDPH_OK;
 }
 
+#ifdef FDPH_CHECK
 // FDPH_CHECK builds: FDPH_E_CHECK if a write ran past the end of a device allocation
 static int check_canaries(fdph_plan_t P) {
     std::vector<unsigned char> h;
@@ -1733,6 +1799,7 @@ static int check_canaries(fdph_plan_t P) {
     }
     return FDPH_OK;
 }
+#endif
 
 template <class T>
 static int upload(fdph_plan_t P, T** out, const std::vector<T>& v) {
@@ -1741,6 +1808,40 @@ static int upload(fdph_plan_t P, T** out, const std::vector<T>& v) {
     // ordered on the plan's stream (a pageable source is staged before the call returns)
     if (!v.empty())
         FDPH_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, P->stream));
+    return FDPH_OK;
+}
+
+// TMA tensor map of the mirrored (hi, lo) ring Dring16 [2 WD][nrhs][NP] (4-byte elements): box =
+// kTcBox sources x nrhs x the longest work item's slots, no swizzle, zero fill outside; encoded
+// through the driver entry point (no link against the driver library) and kept in device memory
+static int make_row_tensor_map(fdph_plan_t P) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    FDPH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return FDPH_E_CUDA;
+    }
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)P->NP, (cuuint64_t)P->nrhs, (cuuint64_t)2 * P->WD};
+    const cuuint64_t strides[2] = {(cuuint64_t)P->NP * 4, (cuuint64_t)P->nrhs * P->NP * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcBox, (cuuint32_t)P->nrhs,
+                               (cuuint32_t)near_max_chunk(P->nrhs, FDPH_FP16)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = ((PFN_cuTensorMapEncodeTiled_v12000)fn)(
+        &map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)P->Dring16, dims, strides, box, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+        return FDPH_E_CUDA;
+    }
+    unsigned char* d = nullptr;
+    int rc = dalloc(P, &d, sizeof(CUtensorMap));
+    if (rc) return rc;
+    FDPH_CUDA(cudaMemcpyAsync(d, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice, P->stream));
+    FDPH_CUDA(cudaStreamSynchronize(P->stream));
+    P->tmap16 = d;
     return FDPH_OK;
 }
 
@@ -1761,6 +1862,8 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.Dring32 = P->Dring32;
     a.Dring16 = P->Dring16;
     a.Dscale = P->Dscale;
+    a.tmap16 = P->tmap16;
+    a.NP = P->NP;
     a.tfar = P->tfar;
     a.Cring = P->Cring;
     a.C = P->C;
@@ -3230,9 +3333,11 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     }
     if ((rc = dalloc(P, &P->tfar, (size_t)P->N * P->nrhs))) return fail(rc);   // far-field traction (scratch)
     if (P->precision == FDPH_FP16 && P->nrhs >= 2) {   // (hi, lo) FP16 rows of the tensor-core near field
-        const size_t c = (size_t)P->WD * P->N * P->nrhs;
+        P->NP = (P->N + 3) & ~3;
+        const size_t c = (size_t)2 * P->WD * P->nrhs * P->NP;
         if ((rc = dalloc(P, &P->Dring16, c)) || (rc = dalloc(P, &P->Dscale, (size_t)P->WD * P->nrhs))) return fail(rc);
         sb += c * 4 + (size_t)P->WD * P->nrhs * 4;
+        if ((rc = make_row_tensor_map(P))) return fail(rc);
     }
     P->state_bytes = sb;
     P->partial_cap = std::max<size_t>(hp.items.size() * 32, 1);
@@ -3258,7 +3363,7 @@ int fdph_reset(fdph_plan_t P) {
     if (P->Dring32)
         FDPH_CUDA(cudaMemsetAsync(P->Dring32, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(float), P->stream));
     if (P->Dring16) {
-        FDPH_CUDA(cudaMemsetAsync(P->Dring16, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(__half2), P->stream));
+        FDPH_CUDA(cudaMemsetAsync(P->Dring16, 0, (size_t)2 * P->WD * P->NP * P->nrhs * sizeof(__half2), P->stream));
         FDPH_CUDA(cudaMemsetAsync(P->Dscale, 0, (size_t)P->WD * P->nrhs * sizeof(float), P->stream));
     }
     if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));

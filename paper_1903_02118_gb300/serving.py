@@ -90,8 +90,10 @@ class Server:
 
     @staticmethod
     def estimate(req):
-        """Footprint bound before the plan exists (operator + rings + histories), bytes."""
-        return req.N * 2_000_000
+        """Device footprint of the request's plan before it exists (footprint_model), bytes."""
+        xy, _ = req.inputs()
+        return footprint_model(xy, req.cfl, req.M, eta=req.eta, leaf=req.leaf, precision=req.precision,
+                               soe_terms=req.soe_terms)
 
     def _admit(self, req):
         torch = self.torch
@@ -221,6 +223,43 @@ class Server:
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "element_steps": steps_done, "plan_s_p50": float(np.percentile(plan_s, 50)),
                 "plan_s_max": float(plan_s.max()), "admission_wait_s_p50": float(np.percentile(wait_s, 50))}
+
+
+def footprint_model(xy, dt, M, eta=0.5, leaf=32, precision=fdph.FP32, soe_terms=16, rank=8, chunk=64, cs=1.0):
+    """Device bytes of a plan, from its block tree alone (fdph_tree_export, host only, milliseconds):
+    the near-field windows dominate -- per inadmissible leaf W slices of ceil(ns / v) v nr stored
+    coefficients (v = 16 bytes / element), W = the leaf's longest wave passage (farthest end point
+    over c dt) + n_c with exponential tails (the whole march M when too little is left to fit a
+    tail), + the static and tail slices; the admissible blocks add their factors and rings
+    (5 low-rank operators per leaf at `rank`, ring slots up to the largest delay); the state adds the
+    slip-rate rings, and the serving loop its chunk buffers."""
+    tx = fdph.tree_export(xy, dt, eta=eta, leaf_size=leaf, extra_steps=-1)
+    perm = tx["perm"]
+    N = xy.shape[0]
+    ax, ay, bx, by = xy[:, 0], xy[:, 1], xy[:, 2], xy[:, 3]
+    mx, my = 0.5 * (ax + bx), 0.5 * (ay + by)
+    nc = int(np.ceil(10.0 * np.hypot(bx - ax, by - ay).max() / (cs * dt) - 1e-9))
+    sw = {fdph.FP64: 8, fdph.FP32: 4, fdph.FP16: 2}[precision]      # window coefficient bytes
+    sa = 8 if precision == fdph.FP64 else 4                           # aux / factor bytes
+    near = far = 0.0
+    wmax = 1
+    for lf in tx["leaves"]:
+        I = perm[lf["r0"]:lf["r0"] + lf["nr"]]
+        J = perm[lf["s0"]:lf["s0"] + lf["ns"]]
+        if lf["kind"] == 0:
+            d = np.maximum(np.hypot(mx[I][:, None] - ax[J][None, :], my[I][:, None] - ay[J][None, :]),
+                           np.hypot(mx[I][:, None] - bx[J][None, :], my[I][:, None] - by[J][None, :]))
+            W = int(np.ceil(d.max() / (cs * dt))) + nc
+            if not soe_terms or M - W < max(512, 2 * W):
+                W = M
+            wmax = max(wmax, W)
+            v = 16 // sw
+            near += W * (-(-lf["ns"] // v) * v) * lf["nr"] * sw + (1 + soe_terms) * (-(-lf["ns"] // 4) * 4) * lf["nr"] * sa
+        else:
+            L = int(np.max(lf["mbar"]) + np.max(lf["Dm"]) + np.max(lf["dm"]) - np.min(lf["dm"])) + 2
+            far += 5 * rank * ((lf["nr"] + lf["ns"]) * sa + 8 * L) + 4 * (lf["nr"] + 2 * lf["ns"])
+    state = (wmax + 1) * N * (8 + 4) + 2 * (wmax + 1) * N * 8 + 16 * N * 8
+    return int(near + far + state + 3 * N * 8 * (chunk + 2))
 
 
 def run_alone(req, chunk=64, device=0, precision=None):

@@ -134,8 +134,10 @@ struct StepArgs {
     __half2* Dring16;         // [2 WD][nrhs][NP] scaled FP16 (hi, lo) pairs of Dring (FP16 plans, nrhs >= 2):
                               // slot s is stored at s and s + WD (a window of <= WD slots never wraps),
                               // all right-hand sides of a slot side by side, rows padded to NP (multiple of 4)
-    float* Dscale;            // [WD] inverse power-of-two scale of each Dring16 row (per right-hand side)
-    const void* tmap16;       // TMA tensor map of Dring16 (device memory): box 36 sources x nrhs x item slots
+    float* Dscale;            // [2 WD][SR] inverse power-of-two scale of each Dring16 row, mirrored like
+                              // Dring16, SR = max(nrhs, 4) floats a slot (16-byte rows for the TMA)
+    const void* tmap16;       // TMA tensor maps (device memory): [0] Dring16, box 36 sources x nrhs x
+                              // item slots; [1] Dscale, box SR x item slots
     int NP;
     double* Cring;            // [WC][N]
     double* C;                // [N] cumulative slip (rounded sum)
@@ -231,7 +233,6 @@ __device__ __forceinline__ StepArgs<T> rhs_args(const StepArgs<T>& a0, int r) {
         if (a0.T_out) a.T_out = a0.T_out + rN;
         a.Dring = a0.Dring + r * a0.rs_D;
         if (a0.Dring32) a.Dring32 = a0.Dring32 + r * a0.rs_D;
-        if (a0.Dscale) a.Dscale = a0.Dscale + (long long)r * a0.WD;
         a.Cring = a0.Cring + r * a0.rs_C;
         a.C = a0.C + rN;
         a.Ccomp = a0.Ccomp + rN;
@@ -297,7 +298,11 @@ __global__ void __launch_bounds__(kRowThreads) tc_rows_kernel(StepArgs<T> a0, in
         out0[p] = v;
         out1[p] = v;
     }
-    if (threadIdx.x == 0) a.Dscale[slot] = pow2f(-sh);
+    if (threadIdx.x == 0) {
+        const int sr = a.nrhs > 4 ? a.nrhs : 4;
+        a.Dscale[(size_t)slot * sr + blockIdx.y] = pow2f(-sh);
+        a.Dscale[(size_t)(slot + a.WD) * sr + blockIdx.y] = pow2f(-sh);
+    }
 }
 
 __global__ void set_step_kernel(int* n_dev, int v) {
@@ -552,6 +557,15 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsign
         : "memory");
 }
 
+// 2-D TMA tile load of the box at (x, y) of the tensor map (global memory) into shared memory
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 3-D TMA tile load of the box at (x, y, z) of the tensor map (global memory) into shared memory,
 // completing `bytes` of the mbarrier's transaction count
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, unsigned long long* bar) {
@@ -712,9 +726,12 @@ __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk
             // (the mirrored ring keeps them contiguous; past the ring the box reads zeros)
             if (warp == 0 && lane == 0 && nsl > 0) {
                 const int z0 = wrap(n - tk.k0 - (nsl - 1), a.WD);
+                constexpr int SR = NR > 4 ? NR : 4;
                 fence_proxy_async();
-                mbar_expect_tx(vbar, (unsigned)(VR * kTcBox * 4));
+                mbar_expect_tx(vbar, (unsigned)(VR * kTcBox * 4 + (VR / NR) * SR * 4));
                 tma_load_3d(vb, a.tmap16, tk.s0 & ~3, 0, z0, vbar);
+                // the rows' scales: a box of SR x VR / NR slots right after the rows
+                tma_load_2d(vb + VR * kTcBox * 4, (const unsigned char*)a.tmap16 + sizeof(CUtensorMap), 0, z0, vbar);
             }
             return;
         }
@@ -799,7 +816,9 @@ struct NearCfg {
     // tensor-core window rows (FP16 window, several right-hand sides): TMA boxes of kTcBox words a
     // row (a multiple of 128 bytes for vec_rows = 128), and 128 bytes of room to align them
     static constexpr bool tc = std::is_same<H, __half>::value && NR >= 2;
-    static constexpr int vec_bytes = tc ? vec_rows * kTcBox * 4 : vec_rows * 32 * (int)sizeof(R);
+    static constexpr int tc_scale_bytes = (vec_rows / NR) * (NR > 4 ? NR : 4) * 4;
+    static constexpr int vec_bytes =
+        tc ? (vec_rows * kTcBox * 4 + tc_scale_bytes + 127) / 128 * 128 : vec_rows * 32 * (int)sizeof(R);
     static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes + (tc ? 128 : 0);
 };
 
@@ -1059,7 +1078,7 @@ __device__ __forceinline__ void tc_slices(const __half* const (&sl)[S], const un
     // column v holds right-hand side v % NR
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-        const float s0 = __ldg(sc[q] + ((2 * t) % NR) * sstride), s1 = __ldg(sc[q] + ((2 * t + 1) % NR) * sstride);
+        const float s0 = sc[q][((2 * t) % NR) * sstride], s1 = sc[q][((2 * t + 1) % NR) * sstride];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             acc[mt][0] = fmaf(c[q][mt][0], s0, acc[mt][0]);
@@ -1248,20 +1267,22 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                             const int ks = q * per + kk;
                             const unsigned* rw = (const unsigned*)vrows + (tk.s0 & 3);
                             auto rows_of = [&](int k) { return rw + (size_t)(nsl - 1 - k) * NR * kTcBox; };
-                            auto scale_of = [&](int k) { return v.Dscale + wrap(v.n - tk.k0 - k, v.WD); };
+                            constexpr int SR = NR > 4 ? NR : 4;
+                            const float* scl = (const float*)(vrows + C::vec_rows * kTcBox * 4);
+                            auto scale_of = [&](int k) { return scl + (nsl - 1 - k) * SR; };
                             if (kk + kNearConsumers < cnt) {
                                 const int ks2 = ks + kNearConsumers;
                                 const __half* const sl2[2] = {(const __half*)buf + (size_t)kk * tk.sl,
                                                               (const __half*)buf + (size_t)(kk + kNearConsumers) * tk.sl};
                                 const unsigned* const rw2[2] = {rows_of(ks), rows_of(ks2)};
                                 const float* const sc2[2] = {scale_of(ks), scale_of(ks2)};
-                                tc_slices<NR, 2>(sl2, rw2, sc2, v.WD, tk.nr, tk.ns, lane, tacc);
+                                tc_slices<NR, 2>(sl2, rw2, sc2, 1, tk.nr, tk.ns, lane, tacc);
                                 kk += kNearConsumers;
                             } else {
                                 const __half* const sl1[1] = {(const __half*)buf + (size_t)kk * tk.sl};
                                 const unsigned* const rw1[1] = {rows_of(ks)};
                                 const float* const sc1[1] = {scale_of(ks)};
-                                tc_slices<NR, 1>(sl1, rw1, sc1, v.WD, tk.nr, tk.ns, lane, tacc);
+                                tc_slices<NR, 1>(sl1, rw1, sc1, 1, tk.nr, tk.ns, lane, tacc);
                             }
                             continue;
                         }
@@ -1822,24 +1843,33 @@ static int make_row_tensor_map(fdph_plan_t P) {
         set_error("cuTensorMapEncodeTiled is not available");
         return FDPH_E_CUDA;
     }
-    alignas(64) CUtensorMap map;
+    alignas(64) CUtensorMap map[2];
+    const cuuint32_t chunk = (cuuint32_t)near_max_chunk(P->nrhs, FDPH_FP16);
     const cuuint64_t dims[3] = {(cuuint64_t)P->NP, (cuuint64_t)P->nrhs, (cuuint64_t)2 * P->WD};
     const cuuint64_t strides[2] = {(cuuint64_t)P->NP * 4, (cuuint64_t)P->nrhs * P->NP * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kTcBox, (cuuint32_t)P->nrhs,
-                               (cuuint32_t)near_max_chunk(P->nrhs, FDPH_FP16)};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcBox, (cuuint32_t)P->nrhs, chunk};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = ((PFN_cuTensorMapEncodeTiled_v12000)fn)(
-        &map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)P->Dring16, dims, strides, box, estr,
-        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    auto encode = ((PFN_cuTensorMapEncodeTiled_v12000)fn);
+    CUresult r = encode(&map[0], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, (void*)P->Dring16, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // the rows' scales: [2 WD][SR] floats, SR = max(nrhs, 4) (16-byte rows), box SR x chunk
+    const cuuint64_t sr = (cuuint64_t)std::max(P->nrhs, 4);
+    const cuuint64_t sdims[2] = {sr, (cuuint64_t)2 * P->WD};
+    const cuuint64_t sstrides[1] = {sr * 4};
+    const cuuint32_t sbox[2] = {(cuuint32_t)sr, chunk};
+    if (r == CUDA_SUCCESS)
+        r = encode(&map[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)P->Dscale, sdims, sstrides, sbox, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
         return FDPH_E_CUDA;
     }
     unsigned char* d = nullptr;
-    int rc = dalloc(P, &d, sizeof(CUtensorMap));
+    int rc = dalloc(P, &d, sizeof(map));
     if (rc) return rc;
-    FDPH_CUDA(cudaMemcpyAsync(d, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice, P->stream));
+    FDPH_CUDA(cudaMemcpyAsync(d, map, sizeof(map), cudaMemcpyHostToDevice, P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));
     P->tmap16 = d;
     return FDPH_OK;
@@ -3335,8 +3365,9 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
     if (P->precision == FDPH_FP16 && P->nrhs >= 2) {   // (hi, lo) FP16 rows of the tensor-core near field
         P->NP = (P->N + 3) & ~3;
         const size_t c = (size_t)2 * P->WD * P->nrhs * P->NP;
-        if ((rc = dalloc(P, &P->Dring16, c)) || (rc = dalloc(P, &P->Dscale, (size_t)P->WD * P->nrhs))) return fail(rc);
-        sb += c * 4 + (size_t)P->WD * P->nrhs * 4;
+        const size_t cs = (size_t)2 * P->WD * std::max(P->nrhs, 4);
+        if ((rc = dalloc(P, &P->Dring16, c)) || (rc = dalloc(P, &P->Dscale, cs))) return fail(rc);
+        sb += c * 4 + cs * 4;
         if ((rc = make_row_tensor_map(P))) return fail(rc);
     }
     P->state_bytes = sb;
@@ -3364,7 +3395,7 @@ int fdph_reset(fdph_plan_t P) {
         FDPH_CUDA(cudaMemsetAsync(P->Dring32, 0, (size_t)P->WD * P->N * P->nrhs * sizeof(float), P->stream));
     if (P->Dring16) {
         FDPH_CUDA(cudaMemsetAsync(P->Dring16, 0, (size_t)2 * P->WD * P->NP * P->nrhs * sizeof(__half2), P->stream));
-        FDPH_CUDA(cudaMemsetAsync(P->Dscale, 0, (size_t)P->WD * P->nrhs * sizeof(float), P->stream));
+        FDPH_CUDA(cudaMemsetAsync(P->Dscale, 0, (size_t)2 * P->WD * std::max(P->nrhs, 4) * sizeof(float), P->stream));
     }
     if (P->rupture) FDPH_CUDA(cudaMemsetAsync(P->fr.slip, 0, P->N * sizeof(double), P->stream));
     FDPH_CUDA(cudaStreamSynchronize(P->stream));

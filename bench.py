@@ -314,24 +314,31 @@ def run_rupture(args, cfg):
 
 def run_serving(args):
     """Continuous batching of rupture scenarios (serving.py) against the same requests served one
-    at a time with FP64 storage.  Requests: Poisson arrivals at 8/s, N log-uniform in [256, 2048]
-    (reduced from [512, 16384]: host plan time), CFL 0.25 or 0.5, M = N / CFL / 2, curved
-    geometries; FP32 storage, exponential tails."""
+    at a time with FP64 storage.  Requests: Poisson arrivals at 8/s, N log-uniform in
+    [n_min, n_max], CFL 0.25 or 0.5, M = m_scale N / CFL, curved geometries; FP32 storage,
+    exponential tails.  The default sizes ([256, 2048], m_scale 1/2) keep the run within minutes;
+    the configured serving workload is --requests 64 --n-min 512 --n-max 16384 --m-scale 1, where
+    --alone-sample K serves only the first K requests one at a time in FP64 (the whole set would
+    take most of an hour)."""
     import torch
     from paper_1903_02118_gb300 import build, fdph, serving
     torch.cuda.set_device(0)
     build.build()
-    kw = dict(n_min=256, n_max=2048, m_scale=0.5)
+    kw = dict(n_min=args.n_min, n_max=args.n_max, m_scale=args.m_scale)
     reqs = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
     mix = serving.Server(max_live=16, chunk=64, planners=args.planners, precision=fdph.FP32).serve(reqs, realtime=True)
-    ref = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)
-    alone = serving.Server(max_live=1, chunk=64, planners=1, precision=fdph.FP64).serve(ref, realtime=True)
+    ns = [r.N for r in reqs]
     line = {"metric": "serving element-steps/s and time to solution", "requests": args.requests,
-            "arrivals": "Poisson 8/s", "N_range": [256, 2048], "M": "N / CFL / 2, CFL in {0.25, 0.5}",
-            "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, "planners": args.planners, **mix},
-            "one_at_a_time_fp64": {"precision": "f64", "max_live": 1, **alone},
-            "stepping_only": batch_vs_streams(fdph, serving),
-            "data": "synthetic"}
+            "arrivals": "Poisson 8/s", "N_range": [args.n_min, args.n_max], "N_served": [min(ns), max(ns)],
+            "M": "%g N / CFL, CFL in {0.25, 0.5}" % args.m_scale,
+            "mix": {"precision": "f32-storage/f64-accumulate", "max_live": 16, "planners": args.planners, **mix}}
+    k = args.requests if args.alone_sample is None else min(args.alone_sample, args.requests)
+    if k:
+        ref = serving.poisson_requests(args.requests, rate=8.0, seed=4, **kw)[:k]
+        alone = serving.Server(max_live=1, chunk=64, planners=1, precision=fdph.FP64).serve(ref, realtime=True)
+        line["one_at_a_time_fp64"] = {"precision": "f64", "max_live": 1, "requests_served": k, **alone}
+    line["stepping_only"] = batch_vs_streams(fdph, serving)
+    line["data"] = "synthetic"
     print(json.dumps(line))
 
 
@@ -492,6 +499,11 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="override M")
     ap.add_argument("--requests", type=int, default=32, help="serving workload: number of requests")
     ap.add_argument("--planners", type=int, default=2, help="serving workload: plan-building threads")
+    ap.add_argument("--n-min", type=int, default=256, help="serving workload: smallest N")
+    ap.add_argument("--n-max", type=int, default=2048, help="serving workload: largest N")
+    ap.add_argument("--m-scale", type=float, default=0.5, help="serving workload: M = m_scale N / CFL")
+    ap.add_argument("--alone-sample", type=int, default=None,
+                    help="serving workload: requests also served one at a time in FP64 (default all)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default near-field work-item length")
     args = ap.parse_args()
     if args.workload == "serving":

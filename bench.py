@@ -486,6 +486,8 @@ def main():
                     help="Eq. 42: 0 scatter into delay rings, 1 delayed-history gather (Sec. 5.3)")
     ap.add_argument("--extra-steps", type=int, default=None,
                     help="n_c: steps of Domain F beyond the source duration (default 10 dx / (c dt))")
+    ap.add_argument("--eps-q", type=float, default=None,
+                    help="quantize the Domain-S transient's taps (App. A) with this eps_Q (0: exact taps)")
     ap.add_argument("--amp-window", type=int, default=None, choices=[0, 1],
                     help="Domain-F amplitude window: 0 the placed discrete window, 1 the pair's own (Eq. 28)")
     ap.add_argument("--steady", type=int, default=1024,
@@ -515,7 +517,7 @@ def main():
             cfg["eps_st"] = 1e-4       # with exponential tails the window only needs to cover the wave
     for k, v in (("eta", args.eta), ("eps_st", args.eps_st), ("eta_scheme", args.eta_scheme), ("lmin", args.lmin),
                  ("leaf", args.leaf), ("extra_steps", args.extra_steps), ("N", args.n), ("M", args.m),
-                 ("amp_window", args.amp_window)):
+                 ("amp_window", args.amp_window), ("eps_q", args.eps_q)):
         if v is not None:
             cfg[k] = v
     if args.workload == "rupture":
@@ -550,7 +552,7 @@ def run_fdph(args, cfg):
                      precision=prec, device=local, stream=stream.cuda_stream, soe_terms=cfg.get("soe", 0),
                      eta_scheme=cfg.get("eta_scheme", 0), lmin=cfg.get("lmin", 0.0),
                      extra_steps=cfg.get("extra_steps", -1), nrhs=R, far_mode=args.far_mode,
-                     amp_window=cfg.get("amp_window", 0))
+                     amp_window=cfg.get("amp_window", 0), eps_q=cfg.get("eps_q", 0.0))
     plan_s = time.perf_counter() - t0
     # near-field work-item length from timed trials (not in --quick runs, whose launch counts the
     # profiler commands rely on)
@@ -652,7 +654,7 @@ def run_fdph(args, cfg):
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg.get("soe", 0), "cfl": 0.5,
                        "eta_scheme": cfg.get("eta_scheme", 0), "lmin": cfg.get("lmin", 0.0),
                        "extra_steps": cfg.get("extra_steps", -1), "nrhs": R, "far_mode": args.far_mode,
-                       "amp_window": cfg.get("amp_window", 0),
+                       "amp_window": cfg.get("amp_window", 0), "eps_q": cfg.get("eps_q", 0.0),
                        "first_timed_step": t_run, "untimed_preroll_steps": P, "near_item_steps": chunk,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -141,6 +141,12 @@ typedef struct fdph_params {
                              pair's travel-time difference: smooth in i and j, hence low rank on
                              curved faults, at the price of an O(dt Kstat) mismatch at the start
                              of Domain S */
+    double eps_q;         /* 0 (default): the Domain-S transient (App. B.3) keeps its Dm_tr exact taps.
+                             > 0: those taps are quantized (App. A, applied to the transient as App. B.3
+                             and App. A.3 do): a staircase of constant values over ranges [b_q, b_q+1)
+                             grown while |h_m - h_b_q| / 2 <= eps_q |(h_b_q + h_m) / 2|, each value the
+                             mean of its range's end taps, evaluated every step by running window sums
+                             Yhat_q(n) = Yhat_q(n - 1) + Y(n - b_q) - Y(n - b_q+1) (Eq. A.4) */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */
@@ -352,6 +358,13 @@ int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* materia
  * exact.  Errors: FDPH_E_ARG (null pointer, m or n < 1), FDPH_E_NAN (non-finite entry). */
 int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
                   int32_t* exact);
+
+/* Host-only inspection of the quantization rule (App. A.1.1) the plan applies to the transient's
+ * taps when eps_q > 0, no device needed: partitions of K (n values) into q ranges [b[r], b[r+1])
+ * with b[0] = 0, b[q] = n, grown while |K_m - K_b| / 2 <= eps_q |(K_b + K_m) / 2|, and the range
+ * values khat[r] = (K_b[r] + K_b[r+1]-1) / 2.  b: n + 1 entries of room, khat: n; *q receives the
+ * count.  Errors: FDPH_E_ARG (null pointer, n < 1, eps_q <= 0), FDPH_E_NAN (non-finite value). */
+int fdph_quantize(const double* K, int32_t n, double eps_q, int32_t* b, double* khat, int32_t* q);
 
 /* Allocation-free plain step.  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory (code running inside another runtime's memory pool or

@@ -54,6 +54,9 @@ Readings where the paper is silent or garbled:
   leaf (cross-approximation pivot), h^tr_m = that fibre normalised at m = 0,
   Khat^tr_ij = K_{ij, a_ij + Dm_j} - Khat^S_ij dt;  Dm_tr = 1 + last m < M with
   |fibre(m)| >= eps_st * mu / (2 cs) (0 if none).
+* eps_q > 0: the transient's Dm_tr exact taps are replaced by their App. A staircase
+  (oracle/quantization.py partition rule, applied to the normalised fibre); the operator then holds
+  the staircase values, which the product evaluates by running window sums.
 * m_S(i, j) = 1 + last k < M with |K_{ij,k} - K^stat_ij dt| >= eps_st * mu/(2 cs)
   (0 if none);  eps_st = 0 keeps the whole kernel (the plain ST-BIEM).
 * Geometry arithmetic is FP64 with distances sqrt(dx*dx + dy*dy), no fused
@@ -71,6 +74,7 @@ import math
 import numpy as np
 
 from . import kernel as kn
+from . import quantization as qz
 
 
 NODAL_TAU = 0.2   # nodal-direction threshold of the waveform choice (reading, see header)
@@ -79,7 +83,7 @@ NODAL_TAU = 0.2   # nodal-direction threshold of the waveform choice (reading, s
 class Params:
     def __init__(self, eta=0.5, leaf=32, eps=1e-4, eps_st=1e-6, extra_steps=-1, lmin=0.0,
                  mu=1.0, cs=1.0, dt=0.5, M=256, soe_terms=0, eps_tr=None, art_interp=False, eta_scheme=0,
-                 amp_window=0, transient=True):
+                 amp_window=0, transient=True, eps_q=0.0):
         self.eta, self.leaf, self.eps, self.eps_st = eta, leaf, eps, eps_st
         self.extra_steps, self.lmin, self.mu, self.cs, self.dt, self.M = extra_steps, lmin, mu, cs, dt, M
         self.soe_terms = soe_terms
@@ -90,6 +94,8 @@ class Params:
         # own continuous Domain F of Eq. 28 (see the header)
         self.amp_window = amp_window
         self.transient = transient     # False drops the 2-D Domain-S transient (App. A.3 study)
+        # eps_Q > 0: the transient's exact taps are quantized (App. A; App. B.3 applies it there)
+        self.eps_q = eps_q
 
 
 def soe_min_len(W):
@@ -308,7 +314,13 @@ def admissible_leaf(el, lf, p, nc, need_operator=True):
                 tail_fit = B @ coef
         if not p.transient:
             Br, rT, exT, h, Dtr, tail_fit = np.zeros_like(Br), 0, False, np.zeros(0), 0, np.zeros(0)
-        TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit, raw=Nc * tc)
+        qb = qh = None
+        if p.eps_q > 0.0 and Dtr > 0:
+            # App. A.1.1 on the normalised fibre: a staircase of constant values over ranges
+            # [b_q, b_q+1) of the exact taps, evaluated by running window sums (Eq. A.4)
+            qb, qh = qz.partitions(h, p.eps_q)
+            h = qz.staircase(qb, qh, Dtr)
+        TR[c] = dict(op=Br, rank=rT, exact=exT, h=h, Dm=Dtr, pivot=(pi, pj), tail=tail_fit, raw=Nc * tc, qb=qb, qh=qh)
     out.update(a=a, kS=kS, F=F, S=dict(op=Sr, rank=rS, exact=exS, raw=Ks), TR=TR)
     return out
 

@@ -97,7 +97,8 @@ struct SbDev {
     int kind, rank, r0, nr, s0, ns, L, LZ, taps, maxdelay, mindm, run0, soe, ident, e0, LH;
     long long f, g, h, ring, zring, dhat, delay, dm, ustate, trc, phi;
     long long uhist;    // delayed-history form: [LH][ns] source values u_j of the last LH steps
-    int mindelay, pad;
+    int mindelay, qn;   // qn: quantized ranges of a transient's taps (0: exact taps)
+    long long qb;       // offset of their qn + 1 bounds in ints
 };
 
 struct NearDev {
@@ -499,14 +500,27 @@ __device__ __forceinline__ void trconv_body(const StepArgs<T>& a, int q, int lan
     const double* Y = a.ring + sb.ring + l;
     if (!FDPH_IDX(sb.ring + (long long)sb.L * sb.rank <= a.rs_ring && l < sb.rank &&
                   sb.zring + (long long)sb.LZ * sb.rank <= a.rs_zring &&
-                  (!sb.soe || sb.ustate + (long long)sb.rank * sb.soe <= a.rs_ustate), a.err))
+                  (!(sb.soe + sb.qn) || sb.ustate + (long long)sb.rank * (sb.soe + sb.qn) <= a.rs_ustate), a.err))
         return;
     double z = 0.0;
-    for (int m = lane; m < sb.taps; m += 32)
-        z += (double)a.fac[sb.h + m] * Y[(long long)wrap(t0 - m, sb.L) * sb.rank];
+    const int su = sb.soe + sb.qn;   // states of one rank index: exponential tail, then running sums
+    if (sb.qn) {
+        // quantized taps (App. A): z = sum_q hhat_q Yhat_q, Yhat_q(t) = Yhat_q(t - 1) + Y(t - b_q)
+        // - Y(t - b_q+1) (Eq. A.4), the running window sums kept in the block's states
+        for (int q = lane; q < sb.qn; q += 32) {
+            const int b0 = a.ints[sb.qb + q], b1 = a.ints[sb.qb + q + 1];
+            double* u = a.ustate + sb.ustate + (long long)l * su + sb.soe + q;
+            const double y = *u + Y[(long long)wrap(t0 - b0, sb.L) * sb.rank] - Y[(long long)wrap(t0 - b1, sb.L) * sb.rank];
+            *u = y;
+            z += (double)a.fac[sb.h + q] * y;
+        }
+    } else {
+        for (int m = lane; m < sb.taps; m += 32)
+            z += (double)a.fac[sb.h + m] * Y[(long long)wrap(t0 - m, sb.L) * sb.rank];
+    }
     if (lane < sb.soe) {
         // tail beyond the exact taps: U_q(t) = rho_q U_q(t - 1) + Y(t - taps), z += c_q U_q(t)
-        double* u = a.ustate + sb.ustate + (long long)l * sb.soe + lane;
+        double* u = a.ustate + sb.ustate + (long long)l * su + lane;
         const double un = a.rho[lane] * *u + Y[(long long)wrap(t0 - sb.taps, sb.L) * sb.rank];
         *u = un;
         z += a.trcoef[sb.trc + lane] * un;
@@ -2695,8 +2709,11 @@ static void fill_stats(fdph_plan_t P) {
             flops += 2.0 * sb.taps * sb.ns;
         }
         if (sb.kind == SB_TR) {
-            far_b += r * (sb.taps * 8.0 + sb.taps * ps + 8.0) + r * sb.soe * 24.0;
-            flops += 2.0 * r * (sb.taps + 2.0 * sb.soe);
+            if (sb.qn)   // two ring reads, a running-sum update and a value per quantized range
+                far_b += r * (sb.qn * (16.0 + 16.0 + ps) + 8.0) + r * sb.soe * 24.0;
+            else
+                far_b += r * (sb.taps * 8.0 + sb.taps * ps + 8.0) + r * sb.soe * 24.0;
+            flops += 2.0 * r * ((sb.qn ? 2.0 * sb.qn : sb.taps) + 2.0 * sb.soe);
         }
     }
     const double push_b = hp.n * (8.0 + 8.0 + 32.0 + 8.0 + 4.0);           // D in, ring, C/comp, Cring, perm
@@ -3083,10 +3100,12 @@ static int check_inputs(const fdph_geometry* g, const fdph_material* m, double d
               (p->eta_scheme != 0 && p->eta_scheme != 1) || (p->eta_scheme == 1 && !(p->lmin > 0.0)) ||
               (p->nrhs != 0 && p->nrhs != 1 && p->nrhs != 2 && p->nrhs != 4 && p->nrhs != kMaxRhs) ||
               (p->far_mode != 0 && p->far_mode != 1) || (p->amp_window != 0 && p->amp_window != 1) ||
+              !(p->eps_q >= 0.0 && p->eps_q < 1.0) ||
               (p->precision != FDPH_FP64 && p->precision != FDPH_FP32 && p->precision != FDPH_FP16) ||
               (p->soe_terms != 0 && (p->soe_terms < 4 || p->soe_terms > kMaxSoe)))) {
         set_error("params: leaf_size in [1, 32], eta >= 0, eps_st >= 0, host_threads >= 0, eta_scheme 0 or 1 (1 needs "
-                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), far_mode 0 or 1, amp_window 0 or 1, precision FP64, FP32 or "
+                  "lmin > 0), nrhs 1, 2, 4 or 8 (0: 1), far_mode 0 or 1, amp_window 0 or 1, eps_q in [0, 1), precision "
+                  "FP64, FP32 or "
                   "FP16, "
                   "soe_terms 0 or in [4, 16]");
         return FDPH_E_ARG;
@@ -3123,6 +3142,7 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.threads = p.host_threads > 0 ? p.host_threads : omp_get_max_threads();
     in.eta_scheme = p.eta_scheme;
     in.amp_window = p.amp_window;
+    in.eps_q = p.eps_q;
     return in;
 }
 
@@ -3140,6 +3160,25 @@ int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, 
     *exact = lr.exact ? 1 : 0;
     std::copy(lr.F.begin(), lr.F.end(), F);
     std::copy(lr.G.begin(), lr.G.end(), G);
+    return FDPH_OK;
+}
+
+int fdph_quantize(const double* K, int32_t n, double eps_q, int32_t* b, double* khat, int32_t* q) {
+    if (!K || !b || !khat || !q || n < 1 || !(eps_q > 0.0)) {
+        set_error("fdph_quantize: null pointer, n < 1 or eps_q <= 0");
+        return FDPH_E_ARG;
+    }
+    for (int m = 0; m < n; ++m)
+        if (!std::isfinite(K[m])) {
+            set_error("fdph_quantize: non-finite value");
+            return FDPH_E_NAN;
+        }
+    std::vector<int32_t> bb;
+    std::vector<double> kh;
+    quantize_partitions(K, n, eps_q, bb, kh);
+    std::copy(bb.begin(), bb.end(), b);
+    std::copy(kh.begin(), kh.end(), khat);
+    *q = (int32_t)kh.size();
     return FDPH_OK;
 }
 
@@ -3278,7 +3317,7 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         sd[q] = {b.kind, b.rank, b.r0, b.nr, b.s0, b.ns, b.L, b.LZ, b.taps, b.maxdelay, b.mindm, b.run0,
                  b.soe, b.ident, b.e0, LH, (long long)b.f, (long long)b.g, (long long)b.h, (long long)b.ring, (long long)b.zring,
                  (long long)b.dhat, (long long)b.delay, (long long)b.dm, (long long)b.ustate, (long long)b.trc,
-                 (long long)b.phi, 0, b.mindelay, 0};
+                 (long long)b.phi, 0, b.mindelay, b.qn, (long long)b.qb};
     }
     // delayed-history form of Eq. 42 (far_mode 1): per block a history [LH][ns] of the source
     // values, recorded every step, and one gather task per (block, rank index)

@@ -52,7 +52,11 @@ struct PlanInputs {
     int threads;       // host threads of the build (OpenMP), > 0
     int eta_scheme;    // 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25)
     int amp_window;    // Domain-F amplitude window: 0 the placed discrete window, 1 the pair's own (Eq. 28)
+    double eps_q;      // > 0: the transient's exact taps quantized (App. A)
 };
+
+// App. A.1.1 partitions of K[0, n): b (q + 1 entries, b[0] = 0, b[q] = n) and range values khat (q)
+void quantize_partitions(const double* K, int n, double eps_q, std::vector<int32_t>& b, std::vector<double>& khat);
 
 // Decay factors rho_q = exp(-lambda_q) of the exponential tail basis, lambda_q spaced
 // geometrically in [0.5/M, 1] (q < Q).

@@ -41,6 +41,8 @@ struct LeafOut {
     std::vector<double> h[2];      // [HM][ns]
     std::vector<double> htr[2];    // exact taps
     std::vector<double> trc[2];    // exponential-tail coefficients of the fibre (if any)
+    std::vector<int32_t> qb[2];    // eps_q > 0: quantized ranges of the taps (bounds) ...
+    std::vector<double> qh[2];     // ... and their values
     int Dtr[2] = {0, 0};
     int trsoe[2] = {0, 0};
     bool ok = true;
@@ -55,6 +57,29 @@ Seg seg_of(const Elements& el, int e) {
     s.len = el.len[e];
     return s;
 }
+
+}  // namespace
+
+// App. A.1.1 (the oracle's reading): from b_q the range grows while |K_m - K_b_q| / 2 <=
+// eps_q |(K_b_q + K_m) / 2|; b_q+1 is the first m that breaks it; khat_q = (K_b_q + K_b_q+1 - 1) / 2.
+void quantize_partitions(const double* K, int n, double eps_q, std::vector<int32_t>& b, std::vector<double>& khat) {
+    b.assign(1, 0);
+    khat.clear();
+    int q0 = 0;
+    while (q0 < n) {
+        int m = q0 + 1;
+        while (m < n) {
+            const double kh = 0.5 * (K[q0] + K[m]);
+            if (0.5 * fabs(K[m] - K[q0]) > eps_q * fabs(kh)) break;
+            ++m;
+        }
+        khat.push_back(0.5 * (K[q0] + K[m - 1]));
+        b.push_back(m);
+        q0 = m;
+    }
+}
+
+namespace {
 
 void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanInputs& in, LeafOut& o) {
     const ClusterNode& tn = tr.nodes[lf.tau];
@@ -192,6 +217,7 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
         o.htr[cc].resize(Dtr);
         for (int m = 0; m < Dtr; ++m) o.htr[cc][m] = fib[m] / fib[0];
         o.trc[cc] = coef;
+        if (in.eps_q > 0.0) quantize_partitions(o.htr[cc].data(), Dtr, in.eps_q, o.qb[cc], o.qh[cc]);
     }
 }
 
@@ -299,7 +325,8 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         const int mindm = *std::min_element(o.art.dm.begin(), o.art.dm.end());
         const int maxdm = *std::max_element(o.art.dm.begin(), o.art.dm.end());
         auto add = [&](int kind, const LowRank& lr, const std::vector<int32_t>& dl, int64_t dl_off,
-                       const std::vector<double>* h, int taps, int soe, const std::vector<double>* trc) {
+                       const std::vector<double>* h, int taps, int soe, const std::vector<double>* trc,
+                       const std::vector<int32_t>* qb = nullptr, const std::vector<double>* qh = nullptr) {
             if (lr.rank <= 0) return;
             SubBlock sb;
             memset(&sb, 0, sizeof(sb));
@@ -313,7 +340,10 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.taps = taps;
             sb.f = append(hp.fac, lr.F.data(), lr.F.size());
             sb.g = append(hp.fac, lr.G.data(), lr.G.size());
-            sb.h = h ? append(hp.fac, h->data(), h->size()) : 0;
+            const bool quant = qh && !qh->empty();   // the taps' staircase values replace the taps
+            sb.h = quant ? append(hp.fac, qh->data(), qh->size()) : h ? append(hp.fac, h->data(), h->size()) : 0;
+            sb.qn = quant ? (int32_t)qh->size() : 0;
+            sb.qb = quant ? append(hp.ints, qb->data(), qb->size()) : 0;
             sb.delay = dl_off;
             sb.dm = dm_off;
             sb.phi = phi_off;
@@ -322,10 +352,11 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.ident = lr.exact ? (lr.m <= lr.n ? 1 : 2) : 0;
             sb.e0 = (int32_t)hp.far_nent;
             hp.far_nent += o.nr;
-            sb.ustate = hp.ustate_len;
-            hp.ustate_len += (int64_t)sb.rank * soe;
+            sb.ustate = hp.ustate_len;   // [rank][soe + qn]: exponential-tail states, then running sums
+            hp.ustate_len += (int64_t)sb.rank * (soe + sb.qn);
             if (kind == SB_TR) {
-                sb.L = sb.maxdelay + mindm + taps + (soe ? 1 : 0);   // + the tail's input Y(t - taps)
+                // + the input Y(t - taps) of the tail and of the last running sum
+                sb.L = sb.maxdelay + mindm + taps + (soe || sb.qn ? 1 : 0);
                 sb.LZ = maxdm - mindm + 1 + ex;
             } else {
                 sb.L = sb.maxdelay + maxdm + 1 + ex;
@@ -380,7 +411,8 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         add(SB_F, o.F[1], dF, dF_off, &o.h[1], o.HM, 0, nullptr);
         add(SB_S, o.S, dS, dS_off, nullptr, 0, 0, nullptr);
         for (int cc = 0; cc < 2; ++cc)
-            if (o.Dtr[cc] > 0) add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc], o.trsoe[cc], &o.trc[cc]);
+            if (o.Dtr[cc] > 0)
+                add(SB_TR, o.TR[cc], dS, dS_off, &o.htr[cc], o.Dtr[cc], o.trsoe[cc], &o.trc[cc], &o.qb[cc], &o.qh[cc]);
     }
     hp.mean_rank = rank_cnt ? rank_sum / rank_cnt : 0.0;
     hp.g_ptr.assign(n + 1, 0);

@@ -29,6 +29,8 @@ struct SubBlock {
     int32_t ident;     // block kept exact: 1 = F is the identity (rank nr), 2 = G is the identity
                        // (rank ns), 0 = low-rank factors
     int32_t e0;        // index of the block's first (block, receiver) entry in block-major order
+    int32_t qn;        // TR with eps_q > 0: quantized ranges of the taps (h then holds their qn values)
+    int64_t qb;        // TR: offset of the qn + 1 range bounds in the int array
 };
 
 struct NearLeaf {

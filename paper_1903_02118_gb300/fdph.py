@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32),
-                ("far_mode", ctypes.c_int32), ("amp_window", ctypes.c_int32)]
+                ("far_mode", ctypes.c_int32), ("amp_window", ctypes.c_int32), ("eps_q", ctypes.c_double)]
 
 
 class Friction(ctypes.Structure):
@@ -69,7 +69,7 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
-           "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run",
+           "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run", "fdph_quantize",
            "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy", "fdph_low_rank"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
@@ -122,6 +122,9 @@ def lib():
         L.fdph_low_rank.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, c_p, c_p,
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.fdph_low_rank.restype = ctypes.c_int
+        L.fdph_quantize.argtypes = [c_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), c_p,
+                                    ctypes.POINTER(ctypes.c_int32)]
+        L.fdph_quantize.restype = ctypes.c_int
         L.fdph_autotune.argtypes = [c_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.fdph_autotune.restype = ctypes.c_int
         L.fdph_selftest_wait_timeout.argtypes = [ctypes.c_int32, ctypes.c_int64]
@@ -135,7 +138,7 @@ def lib():
                      "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
                      "fdph_tree_export", "fdph_set_profiling", "fdph_kernel_times", "fdph_plain_step_noalloc",
                      "fdph_rupture_init", "fdph_rupture_step", "fdph_rupture_run", "fdph_rupture_slip",
-                     "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run",
+                     "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run", "fdph_quantize",
                      "fdph_batch_rupture_run", "fdph_batch_synchronize"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -167,12 +170,12 @@ def default_params():
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
                 device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None,
-                nrhs=None, far_mode=None, amp_window=None):
+                nrhs=None, far_mode=None, amp_window=None, eps_q=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
                  ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs), ("far_mode", far_mode),
-                 ("amp_window", amp_window),
+                 ("amp_window", amp_window), ("eps_q", eps_q),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)
@@ -376,6 +379,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def quantize(K, eps_q):
+    """The plan's quantization rule (fdph_quantize): returns (b, khat) for the values K."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    n = K.shape[0]
+    b = np.zeros(n + 1, dtype=np.int32)
+    kh = np.zeros(n)
+    q = ctypes.c_int32()
+    _check(lib().fdph_quantize(ctypes.c_void_p(K.ctypes.data), n, float(eps_q), b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               ctypes.c_void_p(kh.ctypes.data), ctypes.byref(q)))
+    return b[:q.value + 1].copy(), kh[:q.value].copy()
 
 
 def low_rank(A, eps):

@@ -521,3 +521,26 @@ def test_delayed_history_gather_equals_scatter(geom, N, M, soe, prec):
     assert (out[0][0] > 0).mean() > 0.1
     tol = 1e-10 if prec == fdph.FP64 else 1e-5
     assert _rel(out[1][0], out[0][0]) < tol and _rel(out[1][1], out[0][1]) < tol
+
+
+@pytest.mark.parametrize("geom,N,M,soe", [("curved", 200, 320, 0), ("kinked", 190, 900, 16)])
+def test_quantized_transient_fp64_equals_compressed_operator(geom, N, M, soe):
+    """eps_q > 0: the Domain-S transient's taps as App. A staircases evaluated by running window
+    sums on the device; the oracle's compressed operator holds the same staircases (its partition
+    rule, oracle/quantization.py), so the FP64 march matches it like the exact taps do."""
+    _need_gpu()
+    eps, leaf, eps_q = 1e-5, 16, 0.05
+    eps_st = 1e-4 if soe else 1e-6
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    el = kn.element_table(xy)
+    p = ofd.Params(eta=0.5, leaf=leaf, eps=eps, eps_st=eps_st, M=M, soe_terms=soe, amp_window=1, eps_q=eps_q)
+    oplan = ofd.build_plan(el, p)
+    assert any(d["TR"][c]["qh"] is not None and len(d["TR"][c]["qh"]) < d["TR"][c]["Dm"]
+               for d in oplan["adm"] for c in "xy")
+    T0 = dense.march_rows_fft(ofd.operator_rows(el, oplan, np.arange(N)), D)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=eps_st, leaf_size=leaf, soe_terms=soe, amp_window=1, eps_q=eps_q)
+    T = _run(plan, D)
+    assert _rel(T, T0) < TOL64
+    plan.reset()                                  # the running sums restart from zero
+    assert _rel(_run(plan, D), T0) < TOL64

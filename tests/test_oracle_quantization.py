@@ -66,3 +66,46 @@ def test_special_cases():
     b_abs, kh = qz.partitions(K, 0.1, eps_abs=1e-3)
     assert len(b_abs) > len(b_rel)
     assert np.abs(qz.staircase(b_abs, kh, 101) - K).max() <= 1e-3 + 1e-15
+
+
+def test_library_partitions_equal_the_oracle_bit_for_bit():
+    """The plan's quantization of the transient taps (fdph_quantize, host only) takes the same
+    ranges and values as the oracle's partition rule: on kernel fibres, a power law and a
+    turning sequence, at several eps_Q."""
+    fdph = pytest.importorskip("paper_1903_02118_gb300.fdph")
+    try:
+        fdph.lib()
+    except ImportError:
+        pytest.skip("libfdph.so not built")
+    seqs = [_fibre(), _fibre(600)[40:] / _fibre(600)[40], np.arange(1, 2001) ** -1.5,
+            np.cos(np.arange(400) / 40.0) + 1.5]
+    for K in seqs:
+        for eps_q in (0.2, 0.05, 0.01, 1e-3):
+            b, kh = qz.partitions(K, eps_q)
+            b2, kh2 = fdph.quantize(K, eps_q)
+            assert np.array_equal(b, b2) and np.array_equal(kh, kh2)
+
+
+def test_quantized_transient_keeps_the_accuracy():
+    """App. A.3: inside FDP=H the solution accuracy is unchanged for eps_Q from 1e-1 to 1e-3.  The
+    oracle's march with the transient's taps quantized (eps_Q = 0.05, 0.01) against the plain march
+    stays within 1 % of the error with exact taps, with far fewer ranges than taps."""
+    from oracle import dense
+    from oracle import fdph as ofd
+    N, M = 200, 400
+    xy = inputs.kinked_fault(N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    el = kn.element_table(xy)
+    rows = np.arange(0, N, 5)
+    T0 = dense.march_rows_fft(kn.discrete_kernel(el, 0.5, M, 1.0, 1.0, receivers=rows), D)
+    errs, ratio = [], []
+    for eq in (0.0, 0.05, 0.01):
+        plan = ofd.build_plan(el, ofd.Params(eta=0.5, leaf=16, eps=1e-4, eps_st=1e-6, M=M, amp_window=1, eps_q=eq),
+                              receivers=rows)
+        T1 = dense.march_rows_fft(ofd.operator_rows(el, plan, rows), D)
+        errs.append(np.linalg.norm(T1 - T0) / np.linalg.norm(T0))
+        if eq:
+            trs = [d["TR"][c] for d in plan["adm"] for c in "xy" if d["TR"][c]["rank"] and d["TR"][c]["Dm"] > 8]
+            ratio.append(np.mean([len(t["qh"]) / t["Dm"] for t in trs]))
+    assert abs(errs[1] - errs[0]) < 0.01 * errs[0] and abs(errs[2] - errs[0]) < 0.01 * errs[0], errs
+    assert ratio[0] < 0.3 and ratio[1] < 0.6, ratio

@@ -147,6 +147,20 @@ typedef struct fdph_params {
                              grown while |h_m - h_b_q| / 2 <= eps_q |(h_b_q + h_m) / 2|, each value the
                              mean of its range's end taps, evaluated every step by running window sums
                              Yhat_q(n) = Yhat_q(n - 1) + Y(n - b_q) - Y(n - b_q+1) (Eq. A.4) */
+    int64_t aca_min;      /* how the admissible blocks are factorised (Sec. 4, Sec. 6.2).  0 (default):
+                             every block formed densely and factorised by pivoted QR + SVD, the
+                             truncated SVD of minimal rank (the definition the LRA approximates).
+                             > 0: a block of at least aca_min entries by adaptive cross approximation
+                             with partial pivoting and reference row / column (ACA+, the H-matrix
+                             construction Sec. 4 names) from rows and columns computed on demand,
+                             recompressed to the rank eps needs: O(rank (N_r + N_s)) kernel
+                             evaluations per block instead of N_r N_s, for plans too large to form
+                             every block (N >= ~32768); a block whose cross approximation does not
+                             converge is formed densely.  The transient's spatial pivot (App. H) on
+                             such a block is the largest entry of alternating row / column searches.
+                             Each block then meets |K - F G^T|_F < eps |K|_F up to the cross
+                             approximation's own error (estimated at 1e-3 eps), but its factors are
+                             not the truncated SVD's.  4096 is a good value */
 } fdph_params;
 
 /* Per-plan statistics (host copy). Bytes are algorithmic: what one step must move. */
@@ -358,6 +372,19 @@ int fdph_tree_export(const fdph_geometry* geometry, const fdph_material* materia
  * exact.  Errors: FDPH_E_ARG (null pointer, m or n < 1), FDPH_E_NAN (non-finite entry). */
 int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
                   int32_t* exact);
+
+/* Host-only inspection of the cross approximation the plan takes for large admissible blocks
+ * (fdph_params.aca_min; Sec. 4 names ACA as the H-matrix construction): A (m x n, row-major) is read
+ * one row or column at a time, as the plan evaluates the kernel on demand.  ACA with partial
+ * pivoting and reference row / column (ACA+) runs to a relative update size of 1e-3 eps, then the
+ * cross is recompressed (QR of both factors, truncated SVD of the small core) to the smallest rank
+ * with |A_aca - F G^T|_F < eps |A_aca|_F.  *converged = 0 when the cross did not converge (more than
+ * min(m, n, 96) crosses, or a reference row / column still large at the end): the plan then factorises
+ * the dense block, and F, G are not written.  F and G are written row-major into buffers of
+ * m * min(m, n, 96) and n * min(m, n, 96) doubles; *evaluated receives the number of entries read.
+ * Errors: FDPH_E_ARG (null pointer, m or n < 1, eps <= 0), FDPH_E_NAN (non-finite entry). */
+int fdph_low_rank_aca(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
+                      int32_t* converged, int64_t* evaluated);
 
 /* Host-only inspection of the quantization rule (App. A.1.1) the plan applies to the transient's
  * taps when eps_q > 0, no device needed: partitions of K (n values) into q ranges [b[r], b[r+1])

@@ -35,6 +35,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <chrono>
 #include <cmath>
@@ -3143,6 +3144,7 @@ static PlanInputs make_inputs(const fdph_material* m, double dt, int M, double e
     in.eta_scheme = p.eta_scheme;
     in.amp_window = p.amp_window;
     in.eps_q = p.eps_q;
+    in.aca_min = p.aca_min > 0 ? (long long)p.aca_min : LLONG_MAX;
     return in;
 }
 
@@ -3160,6 +3162,38 @@ int fdph_low_rank(const double* A, int32_t m, int32_t n, double eps, double* F, 
     *exact = lr.exact ? 1 : 0;
     std::copy(lr.F.begin(), lr.F.end(), F);
     std::copy(lr.G.begin(), lr.G.end(), G);
+    return FDPH_OK;
+}
+
+int fdph_low_rank_aca(const double* A, int32_t m, int32_t n, double eps, double* F, double* G, int32_t* rank,
+                      int32_t* converged, int64_t* evaluated) {
+    if (!A || !F || !G || !rank || !converged || !evaluated || m < 1 || n < 1 || !(eps > 0.0)) {
+        set_error("fdph_low_rank_aca: null pointer, m or n < 1 or eps <= 0");
+        return FDPH_E_ARG;
+    }
+    for (long long q = 0; q < (long long)m * n; ++q)
+        if (!std::isfinite(A[q])) {
+            set_error("fdph_low_rank_aca: non-finite entry");
+            return FDPH_E_NAN;
+        }
+    long long count = 0;
+    auto row = [&](int i, double* out) {
+        std::copy(A + (size_t)i * n, A + (size_t)(i + 1) * n, out);
+        count += n;
+    };
+    auto col = [&](int j, double* out) {
+        for (int i = 0; i < m; ++i) out[i] = A[(size_t)i * n + j];
+        count += m;
+    };
+    LowRank lr;
+    const bool ok = low_rank_aca(row, col, m, n, eps, lr);
+    *converged = ok ? 1 : 0;
+    *rank = ok ? lr.rank : 0;
+    *evaluated = count;
+    if (ok) {
+        std::copy(lr.F.begin(), lr.F.end(), F);
+        std::copy(lr.G.begin(), lr.G.end(), G);
+    }
     return FDPH_OK;
 }
 

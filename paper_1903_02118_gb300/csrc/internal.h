@@ -3,6 +3,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <climits>
+#include <functional>
 #include <vector>
 
 namespace fdph {
@@ -53,6 +55,7 @@ struct PlanInputs {
     int eta_scheme;    // 0: constant eta (Eq. 8); 1: constant eta^2 dist (Eq. 25)
     int amp_window;    // Domain-F amplitude window: 0 the placed discrete window, 1 the pair's own (Eq. 28)
     double eps_q;      // > 0: the transient's exact taps quantized (App. A)
+    long long aca_min = LLONG_MAX;   // blocks of at least this many entries: cross approximation
 };
 
 // App. A.1.1 partitions of K[0, n): b (q + 1 entries, b[0] = 0, b[q] = n) and range values khat (q)
@@ -73,13 +76,21 @@ ArtInts art_integers(const Elements& el, const Tree& tr, const Leaf& lf, const P
 
 // Truncated SVD low-rank approximation with the Frobenius criterion.
 // A is m x n row-major.  On return: rank r, F (m x r, row-major), G (n x r, row-major) with
-// A_r = F G^T; exact = true when the block is kept exact (rank * (m + n) >= m * n).
+// A_r = F G^T; exact = true when the block is kept exact (rank * (m + n) >= m * n), which
+// allow_exact = false turns off (the truncation is returned whatever its rank).
 struct LowRank {
     int m = 0, n = 0, rank = 0;
     bool exact = false;
     std::vector<double> F, G;
 };
-void low_rank(const double* A, int m, int n, double eps, LowRank& out);
+void low_rank(const double* A, int m, int n, double eps, LowRank& out, bool allow_exact = true);
+// Adaptive cross approximation with reference row and column (ACA+) to 1e-3 eps, entries computed on
+// demand (row(i, out[n]), col(j, out[m])), then recompressed to the truncated SVD of the
+// approximation at eps.  False when it did not converge within 96 crosses, the reference row /
+// column show a missed part, or the rank would keep the block exact (the caller then forms the
+// block and takes low_rank).
+bool low_rank_aca(const std::function<void(int, double*)>& row, const std::function<void(int, double*)>& col, int m,
+                  int n, double eps, LowRank& out);
 
 void set_error(const std::string& msg);
 

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <functional>
 #include <numeric>
 #include <vector>
 
@@ -87,7 +88,7 @@ void hestenes(std::vector<double>& X, int rows, int cols, std::vector<double>& V
 
 }  // namespace
 
-void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
+void low_rank(const double* A, int m, int n, double eps, LowRank& out, bool allow_exact) {
     out.m = m;
     out.n = n;
     out.rank = 0;
@@ -248,7 +249,7 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out) {
     int r = kr;
     for (int l = 0; l <= kr; ++l)
         if (sqrt(tail[l]) < lim) { r = l; break; }
-    if ((long)r * (m + n) >= (long)m * n) {
+    if (allow_exact && (long)r * (m + n) >= (long)m * n) {
         keep_exact();
         return;
     }
@@ -349,6 +350,209 @@ void soe_solve(const std::vector<double>& rho, int len, const double* g, double*
             cr[i] = s / G[(size_t)i * Q + i];
         }
     }
+}
+
+}  // namespace fdph
+
+namespace fdph {
+
+namespace {
+
+// deterministic generator for the reference rows / columns of the cross approximation
+struct Lcg {
+    unsigned long long s;
+    explicit Lcg(unsigned long long seed) : s(seed * 6364136223846793005ULL + 1442695040888963407ULL) {}
+    int below(int n) {
+        s = s * 6364136223846793005ULL + 1442695040888963407ULL;
+        return (int)((s >> 33) % (unsigned long long)n);
+    }
+};
+
+// Q R of the columns of X (rows x k, column-major) by Gram-Schmidt applied twice per column; X is
+// replaced by Q, R (k x k, column-major, upper) is returned.  A column that vanishes after its
+// projections stays zero (its row of R is zero).
+std::vector<double> cgs2(std::vector<double>& X, int rows, int k) {
+    std::vector<double> R((size_t)k * k, 0.0);
+    for (int c = 0; c < k; ++c) {
+        double* x = &X[(size_t)c * rows];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int p = 0; p < c; ++p) {
+                const double* q = &X[(size_t)p * rows];
+                const double d = dot4(q, x, rows);
+                R[(size_t)c * k + p] += d;
+                for (int i = 0; i < rows; ++i) x[i] -= d * q[i];
+            }
+        const double nx = sqrt(dot4(x, x, rows));
+        R[(size_t)c * k + c] = nx;
+        const double inv = nx > 0.0 ? 1.0 / nx : 0.0;
+        for (int i = 0; i < rows; ++i) x[i] *= inv;
+    }
+    return R;
+}
+
+}  // namespace
+
+bool low_rank_aca(const std::function<void(int, double*)>& row, const std::function<void(int, double*)>& col, int m,
+                  int n, double eps, LowRank& out) {
+    out.m = m;
+    out.n = n;
+    out.rank = 0;
+    out.exact = false;
+    out.F.clear();
+    out.G.clear();
+    if (m < 2 || n < 2 || !(eps > 0.0)) return false;
+    const double tol = 1e-3 * eps;
+    const int kmax = std::min(std::min(m, n), 96);
+    std::vector<std::vector<double>> U, V;            // A ~ sum_l U_l V_l^T
+    std::vector<char> rused(m, 0), cused(n, 0);
+    std::vector<double> r(n), c(m), rref(n), cref(m);
+    Lcg rng(0x5eedULL + (unsigned long long)m * 131071ULL + (unsigned long long)n);
+    auto resid_row = [&](int i, std::vector<double>& out_r) {
+        row(i, out_r.data());
+        for (size_t l = 0; l < U.size(); ++l) {
+            const double f = U[l][i];
+            for (int j = 0; j < n; ++j) out_r[j] -= f * V[l][j];
+        }
+    };
+    auto resid_col = [&](int j, std::vector<double>& out_c) {
+        col(j, out_c.data());
+        for (size_t l = 0; l < U.size(); ++l) {
+            const double f = V[l][j];
+            for (int i = 0; i < m; ++i) out_c[i] -= f * U[l][i];
+        }
+    };
+    auto argmax_free = [](const std::vector<double>& x, const std::vector<char>& used) {
+        int best = -1;
+        double bv = -1.0;
+        for (size_t t = 0; t < x.size(); ++t)
+            if (!used[t] && fabs(x[t]) > bv) {
+                bv = fabs(x[t]);
+                best = (int)t;
+            }
+        return best;
+    };
+    auto pick_free = [&](const std::vector<char>& used, int count) {
+        for (int tries = 0; tries < 64; ++tries) {
+            const int t = rng.below(count);
+            if (!used[t]) return t;
+        }
+        for (int t = 0; t < count; ++t)
+            if (!used[t]) return t;
+        return -1;
+    };
+    int iref = pick_free(rused, m), jref = pick_free(cused, n);
+    resid_row(iref, rref);
+    resid_col(jref, cref);
+    double norm2 = 0.0;
+    int small = 0, vanished = 0;
+    bool converged = false;
+    for (int k = 0; k < kmax; ++k) {
+        // pivot from the larger of the reference row's and the reference column's residuals (ACA+)
+        const int j1 = argmax_free(rref, cused), i1 = argmax_free(cref, rused);
+        if (j1 < 0 || i1 < 0) break;
+        int is, js;
+        if (fabs(rref[j1]) >= fabs(cref[i1])) {
+            js = j1;
+            resid_col(js, c);
+            is = argmax_free(c, rused);
+            resid_row(is, r);
+        } else {
+            is = i1;
+            resid_row(is, r);
+            js = argmax_free(r, cused);
+            resid_col(js, c);
+        }
+        const double piv = r[js];
+        if (!(fabs(piv) > 1e-300)) {
+            // the residual vanished on the reference row and column and on the cross through their
+            // largest entries: a few fresh references before concluding that the rest is zero
+            if (++vanished > 3) {
+                converged = true;
+                break;
+            }
+            rused[iref] = 1;
+            cused[jref] = 1;
+            iref = pick_free(rused, m);
+            jref = pick_free(cused, n);
+            if (iref < 0 || jref < 0) {
+                converged = true;
+                break;
+            }
+            resid_row(iref, rref);
+            resid_col(jref, cref);
+            --k;
+            continue;
+        }
+        std::vector<double> u(m), v(r);
+        for (int i = 0; i < m; ++i) u[i] = c[i] / piv;
+        rused[is] = 1;
+        cused[js] = 1;
+        // |S + u v^T|_F^2 = |S|_F^2 + 2 sum_l (u . U_l)(v . V_l) + |u|^2 |v|^2
+        const double uu = dot4(u.data(), u.data(), m), vv = dot4(v.data(), v.data(), n);
+        double cross = 0.0;
+        for (size_t l = 0; l < U.size(); ++l) cross += dot4(u.data(), U[l].data(), m) * dot4(v.data(), V[l].data(), n);
+        norm2 += 2.0 * cross + uu * vv;
+        // the reference row and column lose the new cross
+        const double ur = u[iref], vc = v[jref];
+        U.push_back(std::move(u));
+        V.push_back(std::move(v));
+        for (int j = 0; j < n; ++j) rref[j] -= ur * V.back()[j];
+        for (int i = 0; i < m; ++i) cref[i] -= vc * U.back()[i];
+        if (rused[iref]) {
+            iref = pick_free(rused, m);
+            if (iref < 0) break;
+            resid_row(iref, rref);
+        }
+        if (cused[jref]) {
+            jref = pick_free(cused, n);
+            if (jref < 0) break;
+            resid_col(jref, cref);
+        }
+        small = sqrt(uu * vv) <= tol * sqrt(std::max(norm2, 0.0)) ? small + 1 : 0;
+        if (small >= 2) {
+            converged = true;
+            break;
+        }
+    }
+    if (!converged) return false;
+    if (U.empty()) return true;   // rank 0: every sampled row and column vanished
+    // the reference row and column are residuals of unused random ones: their energy, scaled to the
+    // whole block, must be within the tolerance, else the cross approximation missed a part
+    const double rr = dot4(rref.data(), rref.data(), n) * m, cc = dot4(cref.data(), cref.data(), m) * n;
+    if (std::max(rr, cc) > 100.0 * tol * tol * norm2) return false;
+    // recompression: U = Qu Ru, V = Qv Rv, core Ru Rv^T truncated at eps (its Frobenius norm is the
+    // approximation's), A ~ (Qu Fc)(Qv Gc)^T
+    const int k = (int)U.size();
+    std::vector<double> Qu((size_t)m * k), Qv((size_t)n * k);
+    for (int l = 0; l < k; ++l) {
+        std::copy(U[l].begin(), U[l].end(), Qu.begin() + (size_t)l * m);
+        std::copy(V[l].begin(), V[l].end(), Qv.begin() + (size_t)l * n);
+    }
+    const std::vector<double> Ru = cgs2(Qu, m, k), Rv = cgs2(Qv, n, k);
+    std::vector<double> core((size_t)k * k, 0.0);   // row-major k x k: (Ru Rv^T)[a][b]
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) {
+            double s = 0.0;
+            for (int l = std::max(a, b); l < k; ++l) s += Ru[(size_t)l * k + a] * Rv[(size_t)l * k + b];
+            core[(size_t)a * k + b] = s;
+        }
+    LowRank cr;
+    low_rank(core.data(), k, k, eps, cr, false);
+    const int rk = cr.rank;
+    if ((long)rk * (m + n) >= (long)m * n) return false;   // the block is kept exact (Sec. 6.2)
+    out.rank = rk;
+    if (rk == 0) return true;
+    out.F.assign((size_t)m * rk, 0.0);
+    out.G.assign((size_t)n * rk, 0.0);
+    for (int a = 0; a < k; ++a)
+        for (int l = 0; l < rk; ++l) {
+            const double f = cr.F[(size_t)a * rk + l], g = cr.G[(size_t)a * rk + l];
+            if (f != 0.0)
+                for (int i = 0; i < m; ++i) out.F[(size_t)i * rk + l] += Qu[(size_t)a * m + i] * f;
+            if (g != 0.0)
+                for (int j = 0; j < n; ++j) out.G[(size_t)j * rk + l] += Qv[(size_t)a * n + j] * g;
+        }
+    return true;
 }
 
 }  // namespace fdph

@@ -96,38 +96,137 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
     const int nr = o.nr, ns = o.ns;
     const double dt = in.dt, mu = in.mu, c = in.cs;
     const double ist[2] = {0.5 * (tn.box.lo[0] + tn.box.hi[0]), 0.5 * (tn.box.lo[1] + tn.box.hi[1])};
-    std::vector<double> Ax((size_t)nr * ns), Ay((size_t)nr * ns), Ks((size_t)nr * ns);
-    std::vector<double> tx((size_t)nr * ns), ty((size_t)nr * ns);
-    std::vector<double> tS((size_t)nr * ns);   // start time of the pair's Domain S (transient pivot)
-    for (int il = 0; il < nr; ++il) {
-        const int ei = tr.perm[o.r0 + il];
-        const double px = el.mx[ei], py = el.my[ei], nx = el.nx[ei], ny = el.ny[ei];
-        for (int jl = 0; jl < ns; ++jl) {
-            const int ej = tr.perm[o.s0 + jl];
-            const Seg s = seg_of(el, ej);
-            const long a = (long)o.art.dm[il] + o.art.mbar[jl];
-            const long kS = a + o.art.Dm[jl];
-            double t_lo = (double)a * dt, t_hi = (double)kS * dt;
-            if (in.amp_window == 1) {
-                // Eq. 28: the pair's own Domain F, the window of i* moved by r_ij - r_{i* j}
-                const double dxi = px - el.mx[ej], dyi = py - el.my[ej];
-                const double dxs = ist[0] - el.mx[ej], dys = ist[1] - el.my[ej];
-                t_lo = (double)o.art.mbar[jl] * dt + (sqrt(dxi * dxi + dyi * dyi) - sqrt(dxs * dxs + dys * dys)) / c;
-                t_hi = t_lo + (double)o.art.Dm[jl] * dt;
-                t_lo = t_lo > 0.0 ? t_lo : 0.0;   // the ramp response is zero before t = 0
+    // the pair's Domain-F window (Eq. 28 or the placed one, reading 5) and Domain-S start
+    auto window = [&](int il, int jl, double& t_lo, double& t_hi) {
+        const long a = (long)o.art.dm[il] + o.art.mbar[jl];
+        const long kS = a + o.art.Dm[jl];
+        t_lo = (double)a * dt;
+        t_hi = (double)kS * dt;
+        if (in.amp_window == 1) {
+            // Eq. 28: the pair's own Domain F, the window of i* moved by r_ij - r_{i* j}
+            const int ei = tr.perm[o.r0 + il], ej = tr.perm[o.s0 + jl];
+            const double dxi = el.mx[ei] - el.mx[ej], dyi = el.my[ei] - el.my[ej];
+            const double dxs = ist[0] - el.mx[ej], dys = ist[1] - el.my[ej];
+            t_lo = (double)o.art.mbar[jl] * dt + (sqrt(dxi * dxi + dyi * dyi) - sqrt(dxs * dxs + dys * dys)) / c;
+            t_hi = t_lo + (double)o.art.Dm[jl] * dt;
+            t_lo = t_lo > 0.0 ? t_lo : 0.0;   // the ramp response is zero before t = 0
+        }
+    };
+    // kind 0, 1: Domain-F amplitude of the x / y stress component on the receiver normal; 2: static
+    // traction kernel; 3, 4: the remainder K - Khat^S dt of the x / y component at the Domain-S start
+    auto entry = [&](int kind, int il, int jl) -> double {
+        const int ei = tr.perm[o.r0 + il], ej = tr.perm[o.s0 + jl];
+        const double px = el.mx[ei], py = el.my[ei];
+        const Seg sg = seg_of(el, ej);
+        double t_lo, t_hi;
+        window(il, jl, t_lo, t_hi);
+        if (kind < 2) {
+            const Stress2 amp = stress_jump(px, py, sg, t_lo, t_hi, mu, c);
+            return kind == 0 ? el.nx[ei] * amp.x : el.ny[ei] * amp.y;
+        }
+        if (kind == 2) {
+            const Stress2 st = stress_static(px, py, sg, mu);
+            return el.nx[ei] * st.x + el.ny[ei] * st.y;
+        }
+        const Stress2 tl = stress_tail(px, py, sg, t_hi, t_hi + dt, mu, c);
+        return kind == 3 ? tl.x : tl.y;   // the stress component; factor() projects it on n_i
+    };
+    // large blocks: cross approximation from rows and columns computed on demand (low_rank_aca),
+    // the dense block only if it does not converge; small blocks: all five blocks formed in one pass
+    const bool aca = (long long)nr * ns >= in.aca_min;
+    std::vector<double> D[5];   // dense blocks of the five kinds (empty on the cross-approximation path)
+    size_t best[2] = {0, 0};    // transient pivots: the largest |remainder| of each stress component
+    double bval[2] = {0.0, 0.0}, bt0[2] = {0.0, 0.0};
+    auto pivot = [&](int il, int jl, double tx, double ty, double t_hi) {
+        const double v[2] = {tx, ty};
+        for (int cc = 0; cc < 2; ++cc)
+            if (fabs(v[cc]) > fabs(bval[cc]) || (il == 0 && jl == 0)) {
+                best[cc] = (size_t)il * ns + jl;
+                bval[cc] = v[cc];
+                bt0[cc] = t_hi;
             }
-            const Stress2 amp = stress_jump(px, py, s, t_lo, t_hi, mu, c);
-            const Stress2 st = stress_static(px, py, s, mu);
-            const Stress2 tl = stress_tail(px, py, s, t_hi, t_hi + dt, mu, c);
-            const size_t q = (size_t)il * ns + jl;
-            tS[q] = t_hi;
-            Ax[q] = nx * amp.x;
-            Ay[q] = ny * amp.y;
-            Ks[q] = nx * st.x + ny * st.y;
-            tx[q] = tl.x;
-            ty[q] = tl.y;
+    };
+    if (!aca) {
+        for (int k = 0; k < 5; ++k) D[k].resize((size_t)nr * ns);
+        for (int il = 0; il < nr; ++il) {
+            const int ei = tr.perm[o.r0 + il];
+            const double px = el.mx[ei], py = el.my[ei], nx = el.nx[ei], ny = el.ny[ei];
+            for (int jl = 0; jl < ns; ++jl) {
+                const Seg sg = seg_of(el, tr.perm[o.s0 + jl]);
+                double t_lo, t_hi;
+                window(il, jl, t_lo, t_hi);
+                const Stress2 amp = stress_jump(px, py, sg, t_lo, t_hi, mu, c);
+                const Stress2 st = stress_static(px, py, sg, mu);
+                const Stress2 tl = stress_tail(px, py, sg, t_hi, t_hi + dt, mu, c);
+                const size_t q = (size_t)il * ns + jl;
+                D[0][q] = nx * amp.x;
+                D[1][q] = ny * amp.y;
+                D[2][q] = nx * st.x + ny * st.y;
+                D[3][q] = nx * tl.x;
+                D[4][q] = ny * tl.y;
+                pivot(il, jl, tl.x, tl.y, t_hi);
+            }
+        }
+    } else {
+        // the largest entry by alternating row / column maxima (the partial pivoting of ACA),
+        // O(N_r + N_s) evaluations per search instead of N_r N_s
+        auto tail = [&](int il, int jl, int cc, double& t_hi) {
+            const int ei = tr.perm[o.r0 + il];
+            double t_lo;
+            window(il, jl, t_lo, t_hi);
+            const Stress2 tl = stress_tail(el.mx[ei], el.my[ei], seg_of(el, tr.perm[o.s0 + jl]), t_hi, t_hi + dt,
+                                           mu, c);
+            return cc == 0 ? tl.x : tl.y;
+        };
+        for (int cc = 0; cc < 2; ++cc) {
+            int pi = 0, pj = -1;
+            for (int round = 0; round < 8; ++round) {
+                int bj = 0;
+                double bv = -1.0;
+                for (int jl = 0; jl < ns; ++jl) {
+                    double th;
+                    const double v = fabs(tail(pi, jl, cc, th));
+                    if (v > bv) bv = v, bj = jl;
+                }
+                int bi = 0;
+                bv = -1.0;
+                for (int il = 0; il < nr; ++il) {
+                    double th;
+                    const double v = fabs(tail(il, bj, cc, th));
+                    if (v > bv) bv = v, bi = il;
+                }
+                const bool same = bi == pi && bj == pj;
+                pi = bi;
+                pj = bj;
+                if (same) break;
+            }
+            double th;
+            bval[cc] = tail(pi, pj, cc, th);
+            bt0[cc] = th;
+            best[cc] = (size_t)pi * ns + pj;
         }
     }
+    auto factor = [&](int kind, LowRank& out) {
+        if (!aca) {
+            low_rank(D[kind].data(), nr, ns, in.eps, out);
+            return;
+        }
+        auto val = [&](int il, int jl) {
+            const int ei = tr.perm[o.r0 + il];
+            const double v = entry(kind, il, jl);
+            return kind == 3 ? el.nx[ei] * v : kind == 4 ? el.ny[ei] * v : v;
+        };
+        auto row = [&](int il, double* out_r) {
+            for (int jl = 0; jl < ns; ++jl) out_r[jl] = val(il, jl);
+        };
+        auto col = [&](int jl, double* out_c) {
+            for (int il = 0; il < nr; ++il) out_c[il] = val(il, jl);
+        };
+        if (low_rank_aca(row, col, nr, ns, in.eps, out)) return;
+        std::vector<double> A((size_t)nr * ns);
+        for (int il = 0; il < nr; ++il) row(il, A.data() + (size_t)il * ns);
+        low_rank(A.data(), nr, ns, in.eps, out);
+    };
     // waveforms at i*
     int HM = 0;
     for (int jl = 0; jl < ns; ++jl) HM = std::max(HM, o.art.Dm[jl]);
@@ -158,21 +257,17 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
             }
         }
     }
-    low_rank(Ax.data(), nr, ns, in.eps, o.F[0]);
-    low_rank(Ay.data(), nr, ns, in.eps, o.F[1]);
-    low_rank(Ks.data(), nr, ns, in.eps, o.S);
+    factor(0, o.F[0]);
+    factor(1, o.F[1]);
+    factor(2, o.S);
     // transient, per component
     const double thr = in.eps_st * mu / (2.0 * c);
     for (int cc = 0; cc < 2; ++cc) {
-        const std::vector<double>& t = cc == 0 ? tx : ty;
-        size_t best = 0;
-        for (size_t q = 1; q < t.size(); ++q)
-            if (fabs(t[q]) > fabs(t[best])) best = q;
-        if (t[best] == 0.0) continue;
-        const int pi = (int)(best / ns), pj = (int)(best % ns);
+        if (bval[cc] == 0.0) continue;
+        const int pi = (int)(best[cc] / ns), pj = (int)(best[cc] % ns);
         const int ei = tr.perm[o.r0 + pi], ej = tr.perm[o.s0 + pj];
         const Seg s = seg_of(el, ej);
-        const double t0 = tS[best];   // kS dt, or the pivot pair's own Domain-S start (amp_window 1)
+        const double t0 = bt0[cc];   // kS dt, or the pivot pair's own Domain-S start (amp_window 1)
         std::vector<double> fib(in.M);
         int last = -1;
         for (int m = 0; m < in.M; ++m) {
@@ -205,13 +300,7 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
             }
         }
         if (Dtr == 0) continue;
-        std::vector<double> B((size_t)nr * ns);
-        for (int il = 0; il < nr; ++il) {
-            const int e = tr.perm[o.r0 + il];
-            const double nc = cc == 0 ? el.nx[e] : el.ny[e];
-            for (int jl = 0; jl < ns; ++jl) B[(size_t)il * ns + jl] = nc * t[(size_t)il * ns + jl];
-        }
-        low_rank(B.data(), nr, ns, in.eps, o.TR[cc]);
+        factor(3 + cc, o.TR[cc]);   // the remainder projected on the receiver normal
         o.Dtr[cc] = Dtr;
         o.trsoe[cc] = nsoe;
         o.htr[cc].resize(Dtr);

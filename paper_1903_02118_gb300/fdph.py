@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("soe_terms", ctypes.c_int32), ("art_interp", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("host_threads", ctypes.c_int32), ("eta_scheme", ctypes.c_int32), ("nrhs", ctypes.c_int32),
-                ("far_mode", ctypes.c_int32), ("amp_window", ctypes.c_int32), ("eps_q", ctypes.c_double)]
+                ("far_mode", ctypes.c_int32), ("amp_window", ctypes.c_int32), ("eps_q", ctypes.c_double),
+                ("aca_min", ctypes.c_int64)]
 
 
 class Friction(ctypes.Structure):
@@ -70,7 +71,8 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
            "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run", "fdph_quantize",
-           "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy", "fdph_low_rank"]
+           "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy", "fdph_low_rank",
+           "fdph_low_rank_aca"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -122,6 +124,10 @@ def lib():
         L.fdph_low_rank.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, c_p, c_p,
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.fdph_low_rank.restype = ctypes.c_int
+        L.fdph_low_rank_aca.argtypes = [c_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, c_p, c_p,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64)]
+        L.fdph_low_rank_aca.restype = ctypes.c_int
         L.fdph_quantize.argtypes = [c_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), c_p,
                                     ctypes.POINTER(ctypes.c_int32)]
         L.fdph_quantize.restype = ctypes.c_int
@@ -170,12 +176,12 @@ def default_params():
 
 def make_params(eta=None, lmin=None, eps_st=None, leaf_size=None, extra_steps=None, precision=None,
                 device=None, stream=None, soe_terms=None, art_interp=None, host_threads=None, eta_scheme=None,
-                nrhs=None, far_mode=None, amp_window=None, eps_q=None):
+                nrhs=None, far_mode=None, amp_window=None, eps_q=None, aca_min=None):
     p = default_params()
     for k, v in (("eta", eta), ("lmin", lmin), ("eps_st", eps_st), ("leaf_size", leaf_size),
                  ("extra_steps", extra_steps), ("precision", precision), ("device", device),
                  ("host_threads", host_threads), ("eta_scheme", eta_scheme), ("nrhs", nrhs), ("far_mode", far_mode),
-                 ("amp_window", amp_window), ("eps_q", eps_q),
+                 ("amp_window", amp_window), ("eps_q", eps_q), ("aca_min", aca_min),
                  ("soe_terms", soe_terms), ("art_interp", None if art_interp is None else int(bool(art_interp)))):
         if v is not None:
             setattr(p, k, v)
@@ -406,6 +412,24 @@ def low_rank(A, eps):
                                ctypes.c_void_p(G.ctypes.data), ctypes.byref(r), ctypes.byref(ex)))
     r = r.value
     return F[:m * r].reshape(m, r), G[:n * r].reshape(n, r), bool(ex.value)
+
+
+def low_rank_aca(A, eps):
+    """The plan's cross approximation of one large block (fdph_low_rank_aca): returns
+    (F, G, evaluated) with A ~ F G^T and the number of entries read, or (None, None, evaluated)
+    when the cross did not converge."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    k = min(m, n, 96)
+    F = np.zeros(m * k)
+    G = np.zeros(n * k)
+    r, ok, ev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().fdph_low_rank_aca(ctypes.c_void_p(A.ctypes.data), m, n, float(eps), ctypes.c_void_p(F.ctypes.data),
+                                   ctypes.c_void_p(G.ctypes.data), ctypes.byref(r), ctypes.byref(ok), ctypes.byref(ev)))
+    if not ok.value:
+        return None, None, ev.value
+    r = r.value
+    return F[:m * r].reshape(m, r), G[:n * r].reshape(n, r), ev.value
 
 
 def tree_export(xy, dt, mu=1.0, cs=1.0, **params):

@@ -189,3 +189,34 @@ def test_low_rank_fallback_zero_and_nan(L):
     A[2, 3] = np.nan
     with pytest.raises(fdph.FdphError):
         fdph.low_rank(A, 1e-4)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+@pytest.mark.parametrize("r0,nr,s0,ns", [(0, 256, 700, 300), (1100, 400, 60, 320)])
+def test_cross_approximation_of_a_large_block(L, eps, r0, nr, s0, ns):
+    """The cross approximation the plan takes for large admissible blocks (Sec. 4): on static-kernel
+    blocks of the curved fault (the oracle's closed form) its product is within eps |A|_F of the
+    block, with at most one rank more than the truncated SVD needs, from a small share of the
+    block's entries."""
+    el = kn.element_table(inputs.curved_fault(1600, inputs.seed_for(1, 0)))
+    A = kn.static_kernel(el, 1.0, receivers=np.arange(r0, r0 + nr), sources=np.arange(s0, s0 + ns))
+    F, G, evaluated = fdph.low_rank_aca(A, eps)
+    assert F is not None
+    r, _ = _svd_truncation(A, eps)
+    assert F.shape[1] <= r + 1
+    assert np.linalg.norm(F @ G.T - A) < eps * np.linalg.norm(A)
+    assert evaluated < 0.5 * nr * ns
+
+
+def test_cross_approximation_exact_rank_and_refusal(L):
+    """A block of exact rank 5 is recovered to rounding with rank 5; a full-rank random block makes
+    the cross approximation give up (the plan then factorises the dense block)."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((300, 5)) @ rng.standard_normal((5, 240))
+    F, G, _ = fdph.low_rank_aca(A, 1e-8)
+    assert F.shape[1] == 5
+    assert np.linalg.norm(F @ G.T - A) < 1e-10 * np.linalg.norm(A)
+    F, G, evaluated = fdph.low_rank_aca(rng.standard_normal((200, 150)), 1e-4)
+    assert F is None and G is None and evaluated > 0
+    with pytest.raises(fdph.FdphError):
+        fdph.low_rank_aca(np.zeros((4, 4)), 0.0)

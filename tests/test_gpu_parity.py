@@ -544,3 +544,24 @@ def test_quantized_transient_fp64_equals_compressed_operator(geom, N, M, soe):
     assert _rel(T, T0) < TOL64
     plan.reset()                                  # the running sums restart from zero
     assert _rel(_run(plan, D), T0) < TOL64
+
+
+@pytest.mark.parametrize("geom,N,leaf,amp,soe", [("curved", 256, 16, 1, 0), ("kinked", 233, 13, 0, 16)])
+def test_cross_approximation_plan_within_eps_of_compressed_operator(geom, N, leaf, amp, soe):
+    """aca_min > 0: the admissible blocks from ACA+ (Sec. 4) instead of the truncated SVD, here every
+    block of at least 12 x 12 entries.  Both sides meet |K_b - F G^T|_F < eps |K_b|_F per block, so
+    their operators differ by at most 2 eps per block; the transient's spatial pivot may land on
+    another pair of similar size, which moves the transient term within its own error (~eps_st).
+    The outputs stay within 10 eps of the oracle's compressed operator, while the dense plan meets
+    the FP64 bound, and differ from it (the cross approximation really ran)."""
+    _need_gpu()
+    M, eps = 320, 1e-5
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, _ = _oracle_fdph(xy, M, eps, leaf, D, soe_terms=soe, amp_window=amp)
+    kw = dict(eta=0.5, eps_st=1e-6, leaf_size=leaf, amp_window=amp, soe_terms=soe)
+    Td = _run(fdph.Plan(xy, 0.5, M, eps, **kw), D)
+    T = _run(fdph.Plan(xy, 0.5, M, eps, aca_min=144, **kw), D)
+    assert _rel(Td, T0) < TOL64
+    assert _rel(T, T0) < 10 * eps
+    assert _rel(T, Td) > 1e-12

@@ -38,6 +38,12 @@ CONFIGS = {
     # dynamic rupture on a planar fault (linear slip weakening), the configured size
     "rupture": dict(name="FDP=H dynamic rupture, 2-D antiplane planar fault, linear slip weakening", N=16384,
                     M=8192, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="straight", amp_window=1),
+    # one large fault planned for M = 65536 steps with 8 slip-rate histories stepped together: the
+    # near-field window in FP16 on the tensor cores, the admissible blocks by cross approximation;
+    # the first `march` steps (the pulse and its waves) are stepped and compared with the FP64 path
+    "large": dict(name="FDP=H large mixed-precision single fault, 2-D antiplane curved fault, 8 right-hand sides",
+                  N=131072, M=65536, eps=1e-4, eta=0.5, leaf=32, eps_st=1e-4, geometry="curved", amp_window=1,
+                  precision="fp16", nrhs=8, aca_min=4096, seed_k=4, march=1024, soe=16),
 }
 DT = 0.5
 DTYPE = {0: "f64", 1: "f32-storage/f64-accumulate", 2: "f16-near-window/f32-storage/f64-accumulate"}
@@ -507,6 +513,8 @@ def main():
     ap.add_argument("--alone-sample", type=int, default=None,
                     help="serving workload: requests also served one at a time in FP64 (default all)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default near-field work-item length")
+    ap.add_argument("--march", type=int, default=None,
+                    help="large workload: steps stepped (the error's samples; >= 1024 keeps the pulse's law)")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)
@@ -522,10 +530,17 @@ def main():
             cfg[k] = v
     if args.workload == "rupture":
         cfg["soe"] = args.soe
+    if args.workload == "large":
+        if args.march is not None:
+            cfg["march"] = args.march
+        if args.nrhs != 1:
+            cfg["nrhs"] = args.nrhs
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.workload == "rupture":
         return run_rupture(args, cfg)
+    if args.workload == "large":
+        return run_large(args, cfg)
     return run_fdph(args, cfg)
 
 
@@ -704,6 +719,115 @@ def run_fdph(args, cfg):
                 setting={k: pl[k] for k in ("N", "M", "eps", "eta", "leaf", "eps_st", "soe", "amp_window", "precision")},
                 **sub_run(fdph, torch, pl, pl_prec, local, stream, K, W, rows, T_pl, hbm_peak)))
         pool.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_large(args, cfg):
+    """The large single fault: plan for M steps with nrhs slip-rate histories, step the first `march`
+    of them (the pulse and its waves), time K steady-state steps, and compare every stepped step at
+    64 sampled receivers and all right-hand sides with the FP64 GPU path of the same plan
+    parameters (planned and stepped after the first plan is released)."""
+    import ctypes
+    import torch
+    from paper_1903_02118_gb300 import replicas
+    world, rank, local = replicas.init()
+    torch.cuda.set_device(local)
+    from paper_1903_02118_gb300 import build, fdph, inputs
+    build.build()
+    N, M, R = cfg["N"], cfg["M"], cfg["nrhs"]
+    S = min(M, cfg["march"])
+    K, W = args.steps, args.warmup
+    k = cfg["seed_k"]
+    xy = inputs.curved_fault(N, inputs.seed_for(k, inputs.GEOMETRY))
+    D = np.empty((S, R, N))
+    for r in range(R):
+        D[:, r] = inputs.gaussian_pulse(N, S, DT, inputs.seed_for(k + 10 * rank + 100 * r, inputs.SLIP))
+    rows = ((np.arange(64) + 0.5) * N / 64).astype(int)
+    rows_d = torch.from_numpy(rows).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = {"fp64": fdph.FP64, "fp32": fdph.FP32, "fp16": fdph.FP16}[cfg["precision"]]
+    kw = dict(eta=cfg["eta"], eps_st=cfg["eps_st"], leaf_size=cfg["leaf"], device=local, stream=stream.cuda_stream,
+              soe_terms=cfg["soe"], amp_window=cfg["amp_window"], nrhs=R, aca_min=cfg["aca_min"])
+    t0 = time.perf_counter()
+    plan = fdph.Plan(xy, DT, M, cfg["eps"], precision=prec, **kw)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+    n0 = min(st["max_window"], S - W - K)
+    if n0 < 0:
+        raise SystemExit("steps + warmup exceed the stepped march of %d steps" % S)
+    Dd = torch.from_numpy(D).cuda()
+    Td = torch.empty_like(Dd)
+    t1 = time.perf_counter()
+    plan.run(S, Dd, Td)
+    plan.synchronize()
+    march_s = time.perf_counter() - t1
+    T_lo = Td.index_select(2, rows_d).cpu().numpy()
+    plan.reset()
+    plan.run(n0 + W, Dd, Td)
+    plan.synchronize()
+    replicas.barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_steps(plan, stream, Dd, Td, n0 + W, K)
+    replicas.barrier(world)
+    ms = replicas.max_over_ranks(ms, world)
+    value = world * N * R * K / (ms * 1e-3)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    kt, roofline = near_roofline(plan, st, Dd, Td, n0 + W, K, hbm_peak)
+    roofline["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (copy)" if peaks else "fallback 6.8 TB/s"
+    roofline["traffic"] = None
+    roofline["traffic_note"] = "no ncu capture of this workload"
+    # end to end through the C ABI with host buffers
+    plan.reset()
+    plan.run(n0 + W, Dd, Td)
+    plan.synchronize()
+    hD = torch.from_numpy(np.ascontiguousarray(D[n0 + W:n0 + W + K])).pin_memory()
+    hT = torch.empty(tuple(hD.shape), dtype=torch.float64).pin_memory()
+    te0 = time.perf_counter()
+    plan.run_host(hD, hT)
+    te = replicas.max_over_ranks(time.perf_counter() - te0, world)
+    e2e = {"value": world * N * R * K / te, "unit": "element-steps/s", "h2d_bytes_per_step": N * R * 8,
+           "d2h_bytes_per_step": N * R * 8, "api": "fdph_run_host (per-step copies, pipelined)"}
+    plan.close()
+    plan = None
+    # the FP64 GPU path of the same plan parameters
+    t0 = time.perf_counter()
+    plan64 = fdph.Plan(xy, DT, M, cfg["eps"], precision=fdph.FP64, **kw)
+    plan64_s = time.perf_counter() - t0
+    st64 = plan64.stats()
+    t1 = time.perf_counter()
+    plan64.run(S, Dd, Td)
+    plan64.synchronize()
+    march64_s = time.perf_counter() - t1
+    T_hi = Td.index_select(2, rows_d).cpu().numpy()
+    plan64.close()
+    err = float(np.linalg.norm(T_lo - T_hi) / np.linalg.norm(T_hi))
+    err_rhs = [float(np.linalg.norm(T_lo[:, r] - T_hi[:, r]) / np.linalg.norm(T_hi[:, r])) for r in range(R)]
+    line = {"metric": "element-steps/s", "value": value, "unit": "element-steps/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
+                       "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg["soe"], "cfl": 0.5, "nrhs": R,
+                       "amp_window": cfg["amp_window"], "aca_min": cfg["aca_min"], "stepped_steps": S,
+                       "first_timed_step": n0 + W,
+                       "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "rel_err_vs_fp64_gpu": err, "rel_err_vs_fp64_gpu_per_rhs": err_rhs,
+            "rel_err_note": ("relative L2 over the %d stepped steps x %d right-hand sides at %d evenly spaced "
+                             "receivers against the FP64 storage path of the same plan parameters" % (S, R, rows.size)),
+            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in kt.values()) // 1),
+            "gpu_launches_note": "library kernels per timed run of %d steps" % K,
+            "roofline": roofline, "clocks": clk.summary(),
+            "plan": {"seconds": plan_s, "fp64_seconds": plan64_s, "march_seconds": march_s,
+                     "fp64_march_seconds": march64_s, "bytes_per_step": st["bytes_per_step"],
+                     "near_bytes_per_step": st["near_bytes_per_step"], "n_admissible": st["n_admissible"],
+                     "n_near": st["n_near"], "mean_rank": st["mean_rank"], "mean_rank_f": st["mean_rank_f"],
+                     "mean_rank_s": st["mean_rank_s"], "mean_rank_tr": st["mean_rank_tr"],
+                     "max_rank": st["max_rank"], "n_exact": st["n_exact"], "max_window": st["max_window"],
+                     "arena_bytes": st["arena_bytes"], "fp64_arena_bytes": st64["arena_bytes"]}}
     if rank == 0:
         print(json.dumps(line))
 

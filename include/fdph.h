@@ -393,6 +393,16 @@ int fdph_low_rank_aca(const double* A, int32_t m, int32_t n, double eps, double*
  * count.  Errors: FDPH_E_ARG (null pointer, n < 1, eps_q <= 0), FDPH_E_NAN (non-finite value). */
 int fdph_quantize(const double* K, int32_t n, double eps_q, int32_t* b, double* khat, int32_t* q);
 
+/* Host-only evaluation of the discrete kernel's Domain-S remainder (App. B.3, App. H) for one
+ * receiver point p = (x, y) and source element seg = (x0, y0, tx, ty, length) (first end point, unit
+ * tangent, length): out[0], out[1] = the global stress components of K(t1, t1 + dt) - Kstat dt,
+ * the ramp-response jump over [t1, t1 + dt] less the static stress per unit slip times dt;
+ * out[2] = the bound the plan's threshold scans use (m_S of App. H for the near pairs, the
+ * transient's taps), an upper bound on |out[0]|, |out[1]| and on any unit projection of them once
+ * both end points' S fronts have passed (+inf before), falling with t1.  No device needed.
+ * Errors: FDPH_E_ARG (null pointer, dt, mu, cs or length <= 0, t1 < 0). */
+int fdph_kernel_tail(const double* p, const double* seg, double t1, double dt, double mu, double cs, double* out);
+
 /* Allocation-free plain step.  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory (code running inside another runtime's memory pool or
  * allocator budget, or where a cudaMalloc would synchronise the device at a bad moment).

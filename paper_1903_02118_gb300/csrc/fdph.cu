@@ -1591,7 +1591,9 @@ __device__ __forceinline__ Seg dev_seg(const GeoDev& g, int p) {
     return s;
 }
 
-// m_S(i, j) = 1 + last k < M with |K_ijk - Kstat_ij dt| >= thr (App. H), 0 if none; M if thr == 0
+// m_S(i, j) = 1 + last k < M with |K_ijk - Kstat_ij dt| >= thr (App. H), 0 if none; M if thr == 0.
+// The scan covers only the steps before the tail bound (stress_tail_bound) falls below thr / 2, so it
+// costs the pair's wave passage plus its decay to thr rather than M steps.
 __global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const int* ps, const int* pns,
                                const long long* pair0, long long npairs, int nleaf, int M, double dt,
                                double mu, double c, double thr, int* ms) {
@@ -1610,8 +1612,18 @@ __global__ void near_ms_kernel(GeoDev g, const int* pr, const int* pnr, const in
         return;
     }
     const Seg s = dev_seg(g, pj);
+    // steps from the first k whose tail bound is below thr / 2 on cannot reach thr (the bound falls
+    // with k; the factor 2 covers rounding): the backward scan starts below that k
+    int k_lo = 0, k_hi = M;
+    while (k_lo < k_hi) {
+        const int mid = (k_lo + k_hi) >> 1;
+        if (stress_tail_bound(g.px[pi], g.py[pi], s, (double)mid * dt, dt, mu, c) < 0.5 * thr)
+            k_hi = mid;
+        else
+            k_lo = mid + 1;
+    }
     int res = 0;
-    for (int k = M - 1; k >= 0; --k) {
+    for (int k = k_lo - 1; k >= 0; --k) {
         const Stress2 v = stress_tail(g.px[pi], g.py[pi], s, (double)k * dt, (double)(k + 1) * dt, mu, c);
         const double tval = g.nx[pi] * v.x + g.ny[pi] * v.y;
         if (fabs(tval) >= thr) {
@@ -3194,6 +3206,19 @@ int fdph_low_rank_aca(const double* A, int32_t m, int32_t n, double eps, double*
         std::copy(lr.F.begin(), lr.F.end(), F);
         std::copy(lr.G.begin(), lr.G.end(), G);
     }
+    return FDPH_OK;
+}
+
+int fdph_kernel_tail(const double* p, const double* seg, double t1, double dt, double mu, double cs, double* out) {
+    if (!p || !seg || !out || !(dt > 0.0) || !(t1 >= 0.0) || !(mu > 0.0) || !(cs > 0.0) || !(seg[4] > 0.0)) {
+        set_error("fdph_kernel_tail: null pointer, dt, mu, cs or the length <= 0, or t1 < 0");
+        return FDPH_E_ARG;
+    }
+    const Seg s{seg[0], seg[1], seg[2], seg[3], seg[4]};
+    const Stress2 v = stress_tail(p[0], p[1], s, t1, t1 + dt, mu, cs);
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = stress_tail_bound(p[0], p[1], s, t1, dt, mu, cs);
     return FDPH_OK;
 }
 

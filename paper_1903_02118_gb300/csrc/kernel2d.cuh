@@ -119,6 +119,23 @@ FDPH_HD Stress2 stress_tail(double px, double py, const Seg& s, double t1, doubl
     return to_global(sX, sY, s);
 }
 
+// Upper bound on |s_X| + |s_Y| of stress_tail(t1, t1 + dt) -- hence on either global component and
+// on any unit projection of it -- once both end points' fronts have passed (c t1 > sqrt(q_e)); +inf
+// before.  From the closed form: |d Theta / dt| = c^2 t / (c^2 t^2 - Y^2) sum_e |e| / W_e(t), and
+// 0 <= dW_minus_static(t1, t1 + dt) <= dt q / (t1 W(t1)); every factor falls with t, so the bound
+// falls with t1 (a threshold scan can stop where it drops below the threshold).
+FDPH_HD double stress_tail_bound(double px, double py, const Seg& s, double t1, double dt, double mu, double c) {
+    const LocalPt p = seg_local(px, py, s);
+    const double ct = c * t1;
+    const double qm = p.q0 > p.q1 ? p.q0 : p.q1;
+    if (!(t1 > 0.0) || !(ct * ct > qm)) return INFINITY;
+    const double w0 = sqrt(ct * ct - p.q0), w1 = sqrt(ct * ct - p.q1);
+    const double dth = dt * c * ct / (ct * ct - p.Y * p.Y) * (fabs(p.e0) / w0 + fabs(p.e1) / w1);
+    const double a0 = dt / (t1 * w0), a1 = dt / (t1 * w1);
+    const double k = mu / (2.0 * M_PI * c);
+    return k * (dth + fabs(p.e1) * a1 + fabs(p.e0) * a0 + fabs(p.Y) * (a0 + a1));
+}
+
 // Static stress vector per unit slip (screw-dislocation pair at the end points).
 FDPH_HD Stress2 stress_static(double px, double py, const Seg& s, double mu) {
     const LocalPt p = seg_local(px, py, s);

@@ -268,9 +268,13 @@ void admissible(const Elements& el, const Tree& tr, const Leaf& lf, const PlanIn
         const int ei = tr.perm[o.r0 + pi], ej = tr.perm[o.s0 + pj];
         const Seg s = seg_of(el, ej);
         const double t0 = bt0[cc];   // kS dt, or the pivot pair's own Domain-S start (amp_window 1)
-        std::vector<double> fib(in.M);
+        std::vector<double> fib(in.M, 0.0);
         int last = -1;
         for (int m = 0; m < in.M; ++m) {
+            // without the tail fit only the taps above thr matter: none follows once the falling
+            // tail bound is below thr / 2 (the factor 2 covers rounding)
+            if (in.soe == 0 && stress_tail_bound(el.mx[ei], el.my[ei], s, t0 + (double)m * dt, dt, mu, c) < 0.5 * thr)
+                break;
             const Stress2 v = stress_tail(el.mx[ei], el.my[ei], s, t0 + (double)m * dt, t0 + (double)(m + 1) * dt,
                                           mu, c);
             fib[m] = cc == 0 ? v.x : v.y;

@@ -72,7 +72,7 @@ EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_st
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
            "fdph_predict", "fdph_commit", "fdph_self", "fdph_batch_create", "fdph_batch_run", "fdph_quantize",
            "fdph_batch_rupture_run", "fdph_batch_synchronize", "fdph_batch_destroy", "fdph_low_rank",
-           "fdph_low_rank_aca"]
+           "fdph_low_rank_aca", "fdph_kernel_tail"]
 KERNEL_NAMES = ["push", "fir", "scatter", "trconv", "near", "gather"]
 
 
@@ -128,6 +128,9 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64)]
         L.fdph_low_rank_aca.restype = ctypes.c_int
+        L.fdph_kernel_tail.argtypes = [c_p, c_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       c_p]
+        L.fdph_kernel_tail.restype = ctypes.c_int
         L.fdph_quantize.argtypes = [c_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), c_p,
                                     ctypes.POINTER(ctypes.c_int32)]
         L.fdph_quantize.restype = ctypes.c_int
@@ -412,6 +415,17 @@ def low_rank(A, eps):
                                ctypes.c_void_p(G.ctypes.data), ctypes.byref(r), ctypes.byref(ex)))
     r = r.value
     return F[:m * r].reshape(m, r), G[:n * r].reshape(n, r), bool(ex.value)
+
+
+def kernel_tail(p, seg, t1, dt, mu=1.0, cs=1.0):
+    """Domain-S remainder of the discrete kernel and its scan bound (fdph_kernel_tail):
+    returns (tail_x, tail_y, bound)."""
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    sg = np.ascontiguousarray(seg, dtype=np.float64)
+    out = np.zeros(3)
+    _check(lib().fdph_kernel_tail(ctypes.c_void_p(pp.ctypes.data), ctypes.c_void_p(sg.ctypes.data), float(t1),
+                                  float(dt), float(mu), float(cs), ctypes.c_void_p(out.ctypes.data)))
+    return out[0], out[1], out[2]
 
 
 def low_rank_aca(A, eps):

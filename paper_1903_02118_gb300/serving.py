@@ -26,9 +26,10 @@ from . import fdph, inputs
 
 class Request:
     def __init__(self, rid, arrival, N, cfl, seed, M=None, eta=0.5, eps=1e-4, eps_st=1e-4, soe_terms=16,
-                 leaf=32, precision=fdph.FP32, geometry="curved", amp_window=1):
+                 leaf=32, precision=fdph.FP32, geometry="curved", amp_window=1, aca_min=4096):
         self.rid, self.arrival, self.N, self.cfl, self.seed = rid, arrival, N, cfl, seed
         self.amp_window = amp_window   # Domain-F amplitude over each pair's own window (Eq. 28)
+        self.aca_min = aca_min         # admissible blocks of >= aca_min entries by cross approximation
         self.M = M if M is not None else int(round(N / cfl))
         self.eta, self.eps, self.eps_st, self.soe_terms = eta, eps, eps_st, soe_terms
         self.leaf, self.precision, self.geometry = leaf, precision, geometry
@@ -105,7 +106,8 @@ class Server:
         prec = self.precision if self.precision is not None else req.precision
         plan = fdph.Plan(xy, dt, req.M, req.eps, eta=req.eta, eps_st=req.eps_st, leaf_size=req.leaf,
                          precision=prec, soe_terms=req.soe_terms, device=self.device,
-                         stream=stream.cuda_stream, host_threads=self.host_threads, amp_window=req.amp_window)
+                         stream=stream.cuda_stream, host_threads=self.host_threads, amp_window=req.amp_window,
+                         aca_min=req.aca_min)
         st = plan.stats()
         foot = st["arena_bytes"] + st["state_bytes"] + 3 * req.N * 8 * (self.chunk + 2)
         with torch.cuda.stream(stream):

@@ -565,3 +565,19 @@ def test_cross_approximation_plan_within_eps_of_compressed_operator(geom, N, lea
     assert _rel(Td, T0) < TOL64
     assert _rel(T, T0) < 10 * eps
     assert _rel(T, Td) > 1e-12
+
+
+@pytest.mark.parametrize("geom,N,leaf", [("curved", 200, 16), ("kinked", 190, 13)])
+def test_bounded_threshold_scans_equal_the_full_scans(geom, N, leaf):
+    """eps_st = 1e-4 over M = 900 steps: the near pairs' m_S (App. H) and the transient's taps
+    (App. B.3) end well inside M, where the plan's scans stop at the falling tail bound; the
+    operator still equals the oracle's, whose scans run over all M steps."""
+    _need_gpu()
+    M, eps = 900, 1e-5
+    xy = _geom(geom, N)
+    D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
+    T0, _ = _oracle_fdph(xy, M, eps, leaf, D, eps_st=1e-4)
+    plan = fdph.Plan(xy, 0.5, M, eps, eta=0.5, eps_st=1e-4, leaf_size=leaf)
+    T = _run(plan, D)
+    assert plan.stats()["max_window"] < M // 2
+    assert _rel(T, T0) < TOL64

@@ -8,6 +8,8 @@ Seeds: a workload with index k uses ``1903021180 + k``; sub-streams add +0
 (geometry), +1000 (slip history), +2000 (friction heterogeneity) and +3000
 (request arrivals).
 """
+import math
+
 import numpy as np
 
 SEED_BASE = 1903021180
@@ -50,9 +52,6 @@ def curved_fault(n, seed, max_slope=0.2, kappa_max=0.1, modes=8, dx=1.0):
     k = np.arange(1, modes + 1)
     w = 2.0 * np.pi * k / L
 
-    def y(x, s):
-        return s * np.sum(a[None, :] * np.sin(w[None, :] * x[:, None] + ph[None, :]), axis=1)
-
     xs = np.linspace(0.0, 1.2 * L, 20001)
     y1 = np.sum(a * w * np.cos(w * xs[:, None] + ph), axis=1)
     y2 = np.sum(-a * w * w * np.sin(w * xs[:, None] + ph), axis=1)
@@ -60,18 +59,29 @@ def curved_fault(n, seed, max_slope=0.2, kappa_max=0.1, modes=8, dx=1.0):
     curv = np.abs(s * y2) / (1.0 + (s * y1) ** 2) ** 1.5
     if curv.max() > kappa_max / dx:
         s *= (kappa_max / dx) / curv.max()
-    pts = [np.array([0.0, y(np.array([0.0]), s)[0]])]
+    # chord marching: each chord end solves (x - x0)^2 + (y(x) - y0)^2 = dx^2, by Newton's method in
+    # scalar arithmetic from the tangent estimate (the slope is at most max_slope: a simple root)
+    a_l, w_l, ph_l = [float(v) for v in a], [float(v) for v in w], [float(v) for v in ph]
+
+    def ys(x):
+        v = d = 0.0
+        for ak, wk, pk in zip(a_l, w_l, ph_l):
+            v += ak * math.sin(wk * x + pk)
+            d += ak * wk * math.cos(wk * x + pk)
+        return s * v, s * d
+
+    x0, y0 = 0.0, ys(0.0)[0]
+    pts = [(x0, y0)]
     for _ in range(n):
-        x0 = pts[-1][0]
-        lo, hi = x0, x0 + dx
-        for _ in range(80):  # bisection for the chord end at distance dx
-            mid = 0.5 * (lo + hi)
-            p = np.array([mid, y(np.array([mid]), s)[0]])
-            if np.hypot(*(p - pts[-1])) < dx:
-                lo = mid
-            else:
-                hi = mid
-        pts.append(np.array([hi, y(np.array([hi]), s)[0]]))
+        x = x0 + dx / math.sqrt(1.0 + ys(x0)[1] ** 2)
+        for _ in range(50):
+            yv, dv = ys(x)
+            step = ((x - x0) ** 2 + (yv - y0) ** 2 - dx * dx) / (2.0 * (x - x0) + 2.0 * (yv - y0) * dv)
+            x -= step
+            if abs(step) <= 1e-15 * (1.0 + abs(x)):
+                break
+        x0, y0 = x, ys(x)[0]
+        pts.append((x0, y0))
     pts = np.array(pts)
     return np.concatenate([pts[:-1], pts[1:]], axis=1)
 

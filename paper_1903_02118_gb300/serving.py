@@ -41,7 +41,13 @@ class Request:
 
     def inputs(self):
         """Fault trace and prestress for linear slip weakening (0.45 + 5 % Gaussian heterogeneity,
-        an overstressed nucleation patch of 64 elements at 0.61; mu_s 0.6, mu_d 0.3, Dc = 6.4)."""
+        an overstressed nucleation patch of 64 elements at 0.61; mu_s 0.6, mu_d 0.3, Dc = 6.4);
+        drawn once per request."""
+        if getattr(self, "_inputs", None) is None:
+            self._inputs = self._draw_inputs()
+        return self._inputs
+
+    def _draw_inputs(self):
         if self.geometry == "curved":
             xy = inputs.curved_fault(self.N, inputs.seed_for(self.seed, inputs.GEOMETRY))
         else:
@@ -92,10 +98,13 @@ class Server:
 
     @staticmethod
     def estimate(req):
-        """Device footprint of the request's plan before it exists (footprint_model), bytes."""
-        xy, _ = req.inputs()
-        return footprint_model(xy, req.cfl, req.M, eta=req.eta, leaf=req.leaf, precision=req.precision,
-                               soe_terms=req.soe_terms)
+        """Device footprint of the request's plan before it exists (footprint_model), bytes; computed
+        once per request (admission asks again while the request waits for room)."""
+        if getattr(req, "_estimate", None) is None:
+            xy, _ = req.inputs()
+            req._estimate = footprint_model(xy, req.cfl, req.M, eta=req.eta, leaf=req.leaf,
+                                            precision=req.precision, soe_terms=req.soe_terms, eps_st=req.eps_st)
+        return req._estimate
 
     def _admit(self, req):
         torch = self.torch
@@ -228,12 +237,14 @@ class Server:
                 "plan_s_max": float(plan_s.max()), "admission_wait_s_p50": float(np.percentile(wait_s, 50))}
 
 
-def footprint_model(xy, dt, M, eta=0.5, leaf=32, precision=fdph.FP32, soe_terms=16, rank=8, chunk=64, cs=1.0):
+def footprint_model(xy, dt, M, eta=0.5, leaf=32, precision=fdph.FP32, soe_terms=16, rank=8, chunk=64, cs=1.0,
+                    eps_st=1e-4):
     """Device bytes of a plan, from its block tree alone (fdph_tree_export, host only, milliseconds):
     the near-field windows dominate -- per inadmissible leaf W slices of ceil(ns / v) v nr stored
     coefficients (v = 16 bytes / element), W = the leaf's longest wave passage (farthest end point
     over c dt) + n_c with exponential tails (the whole march M when too little is left to fit a
-    tail), + the static and tail slices; the admissible blocks add their factors and rings
+    tail), or + the steps the remainder takes to decay to eps_st without them (the paper's cut),
+    + the static and tail slices; the admissible blocks add their factors and rings
     (5 low-rank operators per leaf at `rank`, ring slots up to the largest delay); the state adds the
     slip-rate rings, and the serving loop its chunk buffers."""
     tx = fdph.tree_export(xy, dt, eta=eta, leaf_size=leaf, extra_steps=-1)
@@ -252,9 +263,14 @@ def footprint_model(xy, dt, M, eta=0.5, leaf=32, precision=fdph.FP32, soe_terms=
         if lf["kind"] == 0:
             d = np.maximum(np.hypot(mx[I][:, None] - ax[J][None, :], my[I][:, None] - ay[J][None, :]),
                            np.hypot(mx[I][:, None] - bx[J][None, :], my[I][:, None] - by[J][None, :]))
-            W = int(np.ceil(d.max() / (cs * dt))) + nc
-            if not soe_terms or M - W < max(512, 2 * W):
-                W = M
+            if soe_terms:
+                W = int(np.ceil(d.max() / (cs * dt))) + nc
+                if M - W < max(512, 2 * W):
+                    W = M
+            else:
+                # the paper's cut: the exact kernel until its remainder falls below eps_st mu / (2 cs),
+                # a remainder of about (dx / (pi cs dt)) / m^2 in those units m steps after the front
+                W = min(M, int(np.ceil(d.max() / (cs * dt) + np.sqrt(1.0 / (np.pi * cs * dt * eps_st)))) + 2)
             wmax = max(wmax, W)
             v = 16 // sw
             near += W * (-(-lf["ns"] // v) * v) * lf["nr"] * sw + (1 + soe_terms) * (-(-lf["ns"] // 4) * 4) * lf["nr"] * sa

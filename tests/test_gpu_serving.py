@@ -27,17 +27,18 @@ def test_mix_equals_alone_and_reports_latency():
 def test_footprint_model_bounds_the_real_plan():
     """The admission estimate (footprint_model: block tree only, no device) against the device
     bytes of the plan once built (operator + state), on curved faults of several sizes: within a
-    factor of two either way, so that admission neither starves nor overfills the HBM budget."""
+    factor of two either way, so that admission neither starves nor overfills the HBM budget; with
+    exponential tails and with the paper's cut (soe_terms 0)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1903_02118_gb300 import build, fdph, inputs, serving
     build.build()
-    for N, cfl in ((512, 0.5), (1500, 0.25), (3000, 0.5)):
+    for N, cfl, soe in ((512, 0.5, 16), (1500, 0.25, 16), (3000, 0.5, 16), (1500, 0.25, 0), (3000, 0.5, 0)):
         xy = inputs.curved_fault(N, inputs.seed_for(3, inputs.GEOMETRY))
         M = int(round(N / cfl))
-        est = serving.footprint_model(xy, cfl, M)
-        plan = fdph.Plan(xy, cfl, M, 1e-4, eta=0.5, eps_st=1e-4, leaf_size=32, soe_terms=16, precision=fdph.FP32)
+        est = serving.footprint_model(xy, cfl, M, soe_terms=soe)
+        plan = fdph.Plan(xy, cfl, M, 1e-4, eta=0.5, eps_st=1e-4, leaf_size=32, soe_terms=soe, precision=fdph.FP32)
         st = plan.stats()
         plan.close()
         real = st["arena_bytes"] + st["state_bytes"]
-        assert 0.5 * real <= est <= 2.0 * real, (N, est, real)
+        assert 0.5 * real <= est <= 2.0 * real, (N, soe, est, real)

@@ -721,35 +721,24 @@ __device__ __forceinline__ NearView near_view(const StepArgs<T>& a) {
 constexpr int kRowsPerWarp = kChunk / kNearConsumers;
 static_assert(kRowsPerWarp * kNearConsumers == kChunk, "vector rows are dealt evenly over the consumer warps");
 
-// tensor-core window rows in the vector buffer, as the TMA box lands: [slot][right-hand side][kTcBox]
-// (hi, lo) words, slots from the item's oldest
+// tensor-core window rows travel with the window slices: each pipeline stage carries kTcPer slices
+// (8 x 32 x 32 FP16 = one 16 KB stage) followed by their rows as one TMA box lands,
+// [slot][right-hand side][kTcBox] (hi, lo) words, slots from the stage's oldest, and then the rows'
+// scales [slot][max(NR, 4)]
 constexpr int kTcBox = 36;
+constexpr int kTcPer = 8;
+// vector rows of the aux items of a tensor-core plan (static tile and tail slices, NR per slice)
+constexpr int kTcVecRows = 32;
 
 template <class R, int NR, int VR, bool TC>
 __device__ __forceinline__ void near_issue(const NearView& a, const NearTask& tk, int warp, int lane,
-                                           double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb,
-                                           unsigned long long* vbar) {
+                                           double (&r)[kRowsPerWarp], double (&dW)[NR], unsigned char* vb) {
     const int n = a.n;
     const int nsl = near_slices<double>(tk, n);
     const bool on = lane < tk.ns;
     const size_t col = (size_t)tk.s0 + (on ? lane : 0);   // lanes past ns zero-fill from a valid address
     if constexpr (TC) {
-        if (!tk.kind) {
-            // the window rows of every right-hand side with one TMA tensor copy: a box of 36 sources
-            // from s0 rounded down to a multiple of 4 (the 16-byte rule of the innermost coordinate;
-            // the consumers index from the remainder) x nrhs x VR / NR slots from the item's oldest
-            // (the mirrored ring keeps them contiguous; past the ring the box reads zeros)
-            if (warp == 0 && lane == 0 && nsl > 0) {
-                const int z0 = wrap(n - tk.k0 - (nsl - 1), a.WD);
-                constexpr int SR = NR > 4 ? NR : 4;
-                fence_proxy_async();
-                mbar_expect_tx(vbar, (unsigned)(VR * kTcBox * 4 + (VR / NR) * SR * 4));
-                tma_load_3d(vb, a.tmap16, tk.s0 & ~3, 0, z0, vbar);
-                // the rows' scales: a box of SR x VR / NR slots right after the rows
-                tma_load_2d(vb + VR * kTcBox * 4, (const unsigned char*)a.tmap16 + sizeof(CUtensorMap), 0, z0, vbar);
-            }
-            return;
-        }
+        if (!tk.kind) return;   // the window rows come with the slices' pipeline stages (producer)
     }
     if (!tk.kind) {
         const int b0 = wrap(n - tk.k0, a.WD);
@@ -822,24 +811,34 @@ template <> struct NearTypes<__half> { using Aux = float; using Row = float; };
 template <class H, int NR = 1>
 struct NearCfg {
     using R = typename NearTypes<H>::Row;
+    // tensor-core window slices (FP16 window, several right-hand sides): their rows and scales ride
+    // in the slices' stages (kTcPer slices a stage), so the vector buffers only hold aux rows
+    static constexpr bool tc = std::is_same<H, __half>::value && NR >= 2;
     // vector rows of one item: 64, or 128 for several right-hand sides in FP32 rows (their window
     // rows go by cp.async, without registers), so that items stay 128 / NR slices long
-    static constexpr int vec_rows = NR >= 2 && sizeof(R) == 4 ? 2 * kChunk : kChunk;
+    static constexpr int vec_rows = tc ? kTcVecRows : NR >= 2 && sizeof(R) == 4 ? 2 * kChunk : kChunk;
+    static constexpr int tc_rows_bytes = kTcPer * NR * kTcBox * 4;
+    static constexpr int tc_scale_bytes = kTcPer * (NR > 4 ? NR : 4) * 4;
+    // one stage: the slices, then (tensor cores) a 128-byte aligned TMA landing zone for rows + scales
+    static constexpr int stage_bytes =
+        tc ? kNearStageBytes + (tc_rows_bytes + tc_scale_bytes + 127) / 128 * 128 : kNearStageBytes;
     // shared-memory pipeline depth, within two CTAs per SM next to the vector buffers and the
     // partial sums of the right-hand sides
     static constexpr int stages = NR >= 8 ? 3 : NR >= 2 ? 4 : sizeof(R) == 4 ? 5 : 4;
-    // tensor-core window rows (FP16 window, several right-hand sides): TMA boxes of kTcBox words a
-    // row (a multiple of 128 bytes for vec_rows = 128), and 128 bytes of room to align them
-    static constexpr bool tc = std::is_same<H, __half>::value && NR >= 2;
-    static constexpr int tc_scale_bytes = (vec_rows / NR) * (NR > 4 ? NR : 4) * 4;
-    static constexpr int vec_bytes =
-        tc ? (vec_rows * kTcBox * 4 + tc_scale_bytes + 127) / 128 * 128 : vec_rows * 32 * (int)sizeof(R);
-    static constexpr int smem = stages * kNearStageBytes + 2 * vec_bytes + (tc ? 128 : 0);
+    static constexpr int vec_bytes = vec_rows * 32 * (int)sizeof(R);
+    // (+ 128 bytes of room to align the stages for the TMA boxes)
+    static constexpr int smem = stages * stage_bytes + 2 * vec_bytes + (tc ? 128 : 0);
 };
 
 // the longest work item (window slices) of a plan: the item's vector rows over its right-hand sides
 static inline int near_max_chunk(int nrhs, int precision) {
+    if (nrhs >= 2 && precision == FDPH_FP16) return kChunk;   // tensor cores: rows ride in the stages
     return (nrhs >= 2 && precision != FDPH_FP64 ? 2 * kChunk : kChunk) / nrhs;
+}
+
+// the longest aux item (static tile and tail slices): its NR rows a slice fill the vector buffer
+static inline int near_aux_chunk(int nrhs, int precision) {
+    return (nrhs >= 2 && precision == FDPH_FP16 ? kTcVecRows : kChunk) / nrhs;
 }
 
 // slice . vector for one receiver lane: 16-byte loads of the source-interleaved slice (plan.h)
@@ -1149,15 +1148,15 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
     __shared__ __align__(8) unsigned long long full[C::stages], empty[C::stages];
     __shared__ double red[2][kNearConsumers][NR][32];
     __shared__ __align__(16) NearTask tcache[kTaskCache];   // this CTA's first work items
-    __shared__ __align__(8) unsigned long long vbar[2];      // TMA rows of the two vector buffers (kTC)
     __shared__ int abort_flag;
     const NearView v0 = kBatch ? NearView{} : near_view(a);
     auto view = [&](const NearTask& tk) -> NearView { return kBatch ? near_view(scen[tk.scen]) : v0; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t0 = a.cta_ptr[blockIdx.x], t1 = a.cta_ptr[blockIdx.x + 1];
-    unsigned char* vbuf = near_smem + C::stages * kNearStageBytes;
+    unsigned char* stage0 = near_smem;
     if constexpr (C::tc)   // TMA boxes land on 128-byte boundaries (the configuration reserves the room)
-        vbuf = (unsigned char*)(((unsigned long long)vbuf + 127) & ~127ull);
+        stage0 = (unsigned char*)(((unsigned long long)near_smem + 127) & ~127ull);
+    unsigned char* vbuf = stage0 + C::stages * C::stage_bytes;
     {
         const int nt = min(t1 - t0, kTaskCache) * (int)(sizeof(NearTask) / sizeof(int4));
         for (int e = threadIdx.x; e < nt; e += blockDim.x)
@@ -1169,8 +1168,6 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kNearConsumers);
         }
-        mbar_init(&vbar[0], 1);
-        mbar_init(&vbar[1], 1);
         abort_flag = 0;
         mbar_fence_init();
     }
@@ -1185,7 +1182,8 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                 const NearView v = view(tk);
                 const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
                 const int nsl = near_slices<T>(tk, v.n);
-                const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
+                const bool tcw = kTC && !tk.kind;   // tensor-core window item: rows ride in the stages
+                const int per = tcw ? kTcPer : min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
                 const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
                 const unsigned char* src = tk.kind ? (const unsigned char*)((const A*)v.stat + tk.off)
                                                    : (const unsigned char*)((const H*)v.tensor + tk.off);
@@ -1193,7 +1191,7 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     const int s = g % C::stages;
                     if (!mbar_wait_bounded(&empty[s], (unsigned)(((g / C::stages) & 1) ^ 1))) {
                         abort_flag = 1;
-                        atomicExch(v.err, 1);
+                        atomicExch(v.err, kErrTimeout);
                     }
                     const int cnt = min(per, nsl - q * per);
                     const unsigned bytes = (unsigned)(cnt * tk.sl * esz);
@@ -1201,11 +1199,24 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                     // check completes the stage without data)
                     const bool ok = FDPH_IDX(tk.off + (long long)(q * per + cnt) * tk.sl <= (tk.kind ? v.len_aux : v.len_tensor),
                                              v.err);
+                    unsigned char* stage = stage0 + s * C::stage_bytes;
                     fence_proxy_async();
-                    mbar_expect_tx(&full[s], ok ? bytes : 0u);
+                    mbar_expect_tx(&full[s], (ok ? bytes : 0u) + (tcw ? (unsigned)(C::tc_rows_bytes + C::tc_scale_bytes) : 0u));
                     if (ok)
-                        bulk_g2s_hint(near_smem + s * kNearStageBytes, src + (size_t)q * per * tk.sl * esz, bytes, &full[s],
-                                      policy);
+                        bulk_g2s_hint(stage, src + (size_t)q * per * tk.sl * esz, bytes, &full[s], policy);
+                    if constexpr (kTC) {
+                        if (tcw) {
+                            // the stage's window rows of every right-hand side with one TMA tensor copy: a
+                            // box of kTcBox sources from s0 rounded down to a multiple of 4 (the 16-byte
+                            // rule of the innermost coordinate; the consumers index from the remainder) x
+                            // nrhs x kTcPer slots from the oldest the stage may hold (the mirrored ring
+                            // keeps them contiguous; past it the box reads zeros), then their scales
+                            const int z0 = wrap(v.n - tk.k0 - (q * kTcPer + kTcPer - 1), v.WD);
+                            tma_load_3d(stage + kNearStageBytes, v.tmap16, tk.s0 & ~3, 0, z0, &full[s]);
+                            tma_load_2d(stage + kNearStageBytes + C::tc_rows_bytes,
+                                        (const unsigned char*)v.tmap16 + sizeof(CUtensorMap), 0, z0, &full[s]);
+                        }
+                    }
                 }
             }
         }
@@ -1217,13 +1228,12 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf, &vbar[0]);
+            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf);
             near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
         }
         cp_async_wait_all();
         consumer_barrier();
         int par = 0;
-        unsigned vph = 0;   // phase bits of vbar[0], vbar[1] (a wait per TMA box of window rows)
         for (int ti = t0; ti < t1; ++ti, par ^= 1) {
             const NearTask tk = nxt;
             const NearView v = vn;
@@ -1231,18 +1241,17 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes,
-                                                    &vbar[par ^ 1]);
+                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
             const int nsl = near_slices<T>(tk, v.n);
-            const int per = min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
-            const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
             // leaves of at most 16 receivers: the warp splits into 32 / span lane groups of span
             // lanes, each taking its own slices (lane = group * span + receiver); tensor-core
             // slices take the whole warp
             const bool tc = kTC && !tk.kind;
+            const int per = tc ? kTcPer : min(kMaxPer, max(1, kNearStageBytes / (tk.sl * esz)));
+            const int nst = nsl > 0 ? (nsl + per - 1) / per : 0;
             const int span = tc || tk.nr > 16 ? 32 : tk.nr > 8 ? 16 : tk.nr > 4 ? 8 : tk.nr > 2 ? 4 : tk.nr > 1 ? 2 : 1;
             const int ngrp = 32 / span, grp = lane / span, ri = lane - grp * span;
             const int li = ri < tk.nr ? ri : 0;         // lanes past nr read a valid element, unused
@@ -1258,45 +1267,37 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int f = 0; f < 4; ++f) tacc[mt][f] = 0.f;
-            if (tc && nsl > 0) {   // this item's window rows (TMA box issued one item ahead)
-                if (!mbar_wait_bounded(&vbar[par], (vph >> par) & 1u)) {
-                    abort_flag = 1;
-                    atomicExch(v.err, kErrTimeout);
-                }
-                vph ^= 1u << par;
-            }
             for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % C::stages;
                 const int cnt = min(per, nsl - q * per);
                 if (!mbar_wait_bounded(&full[s], (unsigned)((g / C::stages) & 1))) {
                     abort_flag = 1;
-                    atomicExch(v.err, 1);
+                    atomicExch(v.err, kErrTimeout);
                 }
-                const unsigned char* buf = near_smem + s * kNearStageBytes;
+                const unsigned char* buf = stage0 + s * C::stage_bytes;
                 for (int kk = warp * ngrp + grp; kk < cnt; kk += kNearConsumers * ngrp) {
                     const R* vrow = (const R*)(vrows + (size_t)(q * per + kk) * NR * 32 * sizeof(R));
                     if constexpr (kTC) {
                         if (tc) {
                             // this warp's slices kk and kk + kNearConsumers of the stage together;
-                            // slice ks of the item: box slot nsl - 1 - ks, ring slot of step n - k0 - ks
-                            const int ks = q * per + kk;
-                            const unsigned* rw = (const unsigned*)vrows + (tk.s0 & 3);
-                            auto rows_of = [&](int k) { return rw + (size_t)(nsl - 1 - k) * NR * kTcBox; };
+                            // stage slice kk (ring slot of step n - k0 - q kTcPer - kk): box slot
+                            // kTcPer - 1 - kk of the rows and scales that came with the stage
+                            const unsigned* rw = (const unsigned*)(buf + kNearStageBytes) + (tk.s0 & 3);
+                            auto rows_of = [&](int k) { return rw + (size_t)(kTcPer - 1 - k) * NR * kTcBox; };
                             constexpr int SR = NR > 4 ? NR : 4;
-                            const float* scl = (const float*)(vrows + C::vec_rows * kTcBox * 4);
-                            auto scale_of = [&](int k) { return scl + (nsl - 1 - k) * SR; };
+                            const float* scl = (const float*)(buf + kNearStageBytes + C::tc_rows_bytes);
+                            auto scale_of = [&](int k) { return scl + (kTcPer - 1 - k) * SR; };
                             if (kk + kNearConsumers < cnt) {
-                                const int ks2 = ks + kNearConsumers;
                                 const __half* const sl2[2] = {(const __half*)buf + (size_t)kk * tk.sl,
                                                               (const __half*)buf + (size_t)(kk + kNearConsumers) * tk.sl};
-                                const unsigned* const rw2[2] = {rows_of(ks), rows_of(ks2)};
-                                const float* const sc2[2] = {scale_of(ks), scale_of(ks2)};
+                                const unsigned* const rw2[2] = {rows_of(kk), rows_of(kk + kNearConsumers)};
+                                const float* const sc2[2] = {scale_of(kk), scale_of(kk + kNearConsumers)};
                                 tc_slices<NR, 2>(sl2, rw2, sc2, 1, tk.nr, tk.ns, lane, tacc);
                                 kk += kNearConsumers;
                             } else {
                                 const __half* const sl1[1] = {(const __half*)buf + (size_t)kk * tk.sl};
-                                const unsigned* const rw1[1] = {rows_of(ks)};
-                                const float* const sc1[1] = {scale_of(ks)};
+                                const unsigned* const rw1[1] = {rows_of(kk)};
+                                const float* const sc1[1] = {scale_of(kk)};
                                 tc_slices<NR, 1>(sl1, rw1, sc1, 1, tk.nr, tk.ns, lane, tacc);
                             }
                             continue;
@@ -1355,11 +1356,6 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             (void)mbar_wait_bounded(&full[s], 0u);
             (void)mbar_wait_bounded(&full[s], 1u);
         }
-        if constexpr (kTC)
-            for (int b = 0; b < 2; ++b) {
-                (void)mbar_wait_bounded(&vbar[b], 0u);
-                (void)mbar_wait_bounded(&vbar[b], 1u);
-            }
     }
 }
 
@@ -1860,7 +1856,7 @@ static int upload(fdph_plan_t P, T** out, const std::vector<T>& v) {
 }
 
 // TMA tensor map of the mirrored (hi, lo) ring Dring16 [2 WD][nrhs][NP] (4-byte elements): box =
-// kTcBox sources x nrhs x the longest work item's slots, no swizzle, zero fill outside; encoded
+// kTcBox sources x nrhs x one stage's kTcPer slots, no swizzle, zero fill outside; encoded
 // through the driver entry point (no link against the driver library) and kept in device memory
 static int make_row_tensor_map(fdph_plan_t P) {
     void* fn = nullptr;
@@ -1871,7 +1867,7 @@ static int make_row_tensor_map(fdph_plan_t P) {
         return FDPH_E_CUDA;
     }
     alignas(64) CUtensorMap map[2];
-    const cuuint32_t chunk = (cuuint32_t)near_max_chunk(P->nrhs, FDPH_FP16);
+    const cuuint32_t chunk = (cuuint32_t)kTcPer;   // one stage's slots
     const cuuint64_t dims[3] = {(cuuint64_t)P->NP, (cuuint64_t)P->nrhs, (cuuint64_t)2 * P->WD};
     const cuuint64_t strides[2] = {(cuuint64_t)P->NP * 4, (cuuint64_t)P->nrhs * P->NP * 4};
     const cuuint32_t box[3] = {(cuuint32_t)kTcBox, (cuuint32_t)P->nrhs, chunk};
@@ -2545,7 +2541,8 @@ static int build_near_begin(fdph_plan_t P, const PlanInputs& in, NearBuild& nb) 
     // (with nrhs right-hand sides an item's vectors, nrhs per slice, fill the same buffer)
     int chunk = near_max_chunk(P->nrhs, P->precision);
     while (chunk > std::max(1, 8 / P->nrhs) && slices / chunk < 4LL * 152 * 3) chunk /= 2;
-    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A), kChunk / P->nrhs);
+    finish_near_layout(hp, W, has_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A),
+                       near_aux_chunk(P->nrhs, P->precision));
     P->near_W = W;
     P->near_tail = has_tail;
     P->chunk = chunk;
@@ -2753,7 +2750,7 @@ static int set_chunk(fdph_plan_t P, int chunk) {
     P->graphs.clear();
     const int64_t tens0 = hp.near_tensor_len, aux0 = hp.near_aux_len, vst0 = hp.vstate_len;
     finish_near_layout(hp, P->near_W, P->near_tail, chunk, 16 / (int)sizeof(H), 16 / (int)sizeof(A),
-                       kChunk / P->nrhs);
+                       near_aux_chunk(P->nrhs, P->precision));
     if (hp.near_tensor_len != tens0 || hp.near_aux_len != aux0 || hp.vstate_len != vst0) {
         // the stored coefficients and states must keep their places (only the items change)
         set_error("set_chunk: near-field layout changed; the plan is unusable");

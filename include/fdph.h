@@ -183,7 +183,7 @@ typedef struct fdph_stats {
     double flops_per_step;     /* multiply-adds x 2 of one full step */
     double plan_seconds;       /* wall time of fdph_plan */
     int32_t n_exact;           /* low-rank operators kept exact (Sec. 6.2 fallback) */
-    int32_t pad_;
+    int32_t n_aca;             /* low-rank operators factorised by cross approximation (aca_min) */
     double mean_rank_f;        /* Domain-F amplitude ranks, weighted by the blocks' entries (the
                                   paper's "mean rank", Sec. 6.4.1); exact blocks count at full rank */
     double mean_rank_s;        /* the same for the Domain-S static blocks */

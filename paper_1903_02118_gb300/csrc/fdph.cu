@@ -2678,6 +2678,7 @@ static void fill_stats(fdph_plan_t P) {
     s.max_rank = hp.max_rank;
     s.mean_rank = hp.mean_rank;
     s.n_exact = hp.n_exact[0] + hp.n_exact[1] + hp.n_exact[2];
+    s.n_aca = hp.n_aca;
     s.mean_rank_f = hp.ent_w[SB_F] > 0 ? hp.rank_w[SB_F] / hp.ent_w[SB_F] : 0.0;
     s.mean_rank_s = hp.ent_w[SB_S] > 0 ? hp.rank_w[SB_S] / hp.ent_w[SB_S] : 0.0;
     s.mean_rank_tr = hp.ent_w[SB_TR] > 0 ? hp.rank_w[SB_TR] / hp.ent_w[SB_TR] : 0.0;

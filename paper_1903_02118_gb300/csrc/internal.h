@@ -81,6 +81,7 @@ ArtInts art_integers(const Elements& el, const Tree& tr, const Leaf& lf, const P
 struct LowRank {
     int m = 0, n = 0, rank = 0;
     bool exact = false;
+    bool aca = false;      // factorised by low_rank_aca
     std::vector<double> F, G;
 };
 void low_rank(const double* A, int m, int n, double eps, LowRank& out, bool allow_exact = true);

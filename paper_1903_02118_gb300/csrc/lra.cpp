@@ -93,6 +93,7 @@ void low_rank(const double* A, int m, int n, double eps, LowRank& out, bool allo
     out.n = n;
     out.rank = 0;
     out.exact = false;
+    out.aca = false;
     out.F.clear();
     out.G.clear();
     double norm2 = 0.0;
@@ -398,6 +399,7 @@ bool low_rank_aca(const std::function<void(int, double*)>& row, const std::funct
     out.n = n;
     out.rank = 0;
     out.exact = false;
+    out.aca = false;
     out.F.clear();
     out.G.clear();
     if (m < 2 || n < 2 || !(eps > 0.0)) return false;
@@ -515,7 +517,10 @@ bool low_rank_aca(const std::function<void(int, double*)>& row, const std::funct
         }
     }
     if (!converged) return false;
-    if (U.empty()) return true;   // rank 0: every sampled row and column vanished
+    if (U.empty()) {   // rank 0: every sampled row and column vanished
+        out.aca = true;
+        return true;
+    }
     // the reference row and column are residuals of unused random ones: their energy, scaled to the
     // whole block, must be within the tolerance, else the cross approximation missed a part
     const double rr = dot4(rref.data(), rref.data(), n) * m, cc = dot4(cref.data(), cref.data(), m) * n;
@@ -541,6 +546,7 @@ bool low_rank_aca(const std::function<void(int, double*)>& row, const std::funct
     const int rk = cr.rank;
     if ((long)rk * (m + n) >= (long)m * n) return false;   // the block is kept exact (Sec. 6.2)
     out.rank = rk;
+    out.aca = true;
     if (rk == 0) return true;
     out.F.assign((size_t)m * rk, 0.0);
     out.G.assign((size_t)n * rk, 0.0);

@@ -498,6 +498,7 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             hp.rank_w[kind] += (double)sb.rank * o.nr * o.ns;   // entry-weighted, as the paper's mean rank
             hp.ent_w[kind] += (double)o.nr * o.ns;
             hp.n_exact[kind] += lr.exact ? 1 : 0;
+            hp.n_aca += lr.aca ? 1 : 0;
             hp.far_entries += (int64_t)lr.F.size() + lr.G.size() + (h ? h->size() : 0);
         };
         add(SB_F, o.F[0], dF, dF_off, &o.h[0], o.HM, 0, nullptr);

@@ -91,6 +91,7 @@ struct HostPlan {
     double mean_rank = 0;
     double rank_w[3] = {0, 0, 0}, ent_w[3] = {0, 0, 0};   // per SubKind: sum rank * entries, sum entries
     int n_exact[3] = {0, 0, 0};                          // per SubKind: sub-blocks kept exact
+    int n_aca = 0;                                       // sub-blocks from cross approximation
     int64_t far_entries = 0;
     int64_t far_nent = 0;                            // (block, receiver) entries
 };

@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("far_entries", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
                 ("state_bytes", ctypes.c_int64), ("bytes_per_step", ctypes.c_double),
                 ("near_bytes_per_step", ctypes.c_double), ("flops_per_step", ctypes.c_double),
-                ("plan_seconds", ctypes.c_double), ("n_exact", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("plan_seconds", ctypes.c_double), ("n_exact", ctypes.c_int32), ("n_aca", ctypes.c_int32),
                 ("mean_rank_f", ctypes.c_double), ("mean_rank_s", ctypes.c_double), ("mean_rank_tr", ctypes.c_double)]
 
     def as_dict(self):

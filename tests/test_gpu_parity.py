@@ -554,18 +554,21 @@ def test_cross_approximation_plan_within_eps_of_compressed_operator(geom, N, lea
     their operators differ by at most 2 eps per block; the transient's spatial pivot may land on
     another pair of similar size, which moves the transient term within its own error (~eps_st).
     The outputs stay within 10 eps of the oracle's compressed operator, while the dense plan meets
-    the FP64 bound, and differ from it (the cross approximation really ran)."""
+    the FP64 bound; the plan statistics show the cross approximation ran (on these low-rank blocks
+    the recompressed crosses often reproduce the truncated SVD to rounding)."""
     _need_gpu()
     M, eps = 320, 1e-5
     xy = _geom(geom, N)
     D = inputs.gaussian_pulse(N, M, 0.5, inputs.seed_for(1, inputs.SLIP))
     T0, _ = _oracle_fdph(xy, M, eps, leaf, D, soe_terms=soe, amp_window=amp)
     kw = dict(eta=0.5, eps_st=1e-6, leaf_size=leaf, amp_window=amp, soe_terms=soe)
-    Td = _run(fdph.Plan(xy, 0.5, M, eps, **kw), D)
-    T = _run(fdph.Plan(xy, 0.5, M, eps, aca_min=144, **kw), D)
+    dense = fdph.Plan(xy, 0.5, M, eps, **kw)
+    Td = _run(dense, D)
+    aca = fdph.Plan(xy, 0.5, M, eps, aca_min=144, **kw)
+    T = _run(aca, D)
+    assert dense.stats()["n_aca"] == 0 and aca.stats()["n_aca"] > 0
     assert _rel(Td, T0) < TOL64
     assert _rel(T, T0) < 10 * eps
-    assert _rel(T, Td) > 1e-12
 
 
 @pytest.mark.parametrize("geom,N,leaf", [("curved", 200, 16), ("kinked", 190, 13)])

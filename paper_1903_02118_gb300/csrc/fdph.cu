@@ -372,11 +372,58 @@ __device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
     a.dhat[sb.dhat + jl] = s0 + s1;
 }
 
-template <class T>
+// The same for NR right-hand sides at once: the taps are read once and feed the NR slip-rate rows
+// (per right-hand side the single-RHS order of operations, so the results are the same bits)
+template <class T, int NR>
+__device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
+    const int n = step_index(a);
+    const SbDev& sb = a.sbs[a.fir_sb[q]];
+    const int jl = a.fir_j[q];
+    const int ns = sb.ns;
+    const T* h = a.fac + sb.h + jl;
+    const double* D = a.Dring + sb.s0 + jl;
+    const int taps = min(sb.taps, n + 1);
+    const int slot = wrap(n, a.WD);
+    if (!FDPH_IDX(taps <= a.WD && sb.s0 + jl < a.N && (long long)sb.dhat + jl < a.rs_dhat, a.err)) return;
+    double s0[NR], s1[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0.0;
+    int m = 0;
+    for (; m + 1 < taps; m += 2) {
+        int t0 = slot - m, t1 = slot - m - 1;
+        t0 += t0 < 0 ? a.WD : 0;
+        t1 += t1 < 0 ? a.WD : 0;
+        const double h0 = (double)h[(long long)m * ns], h1 = (double)h[(long long)(m + 1) * ns];
+        const double* d0 = D + (size_t)t0 * a.N;
+        const double* d1 = D + (size_t)t1 * a.N;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            s0[r] += h0 * d0[r * a.rs_D];
+            s1[r] += h1 * d1[r * a.rs_D];
+        }
+    }
+    if (m < taps) {
+        int t0 = slot - m;
+        t0 += t0 < 0 ? a.WD : 0;
+        const double h0 = (double)h[(long long)m * ns];
+        const double* d0 = D + (size_t)t0 * a.N;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s0[r] += h0 * d0[r * a.rs_D];
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = s0[r] + s1[r];
+}
+
+// NR = 1: one grid row per right-hand side; NR > 1: all of them in one thread
+template <class T, int NR>
 __global__ void fir_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < a.n_fir) fir_body(a, q);
+    if constexpr (NR == 1) {
+        const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+        if (q < a.n_fir) fir_body(a, q);
+    } else {
+        if (q < a0.n_fir) fir_body_nr<T, NR>(a0, q);
+    }
 }
 
 // source quantity u_j of Eq. 42 for block kind: Dhat (Domain F), dt * cumulative slip (Domain S,
@@ -434,11 +481,82 @@ __device__ __forceinline__ void scatter_body(const StepArgs<T>& a, int w, int la
     }
 }
 
-template <class T>
+// The same for NR right-hand sides at once: g and the task's indices are read once (per right-hand
+// side the single-RHS order of operations)
+template <class T, int NR>
+__device__ __forceinline__ void scatter_body_nr(const StepArgs<T>& a, int w, int lane) {
+    const int n = step_index(a);
+    const int4 tk = a.sc_tasks[w];
+    const SbDev& sb = a.sbs[tk.x];
+    const int lg = tk.w, G = 1 << lg;
+    const int gi = lane >> lg, lj = lane & (G - 1);
+    if (gi >= tk.z) return;
+    const int run = tk.y + gi;
+    const int delay = a.run_delay[run], st = a.run_start[run], len = a.run_len[run];
+    const int rank = sb.rank;
+    double* r0 = a.ring + sb.ring + (long long)wrap(n + delay, sb.L) * rank;
+    const int dslot = sb.kind == SB_TR ? wrap(n, a.WD) : 0;
+    if (!FDPH_IDX(sb.ring + (long long)(wrap(n + delay, sb.L) + 1) * rank <= a.rs_ring &&
+                  (sb.ident != 2 || sb.ns <= rank), a.err))
+        return;
+    auto sv = [&](int jl, int r) -> double {   // source_value of right-hand side r
+        if (sb.kind == SB_F) return a.dhat[r * a.rs_dhat + sb.dhat + jl];
+        if (sb.kind == SB_S) return a.dt * a.C[(long long)r * a.N + sb.s0 + jl];
+        return a.Dring[r * a.rs_D + (size_t)dslot * a.N + sb.s0 + jl];
+    };
+    if (sb.ident == 2) {
+        for (int u = lj; u < len; u += G) {
+            const int jl = a.src_order[st + u];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) r0[r * a.rs_ring + jl] = sv(jl, r);
+        }
+        return;
+    }
+    const bool fresh = delay == sb.maxdelay;
+    const T* g = a.fac + sb.g;
+    if (len == 1) {
+        const int jl = a.src_order[st];
+        double u[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) u[r] = sv(jl, r);
+        const T* gj = g + (long long)jl * rank;
+        for (int l = lj; l < rank; l += G) {
+            const double gl = (double)gj[l];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                double* rr = r0 + r * a.rs_ring;
+                rr[l] = fresh ? gl * u[r] : rr[l] + gl * u[r];
+            }
+        }
+        return;
+    }
+    for (int l = lj; l < rank; l += G) {
+        double sum[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sum[r] = 0.0;
+        for (int u = 0; u < len; ++u) {
+            const int jl = a.src_order[st + u];
+            const double gl = (double)g[(long long)jl * rank + l];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sum[r] += gl * sv(jl, r);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            double* rr = r0 + r * a.rs_ring;
+            rr[l] = fresh ? sum[r] : rr[l] + sum[r];
+        }
+    }
+}
+
+template <class T, int NR>
 __global__ void scatter_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w < a.n_sct) scatter_body(a, w, threadIdx.x & 31);
+    if constexpr (NR == 1) {
+        const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+        if (w < a.n_sct) scatter_body(a, w, threadIdx.x & 31);
+    } else {
+        if (w < a0.n_sct) scatter_body_nr<T, NR>(a0, w, threadIdx.x & 31);
+    }
 }
 
 // Delayed-history form of Eq. 42 (the gather variant of Sec. 5.3): instead of adding g_{l,j} u_j
@@ -1405,11 +1523,78 @@ __device__ __forceinline__ void far_eval_body(const StepArgs<T>& a, int w, int l
     if (valid && lj == 0) a.fval[a.e_pos[sb.e0 + il]] = s;
 }
 
-template <class T>
+// The same for NR right-hand sides at once: the task, delays and factor row are read once (per
+// right-hand side the single-RHS order of operations)
+template <class T, int NR>
+__device__ __forceinline__ void far_eval_body_nr(const StepArgs<T>& a, int w, int lane) {
+    const int n = step_index(a);
+    const int4 tk = a.ev_tasks[w];
+    const SbDev& sb = a.sbs[tk.x];
+    const int lg = tk.w, G = 1 << lg;
+    const int gi = lane >> lg, lj = lane & (G - 1);
+    const int il = tk.y + gi;
+    bool valid = gi < tk.z;
+    double s[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) s[r] = 0.0;
+    if (valid)
+        valid = FDPH_IDX((sb.kind == SB_TR ? sb.zring + (long long)sb.LZ * sb.rank <= a.rs_zring
+                                           : sb.ring + (long long)sb.L * sb.rank <= a.rs_ring) &&
+                             (sb.ident != 1 || il < sb.rank) && a.e_pos[sb.e0 + il] < a.rs_fval,
+                         a.err);
+    if (valid) {
+        const bool tr = sb.kind == SB_TR;
+        const double* base = tr ? a.zring + sb.zring : a.ring + sb.ring;
+        const long long rs = tr ? a.rs_zring : a.rs_ring;
+        const int len = tr ? sb.LZ : sb.L;
+        const int rank = sb.rank;
+        const int t = n - a.ints[sb.dm + il];
+        const double* rw = base + (long long)wrap(t, len) * rank;
+        if (a.phi) {
+            const double ph = a.phi[sb.phi + il];
+            const double* rw1 = base + (long long)wrap(t - 1, len) * rank;
+            if (sb.ident == 1) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) s[r] = (1.0 - ph) * rw[r * rs + il] + ph * rw1[r * rs + il];
+            } else {
+                const T* f = a.fac + sb.f + (long long)il * rank;
+                for (int l = lj; l < rank; l += G) {
+                    const double fl = (double)f[l];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) s[r] += fl * ((1.0 - ph) * rw[r * rs + l] + ph * rw1[r * rs + l]);
+                }
+            }
+        } else if (sb.ident == 1) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s[r] = rw[r * rs + il];
+        } else {
+            const T* f = a.fac + sb.f + (long long)il * rank;
+            for (int l = lj; l < rank; l += G) {
+                const double fl = (double)f[l];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) s[r] += fl * rw[r * rs + l];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        for (int o = G >> 1; o > 0; o >>= 1) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
+    if (valid && lj == 0) {
+        const long long pos = a.e_pos[sb.e0 + il];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a.fval[r * a.rs_fval + pos] = s[r];
+    }
+}
+
+template <class T, int NR>
 __global__ void far_eval_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w < a.n_evt) far_eval_body(a, w, threadIdx.x & 31);   // warp-uniform
+    if constexpr (NR == 1) {
+        const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+        if (w < a.n_evt) far_eval_body(a, w, threadIdx.x & 31);   // warp-uniform
+    } else {
+        if (w < a0.n_evt) far_eval_body_nr<T, NR>(a0, w, threadIdx.x & 31);
+    }
 }
 
 // Eq. 39 summed per receiver: one warp per receiver adds its far entries (fixed order) into
@@ -1423,11 +1608,32 @@ __device__ __forceinline__ void far_sum_body(const StepArgs<T>& a, int p, int la
     if (lane == 0) a.tfar[p] = s;
 }
 
-template <class T>
+template <class T, int NR>
+__device__ __forceinline__ void far_sum_body_nr(const StepArgs<T>& a, int p, int lane) {
+    double s[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) s[r] = 0.0;
+    for (int e = a.g_ptr[p] + lane; e < a.g_ptr[p + 1]; e += 32)
+        if (FDPH_IDX(e < a.rs_fval, a.err)) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s[r] += a.fval[r * a.rs_fval + e];
+        }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        for (int o = 16; o > 0; o >>= 1) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
+        if (lane == 0) a.tfar[(long long)r * a.N + p] = s[r];
+    }
+}
+
+template <class T, int NR>
 __global__ void far_sum_kernel(StepArgs<T> a0) {
-    const StepArgs<T> a = rhs_args(a0, blockIdx.y);
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (p < a.N) far_sum_body(a, p, threadIdx.x & 31);   // warp-uniform
+    if constexpr (NR == 1) {
+        const StepArgs<T> a = rhs_args(a0, blockIdx.y);
+        if (p < a.N) far_sum_body(a, p, threadIdx.x & 31);   // warp-uniform
+    } else {
+        if (p < a0.N) far_sum_body_nr<T, NR>(a0, p, threadIdx.x & 31);
+    }
 }
 
 // the step's output: far-field traction + the receiver's near-field partial sums (a few per
@@ -1995,6 +2201,33 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// Launches of the far-field kernels: one grid row per right-hand side for one of them, one thread
+// (or warp) for all of them otherwise, so that factors and indices are read once per step
+#define FDPH_LAUNCH_NR(K, grid, threads, st, a)                                          \
+    switch ((a).nrhs) {                                                                  \
+        case 2: K<T, 2><<<(grid), (threads), 0, (st)>>>(a); break;                     \
+        case 4: K<T, 4><<<(grid), (threads), 0, (st)>>>(a); break;                     \
+        case 8: K<T, 8><<<(grid), (threads), 0, (st)>>>(a); break;                     \
+        default: K<T, 1><<<dim3((grid), (a).nrhs), (threads), 0, (st)>>>(a); break;    \
+    }
+
+template <class T>
+static void launch_fir(const StepArgs<T>& a, cudaStream_t s) {
+    FDPH_LAUNCH_NR(fir_kernel, blocks(a.n_fir, 128), 128, s, a)
+}
+template <class T>
+static void launch_scatter(const StepArgs<T>& a, cudaStream_t s) {
+    FDPH_LAUNCH_NR(scatter_kernel, blocks((long long)a.n_sct * 32, 128), 128, s, a)
+}
+template <class T>
+static void launch_far_eval(const StepArgs<T>& a, cudaStream_t s) {
+    FDPH_LAUNCH_NR(far_eval_kernel, blocks((long long)a.n_evt * 32, 128), 128, s, a)
+}
+template <class T>
+static void launch_far_sum(const StepArgs<T>& a, cudaStream_t s) {
+    FDPH_LAUNCH_NR(far_sum_kernel, blocks((long long)a.N * 32, 128), 128, s, a)
+}
+
 // Eq. 42 of a step: scatter into the delay rings, or (far_mode 1) record the source values and
 // gather the completed slot from the histories
 template <class T>
@@ -2003,7 +2236,7 @@ static void eq42(const StepArgs<T>& a, cudaStream_t s) {
         record_kernel<T><<<dim3(blocks(a.n_rec, 128), a.nrhs), 128, 0, s>>>(a);
         if (a.n_gat) hgather_kernel<T><<<dim3(blocks((long long)a.n_gat * 32, 128), a.nrhs), 128, 0, s>>>(a);
     } else if (a.n_sct) {
-        scatter_kernel<T><<<dim3(blocks((long long)a.n_sct * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        launch_scatter<T>(a, s);
     }
 }
 
@@ -2061,11 +2294,11 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         cudaEventRecord(P->ev_fork, s);
         cudaStreamWaitEvent(P->side[0], P->ev_fork, 0);
         cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
-        if (a.n_fir) fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, P->side[0]>>>(a);
+        if (a.n_fir) launch_fir<T>(a, P->side[0]);
         eq42<T>(a, P->side[0]);
         if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
-        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
-        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
+        if (a.n_evt) launch_far_eval<T>(a, P->side[1]);
+        launch_far_sum<T>(a, P->side[1]);
         if (a.n_cta) launch_near<T>(P, a, s);
         cudaEventRecord(P->ev_join[0], P->side[0]);
         cudaEventRecord(P->ev_join[1], P->side[1]);
@@ -2075,7 +2308,7 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
         return;
     }
     // serial order (per-kernel timing)
-    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); launch_fir<T>(a, s); }
     { ProfScope ps(P, 2); eq42<T>(a, s); }
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a); }
     if (a.n_cta) {
@@ -2084,8 +2317,8 @@ static void enqueue_step(fdph_plan_t P, const StepArgs<T>& a, cudaStream_t s) {
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        if (a.n_evt) launch_far_eval<T>(a, s);
+        launch_far_sum<T>(a, s);
         gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
@@ -2287,8 +2520,8 @@ static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
     }
     {
         ProfScope ps(P, 5);
-        if (a.n_evt) far_eval_kernel<T><<<dim3(blocks((long long)a.n_evt * 32, 128), a.nrhs), 128, 0, s>>>(a);
-        far_sum_kernel<T><<<dim3(blocks((long long)a.N * 32, 128), a.nrhs), 128, 0, s>>>(a);
+        if (a.n_evt) launch_far_eval<T>(a, s);
+        launch_far_sum<T>(a, s);
         gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
     }
 }
@@ -2299,7 +2532,7 @@ template <class T>
 static void enqueue_commit(fdph_plan_t P, StepArgs<T> a, const double* D, cudaStream_t s) {
     a.D_in = D;
     { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }
-    if (a.n_fir) { ProfScope ps(P, 1); fir_kernel<T><<<dim3(blocks(a.n_fir, 128), a.nrhs), 128, 0, s>>>(a); }
+    if (a.n_fir) { ProfScope ps(P, 1); launch_fir<T>(a, s); }
     { ProfScope ps(P, 2); eq42<T>(a, s); }
 }
 

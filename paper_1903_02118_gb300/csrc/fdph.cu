@@ -162,6 +162,10 @@ struct StepArgs {
     const int* fir_sb;
     const int* fir_j;
     int n_fir;
+    const int* sfir_ptr;      // [N + 1] the FIR tasks by source element (CSR into sfir_q)
+    const int* sfir_q;
+    const int* sfir_tmax;     // [N] longest waveform of the source's tasks
+    int sfir_taps;            // longest waveform of all (shared-memory rows of a warp)
     const int* tr_sb;
     const int* tr_l;
     int n_tr;
@@ -349,8 +353,7 @@ __device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
     const int n = step_index(a);
     const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
-    const int ns = sb.ns;
-    const T* h = a.fac + sb.h + jl;
+    const T* h = a.fac + sb.h + (long long)jl * sb.taps;   // the source's taps, contiguous
     const double* D = a.Dring + sb.s0 + jl;
     const int taps = min(sb.taps, n + 1);   // taps <= WD, so one wrap-around at most
     const int slot = wrap(n, a.WD);
@@ -361,13 +364,13 @@ __device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
         int t0 = slot - m, t1 = slot - m - 1;
         t0 += t0 < 0 ? a.WD : 0;
         t1 += t1 < 0 ? a.WD : 0;
-        s0 += (double)h[(long long)m * ns] * D[(size_t)t0 * a.N];
-        s1 += (double)h[(long long)(m + 1) * ns] * D[(size_t)t1 * a.N];
+        s0 += (double)h[m] * D[(size_t)t0 * a.N];
+        s1 += (double)h[m + 1] * D[(size_t)t1 * a.N];
     }
     if (m < taps) {
         int t0 = slot - m;
         t0 += t0 < 0 ? a.WD : 0;
-        s0 += (double)h[(long long)m * ns] * D[(size_t)t0 * a.N];
+        s0 += (double)h[m] * D[(size_t)t0 * a.N];
     }
     a.dhat[sb.dhat + jl] = s0 + s1;
 }
@@ -379,8 +382,7 @@ __device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
     const int n = step_index(a);
     const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
-    const int ns = sb.ns;
-    const T* h = a.fac + sb.h + jl;
+    const T* h = a.fac + sb.h + (long long)jl * sb.taps;
     const double* D = a.Dring + sb.s0 + jl;
     const int taps = min(sb.taps, n + 1);
     const int slot = wrap(n, a.WD);
@@ -393,7 +395,7 @@ __device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
         int t0 = slot - m, t1 = slot - m - 1;
         t0 += t0 < 0 ? a.WD : 0;
         t1 += t1 < 0 ? a.WD : 0;
-        const double h0 = (double)h[(long long)m * ns], h1 = (double)h[(long long)(m + 1) * ns];
+        const double h0 = (double)h[m], h1 = (double)h[m + 1];
         const double* d0 = D + (size_t)t0 * a.N;
         const double* d1 = D + (size_t)t1 * a.N;
 #pragma unroll
@@ -405,7 +407,7 @@ __device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
     if (m < taps) {
         int t0 = slot - m;
         t0 += t0 < 0 ? a.WD : 0;
-        const double h0 = (double)h[(long long)m * ns];
+        const double h0 = (double)h[m];
         const double* d0 = D + (size_t)t0 * a.N;
 #pragma unroll
         for (int r = 0; r < NR; ++r) s0[r] += h0 * d0[r * a.rs_D];
@@ -423,6 +425,63 @@ __global__ void fir_kernel(StepArgs<T> a0) {
         if (q < a.n_fir) fir_body(a, q);
     } else {
         if (q < a0.n_fir) fir_body_nr<T, NR>(a0, q);
+    }
+}
+
+// Eq. 32 source-major (the single-plan step): one warp per source element j, which copies its
+// last taps slip rates of every right-hand side to shared memory once, then its lanes take j's
+// FIR tasks (one per F block containing j, ~10^2 at large N) and sum each task's contiguous taps
+// against the shared rows.  The sub-block-major kernel above reads a source's slip rates once
+// per task; this reads them once per step.  Per task and right-hand side the sums run in the
+// same order (even and odd taps apart), so the results are the same bits.
+constexpr int kSfirWarps = 4;
+
+template <class T, int NR>
+__global__ void __launch_bounds__(32 * kSfirWarps) sfir_kernel(StepArgs<T> a) {
+    extern __shared__ double sfir_rows[];   // per warp [sfir_taps][NR]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kSfirWarps + warp;
+    if (p >= a.N) return;   // warp-uniform
+    const int e0 = a.sfir_ptr[p], e1 = a.sfir_ptr[p + 1];
+    if (e0 == e1) return;
+    const int n = step_index(a);
+    const int tmax = min(a.sfir_tmax[p], n + 1);
+    double* sd = sfir_rows + (size_t)warp * a.sfir_taps * NR;
+    if (!FDPH_IDX(tmax <= a.WD && a.sfir_tmax[p] <= a.sfir_taps, a.err)) return;
+    const int slot = wrap(n, a.WD);
+    for (int m = lane; m < tmax; m += 32) {
+        int t = slot - m;
+        t += t < 0 ? a.WD : 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sd[m * NR + r] = a.Dring[r * a.rs_D + (size_t)t * a.N + p];
+    }
+    __syncwarp();
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int q = a.sfir_q[e];
+        const SbDev& sb = a.sbs[a.fir_sb[q]];
+        const int jl = a.fir_j[q];
+        const int taps = min(sb.taps, n + 1);
+        if (!FDPH_IDX(taps <= tmax && (long long)sb.dhat + jl < a.rs_dhat, a.err)) continue;
+        const T* h = a.fac + sb.h + (long long)jl * sb.taps;
+        double s0[NR], s1[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0.0;
+        int m = 0;
+        for (; m + 1 < taps; m += 2) {
+            const double h0 = (double)h[m], h1 = (double)h[m + 1];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                s0[r] += h0 * sd[m * NR + r];
+                s1[r] += h1 * sd[(m + 1) * NR + r];
+            }
+        }
+        if (m < taps) {
+            const double h0 = (double)h[m];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s0[r] += h0 * sd[m * NR + r];
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = s0[r] + s1[r];
     }
 }
 
@@ -1939,6 +1998,7 @@ struct fdph_plan_s {
     int4 *sc_tasks = nullptr, *ev_tasks = nullptr;
     int n_sct = 0, n_evt = 0;
     double* fval = nullptr;
+    int *sfir_ptr = nullptr, *sfir_q = nullptr, *sfir_tmax = nullptr;
     int *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
         *tr_l = nullptr, *g_ptr = nullptr, *g_sb = nullptr, *g_il = nullptr;
     NearDev* near = nullptr;
@@ -2143,6 +2203,10 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.fir_sb = P->fir_sb;
     a.fir_j = P->fir_j;
     a.n_fir = (int)P->hp.fir_sb.size();
+    a.sfir_ptr = P->sfir_ptr;
+    a.sfir_q = P->sfir_q;
+    a.sfir_tmax = P->sfir_tmax;
+    a.sfir_taps = P->hp.max_taps;
     a.tr_sb = P->tr_sb;
     a.tr_l = P->tr_l;
     a.n_tr = (int)P->hp.tr_sb.size();
@@ -2213,6 +2277,17 @@ struct ProfScope {
 
 template <class T>
 static void launch_fir(const StepArgs<T>& a, cudaStream_t s) {
+    const size_t smem = (size_t)kSfirWarps * a.sfir_taps * a.nrhs * sizeof(double);
+    if (a.sfir_ptr && a.sfir_taps > 0 && smem <= 48 * 1024) {   // source-major (no opt-in shared memory)
+        const unsigned g = blocks(a.N, kSfirWarps);
+        switch (a.nrhs) {
+            case 2: sfir_kernel<T, 2><<<g, 32 * kSfirWarps, smem, s>>>(a); break;
+            case 4: sfir_kernel<T, 4><<<g, 32 * kSfirWarps, smem, s>>>(a); break;
+            case 8: sfir_kernel<T, 8><<<g, 32 * kSfirWarps, smem, s>>>(a); break;
+            default: sfir_kernel<T, 1><<<g, 32 * kSfirWarps, smem, s>>>(a); break;
+        }
+        return;
+    }
     FDPH_LAUNCH_NR(fir_kernel, blocks(a.n_fir, 128), 128, s, a)
 }
 template <class T>
@@ -2949,7 +3024,7 @@ static void fill_stats(fdph_plan_t P) {
             flops += 2.0 * (sb.nr + sb.ns) * r;
         }
         if (sb.kind == SB_F) {
-            far_b += (double)sb.taps * sb.ns * (ps + 8.0) + sb.ns * 16.0;   // h, D history, Dhat
+            far_b += (double)sb.taps * sb.ns * ps + sb.ns * 8.0;   // h, Dhat (the D history below)
             flops += 2.0 * sb.taps * sb.ns;
         }
         if (sb.kind == SB_TR) {
@@ -2960,6 +3035,7 @@ static void fill_stats(fdph_plan_t P) {
             flops += 2.0 * r * ((sb.qn ? 2.0 * sb.qn : sb.taps) + 2.0 * sb.soe);
         }
     }
+    for (int32_t t : hp.sfir_tmax) far_b += t * 8.0;                          // each source's D history, once
     const double push_b = hp.n * (8.0 + 8.0 + 32.0 + 8.0 + 4.0);           // D in, ring, C/comp, Cring, perm
     const double out_b = hp.n * (8.0 + 4.0) + (double)hp.np_idx.size() * 12.0;
     s.bytes_per_step = near_b + far_b + push_b + out_b;
@@ -3643,6 +3719,8 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = upload(P, &P->run_len, hp.run_len)) || (rc = upload(P, &P->src_order, hp.src_order)) ||
         (rc = upload(P, &P->e_pos, hp.e_pos)) ||
         (rc = upload(P, &P->fir_sb, hp.fir_sb)) || (rc = upload(P, &P->fir_j, hp.fir_j)) ||
+        (rc = upload(P, &P->sfir_ptr, hp.sfir_ptr)) || (rc = upload(P, &P->sfir_q, hp.sfir_q)) ||
+        (rc = upload(P, &P->sfir_tmax, hp.sfir_tmax)) ||
         (rc = upload(P, &P->tr_sb, hp.tr_sb)) || (rc = upload(P, &P->tr_l, hp.tr_l)) ||
         (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
         (rc = upload(P, &P->g_il, hp.g_il)))

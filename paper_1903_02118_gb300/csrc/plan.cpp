@@ -434,7 +434,15 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
             sb.f = append(hp.fac, lr.F.data(), lr.F.size());
             sb.g = append(hp.fac, lr.G.data(), lr.G.size());
             const bool quant = qh && !qh->empty();   // the taps' staircase values replace the taps
-            sb.h = quant ? append(hp.fac, qh->data(), qh->size()) : h ? append(hp.fac, h->data(), h->size()) : 0;
+            if (kind == SB_F && h) {
+                // Domain-F waveforms source-major, [j][taps]: a FIR task reads its taps contiguously
+                std::vector<double> hj((size_t)o.ns * taps);
+                for (int j = 0; j < o.ns; ++j)
+                    for (int m = 0; m < taps; ++m) hj[(size_t)j * taps + m] = (*h)[(size_t)m * o.ns + j];
+                sb.h = append(hp.fac, hj.data(), hj.size());
+            } else {
+                sb.h = quant ? append(hp.fac, qh->data(), qh->size()) : h ? append(hp.fac, h->data(), h->size()) : 0;
+            }
             sb.qn = quant ? (int32_t)qh->size() : 0;
             sb.qb = quant ? append(hp.ints, qb->data(), qb->size()) : 0;
             sb.delay = dl_off;
@@ -515,6 +523,25 @@ int build_host_far(const Elements& el, const PlanInputs& in, HostPlan& hp) {
         for (auto& e : recv[p]) {
             hp.g_sb.push_back(e.first);
             hp.g_il.push_back(e.second);
+        }
+    }
+    // the FIR tasks by source element (CSR, tasks of one source in task order) and each source's
+    // longest waveform: a source's recent slip rates are read once for all its tasks
+    hp.sfir_ptr.assign(n + 1, 0);
+    hp.sfir_tmax.assign(n, 0);
+    for (size_t q = 0; q < hp.fir_sb.size(); ++q) {
+        const SubBlock& sb = hp.sbs[hp.fir_sb[q]];
+        const int p = sb.s0 + hp.fir_j[q];
+        hp.sfir_ptr[p + 1] += 1;
+        hp.sfir_tmax[p] = std::max(hp.sfir_tmax[p], sb.taps);
+    }
+    for (int p = 0; p < n; ++p) hp.sfir_ptr[p + 1] += hp.sfir_ptr[p];
+    hp.sfir_q.assign(hp.fir_sb.size(), 0);
+    {
+        std::vector<int32_t> fill(hp.sfir_ptr.begin(), hp.sfir_ptr.end() - 1);
+        for (size_t q = 0; q < hp.fir_sb.size(); ++q) {
+            const int p = hp.sbs[hp.fir_sb[q]].s0 + hp.fir_j[q];
+            hp.sfir_q[fill[p]++] = (int32_t)q;
         }
     }
     // block-major list of the same entries; recv[p] was filled in increasing block order, so the

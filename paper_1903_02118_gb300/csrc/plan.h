@@ -72,6 +72,7 @@ struct HostPlan {
     std::vector<int32_t> ints;                       // delays, dm
     std::vector<int32_t> run_delay, run_start, run_len, src_order;
     std::vector<int32_t> fir_sb, fir_j;              // FIR tasks
+    std::vector<int32_t> sfir_ptr, sfir_q, sfir_tmax; // FIR tasks by source element, longest taps
     std::vector<int32_t> tr_sb, tr_l;                // transient convolution tasks
     std::vector<int32_t> g_ptr, g_sb, g_il;          // gather CSR (receiver-major)
     std::vector<int32_t> e_pos;                      // CSR slot of each entry, block-major order

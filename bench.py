@@ -759,6 +759,7 @@ def run_large(args, cfg):
     t0 = time.perf_counter()
     plan = fdph.Plan(xy, DT, M, cfg["eps"], precision=prec, **kw)
     plan_s = time.perf_counter() - t0
+    chunk = plan.autotune(16)   # near-field item length and FIR form, timed on a saved state
     st = plan.stats()
     n0 = min(st["max_window"], S - W - K)
     if n0 < 0:
@@ -818,6 +819,7 @@ def run_large(args, cfg):
             "config": {"workload": cfg["name"], "N": N, "M": M, "eps": cfg["eps"], "eta": cfg["eta"],
                        "leaf": cfg["leaf"], "eps_st": cfg["eps_st"], "soe_terms": cfg["soe"], "cfl": 0.5, "nrhs": R,
                        "amp_window": cfg["amp_window"], "aca_min": cfg["aca_min"], "stepped_steps": S,
+                       "near_item_steps": chunk,
                        "first_timed_step": n0 + W,
                        "l2": "operator %.2f GB > L2 (no flush needed)" % (st["arena_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

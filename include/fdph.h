@@ -316,9 +316,12 @@ int fdph_selftest_wait_timeout(int32_t device, int64_t polls);
 
 /* Autotuner of the near-field work items (no counterpart in the paper): times `steps` replayed
  * steps (1..1024; plan's M >= steps + 2) at a steady-state step index for work items of 64, 32
- * and 16 kernel steps (divided by nrhs), keeps the fastest and writes it to *chunk (may be NULL).  The plan's state
- * and step index are saved and restored, so results continue as before (summation order within
- * the near field may change: rounding-level differences).  Cached step graphs are dropped.
+ * and 16 kernel steps (divided by nrhs unless the tensor cores take them), keeps the fastest and
+ * writes it to *chunk (may be NULL); then times the other form of the Eq. 32 FIR (source-major,
+ * the default where the F blocks hold each source ~100 times or more, or sub-block-major; both
+ * give the same bits) and keeps the faster.  The plan's state and step index are saved and
+ * restored, so results continue as before (summation order within the near field may change:
+ * rounding-level differences).  Cached step graphs are dropped.
  * Errors: FDPH_E_ARG, FDPH_E_STATE (profiling on), FDPH_E_OOM, FDPH_E_CUDA. */
 int fdph_autotune(fdph_plan_t plan, int32_t steps, int32_t* chunk);
 

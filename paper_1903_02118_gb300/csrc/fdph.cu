@@ -348,31 +348,39 @@ __global__ void push_kernel(StepArgs<T> a0) {
     if (p < a.N) push_body(a, p, false);
 }
 
+// The slip-rate history and the sums in the factor type: FP32 plans read the FP32 copy of the ring
+// and add in FP32 (this GPU's FP64 rate is a small fraction of its FP32 rate, and the ~27 taps of
+// a waveform lose ~2^-24 sqrt(27) relative), FP64 plans stay in FP64
+template <class T>
+__device__ __forceinline__ const T* fir_ring(const StepArgs<T>& a) {
+    if constexpr (sizeof(T) == 4) return a.Dring32; else return a.Dring;
+}
+
 template <class T>
 __device__ __forceinline__ void fir_body(const StepArgs<T>& a, int q) {
     const int n = step_index(a);
     const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
     const T* h = a.fac + sb.h + (long long)jl * sb.taps;   // the source's taps, contiguous
-    const double* D = a.Dring + sb.s0 + jl;
+    const T* D = fir_ring(a) + sb.s0 + jl;
     const int taps = min(sb.taps, n + 1);   // taps <= WD, so one wrap-around at most
     const int slot = wrap(n, a.WD);
     if (!FDPH_IDX(taps <= a.WD && sb.s0 + jl < a.N && (long long)sb.dhat + jl < a.rs_dhat, a.err)) return;
-    double s0 = 0.0, s1 = 0.0;
+    T s0 = 0, s1 = 0;
     int m = 0;
     for (; m + 1 < taps; m += 2) {
         int t0 = slot - m, t1 = slot - m - 1;
         t0 += t0 < 0 ? a.WD : 0;
         t1 += t1 < 0 ? a.WD : 0;
-        s0 += (double)h[m] * D[(size_t)t0 * a.N];
-        s1 += (double)h[m + 1] * D[(size_t)t1 * a.N];
+        s0 += h[m] * D[(size_t)t0 * a.N];
+        s1 += h[m + 1] * D[(size_t)t1 * a.N];
     }
     if (m < taps) {
         int t0 = slot - m;
         t0 += t0 < 0 ? a.WD : 0;
-        s0 += (double)h[m] * D[(size_t)t0 * a.N];
+        s0 += h[m] * D[(size_t)t0 * a.N];
     }
-    a.dhat[sb.dhat + jl] = s0 + s1;
+    a.dhat[sb.dhat + jl] = (double)(s0 + s1);
 }
 
 // The same for NR right-hand sides at once: the taps are read once and feed the NR slip-rate rows
@@ -383,21 +391,21 @@ __device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
     const SbDev& sb = a.sbs[a.fir_sb[q]];
     const int jl = a.fir_j[q];
     const T* h = a.fac + sb.h + (long long)jl * sb.taps;
-    const double* D = a.Dring + sb.s0 + jl;
+    const T* D = fir_ring(a) + sb.s0 + jl;
     const int taps = min(sb.taps, n + 1);
     const int slot = wrap(n, a.WD);
     if (!FDPH_IDX(taps <= a.WD && sb.s0 + jl < a.N && (long long)sb.dhat + jl < a.rs_dhat, a.err)) return;
-    double s0[NR], s1[NR];
+    T s0[NR], s1[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0.0;
+    for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0;
     int m = 0;
     for (; m + 1 < taps; m += 2) {
         int t0 = slot - m, t1 = slot - m - 1;
         t0 += t0 < 0 ? a.WD : 0;
         t1 += t1 < 0 ? a.WD : 0;
-        const double h0 = (double)h[m], h1 = (double)h[m + 1];
-        const double* d0 = D + (size_t)t0 * a.N;
-        const double* d1 = D + (size_t)t1 * a.N;
+        const T h0 = h[m], h1 = h[m + 1];
+        const T* d0 = D + (size_t)t0 * a.N;
+        const T* d1 = D + (size_t)t1 * a.N;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             s0[r] += h0 * d0[r * a.rs_D];
@@ -407,13 +415,13 @@ __device__ __forceinline__ void fir_body_nr(const StepArgs<T>& a, int q) {
     if (m < taps) {
         int t0 = slot - m;
         t0 += t0 < 0 ? a.WD : 0;
-        const double h0 = (double)h[m];
-        const double* d0 = D + (size_t)t0 * a.N;
+        const T h0 = h[m];
+        const T* d0 = D + (size_t)t0 * a.N;
 #pragma unroll
         for (int r = 0; r < NR; ++r) s0[r] += h0 * d0[r * a.rs_D];
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = s0[r] + s1[r];
+    for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = (double)(s0[r] + s1[r]);
 }
 
 // NR = 1: one grid row per right-hand side; NR > 1: all of them in one thread
@@ -438,7 +446,8 @@ constexpr int kSfirWarps = 4;
 
 template <class T, int NR>
 __global__ void __launch_bounds__(32 * kSfirWarps) sfir_kernel(StepArgs<T> a) {
-    extern __shared__ double sfir_rows[];   // per warp [sfir_taps][NR]
+    extern __shared__ __align__(8) unsigned char sfir_smem[];
+    T* sfir_rows = (T*)sfir_smem;           // per warp [sfir_taps][NR]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x * kSfirWarps + warp;
     if (p >= a.N) return;   // warp-uniform
@@ -446,14 +455,15 @@ __global__ void __launch_bounds__(32 * kSfirWarps) sfir_kernel(StepArgs<T> a) {
     if (e0 == e1) return;
     const int n = step_index(a);
     const int tmax = min(a.sfir_tmax[p], n + 1);
-    double* sd = sfir_rows + (size_t)warp * a.sfir_taps * NR;
+    T* sd = sfir_rows + (size_t)warp * a.sfir_taps * NR;
+    const T* ring = fir_ring(a);
     if (!FDPH_IDX(tmax <= a.WD && a.sfir_tmax[p] <= a.sfir_taps, a.err)) return;
     const int slot = wrap(n, a.WD);
     for (int m = lane; m < tmax; m += 32) {
         int t = slot - m;
         t += t < 0 ? a.WD : 0;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) sd[m * NR + r] = a.Dring[r * a.rs_D + (size_t)t * a.N + p];
+        for (int r = 0; r < NR; ++r) sd[m * NR + r] = ring[r * a.rs_D + (size_t)t * a.N + p];
     }
     __syncwarp();
     for (int e = e0 + lane; e < e1; e += 32) {
@@ -463,12 +473,12 @@ __global__ void __launch_bounds__(32 * kSfirWarps) sfir_kernel(StepArgs<T> a) {
         const int taps = min(sb.taps, n + 1);
         if (!FDPH_IDX(taps <= tmax && (long long)sb.dhat + jl < a.rs_dhat, a.err)) continue;
         const T* h = a.fac + sb.h + (long long)jl * sb.taps;
-        double s0[NR], s1[NR];
+        T s0[NR], s1[NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0.0;
+        for (int r = 0; r < NR; ++r) s0[r] = s1[r] = 0;
         int m = 0;
         for (; m + 1 < taps; m += 2) {
-            const double h0 = (double)h[m], h1 = (double)h[m + 1];
+            const T h0 = h[m], h1 = h[m + 1];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 s0[r] += h0 * sd[m * NR + r];
@@ -476,12 +486,12 @@ __global__ void __launch_bounds__(32 * kSfirWarps) sfir_kernel(StepArgs<T> a) {
             }
         }
         if (m < taps) {
-            const double h0 = (double)h[m];
+            const T h0 = h[m];
 #pragma unroll
             for (int r = 0; r < NR; ++r) s0[r] += h0 * sd[m * NR + r];
         }
 #pragma unroll
-        for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = s0[r] + s1[r];
+        for (int r = 0; r < NR; ++r) a.dhat[r * a.rs_dhat + sb.dhat + jl] = (double)(s0[r] + s1[r]);
     }
 }
 
@@ -1999,6 +2009,7 @@ struct fdph_plan_s {
     int n_sct = 0, n_evt = 0;
     double* fval = nullptr;
     int *sfir_ptr = nullptr, *sfir_q = nullptr, *sfir_tmax = nullptr;
+    bool sfir = false;        // Eq. 32 source-major (sfir_kernel) rather than sub-block-major
     int *fir_sb = nullptr, *fir_j = nullptr, *tr_sb = nullptr,
         *tr_l = nullptr, *g_ptr = nullptr, *g_sb = nullptr, *g_il = nullptr;
     NearDev* near = nullptr;
@@ -2203,7 +2214,7 @@ static StepArgs<T> make_args(fdph_plan_t P, const double* D, double* T_) {
     a.fir_sb = P->fir_sb;
     a.fir_j = P->fir_j;
     a.n_fir = (int)P->hp.fir_sb.size();
-    a.sfir_ptr = P->sfir_ptr;
+    a.sfir_ptr = P->sfir ? P->sfir_ptr : nullptr;   // (null: the sub-block-major FIR)
     a.sfir_q = P->sfir_q;
     a.sfir_tmax = P->sfir_tmax;
     a.sfir_taps = P->hp.max_taps;
@@ -2277,7 +2288,7 @@ struct ProfScope {
 
 template <class T>
 static void launch_fir(const StepArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)kSfirWarps * a.sfir_taps * a.nrhs * sizeof(double);
+    const size_t smem = (size_t)kSfirWarps * a.sfir_taps * a.nrhs * sizeof(T);
     if (a.sfir_ptr && a.sfir_taps > 0 && smem <= 48 * 1024) {   // source-major (no opt-in shared memory)
         const unsigned g = blocks(a.N, kSfirWarps);
         switch (a.nrhs) {
@@ -3725,6 +3736,8 @@ int fdph_plan(const fdph_geometry* geometry, const fdph_material* material, doub
         (rc = upload(P, &P->g_ptr, hp.g_ptr)) || (rc = upload(P, &P->g_sb, hp.g_sb)) ||
         (rc = upload(P, &P->g_il, hp.g_il)))
         return fail(rc);
+    // the source-major FIR where sources sit in many F blocks (large N; fdph_autotune times both)
+    P->sfir = hp.fir_sb.size() >= (size_t)100 * hp.n;
     if (P->precision != FDPH_FP64) {
         std::vector<float> f(hp.fac.begin(), hp.fac.end());
         float* d = nullptr;
@@ -3961,9 +3974,33 @@ int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
             best = c;
         }
     }
+    if (!rc) rc = set_chunk_any(P, best);
+    // then the other form of Eq. 32 (source-major or sub-block-major) at that item length
+    if (!rc && P->sfir_ptr && P->hp.max_taps > 0) {
+        const bool first = P->sfir;
+        P->sfir = !first;
+        FDPH_CUDA(cudaStreamSynchronize(P->stream));
+        for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);   // they hold the old launches
+        P->graphs.clear();
+        P->n = n0;
+        rc = P->precision != FDPH_FP64 ? run_graph<float>(P, 2, Dz, Tz) : run_graph<double>(P, 2, Dz, Tz);
+        float ms = 1e30f;
+        if (!rc) {
+            cudaEventRecord(e0, P->stream);
+            rc = P->precision != FDPH_FP64 ? run_graph<float>(P, steps, Dz, Tz) : run_graph<double>(P, steps, Dz, Tz);
+            cudaEventRecord(e1, P->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rc || !(ms < best_ms)) {
+            P->sfir = first;
+            FDPH_CUDA(cudaStreamSynchronize(P->stream));
+            for (auto& ge : P->graphs) cudaGraphExecDestroy(ge.ex);
+            P->graphs.clear();
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!rc) rc = set_chunk_any(P, best);
     int rc2 = fdph_load_state(P, saved.data(), saved.size());
     if (rc) return rc;
     if (rc2) return rc2;

@@ -1409,17 +1409,25 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
         }
     } else {
         // ---------------- consumers
-        double rows[kRowsPerWarp], dW[NR];
+        // Vector rows are staged one item ahead (registers for aux rows, cp.async for window rows).
+        // Tensor-core plans stage nothing: their window rows ride in the stages, and their few aux
+        // items load their rows when they start, so that no staged aux rows stay live in
+        // registers across the MMA loop of a window item
+        constexpr bool kAhead = !kTC;
         NearTask nxt;
         NearView vn;
         if (t0 < t1) {
             nxt = task(t0);
             vn = view(nxt);
-            near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf);
-            near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
+            if constexpr (kAhead) {
+                double rows[kRowsPerWarp], dW[NR];
+                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf);
+                near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf);
+            }
         }
         cp_async_wait_all();
         consumer_barrier();
+        [[maybe_unused]] double rows[kAhead ? kRowsPerWarp : 1], dW[kAhead ? NR : 1];
         int par = 0;
         for (int ti = t0; ti < t1; ++ti, par ^= 1) {
             const NearTask tk = nxt;
@@ -1428,7 +1436,16 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
             if (ti + 1 < t1) {
                 nxt = task(ti + 1);
                 vn = view(nxt);
-                near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+                if constexpr (kAhead)
+                    near_issue<R, NR, C::vec_rows, kTC>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            }
+            if constexpr (!kAhead) {
+                if (tk.kind) {   // an aux item of a tensor-core plan: its rows now
+                    double ar[kRowsPerWarp], adw[NR];
+                    near_issue<R, NR, C::vec_rows, kTC>(v, tk, warp, lane, ar, adw, vbuf + par * C::vec_bytes);
+                    near_commit<R, NR>(v, tk, warp, lane, ar, adw, vbuf + par * C::vec_bytes);
+                    consumer_barrier();
+                }
             }
             const unsigned char* vrows = vbuf + par * C::vec_bytes;
             const int esz = tk.kind ? (int)sizeof(A) : (int)sizeof(H);
@@ -1511,7 +1528,8 @@ __global__ void __launch_bounds__(kNearThreads, NR == 1 ? 3 : 2) near_kernel(Ste
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            if (ti + 1 < t1) near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
+            if constexpr (kAhead)
+                if (ti + 1 < t1) near_commit<R, NR>(vn, nxt, warp, lane, rows, dW, vbuf + (par ^ 1) * C::vec_bytes);
             if (tc) {
                 if constexpr (kTC) tc_item_to_red<NR>(tacc, lane, tk.nr, v.kinv, red[par][warp]);
             } else {

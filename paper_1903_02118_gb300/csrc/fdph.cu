@@ -2,12 +2,14 @@
 //
 // One time step n (Eq. 4 evaluated through the plan's operator) runs these kernels (captured
 // as one CUDA graph: FIR + scatter and transient + Eq. 39 on two side streams, concurrently with
-// the near field, all joined before gather; grid y = right-hand side):
+// the near field, all joined before gather; several right-hand sides go through one launch, the
+// far-field kernels taking all of them in a thread or warp):
 //   push     D_n -> slip-rate ring (internal order); cumulative slip C_j(n) = sum_{s<=n} D_j,s
 //            with a compensated (Kahan) FP64 sum, -> cumulative-slip ring; with the tensor-core
 //            near field (FP16 window, several right-hand sides) also the ring row's scaled FP16
 //            (hi, lo) copy (tc_rows)
-//   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}
+//   fir      Domain F, formula 1 (Eq. 32): Dhat_j = sum_{m < Dm_j} h_{j,m} D_{j,n-m}, per F block
+//            and source (fir), or per source for all its F blocks (sfir), in the factor type
 //   scatter  formula 2 (Eq. 42): Tbar'_l[n + delay_j] += g_{l,j} u_j for every run of sources
 //            (rings are stored [slot][rank] so that one receiver's ranks share a sector)
 //            with equal delay (no atomics: one writer per ring slot); u = Dhat (Domain F),

@@ -55,8 +55,8 @@ METRIC_REL_ERR = 1e-4      # the metric's accuracy condition (relative error vs 
 # near-field coefficient: the near bytes scale with the stored coefficients, so a full launch's
 # traffic is this figure times the plan's coefficients.  Reported only while the near-field
 # kernel's source (near_kernel_source_hash) is the one that was captured.
-NEAR_NCU = {"source_sha256": "4e0d7f70b227e1b5dd16d611bf95ba30d3ffb19020e04f9b478b17095f1e5e7a",
-            "dram_bytes_per_coefficient": 4.1475, "precision": 1, "nrhs": 1,
+NEAR_NCU = {"source_sha256": "c08939cd1e5992346e6387f5e23eac9888631ec999bc2fb830ab141666903a18",
+            "dram_bytes_per_coefficient": 4.1471, "precision": 1, "nrhs": 1,
             "capture": "profiles/near_kernel_curved_n2048_m1024_fp32_soe16.md (curved N = 2048, M = 1024, FP32, "
                        "Q = 16, two steady-state launches)"}
 

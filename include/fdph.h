@@ -331,6 +331,13 @@ int fdph_reset(fdph_plan_t plan);
 /* Current step index (number of steps taken since plan or reset). */
 int fdph_current_step(fdph_plan_t plan, int32_t* n);
 
+/* The cudaStream_t the plan runs on (params.cuda_stream, or the non-blocking stream the plan
+ * created when that was NULL; it lives as long as the plan).  Callers that order their own work
+ * with a plan's steps, or build plans on several threads at once, should use this stream rather
+ * than one shared with other work: a stream being captured into a step graph takes in whatever
+ * any thread submits to it.  Errors: FDPH_E_ARG (null pointer). */
+int fdph_plan_stream(fdph_plan_t plan, void** stream);
+
 /* Wait for all work queued on the plan's stream. */
 int fdph_synchronize(fdph_plan_t plan);
 

@@ -2619,6 +2619,20 @@ template <class T>
 static void enqueue_predict(fdph_plan_t P, StepArgs<T> a, cudaStream_t s) {
     a.D_in = nullptr;
     { ProfScope ps(P, 0); push_kernel<T><<<dim3(blocks(a.N, 256), a.nrhs), 256, 0, s>>>(a); }          // D_n = 0
+    if (!P->prof && P->side[1]) {
+        // the transient convolution and Eq. 39 read ring slots completed by earlier steps and the
+        // near field reads the slip-rate rows: the two branches run concurrently after push
+        cudaEventRecord(P->ev_fork, s);
+        cudaStreamWaitEvent(P->side[1], P->ev_fork, 0);
+        if (a.n_tr) trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, P->side[1]>>>(a);
+        if (a.n_evt) launch_far_eval<T>(a, P->side[1]);
+        launch_far_sum<T>(a, P->side[1]);
+        if (a.n_cta) launch_near<T>(P, a, s);
+        cudaEventRecord(P->ev_join[1], P->side[1]);
+        cudaStreamWaitEvent(s, P->ev_join[1], 0);
+        gather_kernel<T><<<dim3(blocks(a.N, 128), a.nrhs), 128, 0, s>>>(a);
+        return;
+    }
     if (a.n_tr) { ProfScope ps(P, 3); trconv_kernel<T><<<dim3(blocks((long long)a.n_tr * 32, 128), a.nrhs), 128, 0, s>>>(a); }
     if (a.n_cta) {
         ProfScope ps(P, 4);
@@ -3223,10 +3237,14 @@ static void enqueue_batch_step(fdph_batch_t B, int kind, const StepArgs<T>* scen
         cudaStreamWaitEvent(bs, B->ev_join[0], 0);
         cudaStreamWaitEvent(bs, B->ev_join[1], 0);
         gather();
-    } else {   // rupture: predict with D_n = 0, friction, commit D_n
+    } else {   // rupture: predict with D_n = 0 (far field beside the near field), friction, commit D_n
         push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 1);
-        far(bs);
+        cudaEventRecord(B->ev_fork, bs);
+        cudaStreamWaitEvent(B->side[1], B->ev_fork, 0);
+        far(B->side[1]);
         if (B->n_cta) launch_near_batch<T>(B, scen, bs);
+        cudaEventRecord(B->ev_join[1], B->side[1]);
+        cudaStreamWaitEvent(bs, B->ev_join[1], 0);
         gather();
         friction_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(B->fr_dev, scen, pre(BW_ELEM), np);
         push_batch<T><<<blocks(tot[BW_ELEM], 256), 256, 0, bs>>>(scen, pre(BW_ELEM), np, 0);
@@ -4026,6 +4044,12 @@ int fdph_autotune(fdph_plan_t P, int32_t steps, int32_t* chunk_out) {
     if (rc2) return rc2;
     if ((rc = check_device_error(P))) return rc;
     if (chunk_out) *chunk_out = best;
+    return FDPH_OK;
+}
+
+int fdph_plan_stream(fdph_plan_t P, void** stream) {
+    if (!P || !stream) return FDPH_E_ARG;
+    *stream = (void*)P->stream;
     return FDPH_OK;
 }
 

@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["fdph_default_params", "fdph_plan", "fdph_step", "fdph_run", "fdph_step_host", "fdph_run_host", "fdph_reset",
-           "fdph_current_step", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
+           "fdph_current_step", "fdph_plan_stream", "fdph_synchronize", "fdph_get_stats", "fdph_save_state", "fdph_load_state",
            "fdph_destroy", "fdph_tree_export", "fdph_strerror", "fdph_last_error", "fdph_set_profiling",
            "fdph_kernel_times", "fdph_plain_step_noalloc", "fdph_rupture_init", "fdph_rupture_step",
            "fdph_rupture_run", "fdph_rupture_slip", "fdph_selftest_wait_timeout", "fdph_autotune",
@@ -95,6 +95,8 @@ def lib():
         L.fdph_run_host.argtypes = [c_p, ctypes.c_int32, c_p, c_p]
         L.fdph_reset.argtypes = [c_p]
         L.fdph_current_step.argtypes = [c_p, ctypes.POINTER(ctypes.c_int32)]
+        L.fdph_plan_stream.argtypes = [c_p, ctypes.POINTER(c_p)]
+        L.fdph_plan_stream.restype = ctypes.c_int
         L.fdph_synchronize.argtypes = [c_p]
         L.fdph_get_stats.argtypes = [c_p, ctypes.POINTER(Stats)]
         L.fdph_save_state.argtypes = [c_p, c_p, ctypes.POINTER(ctypes.c_size_t)]
@@ -255,6 +257,13 @@ class Plan:
         n = ctypes.c_int32()
         _check(lib().fdph_current_step(self.handle, ctypes.byref(n)))
         return n.value
+
+    @property
+    def stream(self):
+        """The cudaStream_t handle (int) the plan runs on (fdph_plan_stream)."""
+        h = ctypes.c_void_p()
+        _check(lib().fdph_plan_stream(self.handle, ctypes.byref(h)))
+        return h.value or 0
 
     def synchronize(self):
         _check(lib().fdph_synchronize(self.handle))

@@ -110,13 +110,15 @@ class Server:
         torch = self.torch
         torch.cuda.set_device(self.device)
         xy, tau0 = req.inputs()
-        stream = torch.cuda.Stream(device=self.device)
         dt = req.cfl  # dx = cs = 1
         prec = self.precision if self.precision is not None else req.precision
+        # each plan on a stream of its own, created by the library: torch's pooled streams repeat,
+        # and a plan being built on a planner thread must not submit work to a stream that the
+        # loop is capturing into another plan's step graph
         plan = fdph.Plan(xy, dt, req.M, req.eps, eta=req.eta, eps_st=req.eps_st, leaf_size=req.leaf,
                          precision=prec, soe_terms=req.soe_terms, device=self.device,
-                         stream=stream.cuda_stream, host_threads=self.host_threads, amp_window=req.amp_window,
-                         aca_min=req.aca_min)
+                         host_threads=self.host_threads, amp_window=req.amp_window, aca_min=req.aca_min)
+        stream = torch.cuda.ExternalStream(plan.stream, device=self.device)
         st = plan.stats()
         foot = st["arena_bytes"] + st["state_bytes"] + 3 * req.N * 8 * (self.chunk + 2)
         with torch.cuda.stream(stream):
